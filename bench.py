@@ -1,0 +1,413 @@
+#!/usr/bin/env python
+"""Benchmark: finite element assembly throughput on GB300.
+
+One step = one pass of the assembly hot path over the workload: per-element
+Jacobians, local matrices and load vectors by quadrature, and the
+deterministic scatter into the CSR values and the load vector (the CSR
+pattern is built once beforehand and reported separately).  Default
+workload: P2 -div(kappa grad u) + u = f on the 64^3 Kuhn cube mesh
+(1,572,864 tets, 2,146,689 dofs, 60,859,905 nonzeros), kappa log-normal per
+element, f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z), 11-point rule, FP64.
+
+Prints one JSON line.  `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1802_03433_gb300 import meshgen as mg  # noqa: E402
+
+# FP64 peak of the element kernels' pipe: 152 SMs x 2 DFMA/clk x 2 flop x
+# 2.07 GHz (GB300 nominal FP64, 1.25 TFLOP/s).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+# FP64 flops (2 x DFMA + DADD + DMUL, ncu SASS counters) executed per element
+# by the element kernel of each workload, and DRAM bytes per launch of the
+# dominant kernel (ncu, dram__bytes_read.sum + dram__bytes_write.sum).  None
+# where not yet captured for the current kernels.
+FP64_FLOP_PER_ELEM = {}
+DRAM_BYTES_PER_LAUNCH = {}
+
+WORKLOADS = {
+    "p2_diffmass_64": dict(kind="p2_diffmass", n=64),
+    "p1_poisson_8": dict(kind="p1_poisson", n=8),
+    "p1_elast_128": dict(kind="elasticity", n=128),
+    "p1_kappa_96": dict(kind="p1_kappa", n=96),
+}
+
+
+def algorithmic_bytes(kind, E, N, ndof, nnz):
+    """Inputs read once + outputs written once (coords 24 B/node, element->node
+    table 16 B/element, coefficients 8 B per field per element, values 8 B/nnz,
+    rhs 8 B/dof)."""
+    coef = {"p1_poisson": 0, "p1_kappa": 8, "p2_diffmass": 8, "elasticity": 16}[kind]
+    return 24 * N + 16 * E + coef * E + 8 * nnz + 8 * ndof
+
+
+def make_inputs(kind, n, seed=0):
+    coords, tets, rng = mg.make_cube(n, 0.2, seed)
+    E = tets.shape[1]
+    d = dict(coords=coords, tets=tets, kind=kind, n=n)
+    if kind == "p1_poisson":
+        d.update(order=1, ndpn=1, form=0, mass=0.0, kappa=None, f_kind=2, f_param=(mg.SIN_AMP,), npts=4)
+    elif kind == "p1_kappa":
+        d.update(order=1, ndpn=1, form=0, mass=0.0, kappa=mg.lognormal(rng, E), f_kind=2,
+                 f_param=(mg.SIN_AMP,), npts=4)
+    elif kind == "p2_diffmass":
+        d.update(order=2, ndpn=1, form=1, mass=1.0, kappa=mg.lognormal(rng, E), f_kind=2,
+                 f_param=(mg.SIN_AMP,), npts=11)
+    elif kind == "elasticity":
+        lam, mu = mg.lame(rng, E)
+        d.update(order=1, ndpn=3, form=2, mass=0.0, lam=lam, mu=mu, f_kind=1, f_param=(0.0, 0.0, -1.0), npts=4)
+    return d
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [l.strip().split(",") for l in self.f.read().splitlines() if l.strip()]
+        self.f.close()
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                mx = float(r[1])
+                for nm, v in zip(names, r[4:8]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- distributed
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        from paper_1802_03433_gb300 import build_lib
+        build_lib.build()
+    if ws > 1:
+        dist.barrier()
+    from paper_1802_03433_gb300 import fea
+
+    wl = WORKLOADS[args.workload]
+    d = make_inputs(wl["kind"], wl["n"], seed=args.seed + rank)
+    dev = torch.device("cuda", local)
+    E = d["tets"].shape[1]
+    N = d["coords"].shape[1]
+
+    mesh = fea.Mesh(d["coords"], d["tets"], device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ndof, nnz = mesh.pattern(d["order"], d["ndpn"])
+    pattern_ms = (time.perf_counter() - t0) * 1e3
+
+    keep = []
+    if d["form"] == 2:
+        lam = torch.as_tensor(d["lam"], device=dev)
+        mu = torch.as_tensor(d["mu"], device=dev)
+        keep += [lam, mu]
+        coeffs = fea.make_coeffs(lam=lam, mu=mu, f_kind=d["f_kind"], f_param=d["f_param"])
+    else:
+        kap = None if d["kappa"] is None else torch.as_tensor(d["kappa"], device=dev)
+        keep.append(kap)
+        coeffs = fea.make_coeffs(kappa=kap, f_kind=d["f_kind"], f_param=d["f_param"])
+    form = fea.make_form(d["form"], d["order"], d["mass"])
+    values = torch.empty(nnz, dtype=torch.float64, device=dev)
+    rhs = torch.empty(ndof, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)  # 256 MB > L2
+    fea.fea_profile_enable(mesh.h, True)
+
+    def timed_loop(prec, steps, warmup, clocks=None):
+        quad = fea.make_quadrature(d["npts"], prec)
+        for _ in range(warmup):
+            fea.fea_assemble(mesh.h, form, coeffs, quad, values, rhs)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        phase = []
+        for k in range(steps):
+            flush.fill_(k)
+            evs[k][0].record()
+            fea.fea_assemble(mesh.h, form, coeffs, quad, values, rhs)
+            evs[k][1].record()
+            phase.append(fea.fea_profile_last(mesh.h))
+        torch.cuda.synchronize()
+        clk = clocks.stop() if clocks else None
+        if ws > 1:
+            dist.barrier()
+        mesh.check()
+        step_ms = [a.elapsed_time(b) for a, b in evs]
+        total = torch.tensor([sum(step_ms)], dtype=torch.float64, device=dev)
+        if ws > 1:
+            dist.all_reduce(total, op=dist.ReduceOp.MAX)
+        return total.item(), step_ms, phase, clk
+
+    clocks = ClockSampler(local) if rank == 0 else None
+    total_ms, step_ms, phase, clk = timed_loop(fea.FEA_FP64, args.steps, args.warmup, clocks)
+    value = ws * E * args.steps / (total_ms / 1e3)
+    elem_ms = statistics.mean(p[0] for p in phase)
+    scat_ms = statistics.mean(p[1] for p in phase)
+
+    # mixed-precision form on the same GPU and workload
+    forms = {"fp64": {"value": value, "ms_per_step": total_ms / args.steps, "elem_ms": elem_ms,
+                      "scatter_ms": scat_ms}}
+    if not args.no_forms:
+        m_total, _, m_phase, _ = timed_loop(fea.FEA_MIXED, max(3, args.steps // 2), args.warmup)
+        ms = m_total / max(3, args.steps // 2)
+        forms["mixed"] = {"value": ws * E / (ms / 1e3), "ms_per_step": ms,
+                          "elem_ms": statistics.mean(p[0] for p in m_phase),
+                          "scatter_ms": statistics.mean(p[1] for p in m_phase)}
+
+    # end to end through the public API with host buffers: H2D of the step's
+    # inputs (coordinates, coefficients) from pinned memory, assembly, D2H of
+    # the assembled values and load vector
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda t: t.cpu().pin_memory()  # noqa: E731
+        hx, hy, hz = pin(mesh.x), pin(mesh.y), pin(mesh.z)
+        hin = [(hx, mesh.x), (hy, mesh.y), (hz, mesh.z)] + [(pin(t), t) for t in keep if t is not None]
+        hv = torch.empty(nnz, dtype=torch.float64).pin_memory()
+        hr = torch.empty(ndof, dtype=torch.float64).pin_memory()
+        quad = fea.make_quadrature(d["npts"], fea.FEA_FP64)
+        steps = max(3, args.steps // 4)
+
+        def e2e_step():
+            for h, dv in hin:
+                dv.copy_(h, non_blocking=True)
+            fea.fea_assemble(mesh.h, form, coeffs, quad, values, rhs)
+            hv.copy_(values, non_blocking=True)
+            hr.copy_(rhs, non_blocking=True)
+
+        for _ in range(args.warmup):
+            e2e_step()
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            e2e_step()
+        b.record()
+        torch.cuda.synchronize()
+        t = torch.tensor([a.elapsed_time(b)], dtype=torch.float64, device=dev)
+        if ws > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        h2d = sum(h.numel() * h.element_size() for h, _ in hin)
+        d2h = hv.numel() * 8 + hr.numel() * 8
+        e2e = {"value": ws * E * steps / (t.item() / 1e3), "unit": "elements/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    # roofline of the dominant kernel
+    key = (args.workload, "fp64")
+    if elem_ms >= scat_ms:
+        flop = FP64_FLOP_PER_ELEM.get(key)
+        if flop is not None:
+            ach = flop * E / (elem_ms / 1e3) / 1e12
+            roof = {"kernel": "element", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                    "traffic": DRAM_BYTES_PER_LAUNCH.get((args.workload, "element"))}
+        else:
+            roof = {"kernel": "element", "bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": None, "traffic": None}
+    else:
+        # scatter: algorithmic bytes = local matrices read once + values/rhs written once
+        nl = (4 if d["order"] == 1 else 10) * d["ndpn"]
+        byts = E * nl * nl * 8 + nnz * 8 + ndof * 8
+        ach = byts / (scat_ms / 1e3) / 1e9
+        peak = _hbm_peak()
+        roof = {"kernel": "scatter", "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "traffic": DRAM_BYTES_PER_LAUNCH.get((args.workload, "scatter"))}
+
+    alg = algorithmic_bytes(d["kind"], E, N, ndof, nnz)
+    out = None
+    if rank == 0:
+        cpu = None
+        if ws == 1 and not args.no_cpu_baseline:
+            cpu = cpu_baseline(d["kind"])
+        out = {
+            "metric": "elements/s assembled into CSR (plain FP64), with % of HBM roofline and the mixed form",
+            "value": value, "unit": "elements/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "elements": E, "nodes": N, "ndof": ndof, "nnz": nnz,
+                       "order": d["order"], "form": {0: "poisson", 1: "diffusion+mass", 2: "elasticity"}[d["form"]],
+                       "npts": d["npts"], "mesh": f"{d['n']}^3 Kuhn cube, interior nodes perturbed 0.2h",
+                       "l2": "256 MB buffer written between timed steps (> 129 MB L2)",
+                       "parallelism": f"independent replica per GPU x{ws}"},
+            "roofline": roof,
+            "hbm": {"algorithmic_bytes": alg, "achieved_gbs": alg / (total_ms / args.steps / 1e3) / 1e9,
+                    "peak_gbs": _hbm_peak(), "frac": alg / (total_ms / args.steps / 1e3) / 1e9 / _hbm_peak()},
+            "forms": forms,
+            "pattern_ms": pattern_ms,
+            "e2e": e2e,
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out))
+    mesh.close()
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
+def _hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except Exception:
+        return 6800.0  # fallback copy bandwidth
+
+
+# ---------------------------------------------------------------- CPU oracle
+CPU_SAMPLE_N = {"p2_diffmass": 40, "p1_poisson": 64, "p1_kappa": 64, "elasticity": 32}
+
+
+def _oracle_assemble(d, edof, rp, ci):
+    import oracle
+    kw = dict(f_kind={1: "const", 2: "sinprod"}[d["f_kind"]], f_param=d["f_param"], npts=d["npts"])
+    if d["form"] == 2:
+        return oracle.assemble(d["coords"], d["tets"], 1, edof, rp, ci, kind="elasticity", lam=d["lam"],
+                               mu=d["mu"], **kw)
+    return oracle.assemble(d["coords"], d["tets"], d["order"], edof, rp, ci, mass=d["mass"], kappa=d["kappa"], **kw)
+
+
+def cpu_baseline(kind):
+    """The oracle, as it stands, on a bounded sample of the workload (same
+    recipe, smaller cube), single-threaded on the host."""
+    import oracle
+    n = CPU_SAMPLE_N[kind]
+    d = make_inputs(kind, n, seed=0)
+    edof, nsd = oracle.dof_table(d["order"], d["coords"].shape[1], d["tets"])
+    rp, ci = oracle.pattern(nsd, edof, ndpn=d["ndpn"])
+    t = time.perf_counter()
+    _oracle_assemble(d, edof, rp, ci)
+    dt = time.perf_counter() - t
+    E = d["tets"].shape[1]
+    return {"value": E / dt, "unit": "elements/s", "cores": 1, "kind": "oracle",
+            "sample": f"{kind} on the {n}^3 cube ({E} tets), values + load assembly, pattern excluded",
+            "seconds": dt}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    import oracle
+    wl = WORKLOADS[args.workload]
+    n = {"p2_diffmass": 16, "p1_poisson": 8, "p1_kappa": 24, "elasticity": 12}[wl["kind"]]
+    d = make_inputs(wl["kind"], n, seed=0)
+    edof, nsd = oracle.dof_table(d["order"], d["coords"].shape[1], d["tets"])
+    rp, ci = oracle.pattern(nsd, edof, ndpn=d["ndpn"])
+    E = d["tets"].shape[1]
+    for _ in range(args.warmup):
+        _oracle_assemble(d, edof, rp, ci)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        _oracle_assemble(d, edof, rp, ci)
+    dt = time.perf_counter() - t
+    value = E * args.steps / dt
+    out = {
+        "impl": "reference", "metric": "elements/s assembled into CSR (plain FP64), with % of HBM roofline and the mixed form",
+        "value": value, "unit": "elements/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample_elements": E,
+                   "note": f"each step assembles a {n}^3 cube of the same recipe (bounded CPU sample)"},
+        "cpu_baseline": {"value": value, "unit": "elements/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{wl['kind']} on the {n}^3 cube ({E} tets) per step"},
+        "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+    return out
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="p2_diffmass_64", choices=sorted(WORKLOADS))
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-forms", action="store_true")
+    args = p.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * fea.h - C ABI of libfea, a GB300 (sm_103a) finite element assembly engine
+ * for P1/P2 tetrahedra.
+ *
+ * What the library computes is the assembled linear system of a weak form
+ * (Cui, Guo & Liu, "GPU Accelerated Finite Element Assembly with Runtime
+ * Compilation", Sec. 4.1):
+ *   Eq. 1-2: the weak form  (grad v, sigma grad u) + lambda (v, u) = (v, f)
+ *            with sigma = kappa I, kappa constant on each element, and
+ *            lambda = mass_coef; and, on vector P1 elements, linear elasticity
+ *            a(u, v) = int lambda div u div v + 2 mu eps(u):eps(v) with the
+ *            Lame parameters constant on each element;
+ *   Eq. 3:   A x = b, where A_ij sums the local entries of every element that
+ *            holds dofs i and j, and b_i the local load entries of every
+ *            element that holds dof i.
+ * The input mesh is what Sec. 5 (Algorithm 1) takes: node coordinates plus
+ * the global node indices of every element.  The matrix is returned in CSR
+ * form, the compressed counterpart of the N x MAX_NZ sparse layout of the
+ * sparse variant of Algorithm 1 (Sec. 5).
+ *
+ * Conventions that hold for every entry point:
+ *  - Array arguments are DEVICE pointers owned by the caller unless a comment
+ *    says otherwise.  8-byte arrays must be 8-byte aligned, 4-byte arrays
+ *    4-byte aligned.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are stream-ordered and asynchronous unless marked
+ *    "synchronises".
+ *  - Scalar dof numbering: P1 dofs are node ids; P2 dofs are node ids followed
+ *    by one dof per mesh edge, the dof of edge (a, b), a < b, being
+ *    n_nodes + the rank of (a, b) in lexicographic order over all edges.
+ *    Vector (elasticity) dofs interleave components: dof = 3 * node + c.
+ *    Element-local order: vertices v0..v3, then edges (0,1), (0,2), (0,3),
+ *    (1,2), (1,3), (2,3).
+ *  - CSR: int32 row_ptr[ndof + 1], int32 col_idx[nnz]; columns strictly
+ *    ascending in each row; every pair of dofs that share an element is
+ *    stored, zeros included.
+ *  - Outputs are fully overwritten, never accumulated into.  No boundary
+ *    conditions are applied (the paper's Neumann problem, Sec. 4.1).
+ *  - The scatter into the CSR values is deterministic: repeated calls on the
+ *    same inputs give bitwise identical results, and the matrix is bitwise
+ *    symmetric.
+ *  - Errors: every entry point returns an fea_status; nothing throws across
+ *    the ABI.  fea_last_error() gives a message for the calling thread.
+ *    Faults found on the device (an index out of range, det J <= 0, a row too
+ *    long for the scatter) are latched in the mesh and returned by the next
+ *    synchronising call or by fea_mesh_check.
+ *  - A mesh handle is not thread-safe: use it from one host thread and one
+ *    stream at a time.
+ */
+#ifndef FEA_H
+#define FEA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fea_mesh fea_mesh;   /* opaque, library-owned */
+typedef struct fea_batch fea_batch; /* opaque, library-owned */
+
+typedef enum {
+  FEA_OK = 0,
+  FEA_ERR_ARG = 1,        /* bad argument (NULL, size, alignment, unsupported combination) */
+  FEA_ERR_INDEX = 2,      /* connectivity entry out of [0, n_nodes) or repeated in an element */
+  FEA_ERR_DEGENERATE = 3, /* an element with det J <= 0 (values are still computed with |det J|) */
+  FEA_ERR_OVERFLOW = 4,   /* nnz above INT32_MAX, or a row too long for the scatter (> 255 entries
+                             per scalar row, or more than 1024 candidate couplings per scalar row) */
+  FEA_ERR_NOMEM = 5,      /* device allocation failed */
+  FEA_ERR_CUDA = 6,       /* a CUDA runtime call failed */
+  FEA_ERR_TIMEOUT = 7,    /* a bounded device-side wait gave up */
+  FEA_ERR_STATE = 8       /* call out of order (e.g. assemble before fea_pattern) */
+} fea_status;
+
+enum { FEA_P1 = 1, FEA_P2 = 2 };
+
+/* Weak forms (Eq. 2 of the paper with sigma = kappa I, plus elasticity). */
+enum {
+  FEA_POISSON = 0,        /* -div(kappa grad u) = f                       */
+  FEA_DIFFUSION_MASS = 1, /* -div(kappa grad u) + mass_coef u = f          */
+  FEA_ELASTICITY = 2      /* -div sigma(u) = f, sigma = lambda tr(eps) I + 2 mu eps; P1 only */
+};
+
+/* Arithmetic of the element kernels. */
+enum {
+  FEA_FP64 = 0,  /* everything in FP64 */
+  FEA_MIXED = 1  /* Jacobian, det J, J^{-1} and the CSR accumulation in FP64;
+                    quadrature-point products (basis gradients, weights, f) in FP32 */
+};
+
+/* Load f. */
+enum {
+  FEA_LOAD_NONE = 0,    /* f = 0 (rhs written as zeros) */
+  FEA_LOAD_CONST = 1,   /* scalar: f = p0; elasticity: f = (p0, p1, p2) */
+  FEA_LOAD_SINPROD = 2  /* scalar: f = p0 sin(pi x) sin(pi y) sin(pi z); elasticity: component
+                           c is p_c times the same product */
+};
+
+typedef struct {
+  int32_t kind;      /* FEA_POISSON, FEA_DIFFUSION_MASS or FEA_ELASTICITY */
+  int32_t order;     /* FEA_P1 or FEA_P2 */
+  double mass_coef;  /* lambda of Eq. 1 (used by FEA_DIFFUSION_MASS) */
+} fea_form;
+
+typedef struct {
+  const double* kappa;        /* [n_elems] per-element kappa, or NULL to use kappa_const */
+  double kappa_const;
+  const double* lame_lambda;  /* [n_elems] or NULL to use lambda_const (elasticity) */
+  double lambda_const;
+  const double* lame_mu;      /* [n_elems] or NULL to use mu_const (elasticity) */
+  double mu_const;
+  int32_t f_kind;             /* FEA_LOAD_* */
+  double f_param[4];
+} fea_coeffs;
+
+typedef struct {
+  int32_t npts; /* load-vector rule: 1 (centroid), 4 (degree 2) or 11 (Keast, degree 4).  The
+                   matrix integrands are polynomials of degree <= 4 on affine elements with
+                   element-constant coefficients and are integrated exactly. */
+  int32_t prec; /* FEA_FP64 or FEA_MIXED */
+} fea_quadrature;
+
+/* Create a mesh handle.  Synchronises.
+ *   x, y, z : [n_nodes] FP64 node coordinates (device).  REFERENCED, not
+ *             copied: they must stay valid, and may be changed in place
+ *             between calls (moving the nodes keeps every pattern valid).
+ *   tets    : [4][n_elems] int32 connectivity, structure-of-arrays (vertex a
+ *             of element e at tets[a * n_elems + e]); copied.
+ * Validates the connectivity (FEA_ERR_INDEX).  *out receives the handle. */
+fea_status fea_mesh_create(const double* x, const double* y, const double* z, int64_t n_nodes,
+                           const int32_t* tets, int64_t n_elems, void* stream, fea_mesh** out);
+
+/* Re-point the referenced coordinate arrays (same n_nodes). */
+fea_status fea_mesh_set_coords(fea_mesh* mesh, const double* x, const double* y, const double* z);
+
+/* Release the handle and everything it owns.  Synchronises the device. */
+fea_status fea_mesh_destroy(fea_mesh* mesh);
+
+/* Synchronise `stream` and return (then clear) any fault latched on the
+ * device by earlier calls on this mesh. */
+fea_status fea_mesh_check(fea_mesh* mesh, void* stream);
+
+/* Build (once; cached in the handle) the global CSR sparsity pattern of the
+ * given element order and dofs per node (1 for scalar forms, 3 for
+ * elasticity), with the structures the deterministic scatter needs.
+ * Synchronises.  Returns the number of dofs and nonzeros. */
+fea_status fea_pattern(fea_mesh* mesh, int32_t order, int32_t dofs_per_node, int64_t* ndof,
+                       int64_t* nnz, void* stream);
+
+/* Copy a built pattern out: row_ptr [ndof + 1], col_idx [nnz] (device). */
+fea_status fea_pattern_copy(fea_mesh* mesh, int32_t order, int32_t dofs_per_node,
+                            int32_t* row_ptr, int32_t* col_idx, void* stream);
+
+/* Copy the element -> scalar dof table of an order whose pattern is built:
+ * [nb][n_elems] int32 SoA, nb = 4 (P1) or 10 (P2), local order as above. */
+fea_status fea_dof_table_copy(fea_mesh* mesh, int32_t order, int32_t* edof, void* stream);
+
+/* Assemble the CSR values and the load vector of a weak form (Eq. 3).
+ *   values : [nnz] FP64 (device), overwritten; may not be NULL.
+ *   rhs    : [ndof] FP64 (device), overwritten; may be NULL to skip the load.
+ * The pattern of (form->order, 1 or 3 dofs per node) must have been built
+ * with fea_pattern.  Asynchronous.  Per-call device scratch is owned by the
+ * handle (allocated on first use, which synchronises once). */
+fea_status fea_assemble(fea_mesh* mesh, const fea_form* form, const fea_coeffs* coeffs,
+                        const fea_quadrature* quad, double* values, double* rhs, void* stream);
+
+/* Reverse mode of fea_assemble for the scalar forms (FEA_POISSON,
+ * FEA_DIFFUSION_MASS; P1 or P2; FP64).  For a scalar loss L with
+ * grad_values = dL/dvalues [nnz] and grad_rhs = dL/drhs [ndof] (either may be
+ * NULL = zero), writes
+ *   grad_kappa [n_elems] = dL/dkappa per element (may be NULL; needs a
+ *                          per-element kappa to be meaningful);
+ *   grad_x     [3][n_nodes] = dL/d(x, y, z) per node, SoA (may be NULL).
+ * Local matrices are recomputed, never stored.  Deterministic. */
+fea_status fea_assemble_backward(fea_mesh* mesh, const fea_form* form, const fea_coeffs* coeffs,
+                                 const fea_quadrature* quad, const double* grad_values,
+                                 const double* grad_rhs, double* grad_kappa, double* grad_x,
+                                 void* stream);
+
+/* Measurement hooks (no counterpart in the paper; used by the benchmark).
+ * When enabled, every fea_assemble on this mesh records CUDA events on its
+ * stream before the element kernel, between the element kernel and the
+ * scatter kernel, and after the scatter kernel. */
+fea_status fea_profile_enable(fea_mesh* mesh, int32_t enable);
+
+/* Wait for the events of the last profiled fea_assemble and return the
+ * durations (ms) of its element kernel and of its scatter kernel.
+ * FEA_ERR_STATE if no profiled call was made. */
+fea_status fea_profile_last(fea_mesh* mesh, float* elem_ms, float* scatter_ms);
+
+/* Message for the last error on the calling thread ("" if none). */
+const char* fea_last_error(void);
+
+/* Name of a status code. */
+const char* fea_status_string(fea_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FEA_H */

@@ -1,0 +1,102 @@
+// fea_assemble: element kernel (local matrices and loads into per-element
+// scratch) followed by the deterministic row-gather scatter into CSR.
+#include <cuda_runtime.h>
+
+#include "elem_kernels.cuh"
+#include "gather.cuh"
+
+namespace fea {
+
+namespace {
+
+template <int NB, int NDPN, typename LT>
+fea_status gather_one(const GatherArgs& G, int rows, int64_t max_tile_nnz, cudaStream_t s) {
+  const size_t smem = (size_t)max_tile_nnz * sizeof(double);
+  static size_t configured = 0;  // opt-in above the 48 KB default, once per instance
+  if (smem > 48 * 1024 && smem > configured) {
+    FEA_CUDA(cudaFuncSetAttribute(k_gather<NB, NDPN, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    configured = smem;
+  }
+  const int64_t tiles = (G.ndof + rows - 1) / rows;
+  if (tiles == 0) return FEA_OK;
+  k_gather<NB, NDPN, LT><<<(unsigned)tiles, rows, smem, s>>>(G);
+  FEA_CUDA(cudaGetLastError());
+  return FEA_OK;
+}
+
+}  // namespace
+
+fea_status launch_gather(int nb, int ndpn, bool mixed, const GatherArgs& G, int rows, int64_t max_tile_nnz,
+                         cudaStream_t s) {
+  if (nb == 4 && ndpn == 1)
+    return mixed ? gather_one<4, 1, float>(G, rows, max_tile_nnz, s) : gather_one<4, 1, double>(G, rows, max_tile_nnz, s);
+  if (nb == 10 && ndpn == 1)
+    return mixed ? gather_one<10, 1, float>(G, rows, max_tile_nnz, s)
+                 : gather_one<10, 1, double>(G, rows, max_tile_nnz, s);
+  if (nb == 4 && ndpn == 3)
+    return mixed ? gather_one<4, 3, float>(G, rows, max_tile_nnz, s) : gather_one<4, 3, double>(G, rows, max_tile_nnz, s);
+  return fail(FEA_ERR_ARG, "no scatter for this element / dof layout");
+}
+
+fea_status assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* co, const fea_quadrature* q,
+                    double* values, double* rhs, cudaStream_t s) {
+  const int order = form->order;
+  const int ndpn = form->kind == FEA_ELASTICITY ? 3 : 1;
+  Pattern* P = m->pat[order][ndpn];
+  Base* B = m->base[order];
+  if (!P || !B) return fail(FEA_ERR_STATE, "fea_assemble: build the pattern with fea_pattern first");
+  const int nb = B->nb, nl = nb * ndpn;
+  const bool mixed = q->prec == FEA_MIXED;
+  const size_t rb = mixed ? sizeof(float) : sizeof(double);
+  const int64_t E = m->n_elems;
+  const int load = rhs ? co->f_kind : FEA_LOAD_NONE;
+  FEA_TRY(ensure_scratch(m->lm, (size_t)E * nl * nl * rb));
+  if (load != FEA_LOAD_NONE) FEA_TRY(ensure_scratch(m->fl, (size_t)E * nl * rb));
+
+  ElemArgs A{};
+  A.x = m->x;
+  A.y = m->y;
+  A.z = m->z;
+  A.tets = m->tets;
+  A.E = E;
+  A.kappa = co->kappa;
+  A.kappa_const = co->kappa_const;
+  A.lam = co->lame_lambda;
+  A.lam_const = co->lambda_const;
+  A.mu = co->lame_mu;
+  A.mu_const = co->mu_const;
+  A.mass = form->mass_coef;
+  for (int i = 0; i < 4; ++i) A.fp[i] = co->f_param[i];
+  A.Lm = m->lm.ptr;
+  A.Fl = load != FEA_LOAD_NONE ? m->fl.ptr : nullptr;
+  A.err = m->err;
+  const int prec = mixed ? FEA_MIXED : FEA_FP64;
+  if (m->profile) FEA_CUDA(cudaEventRecord(m->ev[0], s));
+  if (form->kind == FEA_ELASTICITY) {
+    FEA_TRY(launch_elem_elast(A, load, q->npts, prec, s));
+  } else {
+    const bool mass = form->kind == FEA_DIFFUSION_MASS && form->mass_coef != 0.0;
+    if (order == 1) FEA_TRY(launch_elem_p1(A, mass, load, q->npts, prec, s));
+    else FEA_TRY(launch_elem_p2(A, mass, load, q->npts, prec, s));
+  }
+
+  GatherArgs G{};
+  G.ndof = P->ndof;
+  G.row_ptr = P->row_ptr;
+  G.inc_ptr = B->inc_ptr;
+  G.inc = B->inc;
+  G.slot = B->slot;
+  G.Lm = m->lm.ptr;
+  G.Fl = A.Fl;
+  G.values = values;
+  G.rhs = rhs;
+  if (m->profile) FEA_CUDA(cudaEventRecord(m->ev[1], s));
+  FEA_TRY(launch_gather(nb, ndpn, mixed, G, P->rows_per_tile, P->max_tile_nnz, s));
+  if (m->profile) {
+    FEA_CUDA(cudaEventRecord(m->ev[2], s));
+    m->profiled = true;
+  }
+  return FEA_OK;
+}
+
+}  // namespace fea

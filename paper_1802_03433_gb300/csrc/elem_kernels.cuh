@@ -1,0 +1,214 @@
+// Element kernels: one thread per element computes its local matrix and load
+// vector (Sec. 5, Algorithm 1, the integrand evaluation of lines 5-7) and
+// writes them to the per-element scratch that the deterministic scatter
+// (gather.cu) reads.  Local matrices are stored full (row-major nl x nl per
+// element, both halves written from the same upper-triangle value), local
+// loads as nl values per element.
+#pragma once
+
+#include <type_traits>
+
+#include "element.cuh"
+#include "internal.cuh"
+
+namespace fea {
+
+struct ElemArgs {
+  const double* x;
+  const double* y;
+  const double* z;
+  const int32_t* tets;  // [4][E]
+  int64_t E;
+  const double* kappa;
+  double kappa_const;
+  const double* lam;
+  double lam_const;
+  const double* mu;
+  double mu_const;
+  double mass;      // mass coefficient (lambda of Eq. 1)
+  double fp[4];     // load amplitudes
+  void* Lm;         // [E][nl][nl] of R
+  void* Fl;         // [E][nl] of R
+  int* err;
+};
+
+constexpr int ELEM_T = 128;
+
+__device__ __forceinline__ void load_element(const ElemArgs& A, int64_t e, double X[4][3]) {
+  int32_t v[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) v[a] = __ldg(A.tets + a * A.E + e);
+  load_vertices(A.x, A.y, A.z, v, X);
+}
+
+__device__ __forceinline__ double dot3(const double* a, const double* b) {
+  return fma(a[0], b[0], fma(a[1], b[1], a[2] * b[2]));
+}
+__device__ __forceinline__ float dot3(const float* a, const float* b) {
+  return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2]));
+}
+
+// grad lambda_a in type R: FP64 path keeps the unscaled cofactors (the
+// 1/det scale is folded into the per-element factor); the mixed path forms
+// J^{-1} in FP64 and rounds it to FP32 once.
+template <typename R>
+__device__ __forceinline__ void grads(const Geo& g, R G[4][3]) {
+  if constexpr (std::is_same<R, double>::value) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) G[a][k] = g.c[a][k];
+  } else {
+    const double inv = 1.0 / g.det;
+#pragma unroll
+    for (int a = 1; a < 4; ++a)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) G[a][k] = __double2float_rn(g.c[a][k] * inv);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) G[0][k] = -(G[1][k] + G[2][k] + G[3][k]);
+  }
+}
+
+// Scale that turns products of grads<R> into |T| grad . grad:
+// FP64: |T| / det^2 = 1 / (6 |det|); mixed: |T| = |det| / 6.
+template <typename R>
+__device__ __forceinline__ double grad_scale(double adet) {
+  if constexpr (std::is_same<R, double>::value) return 1.0 / (6.0 * adet);
+  else return adet * (1.0 / 6.0);
+}
+
+template <typename R>
+__device__ __forceinline__ void vertices_r(const double X[4][3], R Xr[4][3]) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Xr[a][k] = to_r<R>(X[a][k]);
+}
+
+// ---------------------------------------------------------------- scalar forms
+// -div(kappa grad u) [+ mass u] on P1 (ORDER 1) or P2 (ORDER 2) tets.
+template <int ORDER, bool MASS, int LOAD, int NPTS, typename R>
+__global__ void __launch_bounds__(ELEM_T) k_elem_scalar(ElemArgs A) {
+  constexpr int NB = ORDER == 1 ? 4 : 10;
+  const int64_t e = (int64_t)blockIdx.x * ELEM_T + threadIdx.x;
+  if (e >= A.E) return;
+  double X[4][3];
+  load_element(A, e, X);
+  Geo g;
+  geometry(X, g);
+  if (!(g.det > 0.0)) atomicOr(A.err, DEV_ERR_DEGENERATE);
+  const double adet = fabs(g.det);
+  const double kap = A.kappa ? __ldg(A.kappa + e) : A.kappa_const;
+  R Gr[4][3];
+  grads<R>(g, Gr);
+  R* __restrict__ Lm = static_cast<R*>(A.Lm) + e * (NB * NB);
+
+  if constexpr (ORDER == 1) {
+    // K_ab = kappa |T| grad lambda_a . grad lambda_b ; M_ab = |T| (1 + delta_ab) / 20
+    const R s = R(kap * grad_scale<R>(adet));
+    [[maybe_unused]] R t = R(0);
+    if constexpr (MASS) t = R(A.mass * adet * (1.0 / 120.0));
+    static_for<10>([&](auto K) {
+      constexpr int a = upper_a(4, K), b = upper_b(4, K);
+      R v = s * dot3(Gr[a], Gr[b]);
+      if constexpr (MASS) v = fma(t, R(a == b ? 2 : 1), v);
+      Lm[a * 4 + b] = v;
+      if constexpr (a != b) Lm[b * 4 + a] = v;
+    });
+  } else {
+    // K_ab = kappa |T| / 20 sum_t num_t (grad lambda_i . grad lambda_j);
+    // M_ab = |T| / 420 * m420_ab
+    R G[4][4];
+    static_for<10>([&](auto K) {
+      constexpr int i = upper_a(4, K), j = upper_b(4, K);
+      G[i][j] = dot3(Gr[i], Gr[j]);
+      if constexpr (i != j) G[j][i] = G[i][j];
+    });
+    const R s = R(kap * grad_scale<R>(adet) * (1.0 / 20.0));
+    [[maybe_unused]] R t = R(0);
+    if constexpr (MASS) t = R(A.mass * adet * (1.0 / 2520.0));
+    static_for<55>([&](auto K) {
+      constexpr int a = upper_a(10, K), b = upper_b(10, K);
+      R v = s * p2_stiff<K, R>(G);
+      if constexpr (MASS) v = fma(t, R(p2_mass420(a, b)), v);
+      Lm[a * 10 + b] = v;
+      if constexpr (a != b) Lm[b * 10 + a] = v;
+    });
+  }
+
+  if constexpr (LOAD != LOAD_NONE) {
+    R Xr[4][3];
+    vertices_r<R>(X, Xr);
+    R Fs[NB];
+    shape_load<ORDER, NPTS, LOAD, R>(Xr, Fs);
+    const R amp = R(A.fp[0] * adet * (1.0 / 6.0));
+    R* __restrict__ Fl = static_cast<R*>(A.Fl) + e * NB;
+#pragma unroll
+    for (int a = 0; a < NB; ++a) Fl[a] = amp * Fs[a];
+  }
+}
+
+// ---------------------------------------------------------------- elasticity
+// K_(a,i),(b,j) = |T| [lam d_i phi_a d_j phi_b + mu d_j phi_a d_i phi_b
+//                      + mu delta_ij grad phi_a . grad phi_b]  on P1 tets.
+template <int LOAD, int NPTS, typename R>
+__global__ void __launch_bounds__(ELEM_T) k_elem_elast(ElemArgs A) {
+  const int64_t e = (int64_t)blockIdx.x * ELEM_T + threadIdx.x;
+  if (e >= A.E) return;
+  double X[4][3];
+  load_element(A, e, X);
+  Geo g;
+  geometry(X, g);
+  if (!(g.det > 0.0)) atomicOr(A.err, DEV_ERR_DEGENERATE);
+  const double adet = fabs(g.det);
+  const double lam = A.lam ? __ldg(A.lam + e) : A.lam_const;
+  const double mu = A.mu ? __ldg(A.mu + e) : A.mu_const;
+  R Gr[4][3];
+  grads<R>(g, Gr);
+  const double sc = grad_scale<R>(adet);
+  const R Ls = R(lam * sc), Ms = R(mu * sc);
+  R Lc[4][3], Mc[4][3], D[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      Lc[a][k] = Ls * Gr[a][k];
+      Mc[a][k] = Ms * Gr[a][k];
+    }
+  static_for<10>([&](auto K) {
+    constexpr int a = upper_a(4, K), b = upper_b(4, K);
+    D[a][b] = Ms * dot3(Gr[a], Gr[b]);
+    if constexpr (a != b) D[b][a] = D[a][b];
+  });
+  R* __restrict__ Lm = static_cast<R*>(A.Lm) + e * 144;
+  static_for<78>([&](auto K) {
+    constexpr int r = upper_a(12, K), c = upper_b(12, K);
+    constexpr int a = r / 3, i = r % 3, b = c / 3, j = c % 3;
+    R v = fma(Lc[a][i], Gr[b][j], Mc[a][j] * Gr[b][i]);
+    if constexpr (i == j) v += D[a][b];
+    Lm[r * 12 + c] = v;
+    if constexpr (r != c) Lm[c * 12 + r] = v;
+  });
+  if constexpr (LOAD != LOAD_NONE) {
+    R Xr[4][3];
+    vertices_r<R>(X, Xr);
+    R Fs[4];
+    shape_load<1, NPTS, LOAD, R>(Xr, Fs);
+    const double vol = adet * (1.0 / 6.0);
+    const R f0 = R(A.fp[0] * vol), f1 = R(A.fp[1] * vol), f2 = R(A.fp[2] * vol);
+    R* __restrict__ Fl = static_cast<R*>(A.Fl) + e * 12;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      Fl[3 * a + 0] = f0 * Fs[a];
+      Fl[3 * a + 1] = f1 * Fs[a];
+      Fl[3 * a + 2] = f2 * Fs[a];
+    }
+  }
+}
+
+// Launchers (one translation unit per element family).
+fea_status launch_elem_p1(const ElemArgs& A, bool mass, int load, int npts, int prec, cudaStream_t s);
+fea_status launch_elem_p2(const ElemArgs& A, bool mass, int load, int npts, int prec, cudaStream_t s);
+fea_status launch_elem_elast(const ElemArgs& A, int load, int npts, int prec, cudaStream_t s);
+
+}  // namespace fea

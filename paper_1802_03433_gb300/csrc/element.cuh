@@ -1,0 +1,311 @@
+// Device-side element math: geometry, quadrature rules, local matrices and
+// local load vectors of P1/P2 tetrahedra (the per-element work of Sec. 5,
+// Algorithm 1: evaluate the weak-form integrand of Eq. 2 on one element).
+//
+// One thread owns one element.  On GB300 the FP64 pipe (about 5e11 FMA/s per
+// GPU) is the scarce resource, so every formula here is written to spend as
+// few FP64 operations as the arithmetic allows:
+//   * geometry works with the unscaled cofactor vectors c_a (grad lambda_a =
+//     c_a / det J) and folds 1/det J into one scale factor per element;
+//   * bilinear forms with element-constant coefficients on affine elements
+//     are polynomials of degree <= 4, integrated exactly in closed form (the
+//     4- and 11-point rules integrate them exactly too, so the values are
+//     those of the quadrature up to rounding);
+//   * only the upper triangle of each symmetric local matrix is computed and
+//     then stored into both halves (bitwise symmetric);
+//   * the load vector is a genuine quadrature of f * phi_a with the
+//     requested rule, the quadrature points built from the rule's symmetry
+//     classes (one FMA per point and coordinate).
+// Template parameter R is the arithmetic type of the quadrature-point
+// products: double (plain FP64) or float (the mixed-precision split, where
+// the Jacobian, det J and J^{-1} stay FP64).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <utility>
+
+namespace fea {
+
+enum : int { LOAD_NONE = 0, LOAD_CONST = 1, LOAD_SIN = 2 };
+
+// ------------------------------------------------------------------ rules
+// 4-point degree-2 rule: permutations of (a, b, b, b), weight 1/4.
+constexpr double R4A = 0.5854101966249684544613761;  // (5 + 3 sqrt 5) / 20
+constexpr double R4B = 0.1381966011250105151795413;  // (5 - sqrt 5) / 20
+// 11-point degree-4 rule (Keast), weights normalised to sum to 1.
+constexpr double K11W0 = -0.07893333333333333333333333;  // 6 * (-74 / 5625), centroid
+constexpr double K11W1 = 0.04573333333333333333333333;   // 6 * 343 / 45000
+constexpr double K11W2 = 0.1493333333333333333333333;    // 6 * 56 / 2250
+constexpr double K11A = 0.7857142857142857142857143;     // 11 / 14
+constexpr double K11B = 0.07142857142857142857142857;    // 1 / 14
+constexpr double K11C1 = 0.3994035761667992049961021;    // (1 + sqrt(5/14)) / 4
+constexpr double K11C2 = 0.1005964238332007950038979;    // (1 - sqrt(5/14)) / 4
+
+// local edge k joins vertices edge_p(k) < edge_q(k)
+__host__ __device__ constexpr int edge_p(int k) { return k < 3 ? 0 : (k < 5 ? 1 : 2); }
+__host__ __device__ constexpr int edge_q(int k) { return k < 3 ? k + 1 : (k < 5 ? k - 1 : 3); }
+
+// Barycentric coordinate v of point q.  11-point ordering: centroid, the four
+// (A, B, B, B) points (vertex q-1 gets A), then the six (C1, C1, C2, C2)
+// points (edge q-5 gets C1 on both its vertices).
+__host__ __device__ constexpr double bary(int npts, int q, int v) {
+  return npts == 1 ? 0.25
+       : npts == 4 ? (v == q ? R4A : R4B)
+       : (q == 0 ? 0.25
+          : q <= 4 ? (v == q - 1 ? K11A : K11B)
+          : ((v == edge_p(q - 5) || v == edge_q(q - 5)) ? K11C1 : K11C2));
+}
+__host__ __device__ constexpr double weight(int npts, int q) {
+  return npts == 1 ? 1.0 : npts == 4 ? 0.25 : (q == 0 ? K11W0 : q <= 4 ? K11W1 : K11W2);
+}
+// Basis function a (order 1: lambda_a; order 2: vertex lambda(2 lambda - 1),
+// edge 4 lambda_p lambda_q) at rule point q.
+__host__ __device__ constexpr double phi_at(int order, int npts, int q, int a) {
+  return order == 1 ? bary(npts, q, a)
+       : a < 4 ? bary(npts, q, a) * (2.0 * bary(npts, q, a) - 1.0)
+       : 4.0 * bary(npts, q, edge_p(a - 4)) * bary(npts, q, edge_q(a - 4));
+}
+// sum_q w_q phi_a(q): the load of f = 1 divided by |T|.
+__host__ __device__ constexpr double wphi_sum(int order, int npts, int a) {
+  double s = 0.0;
+  for (int q = 0; q < npts; ++q) s += weight(npts, q) * phi_at(order, npts, q, a);
+  return s;
+}
+
+// ------------------------------------------------------------------ P2 tables
+// d phi_a / d lambda_i for the P2 basis, as (i, alpha + sum_k beta_k lambda_k):
+//   vertex v: (v, -1 + 4 lambda_v);  edge (p, q): (p, 4 lambda_q), (q, 4 lambda_p).
+struct LinForm {
+  int i = 0, alpha = 0;
+  int beta[4] = {0, 0, 0, 0};
+};
+struct DPhi {
+  int n = 0;
+  LinForm f[2] = {};
+};
+__host__ __device__ constexpr DPhi p2_dphi(int a) {
+  DPhi d{};
+  if (a < 4) {
+    d.n = 1;
+    d.f[0].i = a;
+    d.f[0].alpha = -1;
+    d.f[0].beta[a] = 4;
+  } else {
+    const int p = edge_p(a - 4), q = edge_q(a - 4);
+    d.n = 2;
+    d.f[0].i = p;
+    d.f[0].beta[q] = 4;
+    d.f[1].i = q;
+    d.f[1].beta[p] = 4;
+  }
+  return d;
+}
+// 20 |T|^{-1} int_T u v for linear forms in barycentrics, using
+// |T|^{-1} int lambda_k lambda_l = (1 + delta_kl) / 20 and int lambda_k = |T| / 4.
+__host__ __device__ constexpr int int20(const LinForm& u, const LinForm& v) {
+  int su = 0, sv = 0;
+  for (int k = 0; k < 4; ++k) {
+    su += u.beta[k];
+    sv += v.beta[k];
+  }
+  int r = 20 * u.alpha * v.alpha + 5 * (u.alpha * sv + v.alpha * su);
+  for (int k = 0; k < 4; ++k)
+    for (int l = 0; l < 4; ++l) r += u.beta[k] * v.beta[l] * (k == l ? 2 : 1);
+  return r;
+}
+// K_ab = kappa |T| / 20 * sum_t num_t * (grad lambda_i_t . grad lambda_j_t).
+struct Terms {
+  int n = 0;
+  int i[4] = {0, 0, 0, 0}, j[4] = {0, 0, 0, 0}, num[4] = {0, 0, 0, 0};
+};
+__host__ __device__ constexpr Terms p2_terms(int a, int b) {
+  Terms t{};
+  const DPhi da = p2_dphi(a), db = p2_dphi(b);
+  for (int x = 0; x < da.n; ++x)
+    for (int y = 0; y < db.n; ++y) {
+      int i = da.f[x].i, j = db.f[y].i;
+      if (i > j) {
+        const int tmp = i;
+        i = j;
+        j = tmp;
+      }
+      const int v = int20(da.f[x], db.f[y]);
+      int found = -1;
+      for (int k = 0; k < t.n; ++k)
+        if (t.i[k] == i && t.j[k] == j) found = k;
+      if (found >= 0) {
+        t.num[found] += v;
+      } else {
+        t.i[t.n] = i;
+        t.j[t.n] = j;
+        t.num[t.n] = v;
+        ++t.n;
+      }
+    }
+  return t;
+}
+// 420 |T|^{-1} int phi_a phi_b for the P2 basis.
+__host__ __device__ constexpr int p2_mass420(int a, int b) {
+  if (a > b) {
+    const int t = a;
+    a = b;
+    b = t;
+  }
+  if (b < 4) return a == b ? 6 : 1;
+  if (a < 4) return (edge_p(b - 4) == a || edge_q(b - 4) == a) ? -4 : -6;
+  if (a == b) return 32;
+  const int p = edge_p(a - 4), q = edge_q(a - 4), r = edge_p(b - 4), s = edge_q(b - 4);
+  return (p == r || p == s || q == r || q == s) ? 16 : 8;
+}
+// Index of the k-th upper-triangle pair (a <= b) of an n x n matrix, row-major.
+__host__ __device__ constexpr int upper_a(int n, int k) {
+  int a = 0;
+  while (k >= n - a) {
+    k -= n - a;
+    ++a;
+  }
+  return a;
+}
+__host__ __device__ constexpr int upper_b(int n, int k) {
+  int a = 0;
+  while (k >= n - a) {
+    k -= n - a;
+    ++a;
+  }
+  return a + k;
+}
+
+// ------------------------------------------------------------------ geometry
+struct Geo {
+  double c[4][3];  // grad lambda_a = c[a] / det
+  double det;
+};
+
+__device__ __forceinline__ void load_vertices(const double* __restrict__ x, const double* __restrict__ y,
+                                              const double* __restrict__ z, const int32_t v[4],
+                                              double X[4][3]) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    X[a][0] = __ldg(x + v[a]);
+    X[a][1] = __ldg(y + v[a]);
+    X[a][2] = __ldg(z + v[a]);
+  }
+}
+
+// J = [x1 - x0, x2 - x0, x3 - x0]; c_1 = e2 x e3, c_2 = e3 x e1, c_3 = e1 x e2
+// are the rows of det(J) J^{-1}; det J = e1 . c_1; c_0 = -(c_1 + c_2 + c_3).
+__device__ __forceinline__ void geometry(const double X[4][3], Geo& g) {
+  double e[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) e[i][k] = X[i + 1][k] - X[0][k];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const double* u = e[(i + 1) % 3];
+    const double* w = e[(i + 2) % 3];
+    g.c[i + 1][0] = fma(u[1], w[2], -u[2] * w[1]);
+    g.c[i + 1][1] = fma(u[2], w[0], -u[0] * w[2]);
+    g.c[i + 1][2] = fma(u[0], w[1], -u[1] * w[0]);
+  }
+  g.det = fma(e[0][0], g.c[1][0], fma(e[0][1], g.c[1][1], e[0][2] * g.c[1][2]));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) g.c[0][k] = -(g.c[1][k] + g.c[2][k] + g.c[3][k]);
+}
+
+template <typename R>
+__device__ __forceinline__ R rsinpi(R v);
+template <>
+__device__ __forceinline__ double rsinpi<double>(double v) { return sinpi(v); }
+template <>
+__device__ __forceinline__ float rsinpi<float>(float v) { return sinpif(v); }
+
+template <typename R>
+__device__ __forceinline__ R to_r(double v);
+template <>
+__device__ __forceinline__ double to_r<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float to_r<float>(double v) { return __double2float_rn(v); }
+
+// Quadrature points of rule NPTS for one coordinate, from the vertex values
+// v[0..3]: x_q = sum_v bary(q, v) v[v], grouped by symmetry class.
+template <int NPTS, typename R>
+__device__ __forceinline__ void quad_coord(const R v[4], R xq[NPTS]) {
+  const R S = (v[0] + v[1]) + (v[2] + v[3]);
+  if constexpr (NPTS == 1) {
+    xq[0] = R(0.25) * S;
+  } else if constexpr (NPTS == 4) {
+    const R bS = R(R4B) * S;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) xq[q] = fma(R(R4A - R4B), v[q], bS);
+  } else {
+    xq[0] = R(0.25) * S;
+    const R bS = R(K11B) * S;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) xq[1 + q] = fma(R(K11A - K11B), v[q], bS);
+    const R cS = R(K11C2) * S;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) xq[5 + k] = fma(R(K11C1 - K11C2), v[edge_p(k)] + v[edge_q(k)], cS);
+  }
+}
+
+// Compile-time loop: f(std::integral_constant<int, I>) for I = 0..N-1.
+template <int... Is, typename F>
+__device__ __forceinline__ void static_for_impl(std::integer_sequence<int, Is...>, F&& f) {
+  (f(std::integral_constant<int, Is>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+  static_for_impl(std::make_integer_sequence<int, N>{}, f);
+}
+
+// Shape load  Fs_a = sum_q w_q s(x_q) phi_a(x_q)  (without the factor |T|),
+// s = 1 (LOAD_CONST) or sin(pi x) sin(pi y) sin(pi z) (LOAD_SIN).
+template <int ORDER, int NPTS, int LOAD, typename R>
+__device__ __forceinline__ void shape_load(const R Xr[4][3], R Fs[ORDER == 1 ? 4 : 10]) {
+  constexpr int NB = ORDER == 1 ? 4 : 10;
+  if constexpr (LOAD == LOAD_CONST) {
+    static_for<NB>([&](auto A) {
+      constexpr double c = wphi_sum(ORDER, NPTS, A);
+      Fs[A] = R(c);
+    });
+  } else {
+    R sq[NPTS];
+#pragma unroll
+    for (int q = 0; q < NPTS; ++q) sq[q] = R(1);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const R v[4] = {Xr[0][c], Xr[1][c], Xr[2][c], Xr[3][c]};
+      R xq[NPTS];
+      quad_coord<NPTS, R>(v, xq);
+#pragma unroll
+      for (int q = 0; q < NPTS; ++q) sq[q] *= rsinpi<R>(xq[q]);
+    }
+    static_for<NB>([&](auto A) {
+      constexpr double c0 = weight(NPTS, 0) * phi_at(ORDER, NPTS, 0, A);
+      R acc = R(c0) * sq[0];
+      static_for<NPTS - 1>([&](auto Q) {
+        constexpr double cq = weight(NPTS, Q + 1) * phi_at(ORDER, NPTS, Q + 1, A);
+        acc = fma(R(cq), sq[Q + 1], acc);
+      });
+      Fs[A] = acc;
+    });
+  }
+}
+
+// ------------------------------------------------------------------ P2 stiffness entries
+// K_ab (upper pair number K) = sum_t num_t * G[i_t][j_t] (scale applied by the caller).
+template <int K, typename R>
+__device__ __forceinline__ R p2_stiff(const R G[4][4]) {
+  constexpr int A = upper_a(10, K), B = upper_b(10, K);
+  constexpr Terms t = p2_terms(A, B);
+  R v = R(t.num[0]) * G[t.i[0]][t.j[0]];
+  if constexpr (t.n > 1) v = fma(R(t.num[1]), G[t.i[1]][t.j[1]], v);
+  if constexpr (t.n > 2) v = fma(R(t.num[2]), G[t.i[2]][t.j[2]], v);
+  if constexpr (t.n > 3) v = fma(R(t.num[3]), G[t.i[3]][t.j[3]], v);
+  return v;
+}
+
+}  // namespace fea

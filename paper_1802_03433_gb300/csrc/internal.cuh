@@ -1,0 +1,114 @@
+// Internal declarations of libfea (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/fea.h"
+
+namespace fea {
+
+// ------------------------------------------------------------------ errors
+// Bits of the device error word latched per mesh.
+enum : int {
+  DEV_ERR_INDEX = 1,
+  DEV_ERR_DEGENERATE = 2,
+  DEV_ERR_OVERFLOW = 4,
+  DEV_ERR_TIMEOUT = 8,
+};
+
+void set_error(const std::string& msg);
+fea_status fail(fea_status st, const std::string& msg);
+fea_status cuda_fail(cudaError_t e, const char* what);
+
+#define FEA_CUDA(call)                                        \
+  do {                                                        \
+    cudaError_t e__ = (call);                                 \
+    if (e__ != cudaSuccess) return ::fea::cuda_fail(e__, #call); \
+  } while (0)
+
+#define FEA_TRY(call)                   \
+  do {                                  \
+    fea_status s__ = (call);            \
+    if (s__ != FEA_OK) return s__;      \
+  } while (0)
+
+// ------------------------------------------------------------------ handle
+// Scalar-dof structures of one element order, shared by the scalar forms and
+// (for P1) by elasticity.
+struct Base {
+  int nb = 0;               // local scalar dofs per element: 4 (P1) or 10 (P2)
+  int64_t nsd = 0;          // number of scalar dofs
+  int32_t* edof = nullptr;  // [nb][E] element -> scalar dof (P1: aliases mesh tets)
+  bool own_edof = false;
+  int32_t* rp = nullptr;    // [nsd + 1] scalar CSR row pointer
+  int32_t* ci = nullptr;    // [nnz] scalar CSR columns
+  int64_t nnz = 0;
+  int32_t* inc_ptr = nullptr;  // [nsd + 1] dof -> incidences
+  int32_t* inc = nullptr;      // [E * nb] incidence = e * nb + a, ascending e per dof
+  uint8_t* slot = nullptr;     // [E * nb][SW] slot of each local column within the row
+  int slot_width = 0;          // SW: 4 (P1) or 16 (P2)
+  int max_row = 0;             // longest scalar row
+  int32_t* emap = nullptr;     // [E][nb][nb] CSR position of local (a, b) (built on demand)
+};
+
+// The dof-level CSR pattern of (order, dofs per node).
+struct Pattern {
+  int order = 0, ndpn = 0;
+  int64_t ndof = 0, nnz = 0;
+  int32_t* row_ptr = nullptr;
+  int32_t* col_idx = nullptr;
+  bool own = false;           // ndpn == 1 aliases the Base arrays
+  int rows_per_tile = 0;      // gather tile height (rows per CTA)
+  int64_t max_tile_nnz = 0;   // largest CSR span of one tile
+};
+
+struct Scratch {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace fea
+
+struct fea_mesh {
+  const double* x = nullptr;
+  const double* y = nullptr;
+  const double* z = nullptr;
+  int64_t n_nodes = 0;
+  int64_t n_elems = 0;
+  int32_t* tets = nullptr;  // [4][E] owned copy
+  int* err = nullptr;       // device error word
+  fea::Base* base[3] = {nullptr, nullptr, nullptr};          // by order
+  fea::Pattern* pat[3][4] = {{nullptr}};                     // by order, ndpn
+  fea::Scratch lm, fl;      // local matrices / local loads of the last assembly
+  bool profile = false;     // record phase events in fea_assemble
+  bool profiled = false;    // events of a call are pending
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+};
+
+namespace fea {
+
+// pattern.cu
+fea_status build_base(fea_mesh* m, int order, cudaStream_t s);
+fea_status build_pattern(fea_mesh* m, int order, int ndpn, cudaStream_t s);
+fea_status build_emap(fea_mesh* m, int order, cudaStream_t s);
+fea_status validate_connectivity(fea_mesh* m, cudaStream_t s);
+void free_base(Base* b);
+void free_pattern(Pattern* p);
+
+// assemble.cu
+fea_status assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* co,
+                    const fea_quadrature* q, double* values, double* rhs, cudaStream_t s);
+
+// adjoint.cu
+fea_status assemble_backward(fea_mesh* m, const fea_form* form, const fea_coeffs* co,
+                             const fea_quadrature* q, const double* gv, const double* gf,
+                             double* gk, double* gx, cudaStream_t s);
+
+// scratch management (fea_api.cu)
+fea_status ensure_scratch(Scratch& sc, size_t bytes);
+fea_status read_and_clear_err(fea_mesh* m, cudaStream_t s);
+
+}  // namespace fea

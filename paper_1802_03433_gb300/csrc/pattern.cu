@@ -1,0 +1,644 @@
+// Global CSR sparsity pattern and the structures of the deterministic scatter.
+//
+// The paper's sparse kernel (Sec. 5, sparse variant of Algorithm 1) receives
+// the row structure as input: the nonzero count of each row (gNbrNodeLen) and
+// the column indices of each row (gNbrNodeIdx), padded to a row width MAX_NZ
+// derived from the mesh and the element type.  Here that structure is built
+// on the GPU from the connectivity alone:
+//
+//  1. dof -> element incidences: histogram, scan, fill, then each dof's list
+//     sorted by element id (so every later step is deterministic);
+//  2. CSR rows: one warp per row gathers the dofs of the row's incident
+//     elements into shared memory, drops repeats and ranks the survivors
+//     (count pass, scan to row_ptr, fill pass);
+//  3. slots: for every incidence (row, element, local a) the position of
+//     each of the element's dofs inside the row, 1 byte each; the scatter
+//     then needs no search;
+//  4. P2: the edge dofs come straight from the P1 pattern - the upper
+//     triangle of row a lists exactly the edges (a, b), b > a, in
+//     lexicographic order, so the rank of an edge is a scan offset plus a
+//     position in a row;
+//  5. vector (3 dofs per node) patterns expand each scalar coupling into a
+//     3 x 3 block.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace fea {
+
+namespace {
+
+constexpr int SCAN_T = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_BLOCK = SCAN_T * SCAN_ITEMS;
+constexpr int ROW_CAP = 1024;   // candidate couplings per scalar row (warp buffer)
+constexpr int UNIQ_WARPS = 4;   // warps per block of the row kernels
+
+// ------------------------------------------------------------------ buffers
+template <typename T>
+fea_status dalloc(T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(FEA_ERR_NOMEM, "device allocation of " + std::to_string(n * sizeof(T)) + " bytes failed");
+  }
+  return FEA_OK;
+}
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+// RAII temporary device buffer.
+template <typename T>
+struct Tmp {
+  T* p = nullptr;
+  ~Tmp() { dfree(p); }
+  fea_status alloc(size_t n) { return dalloc(&p, n); }
+};
+
+int blocks_for(int64_t n, int t) { return (int)std::max<int64_t>(1, (n + t - 1) / t); }
+
+// ------------------------------------------------------------------ scan
+__device__ __forceinline__ int64_t warp_incl_scan(int64_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += y;
+  }
+  return v;
+}
+
+// Exclusive block scan of one value per thread; returns the exclusive prefix
+// and sets *total to the block sum.
+__device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t* total) {
+  __shared__ int64_t ws[33];  // per-warp prefixes, then the block total
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  int64_t inc = warp_incl_scan(v);
+  if (lane == 31) ws[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t w = lane < nw ? ws[lane] : 0;
+    int64_t wi = warp_incl_scan(w);
+    if (lane < nw) ws[lane] = wi - w;
+    if (lane == 31) ws[32] = wi;
+  }
+  __syncthreads();
+  int64_t ex = ws[warp] + inc - v;
+  *total = ws[32];
+  __syncthreads();
+  return ex;
+}
+
+template <typename TI>
+__global__ void __launch_bounds__(SCAN_T) k_scan_local(const TI* __restrict__ in, int64_t n,
+                                                       int64_t* __restrict__ out, int64_t* __restrict__ bsum) {
+  const int64_t base = (int64_t)blockIdx.x * SCAN_BLOCK + (int64_t)threadIdx.x * SCAN_ITEMS;
+  int64_t v[SCAN_ITEMS];
+  int64_t ts = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    const int64_t i = base + k;
+    v[k] = i < n ? (int64_t)in[i] : 0;
+    ts += v[k];
+  }
+  int64_t total;
+  int64_t ex = block_excl_scan(ts, &total);
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    const int64_t i = base + k;
+    if (i < n) out[i] = ex;
+    ex += v[k];
+  }
+  if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+// Single block: exclusive scan of the block sums in place; total -> *tot.
+__global__ void __launch_bounds__(1024) k_scan_sums(int64_t* __restrict__ bsum, int64_t nb,
+                                                    int64_t* __restrict__ tot) {
+  int64_t carry = 0;
+  for (int64_t s = 0; s < nb; s += blockDim.x) {
+    const int64_t i = s + threadIdx.x;
+    const int64_t v = i < nb ? bsum[i] : 0;
+    int64_t total;
+    const int64_t ex = block_excl_scan(v, &total);
+    if (i < nb) bsum[i] = carry + ex;
+    carry += total;
+  }
+  if (threadIdx.x == 0) *tot = carry;
+}
+
+__global__ void k_scan_add(int64_t* __restrict__ out, int64_t n, const int64_t* __restrict__ bsum) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] += bsum[i / SCAN_BLOCK];
+}
+
+// out[0..n] = exclusive scan of in[0..n), out[n] = total.
+template <typename TI>
+fea_status scan(const TI* in, int64_t n, int64_t* out, cudaStream_t s) {
+  const int64_t nb = std::max<int64_t>(1, (n + SCAN_BLOCK - 1) / SCAN_BLOCK);
+  Tmp<int64_t> bsum;
+  FEA_TRY(bsum.alloc(nb));
+  k_scan_local<TI><<<(unsigned)nb, SCAN_T, 0, s>>>(in, n, out, bsum.p);
+  k_scan_sums<<<1, 1024, 0, s>>>(bsum.p, nb, out + n);
+  k_scan_add<<<blocks_for(n, 256), 256, 0, s>>>(out, n, bsum.p);
+  FEA_CUDA(cudaGetLastError());
+  FEA_CUDA(cudaStreamSynchronize(s));  // bsum is freed on return
+  return FEA_OK;
+}
+
+__global__ void k_i64_to_i32(const int64_t* __restrict__ in, int64_t n, int32_t* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (int32_t)in[i];
+}
+
+fea_status read_i64(const int64_t* d, int64_t* h, cudaStream_t s) {
+  FEA_CUDA(cudaMemcpyAsync(h, d, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  FEA_CUDA(cudaStreamSynchronize(s));
+  return FEA_OK;
+}
+
+// Exclusive scan of int32 counts into an int32 pointer array of n + 1,
+// failing with FEA_ERR_OVERFLOW when the total does not fit int32.
+fea_status scan_to_ptr32(const int32_t* cnt, int64_t n, int32_t* ptr, int64_t* total, cudaStream_t s,
+                         const char* what) {
+  Tmp<int64_t> p64;
+  FEA_TRY(p64.alloc(n + 1));
+  FEA_TRY(scan(cnt, n, p64.p, s));
+  FEA_TRY(read_i64(p64.p + n, total, s));
+  if (*total > (int64_t)INT32_MAX)
+    return fail(FEA_ERR_OVERFLOW, std::string(what) + " count " + std::to_string(*total) + " exceeds INT32_MAX");
+  k_i64_to_i32<<<blocks_for(n + 1, 256), 256, 0, s>>>(p64.p, n + 1, ptr);
+  FEA_CUDA(cudaGetLastError());
+  FEA_CUDA(cudaStreamSynchronize(s));
+  return FEA_OK;
+}
+
+// ------------------------------------------------------------------ validation
+__global__ void k_validate(const int32_t* __restrict__ tets, int64_t E, int64_t N, int* err) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  int32_t v[4];
+  bool bad = false;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    v[a] = tets[a * E + e];
+    bad |= v[a] < 0 || (int64_t)v[a] >= N;
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = a + 1; b < 4; ++b) bad |= v[a] == v[b];
+  if (bad) atomicOr(err, DEV_ERR_INDEX);
+}
+
+// ------------------------------------------------------------------ incidences
+__global__ void k_inc_count(const int32_t* __restrict__ edof, int64_t n, int32_t* __restrict__ cnt) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) atomicAdd(cnt + edof[i], 1);
+}
+
+// edof is SoA [nb][E]: entry i is local dof a = i / E of element e = i % E.
+__global__ void k_inc_fill(const int32_t* __restrict__ edof, int64_t E, int nb,
+                           const int32_t* __restrict__ ptr, int32_t* __restrict__ cursor,
+                           int32_t* __restrict__ inc) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= E * nb) return;
+  const int64_t a = i / E, e = i - a * E;
+  const int32_t d = edof[i];
+  const int32_t pos = ptr[d] + atomicAdd(cursor + d, 1);
+  inc[pos] = (int32_t)(e * nb + a);
+}
+
+// Insertion sort of every dof's incidence list (ascending element id).
+__global__ void k_inc_sort(const int32_t* __restrict__ ptr, int64_t n, int32_t* __restrict__ inc) {
+  const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= n) return;
+  const int32_t b = ptr[d], e = ptr[d + 1];
+  for (int32_t i = b + 1; i < e; ++i) {
+    const int32_t v = inc[i];
+    int32_t j = i - 1;
+    while (j >= b && inc[j] > v) {
+      inc[j + 1] = inc[j];
+      --j;
+    }
+    inc[j + 1] = v;
+  }
+}
+
+// ------------------------------------------------------------------ rows
+// One warp per scalar row.  The row's candidate columns are the nb dofs of
+// each incident element; repeats are dropped and each survivor's column is
+// its rank among the survivors.  count mode (col_idx == NULL): writes the
+// number of distinct columns; fill mode: writes the sorted columns.
+template <int NB>
+__global__ void __launch_bounds__(32 * UNIQ_WARPS) k_row_unique(int64_t nrows, const int32_t* __restrict__ inc_ptr,
+                                                                const int32_t* __restrict__ inc,
+                                                                const int32_t* __restrict__ edof, int64_t E,
+                                                                const int32_t* __restrict__ row_ptr,
+                                                                int32_t* __restrict__ counts,
+                                                                int32_t* __restrict__ col_idx, int* err) {
+  __shared__ int32_t sbuf[UNIQ_WARPS][ROW_CAP];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int32_t* buf = sbuf[w];
+  const int64_t nwarps = (int64_t)gridDim.x * UNIQ_WARPS;
+  for (int64_t row = (int64_t)blockIdx.x * UNIQ_WARPS + w; row < nrows; row += nwarps) {
+    const int32_t i0 = inc_ptr[row], i1 = inc_ptr[row + 1];
+    const int k = (i1 - i0) * NB;
+    if (k > ROW_CAP) {
+      if (lane == 0) {
+        atomicOr(err, DEV_ERR_OVERFLOW);
+        if (!col_idx) counts[row] = 0;
+      }
+      continue;
+    }
+    for (int t = lane; t < k; t += 32) {
+      const int32_t p = inc[i0 + t / NB];
+      const int64_t e = p / NB;
+      buf[t] = edof[(int64_t)(t % NB) * E + e];
+    }
+    __syncwarp();
+    uint32_t dup = 0;  // bit j: item lane + 32 j repeats an earlier item
+    for (int j = 0; lane + 32 * j < k; ++j) {
+      const int t = lane + 32 * j;
+      const int32_t v = buf[t];
+      for (int u = 0; u < t; ++u)
+        if (buf[u] == v) {
+          dup |= 1u << j;
+          break;
+        }
+    }
+    __syncwarp();
+    for (int j = 0; lane + 32 * j < k; ++j)
+      if (dup >> j & 1u) buf[lane + 32 * j] = -1;
+    __syncwarp();
+    if (!col_idx) {
+      int c = 0;
+      for (int j = 0; lane + 32 * j < k; ++j) c += !(dup >> j & 1u);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+      if (lane == 0) counts[row] = c;
+    } else {
+      const int32_t base = row_ptr[row];
+      for (int j = 0; lane + 32 * j < k; ++j) {
+        if (dup >> j & 1u) continue;
+        const int32_t v = buf[lane + 32 * j];
+        int rank = 0;
+        for (int u = 0; u < k; ++u) {
+          const int32_t q = buf[u];
+          rank += (q >= 0 && q < v);
+        }
+        col_idx[base + rank] = v;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Position of every local dof of each incidence inside the incidence's row.
+template <int NB, int SW>
+__global__ void k_slots(int64_t nrows, const int32_t* __restrict__ inc_ptr, const int32_t* __restrict__ inc,
+                        const int32_t* __restrict__ edof, int64_t E, const int32_t* __restrict__ rp,
+                        const int32_t* __restrict__ ci, uint8_t* __restrict__ slot, int* err) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  const int32_t lo = rp[r], len = rp[r + 1] - lo;
+  if (len > 255) {
+    atomicOr(err, DEV_ERR_OVERFLOW);
+    return;
+  }
+  for (int32_t i = inc_ptr[r]; i < inc_ptr[r + 1]; ++i) {
+    const int64_t e = inc[i] / NB;
+    for (int b = 0; b < NB; ++b) {
+      const int32_t c = edof[(int64_t)b * E + e];
+      int l = 0, h = len;
+      while (l < h) {
+        const int m = (l + h) >> 1;
+        if (ci[lo + m] < c) l = m + 1;
+        else h = m;
+      }
+      slot[(int64_t)i * SW + b] = (uint8_t)l;
+    }
+  }
+}
+
+__global__ void k_max_row(const int32_t* __restrict__ rp, int64_t n, int* out) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) atomicMax(out, rp[r + 1] - rp[r]);
+}
+
+__global__ void k_tile_max(const int32_t* __restrict__ rp, int64_t n, int rows, int* out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t r0 = t * rows;
+  if (r0 >= n) return;
+  const int64_t r1 = std::min<int64_t>(r0 + rows, n);
+  atomicMax(out, rp[r1] - rp[r0]);
+}
+
+// ------------------------------------------------------------------ P2 edges
+// Number of columns above the diagonal in each P1 row = edges (a, b), b > a.
+__global__ void k_upper_count(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int64_t N,
+                              int32_t* __restrict__ cnt) {
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= N) return;
+  int32_t c = 0;
+  for (int32_t p = rp[a]; p < rp[a + 1]; ++p) c += ci[p] > a;
+  cnt[a] = c;
+}
+
+__device__ __forceinline__ int32_t lower_bound(const int32_t* __restrict__ c, int32_t lo, int32_t hi, int32_t v) {
+  while (lo < hi) {
+    const int32_t m = (lo + hi) >> 1;
+    if (c[m] < v) lo = m + 1;
+    else hi = m;
+  }
+  return lo;
+}
+
+// edof2 [10][E]: vertices, then edge k = (p, q): N + ebase[a] + index of b
+// among the columns of row a above the diagonal, a = min, b = max.
+__global__ void k_p2_edof(const int32_t* __restrict__ tets, int64_t E, int64_t N, const int32_t* __restrict__ rp,
+                          const int32_t* __restrict__ ci, const int64_t* __restrict__ ebase,
+                          int32_t* __restrict__ edof2) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 10 * E) return;
+  const int64_t k = i / E, e = i - k * E;
+  if (k < 4) {
+    edof2[i] = tets[i];
+    return;
+  }
+  const int kk = (int)k - 4;
+  const int p = kk < 3 ? 0 : (kk < 5 ? 1 : 2);
+  const int q = kk < 3 ? kk + 1 : (kk < 5 ? kk - 1 : 3);
+  int32_t a = tets[(int64_t)p * E + e], b = tets[(int64_t)q * E + e];
+  if (a > b) {
+    const int32_t t = a;
+    a = b;
+    b = t;
+  }
+  const int32_t lo = rp[a], hi = rp[a + 1];
+  const int32_t first_up = lower_bound(ci, lo, hi, a + 1);
+  const int32_t pos = lower_bound(ci, lo, hi, b);
+  edof2[i] = (int32_t)(N + ebase[a] + (pos - first_up));
+}
+
+// ------------------------------------------------------------------ vector expansion
+__global__ void k_expand_rowptr(const int32_t* __restrict__ rp, int64_t N, int ndpn, int32_t* __restrict__ rp3) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r > N * ndpn) return;
+  if (r == N * ndpn) {
+    rp3[r] = (int32_t)((int64_t)ndpn * ndpn * rp[N]);
+    return;
+  }
+  const int64_t a = r / ndpn, c = r - a * ndpn;
+  rp3[r] = (int32_t)((int64_t)ndpn * ndpn * rp[a] + ndpn * c * (int64_t)(rp[a + 1] - rp[a]));
+}
+
+__global__ void k_expand_cols(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int64_t N, int ndpn,
+                              const int32_t* __restrict__ rp3, int32_t* __restrict__ ci3) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N * ndpn) return;
+  const int64_t a = r / ndpn;
+  int32_t o = rp3[r];
+  for (int32_t p = rp[a]; p < rp[a + 1]; ++p)
+    for (int d = 0; d < ndpn; ++d) ci3[o++] = ndpn * ci[p] + d;
+}
+
+// ------------------------------------------------------------------ emap
+__global__ void k_emap(int64_t nrows, int nb, int sw, const int32_t* __restrict__ inc_ptr,
+                       const int32_t* __restrict__ inc, const uint8_t* __restrict__ slot,
+                       const int32_t* __restrict__ rp, int32_t* __restrict__ emap) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  for (int32_t i = inc_ptr[r]; i < inc_ptr[r + 1]; ++i) {
+    const int64_t p = inc[i];  // e * nb + a
+    for (int b = 0; b < nb; ++b) emap[p * nb + b] = rp[r] + slot[(int64_t)i * sw + b];
+  }
+}
+
+fea_status check_err(fea_mesh* m, cudaStream_t s, const char* what) {
+  FEA_CUDA(cudaGetLastError());
+  FEA_CUDA(cudaStreamSynchronize(s));
+  int h = 0;
+  FEA_CUDA(cudaMemcpy(&h, m->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h & DEV_ERR_OVERFLOW) {
+    FEA_CUDA(cudaMemset(m->err, 0, sizeof(int)));
+    return fail(FEA_ERR_OVERFLOW, std::string(what) +
+                                      ": a row exceeds the scatter limits (more than 1024 candidate "
+                                      "couplings or more than 255 entries in a scalar row)");
+  }
+  if (h & DEV_ERR_INDEX) {
+    FEA_CUDA(cudaMemset(m->err, 0, sizeof(int)));
+    return fail(FEA_ERR_INDEX, std::string(what) + ": connectivity index out of range or repeated");
+  }
+  return FEA_OK;
+}
+
+template <int NB>
+fea_status rows_and_slots(fea_mesh* m, Base* B, cudaStream_t s) {
+  const int64_t n = B->nsd, E = m->n_elems;
+  const int uniq_blocks = (int)std::min<int64_t>(std::max<int64_t>(1, (n + UNIQ_WARPS - 1) / UNIQ_WARPS), 152 * 64);
+  Tmp<int32_t> cnt;
+  FEA_TRY(cnt.alloc(n));
+  k_row_unique<NB><<<uniq_blocks, 32 * UNIQ_WARPS, 0, s>>>(n, B->inc_ptr, B->inc, B->edof, E, nullptr, cnt.p,
+                                                           nullptr, m->err);
+  FEA_TRY(check_err(m, s, "pattern"));
+  FEA_TRY(dalloc(&B->rp, n + 1));
+  FEA_TRY(scan_to_ptr32(cnt.p, n, B->rp, &B->nnz, s, "nonzero"));
+  FEA_TRY(dalloc(&B->ci, B->nnz));
+  k_row_unique<NB><<<uniq_blocks, 32 * UNIQ_WARPS, 0, s>>>(n, B->inc_ptr, B->inc, B->edof, E, B->rp, nullptr,
+                                                           B->ci, m->err);
+  FEA_TRY(check_err(m, s, "pattern"));
+  constexpr int SW = NB == 4 ? 4 : 16;
+  B->slot_width = SW;
+  FEA_TRY(dalloc(&B->slot, (size_t)E * NB * SW));
+  k_slots<NB, SW><<<blocks_for(n, 128), 128, 0, s>>>(n, B->inc_ptr, B->inc, B->edof, E, B->rp, B->ci, B->slot,
+                                                    m->err);
+  FEA_TRY(check_err(m, s, "slots"));
+  Tmp<int> mx;
+  FEA_TRY(mx.alloc(1));
+  FEA_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(int), s));
+  k_max_row<<<blocks_for(n, 256), 256, 0, s>>>(B->rp, n, mx.p);
+  FEA_CUDA(cudaMemcpyAsync(&B->max_row, mx.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FEA_CUDA(cudaStreamSynchronize(s));
+  return FEA_OK;
+}
+
+fea_status incidences(fea_mesh* m, Base* B, cudaStream_t s) {
+  const int64_t E = m->n_elems, n = B->nsd, nI = E * B->nb;
+  if (nI > (int64_t)INT32_MAX) return fail(FEA_ERR_OVERFLOW, "elements x local dofs exceeds INT32_MAX");
+  Tmp<int32_t> cnt, cur;
+  FEA_TRY(cnt.alloc(n));
+  FEA_TRY(cur.alloc(n));
+  FEA_CUDA(cudaMemsetAsync(cnt.p, 0, n * sizeof(int32_t), s));
+  FEA_CUDA(cudaMemsetAsync(cur.p, 0, n * sizeof(int32_t), s));
+  k_inc_count<<<blocks_for(nI, 256), 256, 0, s>>>(B->edof, nI, cnt.p);
+  FEA_TRY(dalloc(&B->inc_ptr, n + 1));
+  int64_t tot = 0;
+  FEA_TRY(scan_to_ptr32(cnt.p, n, B->inc_ptr, &tot, s, "incidence"));
+  FEA_TRY(dalloc(&B->inc, nI));
+  k_inc_fill<<<blocks_for(nI, 256), 256, 0, s>>>(B->edof, E, B->nb, B->inc_ptr, cur.p, B->inc);
+  k_inc_sort<<<blocks_for(n, 128), 128, 0, s>>>(B->inc_ptr, n, B->inc);
+  FEA_CUDA(cudaGetLastError());
+  FEA_CUDA(cudaStreamSynchronize(s));
+  return FEA_OK;
+}
+
+}  // namespace
+
+void free_base(Base* b) {
+  if (!b) return;
+  if (b->own_edof) dfree(b->edof);
+  dfree(b->rp);
+  dfree(b->ci);
+  dfree(b->inc_ptr);
+  dfree(b->inc);
+  dfree(b->slot);
+  dfree(b->emap);
+  delete b;
+}
+
+void free_pattern(Pattern* p) {
+  if (!p) return;
+  if (p->own) {
+    dfree(p->row_ptr);
+    dfree(p->col_idx);
+  }
+  delete p;
+}
+
+fea_status validate_connectivity(fea_mesh* m, cudaStream_t s) {
+  if (m->n_elems > 0)
+    k_validate<<<blocks_for(m->n_elems, 256), 256, 0, s>>>(m->tets, m->n_elems, m->n_nodes, m->err);
+  return check_err(m, s, "mesh");
+}
+
+fea_status build_base(fea_mesh* m, int order, cudaStream_t s) {
+  if (m->base[order]) return FEA_OK;
+  if (order == 2) FEA_TRY(build_base(m, 1, s));
+  Base* B = new Base();
+  B->nb = order == 1 ? 4 : 10;
+  const int64_t E = m->n_elems, N = m->n_nodes;
+  fea_status st = FEA_OK;
+  do {
+    if (order == 1) {
+      B->edof = m->tets;
+      B->nsd = N;
+    } else {
+      const Base* P1 = m->base[1];
+      Tmp<int32_t> up;
+      Tmp<int64_t> ebase;
+      if ((st = up.alloc(N)) != FEA_OK) break;
+      if ((st = ebase.alloc(N + 1)) != FEA_OK) break;
+      k_upper_count<<<blocks_for(N, 256), 256, 0, s>>>(P1->rp, P1->ci, N, up.p);
+      if ((st = scan(up.p, N, ebase.p, s)) != FEA_OK) break;
+      int64_t nedges = 0;
+      if ((st = read_i64(ebase.p + N, &nedges, s)) != FEA_OK) break;
+      if (N + nedges > (int64_t)INT32_MAX) {
+        st = fail(FEA_ERR_OVERFLOW, "P2 dof count exceeds INT32_MAX");
+        break;
+      }
+      B->nsd = N + nedges;
+      if ((st = dalloc(&B->edof, (size_t)10 * E)) != FEA_OK) break;
+      B->own_edof = true;
+      if (E > 0)
+        k_p2_edof<<<blocks_for(10 * E, 256), 256, 0, s>>>(m->tets, E, N, P1->rp, P1->ci, ebase.p, B->edof);
+      cudaError_t ce = cudaStreamSynchronize(s);
+      if (ce != cudaSuccess) {
+        st = cuda_fail(ce, "p2 edof");
+        break;
+      }
+    }
+    if ((st = incidences(m, B, s)) != FEA_OK) break;
+    st = order == 1 ? rows_and_slots<4>(m, B, s) : rows_and_slots<10>(m, B, s);
+  } while (0);
+  if (st != FEA_OK) {
+    free_base(B);
+    return st;
+  }
+  m->base[order] = B;
+  return FEA_OK;
+}
+
+fea_status build_pattern(fea_mesh* m, int order, int ndpn, cudaStream_t s) {
+  if (m->pat[order][ndpn]) return FEA_OK;
+  FEA_TRY(build_base(m, order, s));
+  Base* B = m->base[order];
+  Pattern* P = new Pattern();
+  P->order = order;
+  P->ndpn = ndpn;
+  P->ndof = B->nsd * ndpn;
+  fea_status st = FEA_OK;
+  do {
+    if (ndpn == 1) {
+      P->row_ptr = B->rp;
+      P->col_idx = B->ci;
+      P->nnz = B->nnz;
+      P->own = false;
+    } else {
+      const int64_t nnz = B->nnz * ndpn * ndpn;
+      if (nnz > (int64_t)INT32_MAX) {
+        st = fail(FEA_ERR_OVERFLOW, "vector pattern nnz " + std::to_string(nnz) + " exceeds INT32_MAX");
+        break;
+      }
+      P->nnz = nnz;
+      P->own = true;
+      if ((st = dalloc(&P->row_ptr, P->ndof + 1)) != FEA_OK) break;
+      if ((st = dalloc(&P->col_idx, nnz)) != FEA_OK) break;
+      k_expand_rowptr<<<blocks_for(P->ndof + 1, 256), 256, 0, s>>>(B->rp, B->nsd, ndpn, P->row_ptr);
+      k_expand_cols<<<blocks_for(P->ndof, 128), 128, 0, s>>>(B->rp, B->ci, B->nsd, ndpn, P->row_ptr, P->col_idx);
+    }
+    // gather tiles: as many rows per CTA (<= 128) as keep the tile's CSR span
+    // within the shared-memory budget
+    Tmp<int> mx;
+    if ((st = mx.alloc(1)) != FEA_OK) break;
+    int rows = 128;
+    for (;;) {
+      cudaMemsetAsync(mx.p, 0, sizeof(int), s);
+      k_tile_max<<<blocks_for((P->ndof + rows - 1) / rows + 1, 256), 256, 0, s>>>(P->row_ptr, P->ndof, rows, mx.p);
+      int h = 0;
+      cudaMemcpyAsync(&h, mx.p, sizeof(int), cudaMemcpyDeviceToHost, s);
+      cudaError_t ce = cudaStreamSynchronize(s);
+      if (ce != cudaSuccess) {
+        st = cuda_fail(ce, "tile sizing");
+        break;
+      }
+      if ((int64_t)h * 8 <= 160 * 1024 || rows == 1) {
+        P->rows_per_tile = rows;
+        P->max_tile_nnz = h;
+        break;
+      }
+      rows /= 2;
+    }
+  } while (0);
+  if (st == FEA_OK && (int64_t)P->max_tile_nnz * 8 > 220 * 1024)
+    st = fail(FEA_ERR_OVERFLOW, "a single row is too long for the shared-memory scatter");
+  if (st != FEA_OK) {
+    free_pattern(P);
+    return st;
+  }
+  m->pat[order][ndpn] = P;
+  return FEA_OK;
+}
+
+fea_status build_emap(fea_mesh* m, int order, cudaStream_t s) {
+  FEA_TRY(build_pattern(m, order, 1, s));
+  Base* B = m->base[order];
+  if (B->emap) return FEA_OK;
+  FEA_TRY(dalloc(&B->emap, (size_t)m->n_elems * B->nb * B->nb));
+  k_emap<<<blocks_for(B->nsd, 128), 128, 0, s>>>(B->nsd, B->nb, B->slot_width, B->inc_ptr, B->inc, B->slot, B->rp,
+                                                 B->emap);
+  FEA_CUDA(cudaGetLastError());
+  return FEA_OK;
+}
+
+}  // namespace fea

@@ -1,0 +1,247 @@
+"""Thin Python binding of libfea (include/fea.h): argument marshalling only.
+
+Every function here forwards torch tensors' device pointers and the current
+CUDA stream to the C entry point of the same name; all assembly work runs in
+the library's CUDA kernels.  There is no CPU fallback: if libfea.so is
+missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfea.so")
+
+FEA_OK = 0
+STATUS = {0: "FEA_OK", 1: "FEA_ERR_ARG", 2: "FEA_ERR_INDEX", 3: "FEA_ERR_DEGENERATE",
+          4: "FEA_ERR_OVERFLOW", 5: "FEA_ERR_NOMEM", 6: "FEA_ERR_CUDA", 7: "FEA_ERR_TIMEOUT",
+          8: "FEA_ERR_STATE"}
+FEA_P1, FEA_P2 = 1, 2
+FEA_POISSON, FEA_DIFFUSION_MASS, FEA_ELASTICITY = 0, 1, 2
+FEA_FP64, FEA_MIXED = 0, 1
+FEA_LOAD_NONE, FEA_LOAD_CONST, FEA_LOAD_SINPROD = 0, 1, 2
+
+
+class FeaError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class fea_form(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("order", C.c_int32), ("mass_coef", C.c_double)]
+
+
+class fea_coeffs(C.Structure):
+    _fields_ = [("kappa", C.c_void_p), ("kappa_const", C.c_double),
+                ("lame_lambda", C.c_void_p), ("lambda_const", C.c_double),
+                ("lame_mu", C.c_void_p), ("mu_const", C.c_double),
+                ("f_kind", C.c_int32), ("f_param", C.c_double * 4)]
+
+
+class fea_quadrature(C.Structure):
+    _fields_ = [("npts", C.c_int32), ("prec", C.c_int32)]
+
+
+_lib = None
+_vp = C.c_void_p
+
+
+def lib() -> C.CDLL:
+    """Load libfea.so (built by build_lib.build()); raise if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise FeaError(-1, "lib", f"{LIB_PATH} not built: run build_lib.build() (no CPU fallback exists)")
+    L = C.CDLL(LIB_PATH)
+    i64p = C.POINTER(C.c_int64)
+    sig = {
+        "fea_mesh_create": [_vp, _vp, _vp, C.c_int64, _vp, C.c_int64, _vp, C.POINTER(_vp)],
+        "fea_mesh_set_coords": [_vp, _vp, _vp, _vp],
+        "fea_mesh_destroy": [_vp],
+        "fea_mesh_check": [_vp, _vp],
+        "fea_pattern": [_vp, C.c_int32, C.c_int32, i64p, i64p, _vp],
+        "fea_pattern_copy": [_vp, C.c_int32, C.c_int32, _vp, _vp, _vp],
+        "fea_dof_table_copy": [_vp, C.c_int32, _vp, _vp],
+        "fea_assemble": [_vp, C.POINTER(fea_form), C.POINTER(fea_coeffs), C.POINTER(fea_quadrature),
+                         _vp, _vp, _vp],
+        "fea_assemble_backward": [_vp, C.POINTER(fea_form), C.POINTER(fea_coeffs),
+                                  C.POINTER(fea_quadrature), _vp, _vp, _vp, _vp, _vp],
+        "fea_profile_enable": [_vp, C.c_int32],
+        "fea_profile_last": [_vp, C.POINTER(C.c_float), C.POINTER(C.c_float)],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    L.fea_last_error.restype = C.c_char_p
+    L.fea_last_error.argtypes = []
+    L.fea_status_string.restype = C.c_char_p
+    L.fea_status_string.argtypes = [C.c_int]
+    _lib = L
+    return L
+
+
+def _check(st: int, where: str):
+    if st != FEA_OK:
+        raise FeaError(st, where, lib().fea_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dev(t, dtype, name):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise FeaError(1, name, f"expected a contiguous CUDA {dtype} tensor")
+    return t
+
+
+# ---------------------------------------------------------------- same-name calls
+def fea_mesh_create(x, y, z, tets, stream=None):
+    """Handle (c_void_p) for coordinates x, y, z [N] float64 and tets [4, E] int32."""
+    for t, n in ((x, "x"), (y, "y"), (z, "z")):
+        _dev(t, torch.float64, n)
+    _dev(tets, torch.int32, "tets")
+    h = C.c_void_p()
+    _check(lib().fea_mesh_create(_ptr(x), _ptr(y), _ptr(z), x.numel(), _ptr(tets), tets.shape[1],
+                                 _stream(stream), C.byref(h)), "fea_mesh_create")
+    return h
+
+
+def fea_mesh_set_coords(h, x, y, z):
+    _check(lib().fea_mesh_set_coords(h, _ptr(x), _ptr(y), _ptr(z)), "fea_mesh_set_coords")
+
+
+def fea_mesh_destroy(h):
+    _check(lib().fea_mesh_destroy(h), "fea_mesh_destroy")
+
+
+def fea_mesh_check(h, stream=None):
+    _check(lib().fea_mesh_check(h, _stream(stream)), "fea_mesh_check")
+
+
+def fea_pattern(h, order, dofs_per_node=1, stream=None):
+    ndof, nnz = C.c_int64(), C.c_int64()
+    _check(lib().fea_pattern(h, order, dofs_per_node, C.byref(ndof), C.byref(nnz), _stream(stream)),
+           "fea_pattern")
+    return ndof.value, nnz.value
+
+
+def fea_pattern_copy(h, order, dofs_per_node, row_ptr, col_idx, stream=None):
+    _check(lib().fea_pattern_copy(h, order, dofs_per_node, _ptr(row_ptr), _ptr(col_idx), _stream(stream)),
+           "fea_pattern_copy")
+
+
+def fea_dof_table_copy(h, order, edof, stream=None):
+    _check(lib().fea_dof_table_copy(h, order, _ptr(edof), _stream(stream)), "fea_dof_table_copy")
+
+
+def make_form(kind, order, mass_coef=0.0):
+    return fea_form(kind, order, mass_coef)
+
+
+def make_coeffs(kappa=None, kappa_const=1.0, lam=None, lam_const=1.0, mu=None, mu_const=1.0,
+                f_kind=FEA_LOAD_NONE, f_param=(0.0, 0.0, 0.0, 0.0)):
+    fp = (C.c_double * 4)(*(list(f_param) + [0.0] * 4)[:4])
+    return fea_coeffs(_ptr(kappa), kappa_const, _ptr(lam), lam_const, _ptr(mu), mu_const, f_kind, fp)
+
+
+def make_quadrature(npts=4, prec=FEA_FP64):
+    return fea_quadrature(npts, prec)
+
+
+def fea_assemble(h, form, coeffs, quad, values, rhs=None, stream=None):
+    _check(lib().fea_assemble(h, C.byref(form), C.byref(coeffs), C.byref(quad), _ptr(values), _ptr(rhs),
+                              _stream(stream)), "fea_assemble")
+
+
+def fea_assemble_backward(h, form, coeffs, quad, grad_values, grad_rhs, grad_kappa, grad_x, stream=None):
+    _check(lib().fea_assemble_backward(h, C.byref(form), C.byref(coeffs), C.byref(quad), _ptr(grad_values),
+                                       _ptr(grad_rhs), _ptr(grad_kappa), _ptr(grad_x), _stream(stream)),
+           "fea_assemble_backward")
+
+
+def fea_profile_enable(h, enable=True):
+    _check(lib().fea_profile_enable(h, 1 if enable else 0), "fea_profile_enable")
+
+
+def fea_profile_last(h):
+    """(element-kernel ms, scatter-kernel ms) of the last profiled fea_assemble."""
+    a, b = C.c_float(), C.c_float()
+    _check(lib().fea_profile_last(h, C.byref(a), C.byref(b)), "fea_profile_last")
+    return a.value, b.value
+
+
+# ---------------------------------------------------------------- convenience wrapper
+class Mesh:
+    """Owns an fea_mesh handle plus the device tensors it references."""
+
+    def __init__(self, coords, tets, device="cuda", stream=None):
+        c = torch.as_tensor(coords, dtype=torch.float64).to(device).contiguous()
+        self.x, self.y, self.z = c[0].contiguous(), c[1].contiguous(), c[2].contiguous()
+        self.tets = torch.as_tensor(tets, dtype=torch.int32).to(device).contiguous()
+        self.n_nodes = self.x.numel()
+        self.n_elems = self.tets.shape[1]
+        self.h = fea_mesh_create(self.x, self.y, self.z, self.tets, stream)
+        self._pat = {}
+
+    def set_coords(self, x, y, z):
+        self.x, self.y, self.z = x, y, z
+        fea_mesh_set_coords(self.h, x, y, z)
+
+    def pattern(self, order=1, dofs_per_node=1):
+        key = (order, dofs_per_node)
+        if key not in self._pat:
+            self._pat[key] = fea_pattern(self.h, order, dofs_per_node)
+        return self._pat[key]
+
+    def pattern_tensors(self, order=1, dofs_per_node=1):
+        ndof, nnz = self.pattern(order, dofs_per_node)
+        rp = torch.empty(ndof + 1, dtype=torch.int32, device=self.x.device)
+        ci = torch.empty(max(nnz, 1), dtype=torch.int32, device=self.x.device)
+        fea_pattern_copy(self.h, order, dofs_per_node, rp, ci)
+        return rp, ci[:nnz]
+
+    def dof_table(self, order=1):
+        self.pattern(order, 1)
+        nb = 4 if order == 1 else 10
+        ed = torch.empty((nb, self.n_elems), dtype=torch.int32, device=self.x.device)
+        if self.n_elems:
+            fea_dof_table_copy(self.h, order, ed)
+        return ed
+
+    def assemble(self, form, coeffs, quad, values=None, rhs=None, with_rhs=True, stream=None):
+        ndpn = 3 if form.kind == FEA_ELASTICITY else 1
+        ndof, nnz = self.pattern(form.order, ndpn)
+        dev = self.x.device
+        if values is None:
+            values = torch.empty(max(nnz, 1), dtype=torch.float64, device=dev)
+        if rhs is None and with_rhs:
+            rhs = torch.empty(ndof, dtype=torch.float64, device=dev)
+        fea_assemble(self.h, form, coeffs, quad, values, rhs, stream)
+        return values[:nnz], rhs
+
+    def check(self, stream=None):
+        fea_mesh_check(self.h, stream)
+
+    def close(self):
+        if self.h is not None:
+            fea_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

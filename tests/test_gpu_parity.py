@@ -1,0 +1,215 @@
+"""GPU parity: the CUDA path through the C-ABI against the CPU oracle.
+
+CSR patterns and P2 dof tables must be bit-exact; values and loads within the
+row-scaled tolerance (1e-12 FP64, 1e-5 mixed).  Sizes are chosen so the
+oracle finishes in seconds while the kernels still run several CTAs with a
+ragged last tile.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from common import TOL_FP64, TOL_MIXED, case, gpu_system, oracle_system, row_scaled_error, vec_scaled_error
+from paper_1802_03433_gb300 import meshgen as mg
+
+pytestmark = pytest.mark.gpu
+
+CASES = [("p1_poisson", 8), ("p1_kappa", 7), ("p2_diffmass", 6), ("p2_poisson", 5), ("elasticity", 5)]
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available()
+    return torch
+
+
+@pytest.mark.parametrize("kind,n", CASES)
+def test_pattern_bit_exact(torch_cuda, kind, n):
+    c = case(kind, n)
+    o = oracle_system(c)
+    g = gpu_system(c)
+    np.testing.assert_array_equal(g["rp"], o["rp"])
+    np.testing.assert_array_equal(g["ci"], o["ci"])
+    if c["order"] == 2:
+        np.testing.assert_array_equal(g["mesh"].dof_table(2).cpu().numpy(), o["edof"])
+
+
+@pytest.mark.parametrize("kind,n", CASES)
+def test_values_fp64(torch_cuda, kind, n):
+    c = case(kind, n)
+    o = oracle_system(c)
+    g = gpu_system(c, prec=0)
+    assert row_scaled_error(o["rp"], o["vals"], g["vals"]) <= TOL_FP64
+    assert vec_scaled_error(o["rhs"], g["rhs"]) <= TOL_FP64
+
+
+@pytest.mark.parametrize("kind,n", CASES)
+def test_values_mixed(torch_cuda, kind, n):
+    c = case(kind, n)
+    o = oracle_system(c)
+    g = gpu_system(c, prec=1)
+    e_vals = row_scaled_error(o["rp"], o["vals"], g["vals"])
+    e_rhs = vec_scaled_error(o["rhs"], g["rhs"])
+    assert e_vals <= TOL_MIXED and e_rhs <= TOL_MIXED
+    assert e_vals > 0.0  # it really ran in reduced precision
+
+
+@pytest.mark.parametrize("kind", ["p1_kappa", "p2_diffmass", "elasticity"])
+def test_deterministic_and_bitwise_symmetric(torch_cuda, kind):
+    c = case(kind, 4, seed=3)
+    g1 = gpu_system(c)
+    g2 = gpu_system(c, mesh=g1["mesh"])
+    assert np.array_equal(g1["vals"].view(np.uint64), g2["vals"].view(np.uint64))
+    assert np.array_equal(g1["rhs"].view(np.uint64), g2["rhs"].view(np.uint64))
+    rp, ci, v = g1["rp"], g1["ci"], g1["vals"]
+    rows = np.repeat(np.arange(rp.size - 1), np.diff(rp))
+    key = rows.astype(np.int64) * (rp.size - 1) + ci
+    tkey = ci.astype(np.int64) * (rp.size - 1) + rows
+    order = np.argsort(tkey)
+    assert np.array_equal(key, np.sort(key))
+    assert np.array_equal(v.view(np.uint64), v[order].view(np.uint64))
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_tiny_meshes_all_forms(torch_cuda, n):
+    for kind in ("p1_kappa", "p2_diffmass", "elasticity"):
+        c = case(kind, n, seed=n)
+        o = oracle_system(c)
+        g = gpu_system(c)
+        np.testing.assert_array_equal(g["ci"], o["ci"])
+        assert row_scaled_error(o["rp"], o["vals"], g["vals"]) <= TOL_FP64
+        assert vec_scaled_error(o["rhs"], g["rhs"]) <= TOL_FP64
+
+
+@pytest.mark.parametrize("npts", [1, 4, 11])
+@pytest.mark.parametrize("order", [1, 2])
+def test_every_rule_and_load(torch_cuda, npts, order):
+    c = case("p2_diffmass" if order == 2 else "p1_kappa", 3, seed=7)
+    c["npts"] = npts
+    for fk, fp in (("const", (2.5,)), ("sinprod", (mg.SIN_AMP,))):
+        c["f_kind"], c["f_param"] = fk, fp
+        o = oracle_system(c)
+        g = gpu_system(c)
+        assert vec_scaled_error(o["rhs"], g["rhs"]) <= TOL_FP64
+        assert row_scaled_error(o["rp"], o["vals"], g["vals"]) <= TOL_FP64
+
+
+def test_unstructured_element_order(torch_cuda):
+    # a randomly permuted element and node numbering: nothing may rely on the
+    # cube ordering
+    c = case("p2_diffmass", 4, seed=9)
+    rng = np.random.default_rng(1)
+    N = c["coords"].shape[1]
+    perm_n = rng.permutation(N)
+    inv = np.empty(N, dtype=np.int64)
+    inv[perm_n] = np.arange(N)
+    perm_e = rng.permutation(c["tets"].shape[1])
+    c["coords"] = np.ascontiguousarray(c["coords"][:, perm_n])
+    c["tets"] = np.ascontiguousarray(inv[c["tets"][:, perm_e]].astype(np.int32))
+    c["kappa"] = np.ascontiguousarray(c["kappa"][perm_e])
+    o = oracle_system(c)
+    g = gpu_system(c)
+    np.testing.assert_array_equal(g["ci"], o["ci"])
+    assert row_scaled_error(o["rp"], o["vals"], g["vals"]) <= TOL_FP64
+
+
+# ---------------------------------------------------------------- edge cases
+def test_mesh_without_elements(torch_cuda):
+    import torch
+    from paper_1802_03433_gb300 import fea
+    coords = np.random.default_rng(0).uniform(size=(3, 5))
+    m = fea.Mesh(coords, np.zeros((4, 0), dtype=np.int32))
+    ndof, nnz = m.pattern(1)
+    assert (ndof, nnz) == (5, 0)
+    vals, rhs = m.assemble(fea.make_form(0, 1), fea.make_coeffs(f_kind=2, f_param=(1.0,)), fea.make_quadrature(4))
+    torch.cuda.synchronize()
+    assert rhs.abs().max().item() == 0.0
+
+
+def test_bad_index_rejected(torch_cuda):
+    from paper_1802_03433_gb300 import fea
+    coords, tets, _ = mg.make_cube(2)
+    tets = tets.copy()
+    tets[2, 5] = coords.shape[1] + 3
+    with pytest.raises(fea.FeaError) as ei:
+        fea.Mesh(coords, tets)
+    assert ei.value.status == 2
+    tets[2, 5] = tets[1, 5]
+    with pytest.raises(fea.FeaError) as ei:
+        fea.Mesh(coords, tets)
+    assert ei.value.status == 2
+
+
+def test_inverted_element_flagged(torch_cuda):
+    import torch
+    from paper_1802_03433_gb300 import fea
+    c = case("p1_kappa", 3)
+    tets = c["tets"].copy()
+    tets[[1, 2], 4] = tets[[2, 1], 4]  # flip one element's orientation
+    m = fea.Mesh(c["coords"], tets)
+    vals, rhs = m.assemble(fea.make_form(0, 1), fea.make_coeffs(f_kind=2, f_param=(1.0,)), fea.make_quadrature(4))
+    torch.cuda.synchronize()
+    with pytest.raises(fea.FeaError) as ei:
+        m.check()
+    assert ei.value.status == 3
+    m.check()  # cleared after being reported
+    # the values still use |det J| and match the oracle on the flipped mesh
+    c["tets"] = tets
+    o = oracle_system(c)
+    assert o["bad"] == 1
+
+
+def test_assemble_before_pattern_is_state_error(torch_cuda):
+    import torch
+    from paper_1802_03433_gb300 import fea
+    coords, tets, _ = mg.make_cube(2)
+    m = fea.Mesh(coords, tets)
+    v = torch.empty(10, dtype=torch.float64, device="cuda")
+    with pytest.raises(fea.FeaError) as ei:
+        fea.fea_assemble(m.h, fea.make_form(0, 2), fea.make_coeffs(), fea.make_quadrature(4), v, None)
+    assert ei.value.status == 8
+    with pytest.raises(fea.FeaError) as ei:
+        fea.fea_assemble(m.h, fea.make_form(0, 1), fea.make_coeffs(), fea.make_quadrature(5), v, None)
+    assert ei.value.status == 1
+
+
+# ---------------------------------------------------------------- full sizes
+def _sampled_rows(c, g, nrows, seed):
+    ndof = g["rp"].size - 1
+    rng = np.random.default_rng(seed)
+    rows = np.unique(np.concatenate([[0, ndof - 1], rng.choice(ndof, nrows, replace=False)]))
+    edof = g["mesh"].dof_table(c["order"]).cpu().numpy()
+    kw = dict(f_kind=c["f_kind"], f_param=c["f_param"], npts=c["npts"])
+    if c["form"] == "elasticity":
+        ref, rhs = oracle.rows(c["coords"], c["tets"], 1, edof, rows, kind="elasticity", lam=c["lam"],
+                               mu=c["mu"], **kw)
+    else:
+        ref, rhs = oracle.rows(c["coords"], c["tets"], c["order"], edof, rows, mass=c["mass"],
+                               kappa=c["kappa"], **kw)
+    worst = 0.0
+    for r in rows:
+        cols, vals = ref[int(r)]
+        lo, hi = g["rp"][r], g["rp"][r + 1]
+        np.testing.assert_array_equal(g["ci"][lo:hi], cols)
+        s = np.abs(vals).max() if vals.size else 1.0
+        worst = max(worst, np.abs(g["vals"][lo:hi] - vals).max() / s)
+        assert abs(g["rhs"][r] - rhs[int(r)]) <= TOL_FP64 * max(1.0, np.abs(g["rhs"]).max())
+    return worst
+
+
+@pytest.mark.parametrize("kind,n", [("p1_poisson", 8), ("p2_diffmass", 64), ("elasticity", 128), ("p1_kappa", 96)])
+def test_full_size_sampled_rows(torch_cuda, kind, n):
+    """The workloads at their full sizes: closed-form pattern size and 64 rows
+    checked entry by entry against the oracle's brute-force row assembly."""
+    c = case(kind, n)
+    g = gpu_system(c)
+    cc = mg.cube_counts(n)
+    nnz = {"p1_poisson": cc["p1_nnz"], "p1_kappa": cc["p1_nnz"], "p2_diffmass": cc["p2_nnz"],
+           "elasticity": 9 * cc["p1_nnz"]}[kind]
+    assert g["rp"][-1] == nnz and g["ci"].size == nnz
+    assert _sampled_rows(c, g, 64, seed=n) <= TOL_FP64
+    if kind == "p2_diffmass":
+        # 1^T A 1 = volume = 1 (the stiffness annihilates constants)
+        assert abs(g["vals"].sum() - 1.0) < 1e-9
+    g["mesh"].close()
