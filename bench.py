@@ -36,10 +36,15 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 # FP64 flops (2 x DFMA + DADD + DMUL, ncu SASS counters) executed per element
 # by the element kernel of each workload, and DRAM bytes per launch of the
-# dominant kernel (ncu, dram__bytes_read.sum + dram__bytes_write.sum).  None
-# where not yet captured for the current kernels.
-FP64_FLOP_PER_ELEM = {}
-DRAM_BYTES_PER_LAUNCH = {}
+# dominant kernel (ncu, dram__bytes_read.sum + dram__bytes_write.sum); the
+# captures are summarised under profiles/.  Absent where not captured for the
+# current kernels.
+FP64_FLOP_PER_ELEM = {
+    ("p2_diffmass_64", "fp64"): 1351.0,   # 518 DFMA + 140 DADD + 175 DMUL per element
+}
+DRAM_BYTES_PER_LAUNCH = {
+    ("p2_diffmass_64", "element"): 131.5e6 + 1599.9e6,
+}
 
 WORKLOADS = {
     "p2_diffmass_64": dict(kind="p2_diffmass", n=64),
@@ -208,6 +213,7 @@ def run_ours(args):
             dist.all_reduce(total, op=dist.ReduceOp.MAX)
         return total.item(), step_ms, phase, clk
 
+    fp64_rate = fea.fea_diag_fp64_rate() / 1e12  # measured FP64 FMA peak, TFLOP/s
     clocks = ClockSampler(local) if rank == 0 else None
     total_ms, step_ms, phase, clk = timed_loop(fea.FEA_FP64, args.steps, args.warmup, clocks)
     value = ws * E * args.steps / (total_ms / 1e3)
@@ -270,11 +276,12 @@ def run_ours(args):
         if flop is not None:
             ach = flop * E / (elem_ms / 1e3) / 1e12
             roof = {"kernel": "element", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "peak_kind": "nominal FP64 (2 DFMA/clk/SM)",
+                    "frac_of_measured_dfma": ach / fp64_rate, "measured_dfma_tflops": fp64_rate,
                     "traffic": DRAM_BYTES_PER_LAUNCH.get((args.workload, "element"))}
         else:
             roof = {"kernel": "element", "bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": None, "traffic": None}
+                    "unit": "TFLOP/s", "frac": None, "measured_dfma_tflops": fp64_rate, "traffic": None}
     else:
         # scatter: algorithmic bytes = local matrices read once + values/rhs written once
         nl = (4 if d["order"] == 1 else 10) * d["ndpn"]

@@ -188,6 +188,15 @@ fea_status fea_profile_enable(fea_mesh* mesh, int32_t enable);
  * FEA_ERR_STATE if no profiled call was made. */
 fea_status fea_profile_last(fea_mesh* mesh, float* elem_ms, float* scatter_ms);
 
+/* Self-check of the FP64 sin(pi x) the element kernels use for the load
+ * vector (no counterpart in the paper): for x [n] (device) writes the kernel
+ * helper's value to mine [n] and CUDA's sinpi to lib [n].  Asynchronous. */
+fea_status fea_diag_sinpi(const double* x, int64_t n, double* mine, double* lib, void* stream);
+
+/* Measure the device's sustained FP64 FMA throughput (flop/s, FMA = 2)
+ * with independent DFMA chains on every SM.  Synchronises. */
+fea_status fea_diag_fp64_rate(double* flops_per_s, void* stream);
+
 /* Message for the last error on the calling thread ("" if none). */
 const char* fea_last_error(void);
 

@@ -50,8 +50,10 @@ fea_status assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* co, con
   const size_t rb = mixed ? sizeof(float) : sizeof(double);
   const int64_t E = m->n_elems;
   const int load = rhs ? co->f_kind : FEA_LOAD_NONE;
-  FEA_TRY(ensure_scratch(m->lm, (size_t)E * nl * nl * rb));
-  if (load != FEA_LOAD_NONE) FEA_TRY(ensure_scratch(m->fl, (size_t)E * nl * rb));
+  // local rows in incidence order: E * nb incidences x ndpn rows x lstride
+  const size_t nrows_local = (size_t)E * nb * ndpn;
+  FEA_TRY(ensure_scratch(m->lm, nrows_local * lstride(nl, (int)rb) * rb));
+  if (load != FEA_LOAD_NONE) FEA_TRY(ensure_scratch(m->fl, nrows_local * rb));
 
   ElemArgs A{};
   A.x = m->x;
@@ -67,6 +69,7 @@ fea_status assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* co, con
   A.mu_const = co->mu_const;
   A.mass = form->mass_coef;
   for (int i = 0; i < 4; ++i) A.fp[i] = co->f_param[i];
+  A.ipos = B->ipos;
   A.Lm = m->lm.ptr;
   A.Fl = load != FEA_LOAD_NONE ? m->fl.ptr : nullptr;
   A.err = m->err;
@@ -84,7 +87,6 @@ fea_status assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* co, con
   G.ndof = P->ndof;
   G.row_ptr = P->row_ptr;
   G.inc_ptr = B->inc_ptr;
-  G.inc = B->inc;
   G.slot = B->slot;
   G.Lm = m->lm.ptr;
   G.Fl = A.Fl;

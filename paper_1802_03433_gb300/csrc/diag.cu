@@ -1,0 +1,65 @@
+// Diagnostic entry points (self-checks of device helpers; no counterpart in
+// the paper).
+#include "element.cuh"
+#include "internal.cuh"
+
+namespace fea {
+namespace {
+__global__ void k_diag_sinpi(const double* __restrict__ x, int64_t n, double* __restrict__ mine,
+                             double* __restrict__ lib) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  mine[i] = sinpi_fp64(x[i]);
+  lib[i] = sinpi(x[i]);
+}
+// Eight independent DFMA chains per thread: the FP64 pipe's sustained FMA
+// rate, the denominator of the element kernels' roofline.
+__global__ void k_diag_dfma(double* __restrict__ out, int iters, double s) {
+  double a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = threadIdx.x * 1e-9 + k;
+  for (int it = 0; it < iters; ++it)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fma(a[k], s, 0.5);
+  double r = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) r += a[k];
+  out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = r;
+}
+}  // namespace
+}  // namespace fea
+
+extern "C" fea_status fea_diag_fp64_rate(double* flops_per_s, void* stream) {
+  if (!flops_per_s) return fea::fail(FEA_ERR_ARG, "flops_per_s is NULL");
+  int dev = 0, sms = 0;
+  FEA_CUDA(cudaGetDevice(&dev));
+  FEA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int blocks = sms * 8, threads = 256, iters = 2048;
+  double* out = nullptr;
+  FEA_CUDA(cudaMallocAsync((void**)&out, sizeof(double) * blocks * threads, s));
+  cudaEvent_t a, b;
+  FEA_CUDA(cudaEventCreate(&a));
+  FEA_CUDA(cudaEventCreate(&b));
+  fea::k_diag_dfma<<<blocks, threads, 0, s>>>(out, iters, 0.999);  // warm-up
+  FEA_CUDA(cudaEventRecord(a, s));
+  for (int r = 0; r < 5; ++r) fea::k_diag_dfma<<<blocks, threads, 0, s>>>(out, iters, 0.999);
+  FEA_CUDA(cudaEventRecord(b, s));
+  FEA_CUDA(cudaEventSynchronize(b));
+  float ms = 0.f;
+  FEA_CUDA(cudaEventElapsedTime(&ms, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  FEA_CUDA(cudaFreeAsync(out, s));
+  FEA_CUDA(cudaStreamSynchronize(s));
+  *flops_per_s = 5.0 * blocks * threads * iters * 8 * 2.0 / (ms * 1e-3);
+  return FEA_OK;
+}
+
+extern "C" fea_status fea_diag_sinpi(const double* x, int64_t n, double* mine, double* lib, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !mine || !lib))) return fea::fail(FEA_ERR_ARG, "bad argument");
+  if (n == 0) return FEA_OK;
+  fea::k_diag_sinpi<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, n, mine, lib);
+  FEA_CUDA(cudaGetLastError());
+  return FEA_OK;
+}

@@ -1,9 +1,11 @@
 // Element kernels: one thread per element computes its local matrix and load
-// vector (Sec. 5, Algorithm 1, the integrand evaluation of lines 5-7) and
-// writes them to the per-element scratch that the deterministic scatter
-// (gather.cu) reads.  Local matrices are stored full (row-major nl x nl per
-// element, both halves written from the same upper-triangle value), local
-// loads as nl values per element.
+// vector (Sec. 5, Algorithm 1: the integrand evaluation that precedes the
+// accumulation into the global system) and writes them to the scratch that
+// the deterministic scatter (gather.cuh) reads.  Each local row (e, a) goes,
+// as one run of vector stores, to the position of incidence (e, a) in the
+// incidence list of global row dof(e, a); the scatter then streams every
+// row's contributions from contiguous memory.  Both halves of the symmetric
+// local matrix come from the same upper-triangle value (bitwise symmetric).
 #pragma once
 
 #include <type_traits>
@@ -27,10 +29,31 @@ struct ElemArgs {
   double mu_const;
   double mass;      // mass coefficient (lambda of Eq. 1)
   double fp[4];     // load amplitudes
-  void* Lm;         // [E][nl][nl] of R
-  void* Fl;         // [E][nl] of R
+  const int32_t* ipos;  // [nb][E] incidence index of (e, a)
+  void* Lm;         // local rows, incidence order, lstride(nl) values apart
+  void* Fl;         // local loads, incidence order
   int* err;
 };
+
+// Store one local row of NL values of type R at p (32-byte aligned) with
+// 16-byte vector stores, zero padding included up to lstride (whole sectors).
+template <int NL>
+__device__ __forceinline__ void store_row(double* __restrict__ p, const double* v) {
+  constexpr int LS = lstride(NL, 8);
+#pragma unroll
+  for (int k = 0; k < LS / 2; ++k)
+    reinterpret_cast<double2*>(p)[k] =
+        make_double2(2 * k < NL ? v[2 * k] : 0.0, 2 * k + 1 < NL ? v[2 * k + 1] : 0.0);
+}
+template <int NL>
+__device__ __forceinline__ void store_row(float* __restrict__ p, const float* v) {
+  constexpr int LS = lstride(NL, 4);
+#pragma unroll
+  for (int k = 0; k < LS / 4; ++k)
+    reinterpret_cast<float4*>(p)[k] =
+        make_float4(4 * k < NL ? v[4 * k] : 0.f, 4 * k + 1 < NL ? v[4 * k + 1] : 0.f,
+                    4 * k + 2 < NL ? v[4 * k + 2] : 0.f, 4 * k + 3 < NL ? v[4 * k + 3] : 0.f);
+}
 
 constexpr int ELEM_T = 128;
 
@@ -101,7 +124,7 @@ __global__ void __launch_bounds__(ELEM_T) k_elem_scalar(ElemArgs A) {
   const double kap = A.kappa ? __ldg(A.kappa + e) : A.kappa_const;
   R Gr[4][3];
   grads<R>(g, Gr);
-  R* __restrict__ Lm = static_cast<R*>(A.Lm) + e * (NB * NB);
+  R Kl[NB][NB];
 
   if constexpr (ORDER == 1) {
     // K_ab = kappa |T| grad lambda_a . grad lambda_b ; M_ab = |T| (1 + delta_ab) / 20
@@ -112,29 +135,35 @@ __global__ void __launch_bounds__(ELEM_T) k_elem_scalar(ElemArgs A) {
       constexpr int a = upper_a(4, K), b = upper_b(4, K);
       R v = s * dot3(Gr[a], Gr[b]);
       if constexpr (MASS) v = fma(t, R(a == b ? 2 : 1), v);
-      Lm[a * 4 + b] = v;
-      if constexpr (a != b) Lm[b * 4 + a] = v;
+      Kl[a][b] = v;
+      Kl[b][a] = v;
     });
   } else {
     // K_ab = kappa |T| / 20 sum_t num_t (grad lambda_i . grad lambda_j);
     // M_ab = |T| / 420 * m420_ab
-    R G[4][4];
+    const R s = R(kap * grad_scale<R>(adet) * (1.0 / 20.0));
+    R G[4][4];  // kappa |T| / 20 * grad lambda_i . grad lambda_j
     static_for<10>([&](auto K) {
       constexpr int i = upper_a(4, K), j = upper_b(4, K);
-      G[i][j] = dot3(Gr[i], Gr[j]);
+      G[i][j] = s * dot3(Gr[i], Gr[j]);
       if constexpr (i != j) G[j][i] = G[i][j];
     });
-    const R s = R(kap * grad_scale<R>(adet) * (1.0 / 20.0));
     [[maybe_unused]] R t = R(0);
     if constexpr (MASS) t = R(A.mass * adet * (1.0 / 2520.0));
     static_for<55>([&](auto K) {
       constexpr int a = upper_a(10, K), b = upper_b(10, K);
-      R v = s * p2_stiff<K, R>(G);
+      R v = p2_stiff<K, R>(G);
       if constexpr (MASS) v = fma(t, R(p2_mass420(a, b)), v);
-      Lm[a * 10 + b] = v;
-      if constexpr (a != b) Lm[b * 10 + a] = v;
+      Kl[a][b] = v;
+      Kl[b][a] = v;
     });
   }
+  constexpr int LS = lstride(NB, sizeof(R));
+  int32_t pos[NB];
+#pragma unroll
+  for (int a = 0; a < NB; ++a) pos[a] = __ldg(A.ipos + a * A.E + e);
+#pragma unroll
+  for (int a = 0; a < NB; ++a) store_row<NB>(static_cast<R*>(A.Lm) + (int64_t)pos[a] * LS, Kl[a]);
 
   if constexpr (LOAD != LOAD_NONE) {
     R Xr[4][3];
@@ -142,9 +171,9 @@ __global__ void __launch_bounds__(ELEM_T) k_elem_scalar(ElemArgs A) {
     R Fs[NB];
     shape_load<ORDER, NPTS, LOAD, R>(Xr, Fs);
     const R amp = R(A.fp[0] * adet * (1.0 / 6.0));
-    R* __restrict__ Fl = static_cast<R*>(A.Fl) + e * NB;
+    R* __restrict__ Fl = static_cast<R*>(A.Fl);
 #pragma unroll
-    for (int a = 0; a < NB; ++a) Fl[a] = amp * Fs[a];
+    for (int a = 0; a < NB; ++a) Fl[pos[a]] = amp * Fs[a];
   }
 }
 
@@ -180,15 +209,22 @@ __global__ void __launch_bounds__(ELEM_T) k_elem_elast(ElemArgs A) {
     D[a][b] = Ms * dot3(Gr[a], Gr[b]);
     if constexpr (a != b) D[b][a] = D[a][b];
   });
-  R* __restrict__ Lm = static_cast<R*>(A.Lm) + e * 144;
+  R Kl[12][12];
   static_for<78>([&](auto K) {
     constexpr int r = upper_a(12, K), c = upper_b(12, K);
     constexpr int a = r / 3, i = r % 3, b = c / 3, j = c % 3;
     R v = fma(Lc[a][i], Gr[b][j], Mc[a][j] * Gr[b][i]);
     if constexpr (i == j) v += D[a][b];
-    Lm[r * 12 + c] = v;
-    if constexpr (r != c) Lm[c * 12 + r] = v;
+    Kl[r][c] = v;
+    Kl[c][r] = v;
   });
+  int32_t pos[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) pos[a] = __ldg(A.ipos + a * A.E + e);
+#pragma unroll
+  constexpr int LS = lstride(12, sizeof(R));
+#pragma unroll
+  for (int r = 0; r < 12; ++r) store_row<12>(static_cast<R*>(A.Lm) + ((int64_t)pos[r / 3] * 3 + r % 3) * LS, Kl[r]);
   if constexpr (LOAD != LOAD_NONE) {
     R Xr[4][3];
     vertices_r<R>(X, Xr);
@@ -196,12 +232,12 @@ __global__ void __launch_bounds__(ELEM_T) k_elem_elast(ElemArgs A) {
     shape_load<1, NPTS, LOAD, R>(Xr, Fs);
     const double vol = adet * (1.0 / 6.0);
     const R f0 = R(A.fp[0] * vol), f1 = R(A.fp[1] * vol), f2 = R(A.fp[2] * vol);
-    R* __restrict__ Fl = static_cast<R*>(A.Fl) + e * 12;
+    R* __restrict__ Fl = static_cast<R*>(A.Fl);
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-      Fl[3 * a + 0] = f0 * Fs[a];
-      Fl[3 * a + 1] = f1 * Fs[a];
-      Fl[3 * a + 2] = f2 * Fs[a];
+      Fl[(int64_t)pos[a] * 3 + 0] = f0 * Fs[a];
+      Fl[(int64_t)pos[a] * 3 + 1] = f1 * Fs[a];
+      Fl[(int64_t)pos[a] * 3 + 2] = f2 * Fs[a];
     }
   }
 }

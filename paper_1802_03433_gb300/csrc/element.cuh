@@ -215,10 +215,47 @@ __device__ __forceinline__ void geometry(const double X[4][3], Geo& g) {
   for (int k = 0; k < 3; ++k) g.c[0][k] = -(g.c[1][k] + g.c[2][k] + g.c[3][k]);
 }
 
+// sin(pi x) in FP64 with 11 FP64 operations (the library sinpi costs about
+// 18 FP64-pipe operations on this part).  Range reduction: adding
+// 1.5 * 2^52 rounds x to the nearest integer n (ties to even) and leaves the
+// parity of n in the lowest mantissa bit; r = x - n is exact, |r| <= 1/2.
+// Then sin(pi x) = (-1)^n r P(r^2), P the degree-7 interpolant of
+// sin(pi r)/r at 8 Chebyshev nodes in r^2 on [0, 1/4] (coefficients from
+// gen_sinpi.py), within 3.4e-16 of sin(pi x).  |x| >= 2^51, infinities and
+// NaNs go to the library function.
+constexpr double SINPI_C0 = 3.1415926535897928787;
+constexpr double SINPI_C1 = -5.16771278004978582274;
+constexpr double SINPI_C2 = 2.55016403986186762969;
+constexpr double SINPI_C3 = -0.59926452882522400508;
+constexpr double SINPI_C4 = 0.0821458788163104269166;
+constexpr double SINPI_C5 = -0.00737036432653041567555;
+constexpr double SINPI_C6 = 0.000465987015804337793336;
+constexpr double SINPI_C7 = -0.0000211336273520529704044;
+
+__device__ __forceinline__ double sinpi_fp64(double x) {
+  const int hi = __double2hiint(x);
+  if ((hi & 0x7FF00000) >= ((1023 + 51) << 20)) return sinpi(x);
+  constexpr double MAGIC = 6755399441055744.0;  // 1.5 * 2^52
+  const double t = x + MAGIC;
+  const double n = t - MAGIC;
+  const double r = x - n;
+  const double u = r * r;
+  double p = fma(SINPI_C7, u, SINPI_C6);
+  p = fma(p, u, SINPI_C5);
+  p = fma(p, u, SINPI_C4);
+  p = fma(p, u, SINPI_C3);
+  p = fma(p, u, SINPI_C2);
+  p = fma(p, u, SINPI_C1);
+  p = fma(p, u, SINPI_C0);
+  const double sv = p * r;
+  const int flip = (__double2loint(t) & 1) << 31;
+  return __hiloint2double(__double2hiint(sv) ^ flip, __double2loint(sv));
+}
+
 template <typename R>
 __device__ __forceinline__ R rsinpi(R v);
 template <>
-__device__ __forceinline__ double rsinpi<double>(double v) { return sinpi(v); }
+__device__ __forceinline__ double rsinpi<double>(double v) { return sinpi_fp64(v); }
 template <>
 __device__ __forceinline__ float rsinpi<float>(float v) { return sinpif(v); }
 
@@ -296,7 +333,7 @@ __device__ __forceinline__ void shape_load(const R Xr[4][3], R Fs[ORDER == 1 ? 4
 }
 
 // ------------------------------------------------------------------ P2 stiffness entries
-// K_ab (upper pair number K) = sum_t num_t * G[i_t][j_t] (scale applied by the caller).
+// K_ab (upper pair number K) = sum_t num_t * G[i_t][j_t] (G already scaled).
 template <int K, typename R>
 __device__ __forceinline__ R p2_stiff(const R G[4][4]) {
   constexpr int A = upper_a(10, K), B = upper_b(10, K);

@@ -7,9 +7,11 @@
 // row-sorted form of a sorted-COO reduction:
 //   * one CTA owns a tile of consecutive CSR rows, whose values form one
 //     contiguous span of `values`; the span is accumulated in shared memory;
-//   * one thread owns one row and walks the row's incidence list (element,
-//     local row a) in ascending element order, adding local row a of each
-//     element at the precomputed slots of the row;
+//   * one thread owns one row; the element kernel has already written the
+//     row's contributions (local row a of every element holding the row's
+//     dof, ascending element order) contiguously, so the thread streams them
+//     with addresses that depend on nothing it loads, two at a time, and adds
+//     each at its precomputed slots;
 //   * the finished span is written to HBM with coalesced stores.
 // Every value is therefore the sum of its contributions in element order,
 // computed by one thread: bitwise reproducible, and bitwise symmetric because
@@ -23,21 +25,61 @@
 
 namespace fea {
 
-// Exact float -> double conversion with integer operations (keeps the
-// conversion off the FP64 pipe): the IEEE-754 binary32 fields are moved into
-// binary64 position with the exponent re-biased by 1023 - 127 = 896.  Zeros,
-// subnormals, infinities and NaNs take the hardware conversion.
-__device__ __forceinline__ double widen(float f) {
-  const uint32_t u = __float_as_uint(f);
-  const uint32_t ex = (u >> 23) & 0xFFu;
-  if (ex - 1u < 0xFEu) {
-    const uint32_t hi = (u & 0x80000000u) | ((ex + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
-    const uint32_t lo = u << 29;
-    return __hiloint2double((int)hi, (int)lo);
+// Exact float -> double conversion of a whole local row with integer
+// operations (keeps the widening off the scarce FP64 pipe): the IEEE-754
+// binary32 fields move into binary64 position with the exponent re-biased by
+// 1023 - 127 = 896; +-0 keeps only its sign.  A row holding a subnormal, an
+// infinity or a NaN (never produced by finite inputs of normal size) takes
+// the hardware conversion instead.
+template <int NL>
+__device__ __forceinline__ void widen_row(const float* v, double* out) {
+  bool special = false;
+#pragma unroll
+  for (int k = 0; k < NL; ++k) {
+    const uint32_t u = __float_as_uint(v[k]);
+    const uint32_t ex = (u >> 23) & 0xFFu;
+    const bool zero = (u & 0x7FFFFFFFu) == 0u;
+    special |= !zero && (ex - 1u >= 0xFEu);
+    uint32_t hi = (u & 0x80000000u) | ((ex + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+    hi = zero ? u : hi;
+    out[k] = __hiloint2double((int)hi, (int)(u << 29));
   }
-  return (double)f;
+  if (special) {
+#pragma unroll
+    for (int k = 0; k < NL; ++k) out[k] = (double)v[k];
+  }
+}
+template <int NL>
+__device__ __forceinline__ void widen_row(const double* v, double* out) {
+#pragma unroll
+  for (int k = 0; k < NL; ++k) out[k] = v[k];
 }
 __device__ __forceinline__ double widen(double d) { return d; }
+__device__ __forceinline__ double widen(float f) {
+  double o;
+  widen_row<1>(&f, &o);
+  return o;
+}
+
+// Add one local row (NL values, distinct target slots) into the row's
+// shared-memory span: all slots are read, then added, then written, so the
+// loads of one incidence do not wait on each other's stores.
+template <int NB, int NDPN, typename LT>
+__device__ __forceinline__ void add_row(double* __restrict__ a, const int s[NB], const LT* v) {
+  constexpr int NL = NB * NDPN;
+  double w[NL], t[NL];
+  widen_row<NL>(v, w);
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+#pragma unroll
+    for (int j = 0; j < NDPN; ++j) t[NDPN * b + j] = a[NDPN * s[b] + j];
+#pragma unroll
+  for (int k = 0; k < NL; ++k) t[k] += w[k];
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+#pragma unroll
+    for (int j = 0; j < NDPN; ++j) a[NDPN * s[b] + j] = t[NDPN * b + j];
+}
 
 // Load NL consecutive values starting at p with the widest aligned vectors.
 template <int NL>
@@ -90,19 +132,35 @@ struct GatherArgs {
   int64_t ndof;
   const int32_t* row_ptr;  // dof-level CSR
   const int32_t* inc_ptr;  // scalar dof -> incidences
-  const int32_t* inc;
-  const uint8_t* slot;
-  const void* Lm;          // [E][NL][NL]
-  const void* Fl;          // [E][NL] or NULL
+  const uint8_t* slot;     // [incidence][SW] column slots
+  const void* Lm;          // local rows in incidence order (lstride apart)
+  const void* Fl;          // local loads in incidence order, or NULL
   double* values;
   double* rhs;             // or NULL
 };
 
+// Loads of one incidence: the column slots, the local row, the local load.
+template <int NB, int NDPN, typename LT>
+struct Contrib {
+  static constexpr int NL = NB * NDPN;
+  int s[NB];
+  LT v[NL];
+  LT f;
+  __device__ __forceinline__ void load(const GatherArgs& G, int32_t i, int comp) {
+    constexpr int LS = lstride(NL, sizeof(LT));
+    load_slots<NB>(G.slot, i, s);
+    load_row<NL>(static_cast<const LT*>(G.Lm) + ((int64_t)i * NDPN + comp) * LS, v);
+    f = G.Fl ? __ldg(static_cast<const LT*>(G.Fl) + (int64_t)i * NDPN + comp) : LT(0);
+  }
+};
+
 // NB local scalar dofs, NDPN dofs per scalar dof, LT local-value type.
+// Incidences are consumed in pairs; the loads of the next pair are issued
+// before the current pair is added (software pipeline), so one pair's memory
+// latency overlaps the other pair's shared-memory adds.
 template <int NB, int NDPN, typename LT>
 __global__ void __launch_bounds__(128) k_gather(GatherArgs G) {
   extern __shared__ double acc[];
-  constexpr int NL = NB * NDPN;
   const int rows = blockDim.x;
   const int64_t r0 = (int64_t)blockIdx.x * rows;
   const int64_t r1 = r0 + rows < G.ndof ? r0 + rows : G.ndof;
@@ -115,22 +173,24 @@ __global__ void __launch_bounds__(128) k_gather(GatherArgs G) {
     const int64_t node = r / NDPN;
     const int comp = (int)(r - node * NDPN);
     double* __restrict__ a = acc + (__ldg(G.row_ptr + r) - base);
-    const LT* __restrict__ Lm = static_cast<const LT*>(G.Lm);
-    const LT* __restrict__ Fl = static_cast<const LT*>(G.Fl);
     double f = 0.0;
     const int32_t i1 = __ldg(G.inc_ptr + node + 1);
-    for (int32_t i = __ldg(G.inc_ptr + node); i < i1; ++i) {
-      const int32_t p = __ldg(G.inc + i);  // e * NB + local a
-      int s[NB];
-      load_slots<NB>(G.slot, i, s);
-      const int64_t lrow = (int64_t)p * NDPN + comp;  // local row (a, comp) of element e
-      LT v[NL];
-      load_row<NL>(Lm + lrow * NL, v);
-#pragma unroll
-      for (int b = 0; b < NB; ++b)
-#pragma unroll
-        for (int j = 0; j < NDPN; ++j) a[NDPN * s[b] + j] += widen(v[NDPN * b + j]);
-      if (Fl) f += widen(__ldg(Fl + lrow));
+    int32_t i = __ldg(G.inc_ptr + node);
+    Contrib<NB, NDPN, LT> c0, c1, n0, n1;
+    if (i < i1) c0.load(G, i, comp);
+    if (i + 1 < i1) c1.load(G, i + 1, comp);
+    while (i < i1) {
+      if (i + 2 < i1) n0.load(G, i + 2, comp);
+      if (i + 3 < i1) n1.load(G, i + 3, comp);
+      add_row<NB, NDPN, LT>(a, c0.s, c0.v);
+      f += widen(c0.f);
+      if (i + 1 < i1) {
+        add_row<NB, NDPN, LT>(a, c1.s, c1.v);
+        f += widen(c1.f);
+      }
+      c0 = n0;
+      c1 = n1;
+      i += 2;
     }
     if (G.rhs) G.rhs[r] = f;
   }

@@ -51,8 +51,16 @@ struct Base {
   uint8_t* slot = nullptr;     // [E * nb][SW] slot of each local column within the row
   int slot_width = 0;          // SW: 4 (P1) or 16 (P2)
   int max_row = 0;             // longest scalar row
+  int32_t* ipos = nullptr;     // [nb][E] incidence index of (element e, local dof a)
   int32_t* emap = nullptr;     // [E][nb][nb] CSR position of local (a, b) (built on demand)
 };
+
+// Local rows are stored in incidence order: local row (e, a[, comp]) of the
+// element with incidence index i = ipos[a][e] lives at row i * ndpn + comp of
+// a buffer whose rows are lstride(nl, bytes) values apart: a whole number of
+// 32-byte DRAM sectors, written in full (padding included), so no sector is
+// ever left partly written (a partly written sector costs a DRAM read-fill).
+__host__ __device__ constexpr int lstride(int nl, int bytes) { return ((nl * bytes + 31) / 32) * 32 / bytes; }
 
 // The dof-level CSR pattern of (order, dofs per node).
 struct Pattern {

@@ -413,6 +413,16 @@ __global__ void k_expand_cols(const int32_t* __restrict__ rp, const int32_t* __r
     for (int d = 0; d < ndpn; ++d) ci3[o++] = ndpn * ci[p] + d;
 }
 
+// ------------------------------------------------------------------ ipos
+// Inverse of the incidence list: ipos[a][e] = i such that inc[i] = e * nb + a.
+__global__ void k_ipos(int64_t nI, int nb, int64_t E, const int32_t* __restrict__ inc, int32_t* __restrict__ ipos) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nI) return;
+  const int64_t p = inc[i];
+  const int64_t e = p / nb, a = p - e * nb;
+  ipos[a * E + e] = (int32_t)i;
+}
+
 // ------------------------------------------------------------------ emap
 __global__ void k_emap(int64_t nrows, int nb, int sw, const int32_t* __restrict__ inc_ptr,
                        const int32_t* __restrict__ inc, const uint8_t* __restrict__ slot,
@@ -488,6 +498,8 @@ fea_status incidences(fea_mesh* m, Base* B, cudaStream_t s) {
   FEA_TRY(dalloc(&B->inc, nI));
   k_inc_fill<<<blocks_for(nI, 256), 256, 0, s>>>(B->edof, E, B->nb, B->inc_ptr, cur.p, B->inc);
   k_inc_sort<<<blocks_for(n, 128), 128, 0, s>>>(B->inc_ptr, n, B->inc);
+  FEA_TRY(dalloc(&B->ipos, nI));
+  k_ipos<<<blocks_for(nI, 256), 256, 0, s>>>(nI, B->nb, E, B->inc, B->ipos);
   FEA_CUDA(cudaGetLastError());
   FEA_CUDA(cudaStreamSynchronize(s));
   return FEA_OK;
@@ -503,6 +515,7 @@ void free_base(Base* b) {
   dfree(b->inc_ptr);
   dfree(b->inc);
   dfree(b->slot);
+  dfree(b->ipos);
   dfree(b->emap);
   delete b;
 }

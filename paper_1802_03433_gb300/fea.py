@@ -73,6 +73,8 @@ def lib() -> C.CDLL:
                                   C.POINTER(fea_quadrature), _vp, _vp, _vp, _vp, _vp],
         "fea_profile_enable": [_vp, C.c_int32],
         "fea_profile_last": [_vp, C.POINTER(C.c_float), C.POINTER(C.c_float)],
+        "fea_diag_sinpi": [_vp, C.c_int64, _vp, _vp, _vp],
+        "fea_diag_fp64_rate": [C.POINTER(C.c_double), _vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -181,6 +183,21 @@ def fea_profile_last(h):
     a, b = C.c_float(), C.c_float()
     _check(lib().fea_profile_last(h, C.byref(a), C.byref(b)), "fea_profile_last")
     return a.value, b.value
+
+
+def fea_diag_sinpi(x, stream=None):
+    """(kernel helper sin(pi x), CUDA sinpi(x)) for a CUDA float64 tensor x."""
+    _dev(x, torch.float64, "x")
+    mine, ref = torch.empty_like(x), torch.empty_like(x)
+    _check(lib().fea_diag_sinpi(_ptr(x), x.numel(), _ptr(mine), _ptr(ref), _stream(stream)), "fea_diag_sinpi")
+    return mine, ref
+
+
+def fea_diag_fp64_rate(stream=None):
+    """Sustained FP64 FMA throughput of the current device (flop/s)."""
+    r = C.c_double()
+    _check(lib().fea_diag_fp64_rate(C.byref(r), _stream(stream)), "fea_diag_fp64_rate")
+    return r.value
 
 
 # ---------------------------------------------------------------- convenience wrapper

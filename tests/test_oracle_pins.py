@@ -492,3 +492,27 @@ def test_grad_matches_central_differences(order):
             cm[c, node] -= h
             fd = (L(cp, s["kappa"]) - L(cm, s["kappa"])) / (2 * h)
             assert abs(fd - gx[c, node]) < 1e-5 * max(1.0, abs(gx[c, node]))
+
+
+@pytest.mark.parametrize("order,kind", [(1, "diffusion"), (2, "diffusion"), (1, "elasticity")])
+def test_rows_routine_matches_full_assembly(order, kind):
+    # the brute-force row assembly used for full-size sampled checks agrees
+    # with the pinned full assembly, entry by entry, pattern included
+    coords, tets, rng = mg.make_cube(3, 0.2, 31)
+    E = tets.shape[1]
+    edof, nsd = oracle.dof_table(order, coords.shape[1], tets)
+    ndpn = 3 if kind == "elasticity" else 1
+    rp, ci = oracle.pattern(nsd, edof, ndpn=ndpn)
+    if kind == "elasticity":
+        lam, mu = mg.lame(rng, E)
+        kw = dict(kind="elasticity", lam=lam, mu=mu, f_kind="const", f_param=(0, 0, -1), npts=4)
+    else:
+        kw = dict(mass=0.7, kappa=mg.lognormal(rng, E), npts=11 if order == 2 else 4)
+    vals, rhs, _ = oracle.assemble(coords, tets, order, edof, rp, ci, **kw)
+    rows = np.arange(0, rp.size - 1, 7)
+    ref, rr = oracle.rows(coords, tets, order, edof, rows, **kw)
+    for r in rows:
+        cols, v = ref[int(r)]
+        np.testing.assert_array_equal(cols, ci[rp[r]:rp[r + 1]])
+        np.testing.assert_allclose(v, vals[rp[r]:rp[r + 1]], rtol=0, atol=1e-15 * max(1, np.abs(v).max()))
+        assert abs(rr[int(r)] - rhs[r]) <= 1e-15 * max(1.0, abs(rhs[r]))
