@@ -1,9 +1,307 @@
-// Reverse mode of the scalar assembly (written below).
+// Reverse mode of the scalar assembly (P1/P2, -div(kappa grad u) + m u = f).
+//
+// For a scalar loss L with G = dL/dvalues (on the CSR pattern) and
+// g = dL/drhs, each element contributes, through its own local matrix and
+// load vector (Eq. 2-3: A and b are sums of element terms),
+//   L_e = kappa |T| S + m |T| sM + |T| sF,
+//   S  = sum_{i<=j} Hc_ij (grad lambda_i . grad lambda_j),
+//        Hc = the element's G entries folded through the stiffness reference
+//        tensor (Hc = G for P1),
+//   sM = sum_ab G_ab Mref_ab,   sF = sum_q w_q f(x_q) Phi_q,
+//   Phi_q = sum_a g_a phi_a(x_q).
+// Hand-derived gradients (one thread per element, local matrices recomputed,
+// never stored):
+//   dL/dkappa_e = |T| S;
+//   dL/dx_c = |T| [ (sigma I - kappa Q) grad lambda_c
+//                   + sum_q w_q Phi_q lambda_c(x_q) grad f(x_q) ],
+//   sigma = kappa S + m sM + sF,  Q = sum_{i=1..3} grad lambda_i dS_i^T,
+//   dS_i = dS/dgrad lambda_i - dS/dgrad lambda_0,
+// using d|T|/dx_c = |T| grad lambda_c and d(grad lambda_i) = -J^{-T} dJ^T
+// grad lambda_i.  The per-vertex vectors of every element are written to the
+// vertex's incidence slot and summed per node in ascending element order by
+// a second kernel (deterministic, no atomics).
+#include <cuda_runtime.h>
+
+#include "element.cuh"
+#include "gather.cuh"
 #include "internal.cuh"
 
 namespace fea {
-fea_status assemble_backward(fea_mesh*, const fea_form*, const fea_coeffs*, const fea_quadrature*, const double*,
-                             const double*, double*, double*, cudaStream_t) {
-  return fail(FEA_ERR_ARG, "backward not available");
+
+namespace {
+
+struct AdjArgs {
+  const double* x;
+  const double* y;
+  const double* z;
+  const int32_t* tets;   // [4][E]
+  const int32_t* edof;   // [nb][E] scalar dofs
+  const int32_t* ipos;   // [nb][E] incidence index of (e, a)
+  const int32_t* rp;     // scalar CSR row pointer
+  const uint8_t* slot;   // [incidence][SW]
+  int64_t E;
+  const double* kappa;
+  double kappa_const;
+  double mass;
+  double fp0;
+  const double* gv;      // dL/dvalues or NULL
+  const double* gf;      // dL/drhs or NULL
+  double* gk;            // dL/dkappa [E] or NULL
+  double* gxs;           // per-incidence vertex gradients [incidence][4]
+  int* err;
+};
+
+constexpr int ADJ_T = 128;
+
+template <int ORDER, bool MASS, int LOAD, int NPTS>
+__global__ void __launch_bounds__(ADJ_T) k_adjoint(AdjArgs A) {
+  constexpr int NB = ORDER == 1 ? 4 : 10;
+  constexpr int SW = ORDER == 1 ? 4 : 16;
+  const int64_t e = (int64_t)blockIdx.x * ADJ_T + threadIdx.x;
+  if (e >= A.E) return;
+  double X[4][3];
+  {
+    int32_t v[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) v[a] = __ldg(A.tets + a * A.E + e);
+    load_vertices(A.x, A.y, A.z, v, X);
+  }
+  Geo geo;
+  geometry(X, geo);
+  if (!(geo.det > 0.0)) atomicOr(A.err, DEV_ERR_DEGENERATE);
+  const double inv = 1.0 / geo.det;
+  const double vol = fabs(geo.det) * (1.0 / 6.0);
+  double g[4][3];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) g[a][k] = geo.c[a][k] * inv;
+  const double kap = A.kappa ? __ldg(A.kappa + e) : A.kappa_const;
+
+  int32_t pos[NB];
+#pragma unroll
+  for (int a = 0; a < NB; ++a) pos[a] = __ldg(A.ipos + a * A.E + e);
+
+  // ---- G entries of this element: Gs_ab = G_ab + G_ba (a < b), G_aa
+  double Hc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) Hc[i][j] = 0.0;
+  double sM = 0.0;
+  if (A.gv) {
+    double Gm[NB][NB];
+#pragma unroll
+    for (int a = 0; a < NB; ++a) {
+      const int32_t row = __ldg(A.edof + a * A.E + e);
+      const int32_t base = __ldg(A.rp + row);
+      int s[NB];
+      load_slots<NB>(A.slot, pos[a], s);
+#pragma unroll
+      for (int b = 0; b < NB; ++b) Gm[a][b] = __ldg(A.gv + base + s[b]);
+    }
+    if constexpr (ORDER == 1) {
+      static_for<10>([&](auto K) {
+        constexpr int a = upper_a(4, K), b = upper_b(4, K);
+        const double gs = a == b ? Gm[a][a] : Gm[a][b] + Gm[b][a];
+        Hc[a][b] += gs;
+        if constexpr (MASS) sM = fma(gs, (a == b ? 2.0 : 1.0) / 20.0, sM);
+      });
+    } else {
+      static_for<55>([&](auto K) {
+        constexpr int a = upper_a(10, K), b = upper_b(10, K);
+        constexpr Terms t = p2_terms(a, b);
+        const double gs = a == b ? Gm[a][a] : Gm[a][b] + Gm[b][a];
+        Hc[t.i[0]][t.j[0]] = fma(gs, t.num[0] / 20.0, Hc[t.i[0]][t.j[0]]);
+        if constexpr (t.n > 1) Hc[t.i[1]][t.j[1]] = fma(gs, t.num[1] / 20.0, Hc[t.i[1]][t.j[1]]);
+        if constexpr (t.n > 2) Hc[t.i[2]][t.j[2]] = fma(gs, t.num[2] / 20.0, Hc[t.i[2]][t.j[2]]);
+        if constexpr (t.n > 3) Hc[t.i[3]][t.j[3]] = fma(gs, t.num[3] / 20.0, Hc[t.i[3]][t.j[3]]);
+        if constexpr (MASS) sM = fma(gs, p2_mass420(a, b) / 420.0, sM);
+      });
+    }
+  }
+  // S = sum_{i<=j} Hc_ij g_i . g_j;  dS/dg_a = sum_j Hsym_aj g_j (Hsym = Hc + Hc^T)
+  double S = 0.0;
+  double dS[4][3];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) dS[a][k] = 0.0;
+  static_for<10>([&](auto K) {
+    constexpr int i = upper_a(4, K), j = upper_b(4, K);
+    const double h = Hc[i][j];
+    S = fma(h, g[i][0] * g[j][0] + g[i][1] * g[j][1] + g[i][2] * g[j][2], S);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      if constexpr (i == j) {
+        dS[i][k] = fma(2.0 * h, g[i][k], dS[i][k]);
+      } else {
+        dS[i][k] = fma(h, g[j][k], dS[i][k]);
+        dS[j][k] = fma(h, g[i][k], dS[j][k]);
+      }
+    }
+  });
+  // Q = sum_{i=1..3} g_i (dS_i - dS_0)^T
+  double Q[3][3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double q = 0.0;
+#pragma unroll
+      for (int i = 1; i < 4; ++i) q = fma(g[i][r], dS[i][c] - dS[0][c], q);
+      Q[r][c] = q;
+    }
+
+  // ---- load terms
+  double sF = 0.0;
+  double lg[4][3];  // sum_q w_q Phi_q lambda_c(x_q) grad f(x_q), per vertex c
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) lg[c][k] = 0.0;
+  if constexpr (LOAD != LOAD_NONE) {
+    if (A.gf) {
+      double gfl[NB];
+#pragma unroll
+      for (int a = 0; a < NB; ++a) gfl[a] = __ldg(A.gf + __ldg(A.edof + a * A.E + e));
+      static_for<NPTS>([&](auto Qi) {
+        constexpr int q = Qi;
+        double Phi = 0.0;
+        static_for<NB>([&](auto Aa) {
+          constexpr double ph = phi_at(ORDER, NPTS, q, Aa);
+          Phi = fma(ph, gfl[Aa], Phi);
+        });
+        const double wPhi = weight(NPTS, q) * Phi;
+        if constexpr (LOAD == LOAD_CONST) {
+          sF = fma(A.fp0, wPhi, sF);
+        } else {
+          double xq[3], sn[3], cs[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            double v = 0.0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v = fma(bary(NPTS, q, c), X[c][k], v);
+            xq[k] = v;
+            sn[k] = sinpi_fp64(v);
+            cs[k] = sinpi_fp64(v + 0.5);
+          }
+          const double f = A.fp0 * sn[0] * sn[1] * sn[2];
+          sF = fma(f, wPhi, sF);
+          const double pw = A.fp0 * 3.14159265358979323846 * wPhi;
+          const double df[3] = {pw * cs[0] * sn[1] * sn[2], pw * sn[0] * cs[1] * sn[2], pw * sn[0] * sn[1] * cs[2]};
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) lg[c][k] = fma(bary(NPTS, q, c), df[k], lg[c][k]);
+        }
+      });
+    }
+  }
+
+  if (A.gk) A.gk[e] = vol * S;
+  const double sigma = kap * S + (MASS ? A.mass * sM : 0.0) + sF;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    double d[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double qg = Q[k][0] * g[c][0] + Q[k][1] * g[c][1] + Q[k][2] * g[c][2];
+      d[k] = vol * (sigma * g[c][k] - kap * qg + lg[c][k]);
+    }
+    double2* out = reinterpret_cast<double2*>(A.gxs + (int64_t)pos[c] * 4);
+    out[0] = make_double2(d[0], d[1]);
+    out[1] = make_double2(d[2], 0.0);
+  }
 }
+
+// dL/dx per node: the node's incidence slots summed in element order.
+__global__ void k_node_grad(int64_t N, const int32_t* __restrict__ inc_ptr, const double* __restrict__ gxs,
+                            double* __restrict__ gx) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  for (int32_t i = __ldg(inc_ptr + n); i < __ldg(inc_ptr + n + 1); ++i) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(gxs + (int64_t)i * 4));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(gxs + (int64_t)i * 4) + 1);
+    s0 += a.x;
+    s1 += a.y;
+    s2 += b.x;
+  }
+  gx[n] = s0;
+  gx[N + n] = s1;
+  gx[2 * N + n] = s2;
+}
+
+template <int ORDER, bool MASS>
+struct AdjLauncher {
+  template <int LOAD, int NPTS>
+  static void go(const AdjArgs& A, cudaStream_t s) {
+    k_adjoint<ORDER, MASS, LOAD, NPTS><<<(unsigned)((A.E + ADJ_T - 1) / ADJ_T), ADJ_T, 0, s>>>(A);
+  }
+  template <int NPTS>
+  static void by_load(const AdjArgs& A, int load, cudaStream_t s) {
+    if (load == LOAD_CONST) go<LOAD_CONST, NPTS>(A, s);
+    else go<LOAD_SIN, NPTS>(A, s);
+  }
+  static void run(const AdjArgs& A, int load, int npts, cudaStream_t s) {
+    if (load == LOAD_NONE) go<LOAD_NONE, 1>(A, s);
+    else if (npts == 1) by_load<1>(A, load, s);
+    else if (npts == 4) by_load<4>(A, load, s);
+    else by_load<11>(A, load, s);
+  }
+};
+
+}  // namespace
+
+fea_status assemble_backward(fea_mesh* m, const fea_form* form, const fea_coeffs* co, const fea_quadrature* q,
+                             const double* gv, const double* gf, double* gk, double* gx, cudaStream_t s) {
+  const int order = form->order;
+  Base* B = m->base[order];
+  if (!B || !m->pat[order][1]) return fail(FEA_ERR_STATE, "fea_assemble_backward: build the pattern first");
+  const int64_t E = m->n_elems, N = m->n_nodes;
+  if (!gk && !gx) return FEA_OK;
+  if (E == 0) {
+    if (gx) FEA_CUDA(cudaMemsetAsync(gx, 0, 3 * N * sizeof(double), s));
+    return FEA_OK;
+  }
+  FEA_TRY(ensure_scratch(m->gxs, (size_t)E * B->nb * 4 * sizeof(double)));
+  AdjArgs A{};
+  A.x = m->x;
+  A.y = m->y;
+  A.z = m->z;
+  A.tets = m->tets;
+  A.edof = B->edof;
+  A.ipos = B->ipos;
+  A.rp = B->rp;
+  A.slot = B->slot;
+  A.E = E;
+  A.kappa = co->kappa;
+  A.kappa_const = co->kappa_const;
+  A.mass = form->mass_coef;
+  A.fp0 = co->f_param[0];
+  A.gv = gv;
+  A.gf = gf;
+  A.gk = gk;
+  A.gxs = static_cast<double*>(m->gxs.ptr);
+  A.err = m->err;
+  const bool mass = form->kind == FEA_DIFFUSION_MASS && form->mass_coef != 0.0;
+  const int load = co->f_kind;
+  if (order == 1) {
+    if (mass) AdjLauncher<1, true>::run(A, load, q->npts, s);
+    else AdjLauncher<1, false>::run(A, load, q->npts, s);
+  } else {
+    if (mass) AdjLauncher<2, true>::run(A, load, q->npts, s);
+    else AdjLauncher<2, false>::run(A, load, q->npts, s);
+  }
+  FEA_CUDA(cudaGetLastError());
+  if (gx) {
+    // vertex dofs are the node ids in both numberings, so the first N rows of
+    // the order's incidence lists are the node lists
+    k_node_grad<<<(unsigned)((N + 127) / 128), 128, 0, s>>>(N, B->inc_ptr, A.gxs, gx);
+    FEA_CUDA(cudaGetLastError());
+  }
+  return FEA_OK;
+}
+
 }  // namespace fea

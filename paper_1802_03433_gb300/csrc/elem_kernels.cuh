@@ -111,10 +111,8 @@ __device__ __forceinline__ void vertices_r(const double X[4][3], R Xr[4][3]) {
 // ---------------------------------------------------------------- scalar forms
 // -div(kappa grad u) [+ mass u] on P1 (ORDER 1) or P2 (ORDER 2) tets.
 template <int ORDER, bool MASS, int LOAD, int NPTS, typename R>
-__global__ void __launch_bounds__(ELEM_T) k_elem_scalar(ElemArgs A) {
+__device__ __forceinline__ void elem_scalar_body(const ElemArgs& A, int64_t e) {
   constexpr int NB = ORDER == 1 ? 4 : 10;
-  const int64_t e = (int64_t)blockIdx.x * ELEM_T + threadIdx.x;
-  if (e >= A.E) return;
   double X[4][3];
   load_element(A, e, X);
   Geo g;
@@ -175,6 +173,12 @@ __global__ void __launch_bounds__(ELEM_T) k_elem_scalar(ElemArgs A) {
 #pragma unroll
     for (int a = 0; a < NB; ++a) Fl[pos[a]] = amp * Fs[a];
   }
+}
+
+template <int ORDER, bool MASS, int LOAD, int NPTS, typename R>
+__global__ void __launch_bounds__(ELEM_T) k_elem_scalar(ElemArgs A) {
+  const int64_t e = (int64_t)blockIdx.x * ELEM_T + threadIdx.x;
+  if (e < A.E) elem_scalar_body<ORDER, MASS, LOAD, NPTS, R>(A, e);
 }
 
 // ---------------------------------------------------------------- elasticity

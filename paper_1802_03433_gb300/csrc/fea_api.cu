@@ -159,6 +159,7 @@ fea_status fea_mesh_destroy(fea_mesh* m) {
     if (m->ev[i]) cudaEventDestroy(m->ev[i]);
   if (m->lm.ptr) cudaFree(m->lm.ptr);
   if (m->fl.ptr) cudaFree(m->fl.ptr);
+  if (m->gxs.ptr) cudaFree(m->gxs.ptr);
   if (m->tets) cudaFree(m->tets);
   if (m->err) cudaFree(m->err);
   delete m;

@@ -159,17 +159,15 @@ struct Contrib {
 // before the current pair is added (software pipeline), so one pair's memory
 // latency overlaps the other pair's shared-memory adds.
 template <int NB, int NDPN, typename LT>
-__global__ void __launch_bounds__(128) k_gather(GatherArgs G) {
-  extern __shared__ double acc[];
-  const int rows = blockDim.x;
-  const int64_t r0 = (int64_t)blockIdx.x * rows;
+__device__ __forceinline__ void gather_tile(const GatherArgs& G, int64_t tile, int rows, double* acc) {
+  const int64_t r0 = tile * rows;
   const int64_t r1 = r0 + rows < G.ndof ? r0 + rows : G.ndof;
   const int32_t base = __ldg(G.row_ptr + r0);
   const int32_t span = __ldg(G.row_ptr + r1) - base;
-  for (int k = threadIdx.x; k < span; k += rows) acc[k] = 0.0;
+  for (int k = threadIdx.x; k < span; k += blockDim.x) acc[k] = 0.0;
   __syncthreads();
   const int64_t r = r0 + threadIdx.x;
-  if (r < r1) {
+  if (threadIdx.x < rows && r < r1) {
     const int64_t node = r / NDPN;
     const int comp = (int)(r - node * NDPN);
     double* __restrict__ a = acc + (__ldg(G.row_ptr + r) - base);
@@ -195,7 +193,13 @@ __global__ void __launch_bounds__(128) k_gather(GatherArgs G) {
     if (G.rhs) G.rhs[r] = f;
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < span; k += rows) G.values[base + k] = acc[k];
+  for (int k = threadIdx.x; k < span; k += blockDim.x) G.values[base + k] = acc[k];
+}
+
+template <int NB, int NDPN, typename LT>
+__global__ void __launch_bounds__(128) k_gather(GatherArgs G) {
+  extern __shared__ double acc[];
+  gather_tile<NB, NDPN, LT>(G, blockIdx.x, blockDim.x, acc);
 }
 
 fea_status launch_gather(int nb, int ndpn, bool mixed, const GatherArgs& G, int rows_per_tile,

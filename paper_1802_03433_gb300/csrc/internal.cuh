@@ -91,6 +91,7 @@ struct fea_mesh {
   fea::Base* base[3] = {nullptr, nullptr, nullptr};          // by order
   fea::Pattern* pat[3][4] = {{nullptr}};                     // by order, ndpn
   fea::Scratch lm, fl;      // local matrices / local loads of the last assembly
+  fea::Scratch gxs;         // per-incidence vertex gradients of the last backward
   bool profile = false;     // record phase events in fea_assemble
   bool profiled = false;    // events of a call are pending
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
