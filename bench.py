@@ -230,6 +230,13 @@ def run_ours(args):
                           "elem_ms": statistics.mean(p[0] for p in m_phase),
                           "scatter_ms": statistics.mean(p[1] for p in m_phase)}
 
+    if not args.no_forms:
+        small = max(3, args.steps // 4)
+        forms["batched"] = bench_batched(fea, torch, dev, small, args.warmup, flush)
+        forms["adjoint"] = bench_adjoint(fea, torch, dev, small, args.warmup, flush)
+        forms["elasticity_128"] = bench_plain(fea, torch, dev, "elasticity", 128, small, args.warmup, flush)
+        forms["p1_kappa_96"] = bench_plain(fea, torch, dev, "p1_kappa", 96, small, args.warmup, flush)
+
     # end to end through the public API with host buffers: H2D of the step's
     # inputs (coordinates, coefficients) from pinned memory, assembly, D2H of
     # the assembled values and load vector
@@ -331,6 +338,151 @@ def _hbm_peak():
             return float(json.load(f)["hbm_gbs"])
     except Exception:
         return 6800.0  # fallback copy bandwidth
+
+
+# ---------------------------------------------------------------- other forms
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def bench_batched(fea, torch, dev, steps, warmup, flush):
+    """256 uneven meshes (n ~ U{4..32}, half P1 / half P2 Poisson, log-normal
+    kappa): one CUDA-graph launch (autotuned) vs one fea_assemble per mesh."""
+    specs = mg.batch()
+    meshes, forms, quads, coeffs, keep = [], [], [], [], []
+    for d in specs:
+        m = fea.Mesh(d["coords"], d["tets"], device=dev)
+        kap = torch.as_tensor(d["kappa"], device=dev)
+        keep.append(kap)
+        meshes.append(m)
+        forms.append(fea.make_form(fea.FEA_POISSON, d["order"]))
+        quads.append(fea.make_quadrature(d["npts"], fea.FEA_FP64))
+        coeffs.append(fea.make_coeffs(kappa=kap, f_kind=fea.FEA_LOAD_SINPROD, f_param=(d["f_amp"],)))
+    E = sum(d["tets"].shape[1] for d in specs)
+    b = fea.Batch(meshes, forms, quads, coeffs, fea.FEA_LOAD_SINPROD)
+    params = b.tune()
+    outs = [(b.values[k], b.rhs[k]) for k in range(len(meshes))]
+
+    def graph_step():
+        b.assemble()
+
+    def separate_step():
+        for m, f, q, c, (v, r) in zip(meshes, forms, quads, coeffs, outs):
+            fea.fea_assemble(m.h, f, c, q, v, r)
+
+    res = {}
+    for name, fn in (("graph", graph_step), ("separate", separate_step)):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for k in range(steps):
+            flush.fill_(k)
+            a, c = _events(torch)
+            a.record()
+            fn()
+            c.record()
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(c)
+        res[name] = tot / steps
+    for m in meshes:
+        m.check()
+    b.close()
+    for m in meshes:
+        m.close()
+    return {"value": E / (res["graph"] / 1e3), "unit": "elements/s", "ms_per_step": res["graph"],
+            "separate_value": E / (res["separate"] / 1e3), "separate_ms_per_step": res["separate"],
+            "launches": {"graph": 1, "separate": 2 * len(specs)},
+            "tuned": {"elements_per_item": params[0], "element_ctas": params[1], "scatter_ctas": params[2]},
+            "meshes": len(specs), "elements": E,
+            "config": "256 Kuhn cubes, n ~ U{4..32} (seed 0), even P1 (4-pt) / odd P2 (11-pt) Poisson, "
+                      "log-normal kappa, sin load, FP64"}
+
+
+def bench_adjoint(fea, torch, dev, steps, warmup, flush):
+    """P1 kappa-diffusion on the 96^3 mesh: forward assembly and the adjoint
+    (dL/dkappa, dL/dx for L = v^T K w + g^T f)."""
+    d = mg.adjoint_p1(96)
+    m = fea.Mesh(d["coords"], d["tets"], device=dev)
+    ndof, nnz = m.pattern(1)
+    rp, ci = m.pattern_tensors(1)
+    rows = torch.repeat_interleave(torch.arange(ndof, device=dev), torch.diff(rp.long()))
+    v, w, g = (torch.as_tensor(d[k], device=dev) for k in ("v", "w", "g"))
+    gV = v[rows] * w[ci.long()]
+    kap = torch.as_tensor(d["kappa"], device=dev)
+    form = fea.make_form(fea.FEA_POISSON, 1)
+    co = fea.make_coeffs(kappa=kap, f_kind=fea.FEA_LOAD_SINPROD, f_param=(mg.SIN_AMP,))
+    q = fea.make_quadrature(4, fea.FEA_FP64)
+    E, N = d["tets"].shape[1], d["coords"].shape[1]
+    vals = torch.empty(nnz, dtype=torch.float64, device=dev)
+    rhs = torch.empty(ndof, dtype=torch.float64, device=dev)
+    gk = torch.empty(E, dtype=torch.float64, device=dev)
+    gx = torch.empty((3, N), dtype=torch.float64, device=dev)
+    res = {}
+    for name, fn in (("forward", lambda: fea.fea_assemble(m.h, form, co, q, vals, rhs)),
+                     ("backward", lambda: fea.fea_assemble_backward(m.h, form, co, q, gV, g, gk, gx))):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for k in range(steps):
+            flush.fill_(k)
+            a, c = _events(torch)
+            a.record()
+            fn()
+            c.record()
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(c)
+        res[name] = tot / steps
+    m.check()
+    m.close()
+    return {"value": E / (res["backward"] / 1e3), "unit": "elements/s (backward)",
+            "backward_ms": res["backward"], "forward_ms": res["forward"],
+            "forward_value": E / (res["forward"] / 1e3), "elements": E,
+            "config": "P1 kappa-diffusion, 96^3 Kuhn cube (5,308,416 tets), 4-pt sin load, FP64"}
+
+
+def bench_plain(fea, torch, dev, kind, n, steps, warmup, flush):
+    """FP64 and mixed assembly of one more workload (elements/s each)."""
+    d = make_inputs(kind, n, seed=0)
+    m = fea.Mesh(d["coords"], d["tets"], device=dev)
+    ndof, nnz = m.pattern(d["order"], d["ndpn"])
+    keep = []
+    if d["form"] == 2:
+        lam, mu = torch.as_tensor(d["lam"], device=dev), torch.as_tensor(d["mu"], device=dev)
+        keep += [lam, mu]
+        co = fea.make_coeffs(lam=lam, mu=mu, f_kind=d["f_kind"], f_param=d["f_param"])
+    else:
+        kap = None if d["kappa"] is None else torch.as_tensor(d["kappa"], device=dev)
+        keep.append(kap)
+        co = fea.make_coeffs(kappa=kap, f_kind=d["f_kind"], f_param=d["f_param"])
+    form = fea.make_form(d["form"], d["order"], d["mass"])
+    vals = torch.empty(nnz, dtype=torch.float64, device=dev)
+    rhs = torch.empty(ndof, dtype=torch.float64, device=dev)
+    fea.fea_profile_enable(m.h, True)
+    E = d["tets"].shape[1]
+    out = {"elements": E}
+    for name, prec in (("fp64", fea.FEA_FP64), ("mixed", fea.FEA_MIXED)):
+        q = fea.make_quadrature(d["npts"], prec)
+        for _ in range(warmup):
+            fea.fea_assemble(m.h, form, co, q, vals, rhs)
+        torch.cuda.synchronize()
+        tot, pe, ps = 0.0, 0.0, 0.0
+        for k in range(steps):
+            flush.fill_(k)
+            a, c = _events(torch)
+            a.record()
+            fea.fea_assemble(m.h, form, co, q, vals, rhs)
+            c.record()
+            e_ms, s_ms = fea.fea_profile_last(m.h)
+            tot += a.elapsed_time(c)
+            pe += e_ms
+            ps += s_ms
+        out[name] = {"value": E / (tot / steps / 1e3), "ms_per_step": tot / steps, "elem_ms": pe / steps,
+                     "scatter_ms": ps / steps}
+    m.check()
+    m.close()
+    return out
 
 
 # ---------------------------------------------------------------- CPU oracle

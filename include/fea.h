@@ -177,6 +177,45 @@ fea_status fea_assemble_backward(fea_mesh* mesh, const fea_form* form, const fea
                                  const double* grad_rhs, double* grad_kappa, double* grad_x,
                                  void* stream);
 
+/* ---- Batched assembly of many independent meshes (no counterpart in the
+ * paper; it batches the per-mesh work of Eq. 3 / Algorithm 1).
+ *
+ * Create a batch over n mesh handles (which stay owned by the caller and
+ * must outlive the batch).  forms[k], quads[k] give mesh k's scalar form
+ * (FEA_POISSON or FEA_DIFFUSION_MASS, P1 or P2, FP64); every P1 mesh must use
+ * the same rule and every P2 mesh the same rule, with (P1, P2) rules in
+ * {(4, 11), (11, 11), (4, 4)}; f_kind is the load kind shared by all meshes.
+ * Builds each mesh's pattern if needed and allocates the batch's scratch.
+ * Synchronises. */
+fea_status fea_batch_create(fea_mesh* const* meshes, int32_t n, const fea_form* forms,
+                            const fea_quadrature* quads, int32_t f_kind, void* stream,
+                            fea_batch** out);
+
+/* Bind per-mesh coefficients and outputs.  coeffs: host array [n] (kappa
+ * pointers are device arrays); values, rhs: HOST arrays [n] of DEVICE
+ * pointers ([nnz_k] and [ndof_k] doubles; rhs may be NULL, or hold NULL
+ * entries, to skip loads).  Copies the descriptors to the device;
+ * synchronises.  The bound pointers are used by every later
+ * fea_batch_assemble until the next bind. */
+fea_status fea_batch_bind(fea_batch* batch, const fea_coeffs* coeffs, double* const* values,
+                          double* const* rhs);
+
+/* Assemble every mesh of the batch: one launch of an internal CUDA graph
+ * holding one persistent element kernel and one persistent scatter kernel
+ * over all meshes.  Asynchronous on `stream`; allocates nothing.  Each
+ * mesh's values and rhs are bitwise those of fea_assemble. */
+fea_status fea_batch_assemble(fea_batch* batch, void* stream);
+
+/* Autotune the batch's launch: times candidate (elements per work item,
+ * persistent element-kernel CTAs) pairs on the device, keeps the fastest and
+ * rebuilds the graph.  params (may be NULL) receives the chosen elements per
+ * item, element-kernel CTAs and the scatter CTA count (one per row tile).
+ * Synchronises; overwrites the bound outputs. */
+fea_status fea_batch_tune(fea_batch* batch, void* stream, int32_t* params);
+
+/* Release the batch (not the meshes).  Synchronises the device. */
+fea_status fea_batch_destroy(fea_batch* batch);
+
 /* Measurement hooks (no counterpart in the paper; used by the benchmark).
  * When enabled, every fea_assemble on this mesh records CUDA events on its
  * stream before the element kernel, between the element kernel and the

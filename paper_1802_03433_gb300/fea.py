@@ -75,6 +75,12 @@ def lib() -> C.CDLL:
         "fea_profile_last": [_vp, C.POINTER(C.c_float), C.POINTER(C.c_float)],
         "fea_diag_sinpi": [_vp, C.c_int64, _vp, _vp, _vp],
         "fea_diag_fp64_rate": [C.POINTER(C.c_double), _vp],
+        "fea_batch_create": [C.POINTER(_vp), C.c_int32, C.POINTER(fea_form), C.POINTER(fea_quadrature),
+                             C.c_int32, _vp, C.POINTER(_vp)],
+        "fea_batch_bind": [_vp, C.POINTER(fea_coeffs), C.POINTER(_vp), C.POINTER(_vp)],
+        "fea_batch_assemble": [_vp, _vp],
+        "fea_batch_tune": [_vp, _vp, C.POINTER(C.c_int32)],
+        "fea_batch_destroy": [_vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -198,6 +204,73 @@ def fea_diag_fp64_rate(stream=None):
     r = C.c_double()
     _check(lib().fea_diag_fp64_rate(C.byref(r), _stream(stream)), "fea_diag_fp64_rate")
     return r.value
+
+
+def fea_batch_create(meshes, forms, quads, f_kind, stream=None):
+    n = len(meshes)
+    hs = (_vp * n)(*[m.h.value if hasattr(m, "h") else m.value for m in meshes])
+    fs = (fea_form * n)(*forms)
+    qs = (fea_quadrature * n)(*quads)
+    out = _vp()
+    _check(lib().fea_batch_create(hs, n, fs, qs, f_kind, _stream(stream), C.byref(out)), "fea_batch_create")
+    return out
+
+
+def fea_batch_bind(b, coeffs, values, rhs=None):
+    n = len(values)
+    cs = (fea_coeffs * n)(*coeffs)
+    vs = (_vp * n)(*[v.data_ptr() for v in values])
+    rs = None if rhs is None else (_vp * n)(*[0 if r is None else r.data_ptr() for r in rhs])
+    _check(lib().fea_batch_bind(b, cs, vs, rs), "fea_batch_bind")
+
+
+def fea_batch_assemble(b, stream=None):
+    _check(lib().fea_batch_assemble(b, _stream(stream)), "fea_batch_assemble")
+
+
+def fea_batch_tune(b, stream=None):
+    p = (C.c_int32 * 3)()
+    _check(lib().fea_batch_tune(b, _stream(stream), p), "fea_batch_tune")
+    return tuple(p)
+
+
+def fea_batch_destroy(b):
+    _check(lib().fea_batch_destroy(b), "fea_batch_destroy")
+
+
+class Batch:
+    """Many meshes assembled by one CUDA-graph launch (fea_batch_*).
+
+    meshes: list of Mesh; forms/quads: per mesh; coeffs: per-mesh fea_coeffs.
+    Owns the output tensors values[k], rhs[k]."""
+
+    def __init__(self, meshes, forms, quads, coeffs, f_kind, with_rhs=True, stream=None):
+        self.meshes = meshes
+        self.h = fea_batch_create(meshes, forms, quads, f_kind, stream)
+        self.values, self.rhs = [], []
+        for m, f in zip(meshes, forms):
+            ndof, nnz = m.pattern(f.order, 1)
+            self.values.append(torch.empty(max(nnz, 1), dtype=torch.float64, device=m.x.device))
+            self.rhs.append(torch.empty(ndof, dtype=torch.float64, device=m.x.device) if with_rhs else None)
+        self.coeffs = coeffs
+        fea_batch_bind(self.h, coeffs, self.values, self.rhs if with_rhs else None)
+
+    def tune(self, stream=None):
+        return fea_batch_tune(self.h, stream)
+
+    def assemble(self, stream=None):
+        fea_batch_assemble(self.h, stream)
+
+    def close(self):
+        if self.h is not None:
+            fea_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------- convenience wrapper
