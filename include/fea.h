@@ -164,6 +164,28 @@ fea_status fea_dof_table_copy(fea_mesh* mesh, int32_t order, int32_t* edof, void
 fea_status fea_assemble(fea_mesh* mesh, const fea_form* form, const fea_coeffs* coeffs,
                         const fea_quadrature* quad, double* values, double* rhs, void* stream);
 
+/* fea_assemble without any device allocation (the paper has no counterpart;
+ * this is a deployment variant).  For callers that cannot let a library
+ * call cudaMalloc - a process whose device memory is reserved by another
+ * allocator, or a latency-critical loop that cannot afford the device
+ * synchronisation cudaMalloc/cudaFree imply.  Same arguments, kernels and
+ * results as fea_assemble, but the per-call scratch (local rows and local
+ * loads) lives in one fixed 32 MiB device array inside the library instead
+ * of the mesh handle: about 200 K P1 scalar elements, 32 K P2 elements or
+ * 25 K P1 elasticity elements in FP64.  Larger meshes are rejected with
+ * FEA_ERR_ARG before anything runs.
+ *  - The array is held by every device that loads the library until the
+ *    process exits.  Its device address is looked up (cudaGetSymbolAddress)
+ *    on the first call on each device, with that device current; make that
+ *    first call before any stream capture.
+ *  - Every call shares the array and it keeps the last call's contents;
+ *    nothing in it needs clearing (every value is written before it is read).
+ *    Calls whose kernels overlap on the GPU (other streams, other threads)
+ *    race on it: serialise them.
+ *  - The pattern must have been built with fea_pattern beforehand. */
+fea_status fea_assemble_noalloc(fea_mesh* mesh, const fea_form* form, const fea_coeffs* coeffs,
+                                const fea_quadrature* quad, double* values, double* rhs, void* stream);
+
 /* Reverse mode of fea_assemble for the scalar forms (FEA_POISSON,
  * FEA_DIFFUSION_MASS; P1 or P2; FP64).  For a scalar loss L with
  * grad_values = dL/dvalues [nnz] and grad_rhs = dL/drhs [ndof] (either may be

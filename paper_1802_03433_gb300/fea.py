@@ -69,6 +69,8 @@ def lib() -> C.CDLL:
         "fea_dof_table_copy": [_vp, C.c_int32, _vp, _vp],
         "fea_assemble": [_vp, C.POINTER(fea_form), C.POINTER(fea_coeffs), C.POINTER(fea_quadrature),
                          _vp, _vp, _vp],
+        "fea_assemble_noalloc": [_vp, C.POINTER(fea_form), C.POINTER(fea_coeffs), C.POINTER(fea_quadrature),
+                                 _vp, _vp, _vp],
         "fea_assemble_backward": [_vp, C.POINTER(fea_form), C.POINTER(fea_coeffs),
                                   C.POINTER(fea_quadrature), _vp, _vp, _vp, _vp, _vp],
         "fea_profile_enable": [_vp, C.c_int32],
@@ -172,6 +174,13 @@ def make_quadrature(npts=4, prec=FEA_FP64):
 def fea_assemble(h, form, coeffs, quad, values, rhs=None, stream=None):
     _check(lib().fea_assemble(h, C.byref(form), C.byref(coeffs), C.byref(quad), _ptr(values), _ptr(rhs),
                               _stream(stream)), "fea_assemble")
+
+
+def fea_assemble_noalloc(h, form, coeffs, quad, values, rhs=None, stream=None):
+    """fea_assemble with the scratch in the library's fixed device array (the
+    call allocates nothing; meshes above the array's 32 MiB are rejected)."""
+    _check(lib().fea_assemble_noalloc(h, C.byref(form), C.byref(coeffs), C.byref(quad), _ptr(values), _ptr(rhs),
+                                      _stream(stream)), "fea_assemble_noalloc")
 
 
 def fea_assemble_backward(h, form, coeffs, quad, grad_values, grad_rhs, grad_kappa, grad_x, stream=None):
