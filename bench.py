@@ -166,6 +166,7 @@ def run_ours(args):
     N = d["coords"].shape[1]
 
     mesh = fea.Mesh(d["coords"], d["tets"], device=dev)
+    fea.fea_mesh_set_stages(mesh.h, args.stages)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ndof, nnz = mesh.pattern(d["order"], d["ndpn"])
@@ -310,6 +311,7 @@ def run_ours(args):
             cpu = cpu_baseline(d["kind"])
         out = {
             "metric": "elements/s assembled into CSR (plain FP64), with % of HBM roofline and the mixed form",
+            "overlap_stages": args.stages,
             "value": value, "unit": "elements/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -560,6 +562,7 @@ def main():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="p2_diffmass_64", choices=sorted(WORKLOADS))
     p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--stages", type=int, default=1, help="element chunks overlapped with the scatter (1 = none)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-forms", action="store_true")

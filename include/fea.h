@@ -133,6 +133,14 @@ fea_status fea_mesh_create(const double* x, const double* y, const double* z, in
 /* Re-point the referenced coordinate arrays (same n_nodes). */
 fea_status fea_mesh_set_coords(fea_mesh* mesh, const double* x, const double* y, const double* z);
 
+/* Number of consecutive element chunks fea_assemble overlaps with the
+ * scatter (1 to 16; default 1 = element kernel, then scatter kernel).
+ * With k > 1, chunk c's element kernel runs on `stream` while the row tiles
+ * completed by chunks < c are scattered on a stream owned by the handle,
+ * joined back to `stream` before the call's work completes.  Results are
+ * bitwise identical for every setting. */
+fea_status fea_mesh_set_stages(fea_mesh* mesh, int32_t stages);
+
 /* Release the handle and everything it owns.  Synchronises the device. */
 fea_status fea_mesh_destroy(fea_mesh* mesh);
 

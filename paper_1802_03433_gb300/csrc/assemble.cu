@@ -2,6 +2,8 @@
 // scratch) followed by the deterministic row-gather scatter into CSR.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "elem_kernels.cuh"
 #include "gather.cuh"
 
@@ -10,16 +12,22 @@ namespace fea {
 namespace {
 
 template <int NB, int NDPN, typename LT>
-fea_status gather_one(const GatherArgs& G, int rows, int64_t max_tile_nnz, cudaStream_t s) {
+fea_status gather_one(const GatherArgs& G, int rows, int64_t max_tile_nnz, cudaStream_t s, const int32_t* tiles,
+                      int64_t ntiles) {
   const size_t smem = (size_t)max_tile_nnz * sizeof(double);
   static size_t configured = 0;  // opt-in above the 48 KB default, once per instance
   if (smem > 48 * 1024 && smem > configured) {
     FEA_CUDA(cudaFuncSetAttribute(k_gather<NB, NDPN, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FEA_CUDA(cudaFuncSetAttribute(k_gather_list<NB, NDPN, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
     configured = smem;
   }
-  const int64_t tiles = (G.ndof + rows - 1) / rows;
-  if (tiles == 0) return FEA_OK;
-  k_gather<NB, NDPN, LT><<<(unsigned)tiles, rows, smem, s>>>(G);
+  if (tiles) {
+    if (ntiles > 0) k_gather_list<NB, NDPN, LT><<<(unsigned)ntiles, rows, smem, s>>>(G, tiles);
+  } else {
+    const int64_t n = (G.ndof + rows - 1) / rows;
+    if (n > 0) k_gather<NB, NDPN, LT><<<(unsigned)n, rows, smem, s>>>(G);
+  }
   FEA_CUDA(cudaGetLastError());
   return FEA_OK;
 }
@@ -27,16 +35,28 @@ fea_status gather_one(const GatherArgs& G, int rows, int64_t max_tile_nnz, cudaS
 }  // namespace
 
 fea_status launch_gather(int nb, int ndpn, bool mixed, const GatherArgs& G, int rows, int64_t max_tile_nnz,
-                         cudaStream_t s) {
+                         cudaStream_t s, const int32_t* tiles, int64_t ntiles) {
   if (nb == 4 && ndpn == 1)
-    return mixed ? gather_one<4, 1, float>(G, rows, max_tile_nnz, s) : gather_one<4, 1, double>(G, rows, max_tile_nnz, s);
+    return mixed ? gather_one<4, 1, float>(G, rows, max_tile_nnz, s, tiles, ntiles)
+                 : gather_one<4, 1, double>(G, rows, max_tile_nnz, s, tiles, ntiles);
   if (nb == 10 && ndpn == 1)
-    return mixed ? gather_one<10, 1, float>(G, rows, max_tile_nnz, s)
-                 : gather_one<10, 1, double>(G, rows, max_tile_nnz, s);
+    return mixed ? gather_one<10, 1, float>(G, rows, max_tile_nnz, s, tiles, ntiles)
+                 : gather_one<10, 1, double>(G, rows, max_tile_nnz, s, tiles, ntiles);
   if (nb == 4 && ndpn == 3)
-    return mixed ? gather_one<4, 3, float>(G, rows, max_tile_nnz, s) : gather_one<4, 3, double>(G, rows, max_tile_nnz, s);
+    return mixed ? gather_one<4, 3, float>(G, rows, max_tile_nnz, s, tiles, ntiles)
+                 : gather_one<4, 3, double>(G, rows, max_tile_nnz, s, tiles, ntiles);
   return fail(FEA_ERR_ARG, "no scatter for this element / dof layout");
 }
+
+namespace {
+
+fea_status launch_elements(const fea_form* form, const ElemArgs& A, int load, int npts, int prec, cudaStream_t s) {
+  if (form->kind == FEA_ELASTICITY) return launch_elem_elast(A, load, npts, prec, s);
+  const bool mass = form->kind == FEA_DIFFUSION_MASS && form->mass_coef != 0.0;
+  return form->order == 1 ? launch_elem_p1(A, mass, load, npts, prec, s) : launch_elem_p2(A, mass, load, npts, prec, s);
+}
+
+}  // namespace
 
 fea_status assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* co, const fea_quadrature* q,
                     double* values, double* rhs, cudaStream_t s) {
@@ -74,14 +94,6 @@ fea_status assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* co, con
   A.Fl = load != FEA_LOAD_NONE ? m->fl.ptr : nullptr;
   A.err = m->err;
   const int prec = mixed ? FEA_MIXED : FEA_FP64;
-  if (m->profile) FEA_CUDA(cudaEventRecord(m->ev[0], s));
-  if (form->kind == FEA_ELASTICITY) {
-    FEA_TRY(launch_elem_elast(A, load, q->npts, prec, s));
-  } else {
-    const bool mass = form->kind == FEA_DIFFUSION_MASS && form->mass_coef != 0.0;
-    if (order == 1) FEA_TRY(launch_elem_p1(A, mass, load, q->npts, prec, s));
-    else FEA_TRY(launch_elem_p2(A, mass, load, q->npts, prec, s));
-  }
 
   GatherArgs G{};
   G.ndof = P->ndof;
@@ -92,8 +104,41 @@ fea_status assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* co, con
   G.Fl = A.Fl;
   G.values = values;
   G.rhs = rhs;
-  if (m->profile) FEA_CUDA(cudaEventRecord(m->ev[1], s));
-  FEA_TRY(launch_gather(nb, ndpn, mixed, G, P->rows_per_tile, P->max_tile_nnz, s));
+
+  const int stages = std::min(std::max(m->stages, 1), 16);
+  if (stages == 1 || E < (int64_t)stages * ELEM_T) {
+    // one element launch, then one scatter launch
+    A.e0 = 0;
+    A.e1 = E;
+    if (m->profile) FEA_CUDA(cudaEventRecord(m->ev[0], s));
+    FEA_TRY(launch_elements(form, A, load, q->npts, prec, s));
+    if (m->profile) FEA_CUDA(cudaEventRecord(m->ev[1], s));
+    FEA_TRY(launch_gather(nb, ndpn, mixed, G, P->rows_per_tile, P->max_tile_nnz, s));
+  } else {
+    // Overlapped: element chunk k runs on `s`; the row tiles that chunk k
+    // completes are scattered on the side stream while chunk k + 1 computes.
+    FEA_TRY(build_stages(m, P, stages, s));
+    if (!m->side) FEA_CUDA(cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking));
+    for (int k = 0; k <= 16; ++k)
+      if (!m->chunk_ev[k]) FEA_CUDA(cudaEventCreateWithFlags(&m->chunk_ev[k], cudaEventDisableTiming));
+    if (m->profile) FEA_CUDA(cudaEventRecord(m->ev[0], s));
+    // the side stream must not start before the work already queued on s
+    FEA_CUDA(cudaEventRecord(m->chunk_ev[16], s));
+    FEA_CUDA(cudaStreamWaitEvent(m->side, m->chunk_ev[16], 0));
+    for (int k = 0; k < stages; ++k) {
+      A.e0 = std::min<int64_t>(E, (int64_t)k * P->chunk);
+      A.e1 = std::min<int64_t>(E, (int64_t)(k + 1) * P->chunk);
+      FEA_TRY(launch_elements(form, A, load, q->npts, prec, s));
+      FEA_CUDA(cudaEventRecord(m->chunk_ev[k], s));
+      FEA_CUDA(cudaStreamWaitEvent(m->side, m->chunk_ev[k], 0));
+      const int64_t t0 = P->stage_ptr[k], t1 = P->stage_ptr[k + 1];
+      FEA_TRY(launch_gather(nb, ndpn, mixed, G, P->rows_per_tile, P->max_tile_nnz, m->side, P->tile_list + t0,
+                            t1 - t0));
+    }
+    if (m->profile) FEA_CUDA(cudaEventRecord(m->ev[1], s));
+    FEA_CUDA(cudaEventRecord(m->chunk_ev[16], m->side));
+    FEA_CUDA(cudaStreamWaitEvent(s, m->chunk_ev[16], 0));
+  }
   if (m->profile) {
     FEA_CUDA(cudaEventRecord(m->ev[2], s));
     m->profiled = true;

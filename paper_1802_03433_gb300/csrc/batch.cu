@@ -249,6 +249,8 @@ fea_status fea_batch_create(fea_mesh* const* meshes, int32_t n, const fea_form* 
       d.el.z = m->z;
       d.el.tets = m->tets;
       d.el.E = m->n_elems;
+      d.el.e0 = 0;
+      d.el.e1 = m->n_elems;
       d.el.kappa_const = 1.0;
       d.el.mass = forms[k].mass_coef;
       d.el.ipos = B->ipos;

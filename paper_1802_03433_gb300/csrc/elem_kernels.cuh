@@ -20,7 +20,8 @@ struct ElemArgs {
   const double* y;
   const double* z;
   const int32_t* tets;  // [4][E]
-  int64_t E;
+  int64_t E;            // element count (the SoA stride)
+  int64_t e0, e1;       // range of elements this launch computes
   const double* kappa;
   double kappa_const;
   const double* lam;
@@ -177,8 +178,8 @@ __device__ __forceinline__ void elem_scalar_body(const ElemArgs& A, int64_t e) {
 
 template <int ORDER, bool MASS, int LOAD, int NPTS, typename R>
 __global__ void __launch_bounds__(ELEM_T) k_elem_scalar(ElemArgs A) {
-  const int64_t e = (int64_t)blockIdx.x * ELEM_T + threadIdx.x;
-  if (e < A.E) elem_scalar_body<ORDER, MASS, LOAD, NPTS, R>(A, e);
+  const int64_t e = A.e0 + (int64_t)blockIdx.x * ELEM_T + threadIdx.x;
+  if (e < A.e1) elem_scalar_body<ORDER, MASS, LOAD, NPTS, R>(A, e);
 }
 
 // ---------------------------------------------------------------- elasticity
@@ -186,8 +187,8 @@ __global__ void __launch_bounds__(ELEM_T) k_elem_scalar(ElemArgs A) {
 //                      + mu delta_ij grad phi_a . grad phi_b]  on P1 tets.
 template <int LOAD, int NPTS, typename R>
 __global__ void __launch_bounds__(ELEM_T) k_elem_elast(ElemArgs A) {
-  const int64_t e = (int64_t)blockIdx.x * ELEM_T + threadIdx.x;
-  if (e >= A.E) return;
+  const int64_t e = A.e0 + (int64_t)blockIdx.x * ELEM_T + threadIdx.x;
+  if (e >= A.e1) return;
   double X[4][3];
   load_element(A, e, X);
   Geo g;

@@ -6,16 +6,16 @@
 
 namespace fea {
 
-inline unsigned elem_blocks(int64_t E) { return (unsigned)((E + ELEM_T - 1) / ELEM_T); }
+inline unsigned elem_blocks(const ElemArgs& A) { return (unsigned)((A.e1 - A.e0 + ELEM_T - 1) / ELEM_T); }
 
 template <int ORDER, bool MASS>
 struct ScalarLauncher {
   template <int LOAD, int NPTS>
   static void go(const ElemArgs& A, int prec, cudaStream_t s) {
     if (prec == FEA_FP64)
-      k_elem_scalar<ORDER, MASS, LOAD, NPTS, double><<<elem_blocks(A.E), ELEM_T, 0, s>>>(A);
+      k_elem_scalar<ORDER, MASS, LOAD, NPTS, double><<<elem_blocks(A), ELEM_T, 0, s>>>(A);
     else
-      k_elem_scalar<ORDER, MASS, LOAD, NPTS, float><<<elem_blocks(A.E), ELEM_T, 0, s>>>(A);
+      k_elem_scalar<ORDER, MASS, LOAD, NPTS, float><<<elem_blocks(A), ELEM_T, 0, s>>>(A);
   }
   template <int NPTS>
   static void by_load(const ElemArgs& A, int load, int prec, cudaStream_t s) {
@@ -23,7 +23,7 @@ struct ScalarLauncher {
     else go<LOAD_SIN, NPTS>(A, prec, s);
   }
   static fea_status run(const ElemArgs& A, int load, int npts, int prec, cudaStream_t s) {
-    if (A.E == 0) return FEA_OK;
+    if (A.e1 <= A.e0) return FEA_OK;
     if (load == LOAD_NONE) go<LOAD_NONE, 1>(A, prec, s);
     else if (npts == 1) by_load<1>(A, load, prec, s);
     else if (npts == 4) by_load<4>(A, load, prec, s);
@@ -37,9 +37,9 @@ struct ElastLauncher {
   template <int LOAD, int NPTS>
   static void go(const ElemArgs& A, int prec, cudaStream_t s) {
     if (prec == FEA_FP64)
-      k_elem_elast<LOAD, NPTS, double><<<elem_blocks(A.E), ELEM_T, 0, s>>>(A);
+      k_elem_elast<LOAD, NPTS, double><<<elem_blocks(A), ELEM_T, 0, s>>>(A);
     else
-      k_elem_elast<LOAD, NPTS, float><<<elem_blocks(A.E), ELEM_T, 0, s>>>(A);
+      k_elem_elast<LOAD, NPTS, float><<<elem_blocks(A), ELEM_T, 0, s>>>(A);
   }
   template <int NPTS>
   static void by_load(const ElemArgs& A, int load, int prec, cudaStream_t s) {
@@ -47,7 +47,7 @@ struct ElastLauncher {
     else go<LOAD_SIN, NPTS>(A, prec, s);
   }
   static fea_status run(const ElemArgs& A, int load, int npts, int prec, cudaStream_t s) {
-    if (A.E == 0) return FEA_OK;
+    if (A.e1 <= A.e0) return FEA_OK;
     if (load == LOAD_NONE) go<LOAD_NONE, 1>(A, prec, s);
     else if (npts == 1) by_load<1>(A, load, prec, s);
     else if (npts == 4) by_load<4>(A, load, prec, s);

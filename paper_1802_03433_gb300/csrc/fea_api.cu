@@ -149,9 +149,19 @@ fea_status fea_mesh_set_coords(fea_mesh* m, const double* x, const double* y, co
   return FEA_OK;
 }
 
+fea_status fea_mesh_set_stages(fea_mesh* m, int32_t stages) {
+  if (!m) return fail(FEA_ERR_ARG, "mesh is NULL");
+  if (stages < 1 || stages > 16) return fail(FEA_ERR_ARG, "stages must be in [1, 16]");
+  m->stages = stages;
+  return FEA_OK;
+}
+
 fea_status fea_mesh_destroy(fea_mesh* m) {
   if (!m) return FEA_OK;
   cudaDeviceSynchronize();
+  for (int k = 0; k <= 16; ++k)
+    if (m->chunk_ev[k]) cudaEventDestroy(m->chunk_ev[k]);
+  if (m->side) cudaStreamDestroy(m->side);
   for (int o = 0; o < 3; ++o)
     for (int d = 0; d < 4; ++d) free_pattern(m->pat[o][d]);
   for (int o = 2; o >= 1; --o) free_base(m->base[o]);

@@ -202,7 +202,15 @@ __global__ void __launch_bounds__(128) k_gather(GatherArgs G) {
   gather_tile<NB, NDPN, LT>(G, blockIdx.x, blockDim.x, acc);
 }
 
+// The row tiles listed in tiles[0 .. gridDim.x).
+template <int NB, int NDPN, typename LT>
+__global__ void __launch_bounds__(128) k_gather_list(GatherArgs G, const int32_t* __restrict__ tiles) {
+  extern __shared__ double acc[];
+  gather_tile<NB, NDPN, LT>(G, __ldg(tiles + blockIdx.x), blockDim.x, acc);
+}
+
 fea_status launch_gather(int nb, int ndpn, bool mixed, const GatherArgs& G, int rows_per_tile,
-                         int64_t max_tile_nnz, cudaStream_t s);
+                         int64_t max_tile_nnz, cudaStream_t s, const int32_t* tiles = nullptr,
+                         int64_t ntiles = -1);
 
 }  // namespace fea

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/fea.h"
 
@@ -71,6 +72,13 @@ struct Pattern {
   bool own = false;           // ndpn == 1 aliases the Base arrays
   int rows_per_tile = 0;      // gather tile height (rows per CTA)
   int64_t max_tile_nnz = 0;   // largest CSR span of one tile
+  // Overlap of element computation and scatter: the elements are processed
+  // in `stages` consecutive chunks; the row tiles whose last element lies in
+  // chunk k are listed in tile_list[stage_ptr[k] .. stage_ptr[k + 1]).
+  int stages = 0;
+  int64_t chunk = 0;
+  int32_t* tile_list = nullptr;
+  std::vector<int64_t> stage_ptr;
 };
 
 struct Scratch {
@@ -92,6 +100,9 @@ struct fea_mesh {
   fea::Pattern* pat[3][4] = {{nullptr}};                     // by order, ndpn
   fea::Scratch lm, fl;      // local matrices / local loads of the last assembly
   fea::Scratch gxs;         // per-incidence vertex gradients of the last backward
+  int stages = 1;           // element chunks overlapped with the scatter (1 = no overlap)
+  cudaStream_t side = nullptr;             // scatter stream of the overlapped path
+  cudaEvent_t chunk_ev[17] = {nullptr};    // chunk done (<= 16 stages) + join
   bool profile = false;     // record phase events in fea_assemble
   bool profiled = false;    // events of a call are pending
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -103,6 +114,7 @@ namespace fea {
 fea_status build_base(fea_mesh* m, int order, cudaStream_t s);
 fea_status build_pattern(fea_mesh* m, int order, int ndpn, cudaStream_t s);
 fea_status build_emap(fea_mesh* m, int order, cudaStream_t s);
+fea_status build_stages(fea_mesh* m, Pattern* P, int stages, cudaStream_t s);
 fea_status validate_connectivity(fea_mesh* m, cudaStream_t s);
 void free_base(Base* b);
 void free_pattern(Pattern* p);

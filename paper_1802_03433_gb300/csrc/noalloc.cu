@@ -96,6 +96,8 @@ extern "C" fea_status fea_assemble_noalloc(fea_mesh* m, const fea_form* form, co
   A.z = m->z;
   A.tets = m->tets;
   A.E = E;
+  A.e0 = 0;
+  A.e1 = E;
   A.kappa = co->kappa;
   A.kappa_const = co->kappa_const;
   A.lam = co->lame_lambda;

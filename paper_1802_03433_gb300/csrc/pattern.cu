@@ -423,6 +423,23 @@ __global__ void k_ipos(int64_t nI, int nb, int64_t E, const int32_t* __restrict_
   ipos[a * E + e] = (int32_t)i;
 }
 
+// ------------------------------------------------------------------ stages
+// Stage of a row tile = chunk of the largest element id among its rows'
+// incidences (each incidence list is sorted, so its last entry).
+__global__ void k_tile_stage(int64_t ndof, int ndpn, int rows, int nb, const int32_t* __restrict__ inc_ptr,
+                             const int32_t* __restrict__ inc, int64_t chunk, int32_t* __restrict__ stage) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t r0 = t * rows;
+  if (r0 >= ndof) return;
+  const int64_t r1 = r0 + rows < ndof ? r0 + rows : ndof;
+  int64_t emax = -1;
+  for (int64_t node = r0 / ndpn; node <= (r1 - 1) / ndpn; ++node) {
+    const int32_t i0 = inc_ptr[node], i1 = inc_ptr[node + 1];
+    if (i1 > i0) emax = max(emax, (int64_t)(inc[i1 - 1] / nb));
+  }
+  stage[t] = emax < 0 ? 0 : (int32_t)(emax / chunk);
+}
+
 // ------------------------------------------------------------------ emap
 __global__ void k_emap(int64_t nrows, int nb, int sw, const int32_t* __restrict__ inc_ptr,
                        const int32_t* __restrict__ inc, const uint8_t* __restrict__ slot,
@@ -522,6 +539,7 @@ void free_base(Base* b) {
 
 void free_pattern(Pattern* p) {
   if (!p) return;
+  dfree(p->tile_list);
   if (p->own) {
     dfree(p->row_ptr);
     dfree(p->col_idx);
@@ -640,6 +658,38 @@ fea_status build_pattern(fea_mesh* m, int order, int ndpn, cudaStream_t s) {
     return st;
   }
   m->pat[order][ndpn] = P;
+  return FEA_OK;
+}
+
+fea_status build_stages(fea_mesh* m, Pattern* P, int stages, cudaStream_t s) {
+  if (P->stages == stages) return FEA_OK;
+  dfree(P->tile_list);
+  P->stage_ptr.clear();
+  P->stages = 0;
+  const Base* B = m->base[P->order];
+  const int64_t ntiles = (P->ndof + P->rows_per_tile - 1) / P->rows_per_tile;
+  const int64_t E = m->n_elems;
+  P->chunk = std::max<int64_t>(1, (E + stages - 1) / stages);
+  std::vector<int32_t> st(ntiles > 0 ? ntiles : 1), list(ntiles > 0 ? ntiles : 1);
+  if (ntiles > 0) {
+    Tmp<int32_t> d;
+    FEA_TRY(d.alloc(ntiles));
+    k_tile_stage<<<blocks_for(ntiles, 128), 128, 0, s>>>(P->ndof, P->ndpn, P->rows_per_tile, B->nb, B->inc_ptr, B->inc,
+                                                          P->chunk, d.p);
+    FEA_CUDA(cudaGetLastError());
+    FEA_CUDA(cudaMemcpyAsync(st.data(), d.p, ntiles * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    FEA_CUDA(cudaStreamSynchronize(s));
+  }
+  // counting sort of the tiles by stage (ascending tile id inside a stage)
+  P->stage_ptr.assign(stages + 1, 0);
+  for (int64_t t = 0; t < ntiles; ++t) P->stage_ptr[std::min(st[t], stages - 1) + 1] += 1;
+  for (int k = 0; k < stages; ++k) P->stage_ptr[k + 1] += P->stage_ptr[k];
+  std::vector<int64_t> cur(P->stage_ptr.begin(), P->stage_ptr.end() - 1);
+  for (int64_t t = 0; t < ntiles; ++t) list[cur[std::min(st[t], stages - 1)]++] = (int32_t)t;
+  FEA_TRY(dalloc(&P->tile_list, ntiles));
+  if (ntiles > 0)
+    FEA_CUDA(cudaMemcpy(P->tile_list, list.data(), ntiles * sizeof(int32_t), cudaMemcpyHostToDevice));
+  P->stages = stages;
   return FEA_OK;
 }
 

@@ -63,6 +63,7 @@ def lib() -> C.CDLL:
         "fea_mesh_create": [_vp, _vp, _vp, C.c_int64, _vp, C.c_int64, _vp, C.POINTER(_vp)],
         "fea_mesh_set_coords": [_vp, _vp, _vp, _vp],
         "fea_mesh_destroy": [_vp],
+        "fea_mesh_set_stages": [_vp, C.c_int32],
         "fea_mesh_check": [_vp, _vp],
         "fea_pattern": [_vp, C.c_int32, C.c_int32, i64p, i64p, _vp],
         "fea_pattern_copy": [_vp, C.c_int32, C.c_int32, _vp, _vp, _vp],
@@ -131,6 +132,10 @@ def fea_mesh_create(x, y, z, tets, stream=None):
 
 def fea_mesh_set_coords(h, x, y, z):
     _check(lib().fea_mesh_set_coords(h, _ptr(x), _ptr(y), _ptr(z)), "fea_mesh_set_coords")
+
+
+def fea_mesh_set_stages(h, stages):
+    _check(lib().fea_mesh_set_stages(h, stages), "fea_mesh_set_stages")
 
 
 def fea_mesh_destroy(h):
