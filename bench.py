@@ -143,6 +143,22 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value, device="cpu"):
+    """The largest of every rank's value (the job finishes with its slowest
+    rank); a plain float without an initialised process group."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def weak_scaling_value(world_size, units_per_rank, steps, total_ms):
+    """Whole-job throughput: every rank processes its own units each step."""
+    return world_size * units_per_rank * steps / (total_ms / 1e3)
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -213,14 +229,11 @@ def run_ours(args):
             dist.barrier()
         mesh.check()
         step_ms = [a.elapsed_time(b) for a, b in evs]
-        total = torch.tensor([sum(step_ms)], dtype=torch.float64, device=dev)
-        if ws > 1:
-            dist.all_reduce(total, op=dist.ReduceOp.MAX)
-        return total.item(), step_ms, phase, clk
+        return max_over_ranks(sum(step_ms), dev), step_ms, phase, clk
 
     clocks = ClockSampler(local) if rank == 0 else None
     total_ms, step_ms, phase, clk = timed_loop(fea.FEA_FP64, args.steps, args.warmup, clocks)
-    value = ws * E * args.steps / (total_ms / 1e3)
+    value = weak_scaling_value(ws, E, args.steps, total_ms)
     elem_ms = statistics.mean(p[0] for p in phase)
     scat_ms = statistics.mean(p[1] for p in phase)
 
@@ -272,12 +285,10 @@ def run_ours(args):
             e2e_step()
         b.record()
         torch.cuda.synchronize()
-        t = torch.tensor([a.elapsed_time(b)], dtype=torch.float64, device=dev)
-        if ws > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = max_over_ranks(a.elapsed_time(b), dev)
         h2d = sum(h.numel() * h.element_size() for h, _ in hin)
         d2h = hv.numel() * 8 + hr.numel() * 8
-        e2e = {"value": ws * E * steps / (t.item() / 1e3), "unit": "elements/s", "h2d_bytes_per_step": h2d,
+        e2e = {"value": weak_scaling_value(ws, E, steps, t_ms), "unit": "elements/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
     # roofline of the dominant kernel

@@ -200,14 +200,17 @@ __global__ void __launch_bounds__(ELEM_T) k_elem_elast(ElemArgs A) {
   R Gr[4][3];
   grads<R>(g, Gr);
   const double sc = grad_scale<R>(adet);
-  const R Ls = R(lam * sc), Ms = R(mu * sc);
-  R Lc[4][3], Mc[4][3], D[4][4];
+  const R Ls = R(lam * sc), Ms = R(mu * sc), LMs = R((lam + mu) * sc);
+  // diagonal entries of a 3x3 block (i == j): the two product terms share
+  // d_i phi_b, so (lam + mu) d_i phi_a d_i phi_b + mu grad phi_a . grad phi_b
+  R Lc[4][3], Mc[4][3], LMc[4][3], D[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       Lc[a][k] = Ls * Gr[a][k];
       Mc[a][k] = Ms * Gr[a][k];
+      LMc[a][k] = LMs * Gr[a][k];
     }
   static_for<10>([&](auto K) {
     constexpr int a = upper_a(4, K), b = upper_b(4, K);
@@ -218,8 +221,9 @@ __global__ void __launch_bounds__(ELEM_T) k_elem_elast(ElemArgs A) {
   static_for<78>([&](auto K) {
     constexpr int r = upper_a(12, K), c = upper_b(12, K);
     constexpr int a = r / 3, i = r % 3, b = c / 3, j = c % 3;
-    R v = fma(Lc[a][i], Gr[b][j], Mc[a][j] * Gr[b][i]);
-    if constexpr (i == j) v += D[a][b];
+    R v;
+    if constexpr (i == j) v = fma(LMc[a][i], Gr[b][i], D[a][b]);
+    else v = fma(Lc[a][i], Gr[b][j], Mc[a][j] * Gr[b][i]);
     Kl[r][c] = v;
     Kl[c][r] = v;
   });
