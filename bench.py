@@ -248,6 +248,30 @@ def run_ours(args):
                           "scatter_ms": statistics.mean(p[1] for p in m_phase)}
 
     if not args.no_forms:
+        # the paper's sparse Algorithm 1 on the same workload: row search +
+        # global FP64 atomicAdd (no scratch, no reproducibility)
+        quad = fea.make_quadrature(d["npts"], fea.FEA_FP64)
+        for _ in range(args.warmup):
+            fea.fea_assemble_atomic(mesh.h, form, coeffs, quad, values, rhs)
+        torch.cuda.synchronize()
+        at, runs = 0.0, []
+        steps_a = max(3, args.steps // 2)
+        for k in range(steps_a):
+            flush.fill_(k)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fea.fea_assemble_atomic(mesh.h, form, coeffs, quad, values, rhs)
+            b.record()
+            torch.cuda.synchronize()
+            at += a.elapsed_time(b)
+            if k < 2:
+                runs.append(values.clone())
+        at = max_over_ranks(at, dev)
+        forms["atomic_alg1"] = {"value": weak_scaling_value(ws, E, steps_a, at), "ms_per_step": at / steps_a,
+                                "bitwise_equal_across_two_runs": bool(torch.equal(runs[0].view(torch.int64),
+                                                                                  runs[1].view(torch.int64))),
+                                "note": "paper's sparse Algorithm 1: global FP64 atomicAdd after a row search"}
+        del runs
         small = max(3, args.steps // 4)
         forms["batched"] = bench_batched(fea, torch, dev, small, args.warmup, flush)
         forms["adjoint"] = bench_adjoint(fea, torch, dev, small, args.warmup, flush)

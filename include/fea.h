@@ -194,6 +194,17 @@ fea_status fea_assemble(fea_mesh* mesh, const fea_form* form, const fea_coeffs* 
 fea_status fea_assemble_noalloc(fea_mesh* mesh, const fea_form* form, const fea_coeffs* coeffs,
                                 const fea_quadrature* quad, double* values, double* rhs, void* stream);
 
+/* The paper's own sparse assembly (Sec. 5, Algorithm 1, sparse variant) as a
+ * comparison point: same arguments and element arithmetic as fea_assemble
+ * (FP64 only), but every local entry is added into the global CSR row with a
+ * global FP64 atomicAdd after a linear search of the row for its column, and
+ * every load entry into rhs the same way; values and rhs are zeroed first.
+ * Allocates nothing.  The order of the additions depends on scheduling, so
+ * results agree with fea_assemble to rounding only and are not reproducible
+ * bit for bit. */
+fea_status fea_assemble_atomic(fea_mesh* mesh, const fea_form* form, const fea_coeffs* coeffs,
+                               const fea_quadrature* quad, double* values, double* rhs, void* stream);
+
 /* Reverse mode of fea_assemble for the scalar forms (FEA_POISSON,
  * FEA_DIFFUSION_MASS; P1 or P2; FP64).  For a scalar loss L with
  * grad_values = dL/dvalues [nnz] and grad_rhs = dL/drhs [ndof] (either may be

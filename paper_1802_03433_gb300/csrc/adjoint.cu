@@ -209,9 +209,7 @@ __global__ void __launch_bounds__(ADJ_T) k_adjoint(AdjArgs A) {
       const double qg = Q[k][0] * g[c][0] + Q[k][1] * g[c][1] + Q[k][2] * g[c][2];
       d[k] = vol * (sigma * g[c][k] - kap * qg + lg[c][k]);
     }
-    double2* out = reinterpret_cast<double2*>(A.gxs + (int64_t)pos[c] * 4);
-    out[0] = make_double2(d[0], d[1]);
-    out[1] = make_double2(d[2], 0.0);
+    st_v4(A.gxs + (int64_t)pos[c] * 4, d[0], d[1], d[2], 0.0);
   }
 }
 
@@ -222,11 +220,11 @@ __global__ void k_node_grad(int64_t N, const int32_t* __restrict__ inc_ptr, cons
   if (n >= N) return;
   double s0 = 0.0, s1 = 0.0, s2 = 0.0;
   for (int32_t i = __ldg(inc_ptr + n); i < __ldg(inc_ptr + n + 1); ++i) {
-    const double2 a = __ldg(reinterpret_cast<const double2*>(gxs + (int64_t)i * 4));
-    const double2 b = __ldg(reinterpret_cast<const double2*>(gxs + (int64_t)i * 4) + 1);
-    s0 += a.x;
-    s1 += a.y;
-    s2 += b.x;
+    double a, b, c, pad;
+    ld_v4(gxs + (int64_t)i * 4, a, b, c, pad);
+    s0 += a;
+    s1 += b;
+    s2 += c;
   }
   gx[n] = s0;
   gx[N + n] = s1;

@@ -12,6 +12,7 @@
 
 #include "element.cuh"
 #include "internal.cuh"
+#include "vecmem.cuh"
 
 namespace fea {
 
@@ -34,26 +35,46 @@ struct ElemArgs {
   void* Lm;         // local rows, incidence order, lstride(nl) values apart
   void* Fl;         // local loads, incidence order
   int* err;
+  // atomic comparison path (the paper's sparse Algorithm 1): search the
+  // column in the global row and atomicAdd into the CSR values / rhs
+  const int32_t* edof;     // [nb][E] scalar dofs
+  const int32_t* rp;       // dof-level CSR
+  const int32_t* ci;
+  double* values;
+  double* rhs;
 };
 
-// Store one local row of NL values of type R at p (32-byte aligned) with
-// 16-byte vector stores, zero padding included up to lstride (whole sectors).
+// Algorithm 1, sparse variant (Sec. 5): each local entry is added into the
+// global row with atomicAdd after a linear search of the row for its column.
+__device__ __forceinline__ void atomic_add_entry(const ElemArgs& A, int64_t row, int32_t col, double v) {
+  const int32_t lo = __ldg(A.rp + row), hi = __ldg(A.rp + row + 1);
+  for (int32_t p = lo; p < hi; ++p)
+    if (__ldg(A.ci + p) == col) {
+      atomicAdd(A.values + p, v);
+      return;
+    }
+}
+
+// Store one local row of NL values of type R at p (32-byte aligned) as whole
+// 32-byte sectors, zero padding included up to lstride.
 template <int NL>
 __device__ __forceinline__ void store_row(double* __restrict__ p, const double* v) {
   constexpr int LS = lstride(NL, 8);
 #pragma unroll
-  for (int k = 0; k < LS / 2; ++k)
-    reinterpret_cast<double2*>(p)[k] =
-        make_double2(2 * k < NL ? v[2 * k] : 0.0, 2 * k + 1 < NL ? v[2 * k + 1] : 0.0);
+  for (int k = 0; k < LS / 4; ++k)
+    st_v4(p + 4 * k, 4 * k < NL ? v[4 * k] : 0.0, 4 * k + 1 < NL ? v[4 * k + 1] : 0.0,
+          4 * k + 2 < NL ? v[4 * k + 2] : 0.0, 4 * k + 3 < NL ? v[4 * k + 3] : 0.0);
 }
 template <int NL>
 __device__ __forceinline__ void store_row(float* __restrict__ p, const float* v) {
   constexpr int LS = lstride(NL, 4);
 #pragma unroll
-  for (int k = 0; k < LS / 4; ++k)
-    reinterpret_cast<float4*>(p)[k] =
-        make_float4(4 * k < NL ? v[4 * k] : 0.f, 4 * k + 1 < NL ? v[4 * k + 1] : 0.f,
-                    4 * k + 2 < NL ? v[4 * k + 2] : 0.f, 4 * k + 3 < NL ? v[4 * k + 3] : 0.f);
+  for (int k = 0; k < LS / 8; ++k) {
+    float w[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) w[j] = 8 * k + j < NL ? v[8 * k + j] : 0.f;
+    st_v8(p + 8 * k, w[0], w[1], w[2], w[3], w[4], w[5], w[6], w[7]);
+  }
 }
 
 constexpr int ELEM_T = 128;
@@ -111,7 +132,7 @@ __device__ __forceinline__ void vertices_r(const double X[4][3], R Xr[4][3]) {
 
 // ---------------------------------------------------------------- scalar forms
 // -div(kappa grad u) [+ mass u] on P1 (ORDER 1) or P2 (ORDER 2) tets.
-template <int ORDER, bool MASS, int LOAD, int NPTS, typename R>
+template <int ORDER, bool MASS, int LOAD, int NPTS, typename R, bool ATOMIC = false>
 __device__ __forceinline__ void elem_scalar_body(const ElemArgs& A, int64_t e) {
   constexpr int NB = ORDER == 1 ? 4 : 10;
   double X[4][3];
@@ -157,35 +178,54 @@ __device__ __forceinline__ void elem_scalar_body(const ElemArgs& A, int64_t e) {
       Kl[b][a] = v;
     });
   }
-  constexpr int LS = lstride(NB, sizeof(R));
-  int32_t pos[NB];
+  if constexpr (ATOMIC) {
+    int32_t d[NB];
 #pragma unroll
-  for (int a = 0; a < NB; ++a) pos[a] = __ldg(A.ipos + a * A.E + e);
+    for (int a = 0; a < NB; ++a) d[a] = __ldg(A.edof + a * A.E + e);
 #pragma unroll
-  for (int a = 0; a < NB; ++a) store_row<NB>(static_cast<R*>(A.Lm) + (int64_t)pos[a] * LS, Kl[a]);
+    for (int a = 0; a < NB; ++a)
+#pragma unroll
+      for (int b = 0; b < NB; ++b) atomic_add_entry(A, d[a], d[b], (double)Kl[a][b]);
+    if constexpr (LOAD != LOAD_NONE) {
+      R Xr[4][3];
+      vertices_r<R>(X, Xr);
+      R Fs[NB];
+      shape_load<ORDER, NPTS, LOAD, R>(Xr, Fs);
+      const R amp = R(A.fp[0] * adet * (1.0 / 6.0));
+#pragma unroll
+      for (int a = 0; a < NB; ++a) atomicAdd(A.rhs + d[a], (double)(amp * Fs[a]));
+    }
+  } else {
+    constexpr int LS = lstride(NB, sizeof(R));
+    int32_t pos[NB];
+#pragma unroll
+    for (int a = 0; a < NB; ++a) pos[a] = __ldg(A.ipos + a * A.E + e);
+#pragma unroll
+    for (int a = 0; a < NB; ++a) store_row<NB>(static_cast<R*>(A.Lm) + (int64_t)pos[a] * LS, Kl[a]);
 
-  if constexpr (LOAD != LOAD_NONE) {
-    R Xr[4][3];
-    vertices_r<R>(X, Xr);
-    R Fs[NB];
-    shape_load<ORDER, NPTS, LOAD, R>(Xr, Fs);
-    const R amp = R(A.fp[0] * adet * (1.0 / 6.0));
-    R* __restrict__ Fl = static_cast<R*>(A.Fl);
+    if constexpr (LOAD != LOAD_NONE) {
+      R Xr[4][3];
+      vertices_r<R>(X, Xr);
+      R Fs[NB];
+      shape_load<ORDER, NPTS, LOAD, R>(Xr, Fs);
+      const R amp = R(A.fp[0] * adet * (1.0 / 6.0));
+      R* __restrict__ Fl = static_cast<R*>(A.Fl);
 #pragma unroll
-    for (int a = 0; a < NB; ++a) Fl[pos[a]] = amp * Fs[a];
+      for (int a = 0; a < NB; ++a) Fl[pos[a]] = amp * Fs[a];
+    }
   }
 }
 
-template <int ORDER, bool MASS, int LOAD, int NPTS, typename R>
+template <int ORDER, bool MASS, int LOAD, int NPTS, typename R, bool ATOMIC = false>
 __global__ void __launch_bounds__(ELEM_T) k_elem_scalar(ElemArgs A) {
   const int64_t e = A.e0 + (int64_t)blockIdx.x * ELEM_T + threadIdx.x;
-  if (e < A.e1) elem_scalar_body<ORDER, MASS, LOAD, NPTS, R>(A, e);
+  if (e < A.e1) elem_scalar_body<ORDER, MASS, LOAD, NPTS, R, ATOMIC>(A, e);
 }
 
 // ---------------------------------------------------------------- elasticity
 // K_(a,i),(b,j) = |T| [lam d_i phi_a d_j phi_b + mu d_j phi_a d_i phi_b
 //                      + mu delta_ij grad phi_a . grad phi_b]  on P1 tets.
-template <int LOAD, int NPTS, typename R>
+template <int LOAD, int NPTS, typename R, bool ATOMIC = false>
 __global__ void __launch_bounds__(ELEM_T) k_elem_elast(ElemArgs A) {
   const int64_t e = A.e0 + (int64_t)blockIdx.x * ELEM_T + threadIdx.x;
   if (e >= A.e1) return;
@@ -227,10 +267,31 @@ __global__ void __launch_bounds__(ELEM_T) k_elem_elast(ElemArgs A) {
     Kl[r][c] = v;
     Kl[c][r] = v;
   });
+  if constexpr (ATOMIC) {
+    int32_t nd[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) nd[a] = __ldg(A.tets + a * A.E + e);
+#pragma unroll
+    for (int r = 0; r < 12; ++r)
+#pragma unroll
+      for (int c = 0; c < 12; ++c)
+        atomic_add_entry(A, 3 * (int64_t)nd[r / 3] + r % 3, 3 * nd[c / 3] + c % 3, (double)Kl[r][c]);
+    if constexpr (LOAD != LOAD_NONE) {
+      R Xr[4][3];
+      vertices_r<R>(X, Xr);
+      R Fs[4];
+      shape_load<1, NPTS, LOAD, R>(Xr, Fs);
+      const double vol = adet * (1.0 / 6.0);
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) atomicAdd(A.rhs + 3 * (int64_t)nd[a] + i, A.fp[i] * vol * (double)Fs[a]);
+    }
+    return;
+  }
   int32_t pos[4];
 #pragma unroll
   for (int a = 0; a < 4; ++a) pos[a] = __ldg(A.ipos + a * A.E + e);
-#pragma unroll
   constexpr int LS = lstride(12, sizeof(R));
 #pragma unroll
   for (int r = 0; r < 12; ++r) store_row<12>(static_cast<R*>(A.Lm) + ((int64_t)pos[r / 3] * 3 + r % 3) * LS, Kl[r]);

@@ -22,6 +22,7 @@
 #include <stdint.h>
 
 #include "internal.cuh"
+#include "vecmem.cuh"
 
 namespace fea {
 
@@ -81,35 +82,29 @@ __device__ __forceinline__ void add_row(double* __restrict__ a, const int s[NB],
     for (int j = 0; j < NDPN; ++j) a[NDPN * s[b] + j] = t[NDPN * b + j];
 }
 
-// Load NL consecutive values starting at p with the widest aligned vectors.
+// Load the NL values of one local row (32-byte aligned, whole sectors).
 template <int NL>
 __device__ __forceinline__ void load_row(const double* __restrict__ p, double v[NL]) {
-  static_assert(NL % 2 == 0, "even row length");
+  constexpr int LS = lstride(NL, 8);
 #pragma unroll
-  for (int k = 0; k < NL / 2; ++k) {
-    const double2 t = __ldg(reinterpret_cast<const double2*>(p) + k);
-    v[2 * k] = t.x;
-    v[2 * k + 1] = t.y;
+  for (int k = 0; k < LS / 4; ++k) {
+    double t[4];
+    ld_v4(p + 4 * k, t[0], t[1], t[2], t[3]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (4 * k + j < NL) v[4 * k + j] = t[j];
   }
 }
 template <int NL>
 __device__ __forceinline__ void load_row(const float* __restrict__ p, float v[NL]) {
-  if constexpr (NL % 4 == 0) {
+  constexpr int LS = lstride(NL, 4);
 #pragma unroll
-    for (int k = 0; k < NL / 4; ++k) {
-      const float4 t = __ldg(reinterpret_cast<const float4*>(p) + k);
-      v[4 * k] = t.x;
-      v[4 * k + 1] = t.y;
-      v[4 * k + 2] = t.z;
-      v[4 * k + 3] = t.w;
-    }
-  } else {
+  for (int k = 0; k < LS / 8; ++k) {
+    float t[8];
+    ld_v8(p + 8 * k, t[0], t[1], t[2], t[3], t[4], t[5], t[6], t[7]);
 #pragma unroll
-    for (int k = 0; k < NL / 2; ++k) {
-      const float2 t = __ldg(reinterpret_cast<const float2*>(p) + k);
-      v[2 * k] = t.x;
-      v[2 * k + 1] = t.y;
-    }
+    for (int j = 0; j < 8; ++j)
+      if (8 * k + j < NL) v[8 * k + j] = t[j];
   }
 }
 

@@ -72,6 +72,8 @@ def lib() -> C.CDLL:
                          _vp, _vp, _vp],
         "fea_assemble_noalloc": [_vp, C.POINTER(fea_form), C.POINTER(fea_coeffs), C.POINTER(fea_quadrature),
                                  _vp, _vp, _vp],
+        "fea_assemble_atomic": [_vp, C.POINTER(fea_form), C.POINTER(fea_coeffs), C.POINTER(fea_quadrature),
+                                _vp, _vp, _vp],
         "fea_assemble_backward": [_vp, C.POINTER(fea_form), C.POINTER(fea_coeffs),
                                   C.POINTER(fea_quadrature), _vp, _vp, _vp, _vp, _vp],
         "fea_profile_enable": [_vp, C.c_int32],
@@ -186,6 +188,13 @@ def fea_assemble_noalloc(h, form, coeffs, quad, values, rhs=None, stream=None):
     call allocates nothing; meshes above the array's 32 MiB are rejected)."""
     _check(lib().fea_assemble_noalloc(h, C.byref(form), C.byref(coeffs), C.byref(quad), _ptr(values), _ptr(rhs),
                                       _stream(stream)), "fea_assemble_noalloc")
+
+
+def fea_assemble_atomic(h, form, coeffs, quad, values, rhs=None, stream=None):
+    """The paper's sparse Algorithm 1: global FP64 atomicAdd after a row search
+    (not reproducible bit for bit; a comparison point)."""
+    _check(lib().fea_assemble_atomic(h, C.byref(form), C.byref(coeffs), C.byref(quad), _ptr(values), _ptr(rhs),
+                                     _stream(stream)), "fea_assemble_atomic")
 
 
 def fea_assemble_backward(h, form, coeffs, quad, grad_values, grad_rhs, grad_kappa, grad_x, stream=None):
