@@ -141,6 +141,15 @@ fea_status fea_mesh_set_coords(fea_mesh* mesh, const double* x, const double* y,
  * bitwise identical for every setting. */
 fea_status fea_mesh_set_stages(fea_mesh* mesh, int32_t stages);
 
+/* Launch shape of fea_assemble's scatter when stages == 1: 0 = one launch of
+ * the two-deep pipelined kernel over all row tiles; 1 = tiles whose CSR span
+ * exceeds 60% of the widest in one such launch, the rest in a second launch
+ * with a smaller shared-memory size and a one-deep kernel (fewer registers,
+ * more CTAs per SM); 2 = one launch of the one-deep kernel; -1 (default) =
+ * automatic: 2 when the pattern mixes long and short rows (P2), else 0.
+ * Results are bitwise identical for every mode. */
+fea_status fea_mesh_set_scatter_classes(fea_mesh* mesh, int32_t mode);
+
 /* Release the handle and everything it owns.  Synchronises the device. */
 fea_status fea_mesh_destroy(fea_mesh* mesh);
 

@@ -13,17 +13,22 @@ namespace {
 
 template <int NB, int NDPN, typename LT>
 fea_status gather_one(const GatherArgs& G, int rows, int64_t max_tile_nnz, cudaStream_t s, const int32_t* tiles,
-                      int64_t ntiles) {
+                      int64_t ntiles, bool deep) {
   const size_t smem = (size_t)max_tile_nnz * sizeof(double);
   static size_t configured = 0;  // opt-in above the 48 KB default, once per instance
   if (smem > 48 * 1024 && smem > configured) {
     FEA_CUDA(cudaFuncSetAttribute(k_gather<NB, NDPN, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    FEA_CUDA(cudaFuncSetAttribute(k_gather_list<NB, NDPN, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    FEA_CUDA(cudaFuncSetAttribute(k_gather_list<NB, NDPN, LT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    FEA_CUDA(cudaFuncSetAttribute(k_gather_list<NB, NDPN, LT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
     configured = smem;
   }
   if (tiles) {
-    if (ntiles > 0) k_gather_list<NB, NDPN, LT><<<(unsigned)ntiles, rows, smem, s>>>(G, tiles);
+    if (ntiles > 0) {
+      if (deep) k_gather_list<NB, NDPN, LT, true><<<(unsigned)ntiles, rows, smem, s>>>(G, tiles);
+      else k_gather_list<NB, NDPN, LT, false><<<(unsigned)ntiles, rows, smem, s>>>(G, tiles);
+    }
   } else {
     const int64_t n = (G.ndof + rows - 1) / rows;
     if (n > 0) k_gather<NB, NDPN, LT><<<(unsigned)n, rows, smem, s>>>(G);
@@ -35,16 +40,16 @@ fea_status gather_one(const GatherArgs& G, int rows, int64_t max_tile_nnz, cudaS
 }  // namespace
 
 fea_status launch_gather(int nb, int ndpn, bool mixed, const GatherArgs& G, int rows, int64_t max_tile_nnz,
-                         cudaStream_t s, const int32_t* tiles, int64_t ntiles) {
+                         cudaStream_t s, const int32_t* tiles, int64_t ntiles, bool deep) {
   if (nb == 4 && ndpn == 1)
-    return mixed ? gather_one<4, 1, float>(G, rows, max_tile_nnz, s, tiles, ntiles)
-                 : gather_one<4, 1, double>(G, rows, max_tile_nnz, s, tiles, ntiles);
+    return mixed ? gather_one<4, 1, float>(G, rows, max_tile_nnz, s, tiles, ntiles, deep)
+                 : gather_one<4, 1, double>(G, rows, max_tile_nnz, s, tiles, ntiles, deep);
   if (nb == 10 && ndpn == 1)
-    return mixed ? gather_one<10, 1, float>(G, rows, max_tile_nnz, s, tiles, ntiles)
-                 : gather_one<10, 1, double>(G, rows, max_tile_nnz, s, tiles, ntiles);
+    return mixed ? gather_one<10, 1, float>(G, rows, max_tile_nnz, s, tiles, ntiles, deep)
+                 : gather_one<10, 1, double>(G, rows, max_tile_nnz, s, tiles, ntiles, deep);
   if (nb == 4 && ndpn == 3)
-    return mixed ? gather_one<4, 3, float>(G, rows, max_tile_nnz, s, tiles, ntiles)
-                 : gather_one<4, 3, double>(G, rows, max_tile_nnz, s, tiles, ntiles);
+    return mixed ? gather_one<4, 3, float>(G, rows, max_tile_nnz, s, tiles, ntiles, deep)
+                 : gather_one<4, 3, double>(G, rows, max_tile_nnz, s, tiles, ntiles, deep);
   return fail(FEA_ERR_ARG, "no scatter for this element / dof layout");
 }
 
@@ -113,7 +118,20 @@ fea_status assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* co, con
     if (m->profile) FEA_CUDA(cudaEventRecord(m->ev[0], s));
     FEA_TRY(launch_elements(form, A, load, q->npts, prec, s));
     if (m->profile) FEA_CUDA(cudaEventRecord(m->ev[1], s));
-    FEA_TRY(launch_gather(nb, ndpn, mixed, G, P->rows_per_tile, P->max_tile_nnz, s));
+    int mode = m->tile_classes;
+    if (mode < 0) mode = (P->n_heavy > 0 && P->n_light > 0) ? 2 : 0;
+    if (mode == 2) {
+      FEA_TRY(launch_gather(nb, ndpn, mixed, G, P->rows_per_tile, P->max_tile_nnz, s, P->class_list,
+                            P->n_heavy + P->n_light, false));
+    } else if (mode == 1 && P->class_list) {
+      // heavy tiles (long rows) with the deep pipeline, then light tiles with
+      // their own smaller shared-memory size and the lighter kernel
+      FEA_TRY(launch_gather(nb, ndpn, mixed, G, P->rows_per_tile, P->heavy_span, s, P->class_list, P->n_heavy, true));
+      FEA_TRY(launch_gather(nb, ndpn, mixed, G, P->rows_per_tile, P->light_span, s, P->class_list + P->n_heavy,
+                            P->n_light, false));
+    } else {
+      FEA_TRY(launch_gather(nb, ndpn, mixed, G, P->rows_per_tile, P->max_tile_nnz, s));
+    }
   } else {
     // Overlapped: element chunk k runs on `s`; the row tiles that chunk k
     // completes are scattered on the side stream while chunk k + 1 computes.

@@ -156,6 +156,13 @@ fea_status fea_mesh_set_stages(fea_mesh* m, int32_t stages) {
   return FEA_OK;
 }
 
+fea_status fea_mesh_set_scatter_classes(fea_mesh* m, int32_t mode) {
+  if (!m) return fail(FEA_ERR_ARG, "mesh is NULL");
+  if (mode < -1 || mode > 2) return fail(FEA_ERR_ARG, "mode must be -1, 0, 1 or 2");
+  m->tile_classes = mode;
+  return FEA_OK;
+}
+
 fea_status fea_mesh_destroy(fea_mesh* m) {
   if (!m) return FEA_OK;
   cudaDeviceSynchronize();

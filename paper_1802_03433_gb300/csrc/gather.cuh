@@ -153,7 +153,7 @@ struct Contrib {
 // Incidences are consumed in pairs; the loads of the next pair are issued
 // before the current pair is added (software pipeline), so one pair's memory
 // latency overlaps the other pair's shared-memory adds.
-template <int NB, int NDPN, typename LT>
+template <int NB, int NDPN, typename LT, bool DEEP = true>
 __device__ __forceinline__ void gather_tile(const GatherArgs& G, int64_t tile, int rows, double* acc) {
   const int64_t r0 = tile * rows;
   const int64_t r1 = r0 + rows < G.ndof ? r0 + rows : G.ndof;
@@ -169,21 +169,34 @@ __device__ __forceinline__ void gather_tile(const GatherArgs& G, int64_t tile, i
     double f = 0.0;
     const int32_t i1 = __ldg(G.inc_ptr + node + 1);
     int32_t i = __ldg(G.inc_ptr + node);
-    Contrib<NB, NDPN, LT> c0, c1, n0, n1;
-    if (i < i1) c0.load(G, i, comp);
-    if (i + 1 < i1) c1.load(G, i + 1, comp);
-    while (i < i1) {
-      if (i + 2 < i1) n0.load(G, i + 2, comp);
-      if (i + 3 < i1) n1.load(G, i + 3, comp);
-      add_row<NB, NDPN, LT>(a, c0.s, c0.v);
-      f += widen(c0.f);
-      if (i + 1 < i1) {
-        add_row<NB, NDPN, LT>(a, c1.s, c1.v);
-        f += widen(c1.f);
+    if constexpr (DEEP) {
+      Contrib<NB, NDPN, LT> c0, c1, n0, n1;
+      if (i < i1) c0.load(G, i, comp);
+      if (i + 1 < i1) c1.load(G, i + 1, comp);
+      while (i < i1) {
+        if (i + 2 < i1) n0.load(G, i + 2, comp);
+        if (i + 3 < i1) n1.load(G, i + 3, comp);
+        add_row<NB, NDPN, LT>(a, c0.s, c0.v);
+        f += widen(c0.f);
+        if (i + 1 < i1) {
+          add_row<NB, NDPN, LT>(a, c1.s, c1.v);
+          f += widen(c1.f);
+        }
+        c0 = n0;
+        c1 = n1;
+        i += 2;
       }
-      c0 = n0;
-      c1 = n1;
-      i += 2;
+    } else {
+      // one incidence in flight ahead of the one being added (fewer registers)
+      Contrib<NB, NDPN, LT> c0, n0;
+      if (i < i1) c0.load(G, i, comp);
+      while (i < i1) {
+        if (i + 1 < i1) n0.load(G, i + 1, comp);
+        add_row<NB, NDPN, LT>(a, c0.s, c0.v);
+        f += widen(c0.f);
+        c0 = n0;
+        ++i;
+      }
     }
     if (G.rhs) G.rhs[r] = f;
   }
@@ -198,14 +211,14 @@ __global__ void __launch_bounds__(128) k_gather(GatherArgs G) {
 }
 
 // The row tiles listed in tiles[0 .. gridDim.x).
-template <int NB, int NDPN, typename LT>
+template <int NB, int NDPN, typename LT, bool DEEP = true>
 __global__ void __launch_bounds__(128) k_gather_list(GatherArgs G, const int32_t* __restrict__ tiles) {
   extern __shared__ double acc[];
-  gather_tile<NB, NDPN, LT>(G, __ldg(tiles + blockIdx.x), blockDim.x, acc);
+  gather_tile<NB, NDPN, LT, DEEP>(G, __ldg(tiles + blockIdx.x), blockDim.x, acc);
 }
 
 fea_status launch_gather(int nb, int ndpn, bool mixed, const GatherArgs& G, int rows_per_tile,
                          int64_t max_tile_nnz, cudaStream_t s, const int32_t* tiles = nullptr,
-                         int64_t ntiles = -1);
+                         int64_t ntiles = -1, bool deep = true);
 
 }  // namespace fea

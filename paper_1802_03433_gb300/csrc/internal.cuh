@@ -79,6 +79,12 @@ struct Pattern {
   int64_t chunk = 0;
   int32_t* tile_list = nullptr;
   std::vector<int64_t> stage_ptr;
+  // Tile classes of the sequential scatter: tiles whose CSR span is at most
+  // `light_span` (the short rows) run in their own launch with a smaller
+  // shared-memory allocation and a lighter kernel, so more CTAs fit per SM.
+  int32_t* class_list = nullptr;   // heavy tiles, then light tiles
+  int64_t n_heavy = 0, n_light = 0;
+  int64_t heavy_span = 0, light_span = 0;
 };
 
 struct Scratch {
@@ -101,6 +107,8 @@ struct fea_mesh {
   fea::Scratch lm, fl;      // local matrices / local loads of the last assembly
   fea::Scratch gxs;         // per-incidence vertex gradients of the last backward
   int stages = 1;           // element chunks overlapped with the scatter (1 = no overlap)
+  int tile_classes = -1;    // sequential scatter: 0 one deep launch, 1 heavy/light split, 2 one light
+                            // launch, -1 automatic (2 when the pattern mixes long and short rows, else 0)
   cudaStream_t side = nullptr;             // scatter stream of the overlapped path
   cudaEvent_t chunk_ev[17] = {nullptr};    // chunk done (<= 16 stages) + join
   bool profile = false;     // record phase events in fea_assemble

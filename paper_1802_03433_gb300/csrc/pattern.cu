@@ -344,6 +344,14 @@ __global__ void k_tile_max(const int32_t* __restrict__ rp, int64_t n, int rows, 
   atomicMax(out, rp[r1] - rp[r0]);
 }
 
+__global__ void k_tile_span(const int32_t* __restrict__ rp, int64_t n, int rows, int32_t* __restrict__ span) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t r0 = t * rows;
+  if (r0 >= n) return;
+  const int64_t r1 = std::min<int64_t>(r0 + rows, n);
+  span[t] = rp[r1] - rp[r0];
+}
+
 // ------------------------------------------------------------------ P2 edges
 // Number of columns above the diagonal in each P1 row = edges (a, b), b > a.
 __global__ void k_upper_count(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int64_t N,
@@ -540,6 +548,7 @@ void free_base(Base* b) {
 void free_pattern(Pattern* p) {
   if (!p) return;
   dfree(p->tile_list);
+  dfree(p->class_list);
   if (p->own) {
     dfree(p->row_ptr);
     dfree(p->col_idx);
@@ -653,6 +662,41 @@ fea_status build_pattern(fea_mesh* m, int order, int ndpn, cudaStream_t s) {
   } while (0);
   if (st == FEA_OK && (int64_t)P->max_tile_nnz * 8 > 220 * 1024)
     st = fail(FEA_ERR_OVERFLOW, "a single row is too long for the shared-memory scatter");
+  if (st == FEA_OK) {
+    // two tile classes: spans up to 60% of the widest go to the light launch
+    const int64_t ntiles = (P->ndof + P->rows_per_tile - 1) / P->rows_per_tile;
+    std::vector<int32_t> span(std::max<int64_t>(ntiles, 1));
+    if (ntiles > 0) {
+      Tmp<int32_t> d;
+      if ((st = d.alloc(ntiles)) == FEA_OK) {
+        k_tile_span<<<blocks_for(ntiles, 256), 256, 0, s>>>(P->row_ptr, P->ndof, P->rows_per_tile, d.p);
+        cudaMemcpyAsync(span.data(), d.p, ntiles * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        cudaError_t ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) st = cuda_fail(ce, "tile spans");
+      }
+    }
+    if (st == FEA_OK) {
+      const int64_t cut = P->max_tile_nnz * 6 / 10;
+      std::vector<int32_t> list;
+      list.reserve(ntiles);
+      for (int64_t t = 0; t < ntiles; ++t)
+        if (span[t] > cut) {
+          list.push_back((int32_t)t);
+          P->heavy_span = std::max<int64_t>(P->heavy_span, span[t]);
+        }
+      P->n_heavy = (int64_t)list.size();
+      for (int64_t t = 0; t < ntiles; ++t)
+        if (span[t] <= cut) {
+          list.push_back((int32_t)t);
+          P->light_span = std::max<int64_t>(P->light_span, span[t]);
+        }
+      P->n_light = ntiles - P->n_heavy;
+      if ((st = dalloc(&P->class_list, std::max<size_t>(list.size(), 1))) == FEA_OK && !list.empty()) {
+        cudaError_t ce = cudaMemcpy(P->class_list, list.data(), list.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+        if (ce != cudaSuccess) st = cuda_fail(ce, "tile classes");
+      }
+    }
+  }
   if (st != FEA_OK) {
     free_pattern(P);
     return st;

@@ -268,3 +268,23 @@ def test_atomic_comparison_path_matches_oracle(torch_cuda, kind, n):
     m.check()
     assert row_scaled_error(o["rp"], o["vals"], v.cpu().numpy()) <= TOL_FP64
     assert vec_scaled_error(o["rhs"], r.cpu().numpy()) <= TOL_FP64
+
+
+@pytest.mark.parametrize("kind,n", [("p1_kappa", 12), ("p2_diffmass", 9), ("elasticity", 8)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_scatter_launch_shapes_bitwise_identical(torch_cuda, kind, n, prec):
+    """One deep launch, heavy/light split, one light launch: same bits."""
+    from paper_1802_03433_gb300 import fea
+    c = case(kind, n, seed=23)
+    m = fea.Mesh(c["coords"], c["tets"])
+    ref = None
+    for mode in (0, 1, 2):
+        fea.fea_mesh_set_scatter_classes(m.h, mode)
+        g = gpu_system(c, prec=prec, mesh=m)
+        if ref is None:
+            ref = g
+            continue
+        assert np.array_equal(g["vals"].view(np.uint64), ref["vals"].view(np.uint64)), mode
+        assert np.array_equal(g["rhs"].view(np.uint64), ref["rhs"].view(np.uint64)), mode
+    o = oracle_system(c)
+    assert row_scaled_error(o["rp"], o["vals"], ref["vals"]) <= (TOL_FP64 if prec == 0 else TOL_MIXED)
