@@ -30,6 +30,8 @@ def lib():
         _lib.orc_assemble.restype = C.c_int64
         _lib.orc_rows.restype = C.c_int64
         _lib.orc_assemble_grad.restype = C.c_int64
+        _lib.orc_tri_rule.restype = C.c_int
+        _lib.orc_assemble_tri.restype = C.c_int64
         _lib.orc_free.argtypes = [C.c_void_p]
     return _lib
 
@@ -207,3 +209,58 @@ def assemble_grad(coords, tets, order, edof, row_ptr, col_idx, grad_values, grad
     if rc < 0:
         raise RuntimeError("local entry without a slot in the pattern")
     return gk, gx
+
+
+# ---------------------------------------------------------------- 2-D triangles
+PAPER_2D = dict(S0=(1.0, 0.0, 0.0, 1.0), Sx=(0.0, -1.0, 1.0, 0.0), Sy=(0.0, -1.0, 1.0, 0.0), lam=1.0,
+                f=(36.0, 0.0, 0.0, -2.0, 0.0, -2.0))
+"""The paper's example (Sec. 4.2): sigma = [[1, -x-y], [x+y, 1]], lambda = 1,
+f = -2 (x^2 + y^2) + 36."""
+
+
+def _v(a, n):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(n))
+    return a
+
+
+def tri_rule(npts: int):
+    b = np.zeros((6, 3))
+    w = np.zeros(6)
+    n = lib().orc_tri_rule(npts, b.ctypes.data_as(_dp), w.ctypes.data_as(_dp))
+    if n == 0:
+        raise ValueError(f"no {npts}-point triangle rule")
+    return b[:n].copy(), w[:n].copy()
+
+
+def local_tri(X, S0=PAPER_2D["S0"], Sx=PAPER_2D["Sx"], Sy=PAPER_2D["Sy"], lam=PAPER_2D["lam"],
+              f=PAPER_2D["f"], npts=6):
+    """Local 3x3 matrices (row = test function), loads and det J of triangles X (n, 3, 2)."""
+    X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 3, 2)
+    n = X.shape[0]
+    Ke, Fe, det = np.empty((n, 3, 3)), np.empty((n, 3)), np.empty(n)
+    keep = [_v(S0, 4), _v(Sx, 4), _v(Sy, 4), _v(f, 6)]
+    lib().orc_local_tri(X.ctypes.data_as(_dp), C.c_int64(n), keep[0].ctypes.data_as(_dp),
+                        keep[1].ctypes.data_as(_dp), keep[2].ctypes.data_as(_dp), C.c_double(lam),
+                        keep[3].ctypes.data_as(_dp), C.c_int(npts), Ke.ctypes.data_as(_dp),
+                        Fe.ctypes.data_as(_dp), det.ctypes.data_as(_dp))
+    return Ke, Fe, det
+
+
+def assemble_tri(coords2, tris, row_ptr, col_idx, S0=PAPER_2D["S0"], Sx=PAPER_2D["Sx"], Sy=PAPER_2D["Sy"],
+                 lam=PAPER_2D["lam"], f=PAPER_2D["f"], npts=6):
+    """Assembled CSR values and load of the 2-D P1 problem (coords2: (2, N))."""
+    coords2 = np.ascontiguousarray(coords2, dtype=np.float64)
+    tris = np.ascontiguousarray(tris, dtype=np.int32)
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+    N = coords2.shape[1]
+    values, rhs = np.empty(int(row_ptr[-1])), np.empty(N)
+    keep = [_v(S0, 4), _v(Sx, 4), _v(Sy, 4), _v(f, 6)]
+    bad = lib().orc_assemble_tri(
+        C.c_int64(N), _d(coords2[0]), _d(coords2[1]), C.c_int64(tris.shape[1]), tris.ctypes.data_as(_ip),
+        keep[0].ctypes.data_as(_dp), keep[1].ctypes.data_as(_dp), keep[2].ctypes.data_as(_dp), C.c_double(lam),
+        keep[3].ctypes.data_as(_dp), C.c_int(npts), row_ptr.ctypes.data_as(_ip), col_idx.ctypes.data_as(_ip),
+        values.ctypes.data_as(_dp), rhs.ctypes.data_as(_dp))
+    if bad < 0:
+        raise RuntimeError("local entry without a slot in the pattern")
+    return values, rhs, int(bad)

@@ -545,4 +545,171 @@ int64_t orc_assemble_grad(int64_t n_nodes, const double* x, const double* y, con
   return 0;
 }
 
+
+}  // extern "C"
+
+namespace {
+
+// ---------------------------------------------------------------- 2-D triangles
+// The paper's worked example (Sec. 4.1-4.2): P1 triangles, Eq. 1 with a
+// matrix coefficient sigma(x, y) and a mass term lambda u, load f.
+//   sigma(x, y) = S0 + x Sx + y Sy (2 x 2, row-major, affine in x and y);
+//   f(x, y) = f0 + f1 x + f2 y + f3 x^2 + f4 x y + f5 y^2.
+// The bilinear form (grad v, sigma grad u): row = test function phi_a,
+// column = trial function phi_b, so A is not symmetric when sigma is not.
+// Triangle rules (barycentric points, weights summing to 1):
+//   1 point: centroid (degree 1); 3 points: permutations of (2/3, 1/6, 1/6),
+//   weight 1/3 (degree 2); 6 points (degree 4): permutations of
+//   (a, a, 1 - 2a) for a = (8 - sqrt 10 +- sqrt(38 - 44 sqrt(2/5))) / 18 with
+//   weights (620 +- sqrt(213125 - 53320 sqrt 10)) / 3720.
+// Matrix integrals use the 6-point rule (exact: integrands of degree <= 2);
+// the load uses the caller's rule.
+struct TriRule { int n; double bary[6][3]; double w[6]; };
+
+TriRule make_tri_rule(int npts) {
+  TriRule r{};
+  if (npts == 1) {
+    r.n = 1;
+    for (int i = 0; i < 3; ++i) r.bary[0][i] = 1.0 / 3.0;
+    r.w[0] = 1.0;
+  } else if (npts == 3) {
+    r.n = 3;
+    for (int q = 0; q < 3; ++q) {
+      for (int i = 0; i < 3; ++i) r.bary[q][i] = (i == q) ? 2.0 / 3.0 : 1.0 / 6.0;
+      r.w[q] = 1.0 / 3.0;
+    }
+  } else if (npts == 6) {
+    r.n = 6;
+    const double s10 = std::sqrt(10.0), t = std::sqrt(38.0 - 44.0 * std::sqrt(0.4));
+    const double a[2] = {(8.0 - s10 + t) / 18.0, (8.0 - s10 - t) / 18.0};
+    const double u = std::sqrt(213125.0 - 53320.0 * s10);
+    const double w[2] = {(620.0 + u) / 3720.0, (620.0 - u) / 3720.0};
+    int q = 0;
+    for (int c = 0; c < 2; ++c)
+      for (int odd = 0; odd < 3; ++odd, ++q) {
+        for (int i = 0; i < 3; ++i) r.bary[q][i] = (i == odd) ? 1.0 - 2.0 * a[c] : a[c];
+        r.w[q] = w[c];
+      }
+  }
+  return r;
+}
+
+struct Form2D {
+  double S0[4], Sx[4], Sy[4];
+  double lambda;
+  double f[6];
+  TriRule mrule, lrule;
+};
+
+// Local 3 x 3 matrix (row-major) and load of one triangle; returns det J.
+double element_tri(const Form2D& F, const double X[3][2], double* Ke, double* Fe) {
+  // J = [x1 - x0, x2 - x0] (columns); grad lambda_1,2 = rows of J^{-1}
+  const double J[2][2] = {{X[1][0] - X[0][0], X[2][0] - X[0][0]}, {X[1][1] - X[0][1], X[2][1] - X[0][1]}};
+  const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  const double area = std::fabs(det) / 2.0;
+  double g[3][2];
+  g[1][0] = J[1][1] / det;
+  g[1][1] = -J[0][1] / det;
+  g[2][0] = -J[1][0] / det;
+  g[2][1] = J[0][0] / det;
+  g[0][0] = -(g[1][0] + g[2][0]);
+  g[0][1] = -(g[1][1] + g[2][1]);
+  for (int i = 0; i < 9; ++i) Ke[i] = 0.0;
+  for (int i = 0; i < 3; ++i) Fe[i] = 0.0;
+  for (int q = 0; q < F.mrule.n; ++q) {
+    const double* L = F.mrule.bary[q];
+    const double x = L[0] * X[0][0] + L[1] * X[1][0] + L[2] * X[2][0];
+    const double y = L[0] * X[0][1] + L[1] * X[1][1] + L[2] * X[2][1];
+    double sig[4];
+    for (int k = 0; k < 4; ++k) sig[k] = F.S0[k] + x * F.Sx[k] + y * F.Sy[k];
+    const double wq = F.mrule.w[q] * area;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        const double sg0 = sig[0] * g[b][0] + sig[1] * g[b][1];
+        const double sg1 = sig[2] * g[b][0] + sig[3] * g[b][1];
+        Ke[3 * a + b] += wq * (g[a][0] * sg0 + g[a][1] * sg1 + F.lambda * L[a] * L[b]);
+      }
+  }
+  for (int q = 0; q < F.lrule.n; ++q) {
+    const double* L = F.lrule.bary[q];
+    const double x = L[0] * X[0][0] + L[1] * X[1][0] + L[2] * X[2][0];
+    const double y = L[0] * X[0][1] + L[1] * X[1][1] + L[2] * X[2][1];
+    const double fv = F.f[0] + F.f[1] * x + F.f[2] * y + F.f[3] * x * x + F.f[4] * x * y + F.f[5] * y * y;
+    const double wq = F.lrule.w[q] * area;
+    for (int a = 0; a < 3; ++a) Fe[a] += wq * fv * L[a];
+  }
+  return det;
+}
+
+Form2D make_form2d(const double* S0, const double* Sx, const double* Sy, double lambda, const double* f, int npts) {
+  Form2D F{};
+  for (int k = 0; k < 4; ++k) {
+    F.S0[k] = S0[k];
+    F.Sx[k] = Sx[k];
+    F.Sy[k] = Sy[k];
+  }
+  F.lambda = lambda;
+  for (int k = 0; k < 6; ++k) F.f[k] = f[k];
+  F.mrule = make_tri_rule(6);
+  F.lrule = make_tri_rule(npts);
+  return F;
+}
+
+}  // namespace
+
+extern "C" {
+
+int orc_tri_rule(int npts, double* bary, double* w) {
+  TriRule r = make_tri_rule(npts);
+  for (int q = 0; q < r.n; ++q) {
+    for (int i = 0; i < 3; ++i) bary[3 * q + i] = r.bary[q][i];
+    w[q] = r.w[q];
+  }
+  return r.n;
+}
+
+// Local matrices (n x 3 x 3) and loads (n x 3) of triangles X (n x 3 x 2).
+void orc_local_tri(const double* Xall, int64_t n, const double* S0, const double* Sx, const double* Sy,
+                   double lambda, const double* f, int npts, double* Ke, double* Fe, double* det) {
+  Form2D F = make_form2d(S0, Sx, Sy, lambda, f, npts);
+  for (int64_t e = 0; e < n; ++e) {
+    double X[3][2];
+    for (int v = 0; v < 3; ++v)
+      for (int c = 0; c < 2; ++c) X[v][c] = Xall[6 * e + 2 * v + c];
+    const double d = element_tri(F, X, Ke + 9 * e, Fe + 3 * e);
+    if (det) det[e] = d;
+  }
+}
+
+// Assembled CSR values and load of the 2-D problem (Eq. 3); tris: 3 x E SoA.
+// Returns the number of triangles with det J <= 0, or -1 on a missing slot.
+int64_t orc_assemble_tri(int64_t n_nodes, const double* x, const double* y, int64_t n_elems, const int32_t* tris,
+                         const double* S0, const double* Sx, const double* Sy, double lambda, const double* f,
+                         int npts, const int32_t* row_ptr, const int32_t* col_idx, double* values, double* rhs) {
+  Form2D F = make_form2d(S0, Sx, Sy, lambda, f, npts);
+  std::fill(values, values + row_ptr[n_nodes], 0.0);
+  std::fill(rhs, rhs + n_nodes, 0.0);
+  int64_t bad = 0;
+  double Ke[9], Fe[3];
+  for (int64_t e = 0; e < n_elems; ++e) {
+    double X[3][2];
+    int32_t nd[3];
+    for (int v = 0; v < 3; ++v) {
+      nd[v] = tris[v * n_elems + e];
+      X[v][0] = x[nd[v]];
+      X[v][1] = y[nd[v]];
+    }
+    if (!(element_tri(F, X, Ke, Fe) > 0)) ++bad;
+    for (int a = 0; a < 3; ++a) {
+      rhs[nd[a]] += Fe[a];
+      for (int b = 0; b < 3; ++b) {
+        const int64_t p = find_pos(row_ptr, col_idx, nd[a], nd[b]);
+        if (p < 0) return -1;
+        values[p] += Ke[3 * a + b];
+      }
+    }
+  }
+  return bad;
+}
+
 }  // extern "C"

@@ -162,3 +162,33 @@ def batch(n_meshes: int = 256, lo: int = 4, hi: int = 32, seed: int = 0) -> list
                         mass=0.0, f_kind="sinprod", f_amp=SIN_AMP,
                         npts=4 if order == 1 else 11))
     return out
+
+
+# --------------------------------------------------------------------------
+# 2-D: the unit square cut into n^2 squares, each split along its
+# (i, j) -> (i + 1, j + 1) diagonal into two counter-clockwise triangles, so an
+# interior node has 6 neighbours (the paper's 2-D P1 structure, Sec. 5).
+# Node id = i + (n + 1) j; element id = 2 (i + n j) + t; interior nodes move
+# by U[-0.2h, 0.2h] per coordinate.
+def tri_square(n: int, perturb: float = 0.2, seed: int = 0):
+    """(coords (2, N) float64, tris (3, 2 n^2) int32)."""
+    m = n + 1
+    h = 1.0 / n
+    g = np.arange(m, dtype=np.float64) * h
+    y, x = np.meshgrid(g, g, indexing="ij")
+    coords = np.stack([x.reshape(-1), y.reshape(-1)]).copy()
+    rng = np.random.default_rng(seed)
+    d = rng.uniform(-perturb * h, perturb * h, size=(m * m, 2))
+    idx = np.arange(m)
+    bi = (idx == 0) | (idx == n)
+    jj, ii = np.meshgrid(bi, bi, indexing="ij")
+    boundary = (ii | jj).reshape(-1)
+    if perturb != 0.0:
+        coords += np.where(boundary[:, None], 0.0, d).T
+    j, i = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    a = (i + m * j).reshape(-1)
+    b, c, dd = a + 1, a + m, a + m + 1
+    tris = np.empty((3, a.size, 2), dtype=np.int64)
+    tris[:, :, 0] = np.stack([a, b, dd])
+    tris[:, :, 1] = np.stack([a, dd, c])
+    return np.ascontiguousarray(coords), np.ascontiguousarray(tris.reshape(3, -1).astype(np.int32))

@@ -87,3 +87,36 @@ def ref_matrices(order):
     """(stiffness, mass) on the reference tet (0,0,0),(1,0,0),(0,1,0),(0,0,1)."""
     V = ((0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1))
     return local_exact(V, order, kappa=1, mass=0), local_exact(V, order, kappa=0, mass=1)
+
+
+# ---------------------------------------------------------------- 2-D
+t1, t2 = sp.symbols("t1 t2")
+
+
+def integrate_tri(V, expr):
+    """Exact integral of a polynomial in x, y over the triangle V."""
+    V = [[sp.Rational(c) for c in v] for v in V]
+    J = sp.Matrix([[V[1][i] - V[0][i], V[2][i] - V[0][i]] for i in range(2)])
+    sub = {x: V[0][0] + J[0, 0] * t1 + J[0, 1] * t2, y: V[0][1] + J[1, 0] * t1 + J[1, 1] * t2}
+    p = sp.Poly(sp.expand(sp.expand(expr).subs(sub)), t1, t2)
+    tot = sp.Rational(0)
+    for (a, b), coef in p.terms():
+        tot += coef * sp.Rational(factorial(a) * factorial(b), factorial(a + b + 2))
+    return abs(J.det()) * tot
+
+
+def local_exact_tri(V, S0, Sx, Sy, lam, f):
+    """Exact 3x3 local matrix (row = test function) and load of
+    (grad v, sigma grad u) + lam (v, u) = (v, f), sigma = S0 + x Sx + y Sy."""
+    V = [[sp.Rational(c) for c in v] for v in V]
+    M = sp.Matrix([[1, 1, 1], [V[0][0], V[1][0], V[2][0]], [V[0][1], V[1][1], V[2][1]]])
+    L = [sp.expand(l) for l in M.inv() * sp.Matrix([1, x, y])]
+    sig = sp.Matrix(2, 2, [sp.nsimplify(S0[k]) + x * sp.nsimplify(Sx[k]) + y * sp.nsimplify(Sy[k]) for k in range(4)])
+    g = [sp.Matrix([sp.diff(l, x), sp.diff(l, y)]) for l in L]
+    K = sp.zeros(3, 3)
+    for a in range(3):
+        for b in range(3):
+            K[a, b] = integrate_tri(V, (g[a].T * sig * g[b])[0] + sp.nsimplify(lam) * L[a] * L[b])
+    fx = sum(sp.nsimplify(c) * mono for c, mono in zip(f, [1, x, y, x * x, x * y, y * y]))
+    F = [integrate_tri(V, fx * L[a]) for a in range(3)]
+    return K, F
