@@ -279,6 +279,7 @@ def run_ours(args):
         forms["adjoint"] = bench_adjoint(fea, torch, dev, small, args.warmup, flush)
         forms["elasticity_128"] = bench_plain(fea, torch, dev, "elasticity", 128, small, args.warmup, flush)
         forms["p1_kappa_96"] = bench_plain(fea, torch, dev, "p1_kappa", 96, small, args.warmup, flush)
+        forms["paper_2d"] = bench_paper_2d(fea, torch, dev, small, args.warmup, flush)
 
     # end to end through the public API with host buffers: H2D of the step's
     # inputs (coordinates, coefficients) from pinned memory, assembly, D2H of
@@ -526,6 +527,42 @@ def bench_plain(fea, torch, dev, kind, n, steps, warmup, flush):
     m.check()
     m.close()
     return out
+
+
+def bench_paper_2d(fea, torch, dev, steps, warmup, flush, n=2048):
+    """The paper's own 2-D example (Sec. 4.2) at the top of its 10K-10M node
+    range: P1 triangles on n^2 squares, sigma = [[1, -x-y], [x+y, 1]],
+    lambda = 1, f = -2 (x^2 + y^2) + 36, 6-point load rule, FP64."""
+    coords, tris = mg.tri_square(n, 0.2, 0)
+    m = fea.Mesh(coords, tris, device=dev)
+    ndof, nnz = m.pattern(1, 1)
+    vals = torch.empty(nnz, dtype=torch.float64, device=dev)
+    rhs = torch.empty(ndof, dtype=torch.float64, device=dev)
+    form = fea.make_form2d()
+    fea.fea_profile_enable(m.h, True)
+    for _ in range(warmup):
+        fea.fea_assemble_2d(m.h, form, vals, rhs)
+    torch.cuda.synchronize()
+    tot, pe, ps = 0.0, 0.0, 0.0
+    for k in range(steps):
+        flush.fill_(k)
+        a, c = _events(torch)
+        a.record()
+        fea.fea_assemble_2d(m.h, form, vals, rhs)
+        c.record()
+        e_ms, s_ms = fea.fea_profile_last(m.h)
+        tot += a.elapsed_time(c)
+        pe += e_ms
+        ps += s_ms
+    m.check()
+    m.close()
+    E = tris.shape[1]
+    ms = tot / steps
+    alg = 16 * ndof + 12 * E + 8 * nnz + 8 * ndof  # coords, connectivity, values, rhs
+    return {"value": E / (ms / 1e3), "unit": "elements/s", "ms_per_step": ms, "elem_ms": pe / steps,
+            "scatter_ms": ps / steps, "elements": E, "nodes": ndof, "nnz": nnz,
+            "hbm_algorithmic_gbs": alg / (ms / 1e3) / 1e9, "hbm_frac": alg / (ms / 1e3) / 1e9 / _hbm_peak(),
+            "config": f"paper's 2-D example on {n}^2 squares (P1 triangles, perturbed), FP64"}
 
 
 # ---------------------------------------------------------------- CPU oracle

@@ -130,6 +130,14 @@ typedef struct {
 fea_status fea_mesh_create(const double* x, const double* y, const double* z, int64_t n_nodes,
                            const int32_t* tets, int64_t n_elems, void* stream, fea_mesh** out);
 
+/* Create a handle for a 2-D mesh of P1 triangles (the paper's worked example,
+ * Sec. 4.1-4.2).  x, y: [n_nodes] FP64 node coordinates (device, referenced);
+ * tris: [3][n_elems] int32 SoA connectivity, counter-clockwise (copied).
+ * Only fea_pattern(mesh, FEA_P1, 1, ...) and fea_assemble_2d apply to it.
+ * Synchronises; validates the connectivity (FEA_ERR_INDEX). */
+fea_status fea_mesh_create_tri(const double* x, const double* y, int64_t n_nodes, const int32_t* tris,
+                               int64_t n_elems, void* stream, fea_mesh** out);
+
 /* Re-point the referenced coordinate arrays (same n_nodes). */
 fea_status fea_mesh_set_coords(fea_mesh* mesh, const double* x, const double* y, const double* z);
 
@@ -180,6 +188,26 @@ fea_status fea_dof_table_copy(fea_mesh* mesh, int32_t order, int32_t* edof, void
  * handle (allocated on first use, which synchronises once). */
 fea_status fea_assemble(fea_mesh* mesh, const fea_form* form, const fea_coeffs* coeffs,
                         const fea_quadrature* quad, double* values, double* rhs, void* stream);
+
+/* The 2-D weak form of Eq. 2 on P1 triangles:
+ *   (grad v, sigma grad u) + lambda (v, u) = (v, f),
+ *   sigma(x, y) = sigma0 + x sigma_x + y sigma_y  (2 x 2, row-major; need not
+ *                 be symmetric - the paper's example is [[1, -x-y], [x+y, 1]]),
+ *   f(x, y) = f0 + f1 x + f2 y + f3 x^2 + f4 x y + f5 y^2. */
+typedef struct {
+  double sigma0[4], sigma_x[4], sigma_y[4];
+  double lambda;
+  double f[6];
+  int32_t npts; /* load rule on triangles: 1, 3 (degree 2) or 6 (degree 4) */
+} fea_form2d;
+
+/* Assemble the 2-D system (Eq. 3) on a triangle mesh: values [nnz], rhs
+ * [n_nodes] (may be NULL) in FP64.  The stiffness and mass integrals are
+ * exact (constant gradients, affine sigma); the load uses the rule npts.  A is
+ * not symmetric when sigma is not; the scatter is the same deterministic one
+ * as fea_assemble.  Asynchronous. */
+fea_status fea_assemble_2d(fea_mesh* mesh, const fea_form2d* form, double* values, double* rhs,
+                           void* stream);
 
 /* fea_assemble without any device allocation (the paper has no counterpart;
  * this is a deployment variant).  For callers that cannot let a library

@@ -56,7 +56,6 @@ constexpr int ADJ_T = 128;
 template <int ORDER, bool MASS, int LOAD, int NPTS>
 __global__ void __launch_bounds__(ADJ_T) k_adjoint(AdjArgs A) {
   constexpr int NB = ORDER == 1 ? 4 : 10;
-  constexpr int SW = ORDER == 1 ? 4 : 16;
   const int64_t e = (int64_t)blockIdx.x * ADJ_T + threadIdx.x;
   if (e >= A.E) return;
   double X[4][3];

@@ -41,6 +41,7 @@ fea_status gather_one(const GatherArgs& G, int rows, int64_t max_tile_nnz, cudaS
 
 fea_status launch_gather(int nb, int ndpn, bool mixed, const GatherArgs& G, int rows, int64_t max_tile_nnz,
                          cudaStream_t s, const int32_t* tiles, int64_t ntiles, bool deep) {
+  if (nb == 3 && ndpn == 1 && !mixed) return gather_one<3, 1, double>(G, rows, max_tile_nnz, s, tiles, ntiles, deep);
   if (nb == 4 && ndpn == 1)
     return mixed ? gather_one<4, 1, float>(G, rows, max_tile_nnz, s, tiles, ntiles, deep)
                  : gather_one<4, 1, double>(G, rows, max_tile_nnz, s, tiles, ntiles, deep);
@@ -65,6 +66,7 @@ fea_status launch_elements(const fea_form* form, const ElemArgs& A, int load, in
 
 fea_status assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* co, const fea_quadrature* q,
                     double* values, double* rhs, cudaStream_t s) {
+  if (m->nvert != 4) return fail(FEA_ERR_ARG, "fea_assemble takes tetrahedral meshes (use fea_assemble_2d)");
   const int order = form->order;
   const int ndpn = form->kind == FEA_ELASTICITY ? 3 : 1;
   Pattern* P = m->pat[order][ndpn];

@@ -66,6 +66,7 @@ extern "C" fea_status fea_assemble_atomic(fea_mesh* m, const fea_form* form, con
   if (q->npts != 1 && q->npts != 4 && q->npts != 11) return fail(FEA_ERR_ARG, "npts must be 1, 4 or 11");
   if (q->prec != FEA_FP64) return fail(FEA_ERR_ARG, "the atomic comparison path runs in FP64");
   if (co->f_kind < FEA_LOAD_NONE || co->f_kind > FEA_LOAD_SINPROD) return fail(FEA_ERR_ARG, "unknown load kind");
+  if (m->nvert != 4) return fail(FEA_ERR_ARG, "fea_assemble_atomic takes tetrahedral meshes");
   const int order = form->order;
   const int ndpn = form->kind == FEA_ELASTICITY ? 3 : 1;
   const Pattern* P = m->pat[order][ndpn];

@@ -188,6 +188,7 @@ fea_status fea_batch_create(fea_mesh* const* meshes, int32_t n, const fea_form* 
   int np1 = 0, np2 = 0;
   for (int k = 0; k < n; ++k) {
     if (!meshes[k]) return fail(FEA_ERR_ARG, "NULL mesh in batch");
+    if (meshes[k]->nvert != 4) return fail(FEA_ERR_ARG, "batches hold tetrahedral meshes");
     if (forms[k].kind == FEA_ELASTICITY) return fail(FEA_ERR_ARG, "batches hold scalar forms");
     if (forms[k].order != FEA_P1 && forms[k].order != FEA_P2) return fail(FEA_ERR_ARG, "bad order");
     if (quads[k].prec != FEA_FP64) return fail(FEA_ERR_ARG, "batches run in FP64");
@@ -342,7 +343,7 @@ fea_status fea_batch_tune(fea_batch* b, void* stream, int32_t* params) {
     }
     return FEA_OK;
   };
-  int bt = b->elem_tile, be = b->elem_grid, bg = b->gather_grid;
+  int bt = b->elem_tile, be = b->elem_grid;
   float best = 1e30f;
   // elements per work item x persistent element-kernel CTAs
   for (int t : tiles) {
@@ -362,7 +363,7 @@ fea_status fea_batch_tune(fea_batch* b, void* stream, int32_t* params) {
   b->elem_tile = bt;
   b->elem_grid = be;
   FEA_TRY(build_items(b));
-  b->gather_grid = bg = b->n_gitems;
+  b->gather_grid = b->n_gitems;
   cudaEventDestroy(a);
   cudaEventDestroy(c);
   FEA_TRY(rebuild_graph(b));

@@ -222,6 +222,34 @@ __global__ void __launch_bounds__(ELEM_T) k_elem_scalar(ElemArgs A) {
   if (e < A.e1) elem_scalar_body<ORDER, MASS, LOAD, NPTS, R, ATOMIC>(A, e);
 }
 
+// Deterministic-path output of the elasticity kernel: local rows in
+// incidence order (whole sectors) and local loads.
+template <int LOAD, int NPTS, typename R>
+__device__ __forceinline__ void elast_store(const ElemArgs& A, int64_t e, const double X[4][3], double adet,
+                                           const R Kl[12][12]) {
+  int32_t pos[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) pos[a] = __ldg(A.ipos + a * A.E + e);
+  constexpr int LS = lstride(12, sizeof(R));
+#pragma unroll
+  for (int r = 0; r < 12; ++r) store_row<12>(static_cast<R*>(A.Lm) + ((int64_t)pos[r / 3] * 3 + r % 3) * LS, Kl[r]);
+  if constexpr (LOAD != LOAD_NONE) {
+    R Xr[4][3];
+    vertices_r<R>(X, Xr);
+    R Fs[4];
+    shape_load<1, NPTS, LOAD, R>(Xr, Fs);
+    const double vol = adet * (1.0 / 6.0);
+    const R f0 = R(A.fp[0] * vol), f1 = R(A.fp[1] * vol), f2 = R(A.fp[2] * vol);
+    R* __restrict__ Fl = static_cast<R*>(A.Fl);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      Fl[(int64_t)pos[a] * 3 + 0] = f0 * Fs[a];
+      Fl[(int64_t)pos[a] * 3 + 1] = f1 * Fs[a];
+      Fl[(int64_t)pos[a] * 3 + 2] = f2 * Fs[a];
+    }
+  }
+}
+
 // ---------------------------------------------------------------- elasticity
 // K_(a,i),(b,j) = |T| [lam d_i phi_a d_j phi_b + mu d_j phi_a d_i phi_b
 //                      + mu delta_ij grad phi_a . grad phi_b]  on P1 tets.
@@ -287,28 +315,8 @@ __global__ void __launch_bounds__(ELEM_T) k_elem_elast(ElemArgs A) {
 #pragma unroll
         for (int i = 0; i < 3; ++i) atomicAdd(A.rhs + 3 * (int64_t)nd[a] + i, A.fp[i] * vol * (double)Fs[a]);
     }
-    return;
-  }
-  int32_t pos[4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) pos[a] = __ldg(A.ipos + a * A.E + e);
-  constexpr int LS = lstride(12, sizeof(R));
-#pragma unroll
-  for (int r = 0; r < 12; ++r) store_row<12>(static_cast<R*>(A.Lm) + ((int64_t)pos[r / 3] * 3 + r % 3) * LS, Kl[r]);
-  if constexpr (LOAD != LOAD_NONE) {
-    R Xr[4][3];
-    vertices_r<R>(X, Xr);
-    R Fs[4];
-    shape_load<1, NPTS, LOAD, R>(Xr, Fs);
-    const double vol = adet * (1.0 / 6.0);
-    const R f0 = R(A.fp[0] * vol), f1 = R(A.fp[1] * vol), f2 = R(A.fp[2] * vol);
-    R* __restrict__ Fl = static_cast<R*>(A.Fl);
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      Fl[(int64_t)pos[a] * 3 + 0] = f0 * Fs[a];
-      Fl[(int64_t)pos[a] * 3 + 1] = f1 * Fs[a];
-      Fl[(int64_t)pos[a] * 3 + 2] = f2 * Fs[a];
-    }
+  } else {
+    elast_store<LOAD, NPTS, R>(A, e, X, adet, Kl);
   }
 }
 

@@ -140,9 +140,46 @@ fea_status fea_mesh_create(const double* x, const double* y, const double* z, in
   return FEA_OK;
 }
 
+fea_status fea_mesh_create_tri(const double* x, const double* y, int64_t n_nodes, const int32_t* tris,
+                               int64_t n_elems, void* stream, fea_mesh** out) {
+  g_last_error.clear();
+  if (!out) return fail(FEA_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!x || !y) return fail(FEA_ERR_ARG, "coordinate array is NULL");
+  if (n_nodes <= 0 || n_nodes > (int64_t)INT32_MAX) return fail(FEA_ERR_ARG, "n_nodes must be in [1, INT32_MAX]");
+  if (n_elems < 0 || n_elems > (int64_t)INT32_MAX / 10) return fail(FEA_ERR_ARG, "n_elems out of range");
+  if (n_elems > 0 && !tris) return fail(FEA_ERR_ARG, "tris is NULL");
+  if (!aligned(x, 8) || !aligned(y, 8) || (tris && !aligned(tris, 4))) return fail(FEA_ERR_ARG, "misaligned array");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  fea_mesh* m = new fea_mesh();
+  m->x = x;
+  m->y = y;
+  m->z = nullptr;
+  m->nvert = 3;
+  m->n_nodes = n_nodes;
+  m->n_elems = n_elems;
+  cudaError_t e = cudaMalloc(&m->err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&m->tets, 3 * (size_t)(n_elems > 0 ? n_elems : 1) * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->err, 0, sizeof(int), s);
+  if (e == cudaSuccess && n_elems > 0)
+    e = cudaMemcpyAsync(m->tets, tris, 3 * (size_t)n_elems * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) {
+    fea_status st = cuda_fail(e, "fea_mesh_create_tri");
+    fea_mesh_destroy(m);
+    return st;
+  }
+  fea_status st = validate_connectivity(m, s);
+  if (st != FEA_OK) {
+    fea_mesh_destroy(m);
+    return st;
+  }
+  *out = m;
+  return FEA_OK;
+}
+
 fea_status fea_mesh_set_coords(fea_mesh* m, const double* x, const double* y, const double* z) {
-  if (!m || !x || !y || !z) return fail(FEA_ERR_ARG, "NULL argument");
-  if (!aligned(x, 8) || !aligned(y, 8) || !aligned(z, 8)) return fail(FEA_ERR_ARG, "misaligned array");
+  if (!m || !x || !y || (!z && m->nvert == 4)) return fail(FEA_ERR_ARG, "NULL argument");
+  if (!aligned(x, 8) || !aligned(y, 8) || (z && !aligned(z, 8))) return fail(FEA_ERR_ARG, "misaligned array");
   m->x = x;
   m->y = y;
   m->z = z;
@@ -193,6 +230,8 @@ fea_status fea_pattern(fea_mesh* m, int32_t order, int32_t dofs_per_node, int64_
   if (order != FEA_P1 && order != FEA_P2) return fail(FEA_ERR_ARG, "order must be FEA_P1 or FEA_P2");
   if (dofs_per_node != 1 && dofs_per_node != 3) return fail(FEA_ERR_ARG, "dofs_per_node must be 1 or 3");
   if (order == FEA_P2 && dofs_per_node != 1) return fail(FEA_ERR_ARG, "vector dofs are P1 only");
+  if (m->nvert == 3 && (order != FEA_P1 || dofs_per_node != 1))
+    return fail(FEA_ERR_ARG, "triangle meshes have the scalar P1 pattern only");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   FEA_TRY(build_pattern(m, order, dofs_per_node, s));
   FEA_TRY(read_and_clear_err(m, s));
@@ -239,6 +278,7 @@ fea_status fea_assemble_backward(fea_mesh* m, const fea_form* form, const fea_co
                                  double* grad_kappa, double* grad_x, void* stream) {
   FEA_TRY(check_form(m, form, coeffs, quad));
   if (form->kind == FEA_ELASTICITY) return fail(FEA_ERR_ARG, "backward is implemented for the scalar forms");
+  if (m->nvert != 4) return fail(FEA_ERR_ARG, "backward takes tetrahedral meshes");
   if (quad->prec != FEA_FP64) return fail(FEA_ERR_ARG, "backward runs in FP64");
   return assemble_backward(m, form, coeffs, quad, grad_values, grad_rhs, grad_kappa, grad_x,
                            static_cast<cudaStream_t>(stream));

@@ -111,10 +111,10 @@ __device__ __forceinline__ void load_row(const float* __restrict__ p, float v[NL
 // Slots of the NB local columns of one incidence (1 byte each).
 template <int NB>
 __device__ __forceinline__ void load_slots(const uint8_t* __restrict__ slot, int64_t i, int s[NB]) {
-  if constexpr (NB == 4) {
+  if constexpr (NB <= 4) {
     const uint32_t w = __ldg(reinterpret_cast<const uint32_t*>(slot) + i);
 #pragma unroll
-    for (int b = 0; b < 4; ++b) s[b] = (w >> (8 * b)) & 0xFF;
+    for (int b = 0; b < NB; ++b) s[b] = (w >> (8 * b)) & 0xFF;
   } else {
     const uint4 w = __ldg(reinterpret_cast<const uint4*>(slot) + i);
     const uint32_t ws[4] = {w.x, w.y, w.z, w.w};

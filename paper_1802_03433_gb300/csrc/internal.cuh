@@ -100,7 +100,8 @@ struct fea_mesh {
   const double* z = nullptr;
   int64_t n_nodes = 0;
   int64_t n_elems = 0;
-  int32_t* tets = nullptr;  // [4][E] owned copy
+  int nvert = 4;            // 4: tetrahedra, 3: triangles (z unused)
+  int32_t* tets = nullptr;  // [nvert][E] owned copy
   int* err = nullptr;       // device error word
   fea::Base* base[3] = {nullptr, nullptr, nullptr};          // by order
   fea::Pattern* pat[3][4] = {{nullptr}};                     // by order, ndpn

@@ -69,6 +69,7 @@ extern "C" fea_status fea_assemble_noalloc(fea_mesh* m, const fea_form* form, co
   if (q->prec != FEA_FP64 && q->prec != FEA_MIXED) return fail(FEA_ERR_ARG, "prec must be FEA_FP64 or FEA_MIXED");
   if (co->f_kind < FEA_LOAD_NONE || co->f_kind > FEA_LOAD_SINPROD) return fail(FEA_ERR_ARG, "unknown load kind");
   if (!values) return fail(FEA_ERR_ARG, "values is NULL");
+  if (m->nvert != 4) return fail(FEA_ERR_ARG, "fea_assemble_noalloc takes tetrahedral meshes");
   const int order = form->order;
   const int ndpn = form->kind == FEA_ELASTICITY ? 3 : 1;
   Pattern* P = m->pat[order][ndpn];

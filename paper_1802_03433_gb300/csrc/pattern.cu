@@ -184,20 +184,21 @@ fea_status scan_to_ptr32(const int32_t* cnt, int64_t n, int32_t* ptr, int64_t* t
 }
 
 // ------------------------------------------------------------------ validation
+template <int NV>
 __global__ void k_validate(const int32_t* __restrict__ tets, int64_t E, int64_t N, int* err) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
-  int32_t v[4];
+  int32_t v[NV];
   bool bad = false;
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
+  for (int a = 0; a < NV; ++a) {
     v[a] = tets[a * E + e];
     bad |= v[a] < 0 || (int64_t)v[a] >= N;
   }
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < NV; ++a)
 #pragma unroll
-    for (int b = a + 1; b < 4; ++b) bad |= v[a] == v[b];
+    for (int b = a + 1; b < NV; ++b) bad |= v[a] == v[b];
   if (bad) atomicOr(err, DEV_ERR_INDEX);
 }
 
@@ -493,7 +494,7 @@ fea_status rows_and_slots(fea_mesh* m, Base* B, cudaStream_t s) {
   k_row_unique<NB><<<uniq_blocks, 32 * UNIQ_WARPS, 0, s>>>(n, B->inc_ptr, B->inc, B->edof, E, B->rp, nullptr,
                                                            B->ci, m->err);
   FEA_TRY(check_err(m, s, "pattern"));
-  constexpr int SW = NB == 4 ? 4 : 16;
+  constexpr int SW = NB <= 4 ? 4 : 16;
   B->slot_width = SW;
   FEA_TRY(dalloc(&B->slot, (size_t)E * NB * SW));
   k_slots<NB, SW><<<blocks_for(n, 128), 128, 0, s>>>(n, B->inc_ptr, B->inc, B->edof, E, B->rp, B->ci, B->slot,
@@ -557,8 +558,10 @@ void free_pattern(Pattern* p) {
 }
 
 fea_status validate_connectivity(fea_mesh* m, cudaStream_t s) {
-  if (m->n_elems > 0)
-    k_validate<<<blocks_for(m->n_elems, 256), 256, 0, s>>>(m->tets, m->n_elems, m->n_nodes, m->err);
+  if (m->n_elems > 0) {
+    if (m->nvert == 3) k_validate<3><<<blocks_for(m->n_elems, 256), 256, 0, s>>>(m->tets, m->n_elems, m->n_nodes, m->err);
+    else k_validate<4><<<blocks_for(m->n_elems, 256), 256, 0, s>>>(m->tets, m->n_elems, m->n_nodes, m->err);
+  }
   return check_err(m, s, "mesh");
 }
 
@@ -566,7 +569,7 @@ fea_status build_base(fea_mesh* m, int order, cudaStream_t s) {
   if (m->base[order]) return FEA_OK;
   if (order == 2) FEA_TRY(build_base(m, 1, s));
   Base* B = new Base();
-  B->nb = order == 1 ? 4 : 10;
+  B->nb = order == 1 ? m->nvert : 10;
   const int64_t E = m->n_elems, N = m->n_nodes;
   fea_status st = FEA_OK;
   do {
@@ -599,7 +602,7 @@ fea_status build_base(fea_mesh* m, int order, cudaStream_t s) {
       }
     }
     if ((st = incidences(m, B, s)) != FEA_OK) break;
-    st = order == 1 ? rows_and_slots<4>(m, B, s) : rows_and_slots<10>(m, B, s);
+    st = B->nb == 3 ? rows_and_slots<3>(m, B, s) : B->nb == 4 ? rows_and_slots<4>(m, B, s) : rows_and_slots<10>(m, B, s);
   } while (0);
   if (st != FEA_OK) {
     free_base(B);

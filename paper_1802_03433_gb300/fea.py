@@ -46,6 +46,19 @@ class fea_quadrature(C.Structure):
     _fields_ = [("npts", C.c_int32), ("prec", C.c_int32)]
 
 
+class fea_form2d(C.Structure):
+    _fields_ = [("sigma0", C.c_double * 4), ("sigma_x", C.c_double * 4), ("sigma_y", C.c_double * 4),
+                ("lambda_", C.c_double), ("f", C.c_double * 6), ("npts", C.c_int32)]
+
+
+def make_form2d(sigma0=(1.0, 0.0, 0.0, 1.0), sigma_x=(0.0, -1.0, 1.0, 0.0), sigma_y=(0.0, -1.0, 1.0, 0.0),
+                lam=1.0, f=(36.0, 0.0, 0.0, -2.0, 0.0, -2.0), npts=6):
+    """Defaults: the paper's example (Sec. 4.2), sigma = [[1, -x-y], [x+y, 1]],
+    lambda = 1, f = -2 (x^2 + y^2) + 36."""
+    D4, D6 = C.c_double * 4, C.c_double * 6
+    return fea_form2d(D4(*sigma0), D4(*sigma_x), D4(*sigma_y), lam, D6(*f), npts)
+
+
 _lib = None
 _vp = C.c_void_p
 
@@ -62,6 +75,8 @@ def lib() -> C.CDLL:
     sig = {
         "fea_mesh_create": [_vp, _vp, _vp, C.c_int64, _vp, C.c_int64, _vp, C.POINTER(_vp)],
         "fea_mesh_set_coords": [_vp, _vp, _vp, _vp],
+        "fea_mesh_create_tri": [_vp, _vp, C.c_int64, _vp, C.c_int64, _vp, C.POINTER(_vp)],
+        "fea_assemble_2d": [_vp, C.POINTER(fea_form2d), _vp, _vp, _vp],
         "fea_mesh_destroy": [_vp],
         "fea_mesh_set_stages": [_vp, C.c_int32],
         "fea_mesh_set_scatter_classes": [_vp, C.c_int32],
@@ -131,6 +146,21 @@ def fea_mesh_create(x, y, z, tets, stream=None):
     _check(lib().fea_mesh_create(_ptr(x), _ptr(y), _ptr(z), x.numel(), _ptr(tets), tets.shape[1],
                                  _stream(stream), C.byref(h)), "fea_mesh_create")
     return h
+
+
+def fea_mesh_create_tri(x, y, tris, stream=None):
+    """Handle of a 2-D triangle mesh: x, y [N] float64, tris [3, E] int32 (CUDA)."""
+    for t, n in ((x, "x"), (y, "y")):
+        _dev(t, torch.float64, n)
+    _dev(tris, torch.int32, "tris")
+    h = C.c_void_p()
+    _check(lib().fea_mesh_create_tri(_ptr(x), _ptr(y), x.numel(), _ptr(tris), tris.shape[1], _stream(stream),
+                                     C.byref(h)), "fea_mesh_create_tri")
+    return h
+
+
+def fea_assemble_2d(h, form2d, values, rhs=None, stream=None):
+    _check(lib().fea_assemble_2d(h, C.byref(form2d), _ptr(values), _ptr(rhs), _stream(stream)), "fea_assemble_2d")
 
 
 def fea_mesh_set_coords(h, x, y, z):
@@ -303,15 +333,20 @@ class Batch:
 
 # ---------------------------------------------------------------- convenience wrapper
 class Mesh:
-    """Owns an fea_mesh handle plus the device tensors it references."""
+    """Owns an fea_mesh handle plus the device tensors it references.
+    coords (3, N) with tets (4, E), or coords (2, N) with triangles (3, E)."""
 
     def __init__(self, coords, tets, device="cuda", stream=None):
         c = torch.as_tensor(coords, dtype=torch.float64).to(device).contiguous()
-        self.x, self.y, self.z = c[0].contiguous(), c[1].contiguous(), c[2].contiguous()
         self.tets = torch.as_tensor(tets, dtype=torch.int32).to(device).contiguous()
-        self.n_nodes = self.x.numel()
         self.n_elems = self.tets.shape[1]
-        self.h = fea_mesh_create(self.x, self.y, self.z, self.tets, stream)
+        if c.shape[0] == 2:
+            self.x, self.y, self.z = c[0].contiguous(), c[1].contiguous(), None
+            self.h = fea_mesh_create_tri(self.x, self.y, self.tets, stream)
+        else:
+            self.x, self.y, self.z = c[0].contiguous(), c[1].contiguous(), c[2].contiguous()
+            self.h = fea_mesh_create(self.x, self.y, self.z, self.tets, stream)
+        self.n_nodes = self.x.numel()
         self._pat = {}
 
     def set_coords(self, x, y, z):
@@ -333,7 +368,7 @@ class Mesh:
 
     def dof_table(self, order=1):
         self.pattern(order, 1)
-        nb = 4 if order == 1 else 10
+        nb = self.tets.shape[0] if order == 1 else 10
         ed = torch.empty((nb, self.n_elems), dtype=torch.int32, device=self.x.device)
         if self.n_elems:
             fea_dof_table_copy(self.h, order, ed)
@@ -348,6 +383,15 @@ class Mesh:
         if rhs is None and with_rhs:
             rhs = torch.empty(ndof, dtype=torch.float64, device=dev)
         fea_assemble(self.h, form, coeffs, quad, values, rhs, stream)
+        return values[:nnz], rhs
+
+    def assemble_2d(self, form2d, values=None, rhs=None, with_rhs=True, stream=None):
+        ndof, nnz = self.pattern(1, 1)
+        if values is None:
+            values = torch.empty(max(nnz, 1), dtype=torch.float64, device=self.x.device)
+        if rhs is None and with_rhs:
+            rhs = torch.empty(ndof, dtype=torch.float64, device=self.x.device)
+        fea_assemble_2d(self.h, form2d, values, rhs, stream)
         return values[:nnz], rhs
 
     def check(self, stream=None):
