@@ -242,14 +242,18 @@ def run_ours(args):
     # mixed-precision form on the same GPU and workload
     forms = {"fp64": {"value": value, "ms_per_step": total_ms / args.steps, "elem_ms": elem_ms,
                       "scatter_ms": scat_ms}}
-    if not args.no_forms:
+    def want(name):
+        return not args.no_forms and (args.forms == "all" or name in args.forms.split(","))
+
+    if want("mixed"):
         m_total, _, m_phase, _ = timed_loop(fea.FEA_MIXED, max(3, args.steps // 2), args.warmup)
         ms = m_total / max(3, args.steps // 2)
         forms["mixed"] = {"value": ws * E / (ms / 1e3), "ms_per_step": ms,
                           "elem_ms": statistics.mean(p[0] for p in m_phase),
                           "scatter_ms": statistics.mean(p[1] for p in m_phase)}
 
-    if not args.no_forms:
+    small = max(3, args.steps // 4)
+    if want("atomic_alg1"):
         # the paper's sparse Algorithm 1 on the same workload: row search +
         # global FP64 atomicAdd (no scratch, no reproducibility)
         quad = fea.make_quadrature(d["npts"], fea.FEA_FP64)
@@ -274,11 +278,15 @@ def run_ours(args):
                                                                                   runs[1].view(torch.int64))),
                                 "note": "paper's sparse Algorithm 1: global FP64 atomicAdd after a row search"}
         del runs
-        small = max(3, args.steps // 4)
+    if want("batched"):
         forms["batched"] = bench_batched(fea, torch, dev, small, args.warmup, flush)
+    if want("adjoint"):
         forms["adjoint"] = bench_adjoint(fea, torch, dev, small, args.warmup, flush)
+    if want("elasticity_128"):
         forms["elasticity_128"] = bench_plain(fea, torch, dev, "elasticity", 128, small, args.warmup, flush)
+    if want("p1_kappa_96"):
         forms["p1_kappa_96"] = bench_plain(fea, torch, dev, "p1_kappa", 96, small, args.warmup, flush)
+    if want("paper_2d"):
         forms["paper_2d"] = bench_paper_2d(fea, torch, dev, small, args.warmup, flush)
 
     # end to end through the public API with host buffers: H2D of the step's
@@ -641,6 +649,9 @@ def main():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-forms", action="store_true")
+    p.add_argument("--forms", default="all",
+                   help="comma list of extra forms to time: mixed, atomic_alg1, batched, adjoint, elasticity_128, "
+                        "p1_kappa_96, paper_2d (default all)")
     args = p.parse_args()
     if args.warmup < 3:
         args.warmup = 3

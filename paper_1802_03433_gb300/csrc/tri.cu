@@ -1,13 +1,22 @@
 // The paper's 2-D worked example (Sec. 4.1-4.2): P1 triangles with the weak
 // form (grad v, sigma grad u) + lambda (v, u) = (v, f) of Eq. 2, where sigma is
 // an affine 2 x 2 matrix field (not necessarily symmetric) and f a quadratic.
-// One thread per triangle: the gradients of the P1 basis are constant on the
-// element and sigma is affine, so  int_T grad phi_a . sigma grad phi_b =
-// |T| grad phi_a . sigma(centroid) grad phi_b  exactly; the mass term is
-// |T| (1 + delta_ab) / 12; the load is a quadrature of f phi_a with the
-// requested rule (1, 3 or 6 points).  The local matrix is stored in full
-// (rows and columns differ), and the same deterministic scatter as the
-// tetrahedral path sums it into CSR.
+// One thread per triangle.  The gradients of the P1 basis are constant on
+// the element and sigma is affine, so
+//   int_T grad phi_a . sigma grad phi_b = |T| grad phi_a . sigma(c) grad phi_b
+// exactly (c the centroid); with grad phi_a = n_a / det (n_a the edge
+// opposite vertex a turned by 90 degrees, det = 2 |T|) that is
+// n_a . sigma(c) n_b / (2 det).  The mass term is lambda |T| (1 + delta_ab) / 12.
+// The load integrates f phi_a with the requested rule (1, 3 or 6 points).
+// Because f is quadratic, f(c + d) = f(c) + grad f(c) . d + q(d) with
+// q(d) = d^T (H / 2) d, and every rule point is c + t d_v (d_v = X_v - c), so
+// the points' f values come from f(c), grad f(c) . d_v and q(d_v).  The
+// 6-point rule has degree 4 >= 3, so it returns the exact integral, which in
+// this form is |T| [f(c) / 3 + grad f(c) . d_a / 12 + (sum_b q(d_b) + 2 q(d_a)) / 60]
+// (from int_T phi_a phi_b phi_c = |T| (1 + delta_ab + delta_ac + delta_bc +
+// 2 delta_abc) / 60 and sum_b d_b = 0); the kernel evaluates that closed form.
+// The local matrix is stored in full (rows and columns differ), and the same
+// deterministic scatter as the tetrahedral path sums it into CSR.
 #include <cuda_runtime.h>
 
 #include "elem_kernels.cuh"
@@ -16,30 +25,13 @@
 namespace fea {
 namespace {
 
-// 6-point degree-4 triangle rule: permutations of (a, a, 1 - 2a),
-// a = (8 - sqrt 10 +- sqrt(38 - 44 sqrt(2/5))) / 18, weights
-// (620 +- sqrt(213125 - 53320 sqrt 10)) / 3720.
-constexpr double T6A1 = 0.4459484909159648863183292538830519883991;
-constexpr double T6A2 = 0.09157621350977074345957146340220150785433;
-constexpr double T6W1 = 0.2233815896780114656950070084331228043703;
-constexpr double T6W2 = 0.1099517436553218676383263249002105289631;
-
-__host__ __device__ constexpr double tri_bary(int npts, int q, int v) {
-  return npts == 1 ? 1.0 / 3.0
-       : npts == 3 ? (v == q ? 2.0 / 3.0 : 1.0 / 6.0)
-       : (q < 3 ? (v == q ? 1.0 - 2.0 * T6A1 : T6A1) : (v == q - 3 ? 1.0 - 2.0 * T6A2 : T6A2));
-}
-__host__ __device__ constexpr double tri_weight(int npts, int q) {
-  return npts == 1 ? 1.0 : npts == 3 ? 1.0 / 3.0 : (q < 3 ? T6W1 : T6W2);
-}
-
 struct TriArgs {
   const double* x;
   const double* y;
   const int32_t* tris;  // [3][E]
   int64_t E;
   double S0[4], Sx[4], Sy[4];
-  double lambda;
+  double lam24;  // lambda / 24
   double f[6];
   const int32_t* ipos;
   double* Lm;
@@ -58,50 +50,76 @@ __global__ void __launch_bounds__(128) k_elem_tri(TriArgs A) {
     X[a][0] = __ldg(A.x + n);
     X[a][1] = __ldg(A.y + n);
   }
+  int32_t pos[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) pos[a] = __ldg(A.ipos + a * A.E + e);
   const double e1x = X[1][0] - X[0][0], e1y = X[1][1] - X[0][1];
   const double e2x = X[2][0] - X[0][0], e2y = X[2][1] - X[0][1];
   const double det = fma(e1x, e2y, -e2x * e1y);
   if (!(det > 0.0)) atomicOr(A.err, DEV_ERR_DEGENERATE);
-  const double inv = 1.0 / det, area = fabs(det) * 0.5;
-  // rows of J^{-1}: grad lambda_1, grad lambda_2; grad lambda_0 = -(sum)
-  double g[3][2];
-  g[1][0] = e2y * inv;
-  g[1][1] = -e2x * inv;
-  g[2][0] = -e1y * inv;
-  g[2][1] = e1x * inv;
-  g[0][0] = -(g[1][0] + g[2][0]);
-  g[0][1] = -(g[1][1] + g[2][1]);
+  const double adet = fabs(det);
+  const double h = 0.5 / adet;
+  // n_a = det * grad phi_a
+  double n[3][2];
+  n[1][0] = e2y;
+  n[1][1] = -e2x;
+  n[2][0] = -e1y;
+  n[2][1] = e1x;
+  n[0][0] = -(e2y - e1y);
+  n[0][1] = -(e1x - e2x);
   const double xc = (X[0][0] + X[1][0] + X[2][0]) * (1.0 / 3.0);
   const double yc = (X[0][1] + X[1][1] + X[2][1]) * (1.0 / 3.0);
-  double sg[4];  // area * sigma(centroid)
+  double sg[4];  // sigma(c) / (2 det)
 #pragma unroll
-  for (int k = 0; k < 4; ++k) sg[k] = area * fma(xc, A.Sx[k], fma(yc, A.Sy[k], A.S0[k]));
-  const double m = A.lambda * area * (1.0 / 12.0);
-  int32_t pos[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) pos[a] = __ldg(A.ipos + a * A.E + e);
+  for (int k = 0; k < 4; ++k) sg[k] = h * fma(xc, A.Sx[k], fma(yc, A.Sy[k], A.S0[k]));
+  const double m = A.lam24 * adet;  // lambda |T| / 12
+  const double m2 = m + m;
   double K[3][3];
 #pragma unroll
   for (int b = 0; b < 3; ++b) {
-    const double s0 = fma(sg[0], g[b][0], sg[1] * g[b][1]);
-    const double s1 = fma(sg[2], g[b][0], sg[3] * g[b][1]);
+    const double s0 = fma(sg[0], n[b][0], sg[1] * n[b][1]);
+    const double s1 = fma(sg[2], n[b][0], sg[3] * n[b][1]);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) K[a][b] = fma(g[a][0], s0, fma(g[a][1], s1, a == b ? 2.0 * m : m));
+    for (int a = 0; a < 3; ++a) K[a][b] = fma(n[a][0], s0, fma(n[a][1], s1, a == b ? m2 : m));
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) st_v4(A.Lm + (int64_t)pos[a] * 4, K[a][0], K[a][1], K[a][2], 0.0);
   if constexpr (LOAD) {
-    double F[3] = {0.0, 0.0, 0.0};
-    static_for<NPTS>([&](auto Q) {
-      constexpr int q = Q;
-      const double x = fma(tri_bary(NPTS, q, 0), X[0][0], fma(tri_bary(NPTS, q, 1), X[1][0], tri_bary(NPTS, q, 2) * X[2][0]));
-      const double y = fma(tri_bary(NPTS, q, 0), X[0][1], fma(tri_bary(NPTS, q, 1), X[1][1], tri_bary(NPTS, q, 2) * X[2][1]));
-      const double fv = fma(fma(A.f[3], x, A.f[4] * y + A.f[1]), x, fma(A.f[5], y, A.f[2]) * y + A.f[0]);
+    const double* f = A.f;
+    const double fc = fma(fma(f[3], xc, fma(f[4], yc, f[1])), xc, fma(fma(f[5], yc, f[2]), yc, f[0]));
+    const double area = 0.5 * adet;
+    double F[3];
+    if constexpr (NPTS == 1) {
+      const double v = area * (1.0 / 3.0) * fc;
 #pragma unroll
-      for (int a = 0; a < 3; ++a) F[a] = fma(tri_weight(NPTS, q) * tri_bary(NPTS, q, a), fv, F[a]);
-    });
+      for (int a = 0; a < 3; ++a) F[a] = v;
+    } else {
+      const double gx = fma(2.0 * f[3], xc, fma(f[4], yc, f[1]));
+      const double gy = fma(2.0 * f[5], yc, fma(f[4], xc, f[2]));
+      double l[3], q[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) A.Fl[pos[a]] = area * F[a];
+      for (int a = 0; a < 3; ++a) {
+        const double dx = X[a][0] - xc, dy = X[a][1] - yc;
+        l[a] = fma(gx, dx, gy * dy);
+        q[a] = fma(fma(f[3], dx, f[4] * dy), dx, f[5] * dy * dy);
+      }
+      if constexpr (NPTS == 3) {
+        // points c + d_v / 2 (barycentric 2/3, 1/6, 1/6), weights |T| / 3
+        double fq[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) fq[a] = fma(0.25, q[a], fma(0.5, l[a], fc));
+        const double base = (fq[0] + fq[1] + fq[2]) * (area * (1.0 / 18.0));
+        const double w = area * (1.0 / 6.0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) F[a] = fma(w, fq[a], base);
+      } else {
+        const double base = area * fma(q[0] + q[1] + q[2], 1.0 / 60.0, fc * (1.0 / 3.0));
+#pragma unroll
+        for (int a = 0; a < 3; ++a) F[a] = fma(area, fma(l[a], 1.0 / 12.0, q[a] * (1.0 / 30.0)), base);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) A.Fl[pos[a]] = F[a];
   }
 }
 
@@ -142,7 +160,7 @@ extern "C" fea_status fea_assemble_2d(fea_mesh* m, const fea_form2d* form, doubl
     A.Sx[k] = form->sigma_x[k];
     A.Sy[k] = form->sigma_y[k];
   }
-  A.lambda = form->lambda;
+  A.lam24 = form->lambda / 24.0;
   for (int k = 0; k < 6; ++k) A.f[k] = form->f[k];
   A.ipos = B->ipos;
   A.Lm = static_cast<double*>(m->lm.ptr);
