@@ -32,6 +32,7 @@ def lib():
         _lib.orc_assemble_grad.restype = C.c_int64
         _lib.orc_tri_rule.restype = C.c_int
         _lib.orc_assemble_tri.restype = C.c_int64
+        _lib.orc_assemble_user.restype = C.c_int64
         _lib.orc_free.argtypes = [C.c_void_p]
     return _lib
 
@@ -264,3 +265,55 @@ def assemble_tri(coords2, tris, row_ptr, col_idx, S0=PAPER_2D["S0"], Sx=PAPER_2D
     if bad < 0:
         raise RuntimeError("local entry without a slot in the pattern")
     return values, rhs, int(bad)
+
+
+# ---------------------------------------------------------------- user coefficients
+POINT_FN = C.CFUNCTYPE(C.c_double, C.c_double, C.c_double, C.c_double)
+
+
+def _point_fn(fn):
+    if fn is None:
+        return None, C.cast(None, POINT_FN)
+    cb = POINT_FN(lambda x, y, z: float(fn(x, y, z)))
+    return cb, cb
+
+
+def assemble_user(coords, tets, order, edof, row_ptr, col_idx, kfn=None, ffn=None, kappa=None,
+                  kappa_const=1.0, mass=0.0, npts=11):
+    """CSR values and load of -div(kappa_T k(x) grad u) + mass u = f(x) with
+    Python point functions k(x, y, z) and f(x, y, z) (None: k = 1, f = 0);
+    stiffness and load by the npts rule (stiffness by the exact 11-point rule
+    when k is None), mass exact."""
+    coords = np.ascontiguousarray(coords, dtype=np.float64)
+    tets = np.ascontiguousarray(tets, dtype=np.int32)
+    edof = np.ascontiguousarray(edof, dtype=np.int32)
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+    (kappa,) = _keep(kappa)
+    ndof = row_ptr.size - 1
+    values, rhs = np.empty(int(row_ptr[-1])), np.empty(ndof)
+    kkeep, kcb = _point_fn(kfn)
+    fkeep, fcb = _point_fn(ffn)
+    bad = lib().orc_assemble_user(
+        C.c_int64(coords.shape[1]), _d(coords[0]), _d(coords[1]), _d(coords[2]), C.c_int64(tets.shape[1]),
+        tets.ctypes.data_as(_ip), C.c_int(order), edof.ctypes.data_as(_ip), C.c_double(mass), _d(kappa),
+        C.c_double(kappa_const), kcb, fcb, C.c_int(npts), C.c_int64(ndof), row_ptr.ctypes.data_as(_ip),
+        col_idx.ctypes.data_as(_ip), values.ctypes.data_as(_dp), rhs.ctypes.data_as(_dp))
+    del kkeep, fkeep
+    if bad < 0:
+        raise RuntimeError("local entry without a slot in the pattern")
+    return values, rhs, int(bad)
+
+
+def local_user(X, order=1, mass=0.0, kfn=None, ffn=None, npts=11):
+    """Local matrices (n, nb, nb) and loads (n, nb) of the user-coefficient form, kappa_T = 1."""
+    X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 4, 3)
+    n = X.shape[0]
+    nb = 4 if order == 1 else 10
+    Ke, Fe = np.empty((n, nb, nb)), np.empty((n, nb))
+    kkeep, kcb = _point_fn(kfn)
+    fkeep, fcb = _point_fn(ffn)
+    lib().orc_local_user(X.ctypes.data_as(_dp), C.c_int64(n), C.c_int(order), C.c_double(mass), kcb, fcb,
+                         C.c_int(npts), Ke.ctypes.data_as(_dp), Fe.ctypes.data_as(_dp))
+    del kkeep, fkeep
+    return Ke, Fe

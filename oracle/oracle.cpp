@@ -713,3 +713,158 @@ int64_t orc_assemble_tri(int64_t n_nodes, const double* x, const double* y, int6
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- user coefficients
+// Scalar form  -div(kappa_T k(x) grad u) + mass_coef u = f(x)  on P1/P2 tets,
+// with k and f caller-supplied point functions.  The paper's system compiles
+// the user's symbolic weak form into the kernel at run time (Sec. 5, runtime
+// compilation); whatever the compiled kernel does, the integrals it must
+// reach are these, taken literally:
+//   * stiffness: sum over the caller's rule of w_q |T| kappa_T k(x_q)
+//     grad phi_a(x_q) . grad phi_b(x_q); when k is absent (k = 1) the
+//     11-point rule is used instead, which is exact for it;
+//   * mass: 11-point rule (exact for P1 and P2 on affine tets);
+//   * load: sum over the caller's rule of w_q |T| f(x_q) phi_a(x_q)
+//     (zero when f is absent).
+namespace {
+
+typedef double (*PointFn)(double, double, double);
+
+double element_user(int order, double mass_coef, double kappa_T, PointFn kfn, PointFn ffn, int npts,
+                    const double X[4][3], double* Ke, double* Fe) {
+  const int nb = (order == 1) ? 4 : 10;
+  double J[3][3];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) J[r][c] = X[c + 1][r] - X[0][r];
+  // J^{-1} by cofactors
+  double adj[3][3];
+  adj[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  adj[0][1] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+  adj[0][2] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+  adj[1][0] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  adj[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+  adj[1][2] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+  adj[2][0] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  adj[2][1] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+  adj[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  const double det = J[0][0] * adj[0][0] + J[0][1] * adj[1][0] + J[0][2] * adj[2][0];
+  const double vol = std::fabs(det) / 6.0;
+  double gl[4][3];
+  for (int i = 1; i < 4; ++i)
+    for (int c = 0; c < 3; ++c) gl[i][c] = adj[i - 1][c] / det;
+  for (int c = 0; c < 3; ++c) gl[0][c] = -(gl[1][c] + gl[2][c] + gl[3][c]);
+  for (int i = 0; i < nb * nb; ++i) Ke[i] = 0.0;
+  for (int i = 0; i < nb; ++i) Fe[i] = 0.0;
+
+  auto point = [&](const double* L, double xq[3]) {
+    for (int c = 0; c < 3; ++c) {
+      xq[c] = 0.0;
+      for (int v = 0; v < 4; ++v) xq[c] += L[v] * X[v][c];
+    }
+  };
+  // stiffness
+  const Rule ks = make_rule(kfn ? npts : 11);
+  for (int q = 0; q < ks.n; ++q) {
+    const double* L = ks.bary[q];
+    double dl[10][4];
+    basis_dlambda(order, L, dl);
+    double gphi[10][3];
+    for (int a = 0; a < nb; ++a)
+      for (int c = 0; c < 3; ++c) {
+        gphi[a][c] = 0.0;
+        for (int i = 0; i < 4; ++i) gphi[a][c] += dl[a][i] * gl[i][c];
+      }
+    double k = kappa_T;
+    if (kfn) {
+      double xq[3];
+      point(L, xq);
+      k *= kfn(xq[0], xq[1], xq[2]);
+    }
+    const double wq = ks.w[q] * vol;
+    for (int a = 0; a < nb; ++a)
+      for (int b = 0; b < nb; ++b)
+        Ke[a * nb + b] += wq * k * (gphi[a][0] * gphi[b][0] + gphi[a][1] * gphi[b][1] + gphi[a][2] * gphi[b][2]);
+  }
+  // mass
+  if (mass_coef != 0.0) {
+    const Rule ms = make_rule(11);
+    for (int q = 0; q < ms.n; ++q) {
+      double phi[10];
+      basis(order, ms.bary[q], phi);
+      const double wq = ms.w[q] * vol;
+      for (int a = 0; a < nb; ++a)
+        for (int b = 0; b < nb; ++b) Ke[a * nb + b] += wq * mass_coef * phi[a] * phi[b];
+    }
+  }
+  // load
+  if (ffn) {
+    const Rule ls = make_rule(npts);
+    for (int q = 0; q < ls.n; ++q) {
+      double phi[10], xq[3];
+      basis(order, ls.bary[q], phi);
+      point(ls.bary[q], xq);
+      const double wq = ls.w[q] * vol;
+      const double f = ffn(xq[0], xq[1], xq[2]);
+      for (int a = 0; a < nb; ++a) Fe[a] += wq * f * phi[a];
+    }
+  }
+  return det;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Assembled CSR values and load of the user-coefficient scalar form (see
+// element_user).  kappa: per-element kappa_T, or kappa_const when NULL;
+// kfn / ffn may be NULL.  Returns the count of elements with det J <= 0, or
+// -1 if a local entry has no slot in the pattern.
+int64_t orc_assemble_user(int64_t n_nodes, const double* x, const double* y, const double* z, int64_t n_elems,
+                          const int32_t* tets, int order, const int32_t* edof, double mass_coef,
+                          const double* kappa, double kappa_const, PointFn kfn, PointFn ffn, int npts,
+                          int64_t ndof, const int32_t* row_ptr, const int32_t* col_idx, double* values,
+                          double* rhs) {
+  (void)n_nodes;
+  const int nb = (order == 1) ? 4 : 10;
+  std::fill(values, values + row_ptr[ndof], 0.0);
+  std::fill(rhs, rhs + ndof, 0.0);
+  std::vector<double> Ke(nb * nb), Fe(nb);
+  int64_t bad = 0;
+  for (int64_t e = 0; e < n_elems; ++e) {
+    double X[4][3];
+    for (int v = 0; v < 4; ++v) {
+      const int32_t n = tets[v * n_elems + e];
+      X[v][0] = x[n];
+      X[v][1] = y[n];
+      X[v][2] = z[n];
+    }
+    const double det = element_user(order, mass_coef, kappa ? kappa[e] : kappa_const, kfn, ffn, npts, X,
+                                    Ke.data(), Fe.data());
+    if (!(det > 0)) ++bad;
+    for (int a = 0; a < nb; ++a) {
+      const int64_t ra = edof[a * n_elems + e];
+      rhs[ra] += Fe[a];
+      for (int b = 0; b < nb; ++b) {
+        const int64_t p = find_pos(row_ptr, col_idx, ra, edof[b * n_elems + e]);
+        if (p < 0) return -1;
+        values[p] += Ke[a * nb + b];
+      }
+    }
+  }
+  return bad;
+}
+
+// Local matrices (nb x nb) and loads (nb) of a list of elements for the
+// user-coefficient form; kappa_T = 1.
+void orc_local_user(const double* Xall /* n x 4 x 3 */, int64_t n, int order, double mass_coef, PointFn kfn,
+                    PointFn ffn, int npts, double* Ke_out, double* Fe_out) {
+  const int nb = (order == 1) ? 4 : 10;
+  for (int64_t e = 0; e < n; ++e) {
+    double X[4][3];
+    for (int v = 0; v < 4; ++v)
+      for (int c = 0; c < 3; ++c) X[v][c] = Xall[12 * e + 3 * v + c];
+    element_user(order, mass_coef, 1.0, kfn, ffn, npts, X, Ke_out + e * nb * nb, Fe_out + e * nb);
+  }
+}
+
+}  // extern "C"
