@@ -286,6 +286,8 @@ def run_ours(args):
         forms["elasticity_128"] = bench_plain(fea, torch, dev, "elasticity", 128, small, args.warmup, flush)
     if want("p1_kappa_96"):
         forms["p1_kappa_96"] = bench_plain(fea, torch, dev, "p1_kappa", 96, small, args.warmup, flush)
+    if want("jit"):
+        forms["jit"] = bench_jit(fea, torch, dev, small, args.warmup, flush)
     if want("paper_2d"):
         forms["paper_2d"] = bench_paper_2d(fea, torch, dev, small, args.warmup, flush)
 
@@ -573,6 +575,56 @@ def bench_paper_2d(fea, torch, dev, steps, warmup, flush, n=2048):
             "config": f"paper's 2-D example on {n}^2 squares (P1 triangles, perturbed), FP64"}
 
 
+def bench_jit(fea, torch, dev, steps, warmup, flush, n=64):
+    """Runtime-specialised (NVRTC) P2 diffusion + mass on the 64^3 cube:
+    compile time, the first call including compile + load, and steady
+    throughput - once for the same mathematics as the precompiled headline
+    kernel (no k, f = 3 pi^2 sin sin sin) and once with a spatially varying
+    coefficient k(x) = 1 + sin(3x) cos(2y) / 2 + z^2 inside the integral."""
+    d = make_inputs("p2_diffmass", n, seed=0)
+    m = fea.Mesh(d["coords"], d["tets"], device=dev)
+    ndof, nnz = m.pattern(2, 1)
+    kap = torch.as_tensor(d["kappa"], device=dev)
+    co = fea.make_coeffs(kappa=kap, f_param=(mg.SIN_AMP, 0.0, 0.0, 0.0))
+    form = fea.make_form(fea.FEA_DIFFUSION_MASS, 2, 1.0)
+    q = fea.make_quadrature(11, fea.FEA_FP64)
+    vals = torch.empty(nnz, dtype=torch.float64, device=dev)
+    rhs = torch.empty(ndof, dtype=torch.float64, device=dev)
+    fexpr = "p0*sinpi_fp64(x)*sinpi_fp64(y)*sinpi_fp64(z)"
+    E = d["tets"].shape[1]
+    fea.fea_profile_enable(m.h, True)
+    out = {}
+    for name, kexpr in (("same_as_headline", None), ("k_of_x", "1 + 0.5*sin(3*x)*cos(2*y) + z*z")):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        j = fea.fea_jit_compile(form, q, kexpr, fexpr)
+        fea.fea_jit_assemble(m.h, j, co, vals, rhs)
+        torch.cuda.synchronize()
+        first_ms = (time.perf_counter() - t0) * 1e3
+        compile_ms, cubin, hit = fea.fea_jit_info(j)
+        for _ in range(warmup):
+            fea.fea_jit_assemble(m.h, j, co, vals, rhs)
+        torch.cuda.synchronize()
+        tot, pe = 0.0, 0.0
+        for k in range(steps):
+            flush.fill_(k)
+            a, c = _events(torch)
+            a.record()
+            fea.fea_jit_assemble(m.h, j, co, vals, rhs)
+            c.record()
+            pe += fea.fea_profile_last(m.h)[0]
+            tot += a.elapsed_time(c)
+        ms = tot / steps
+        out[name] = {"value": E / (ms / 1e3), "unit": "elements/s", "ms_per_step": ms, "elem_ms": pe / steps,
+                     "compile_ms": compile_ms, "cache_hit": hit, "cubin_bytes": cubin,
+                     "first_call_ms_including_compile": first_ms, "k_expr": kexpr, "f_expr": fexpr}
+        fea.fea_jit_destroy(j)
+    m.check()
+    m.close()
+    out["config"] = f"P2 diffusion + mass, {n}^3 cube, 11-point rule, FP64, kernels compiled at run time (NVRTC)"
+    return out
+
+
 # ---------------------------------------------------------------- CPU oracle
 CPU_SAMPLE_N = {"p2_diffmass": 40, "p1_poisson": 64, "p1_kappa": 64, "elasticity": 32}
 
@@ -651,7 +703,7 @@ def main():
     p.add_argument("--no-forms", action="store_true")
     p.add_argument("--forms", default="all",
                    help="comma list of extra forms to time: mixed, atomic_alg1, batched, adjoint, elasticity_128, "
-                        "p1_kappa_96, paper_2d (default all)")
+                        "p1_kappa_96, paper_2d, jit (default all)")
     args = p.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -314,6 +314,51 @@ fea_status fea_diag_sinpi(const double* x, int64_t n, double* mine, double* lib,
  * with independent DFMA chains on every SM.  Synchronises. */
 fea_status fea_diag_fp64_rate(double* flops_per_s, void* stream);
 
+/* ---------------------------------------------------------------- runtime specialisation
+ * Sec. 5 (runtime compilation): the paper turns the user's weak form into
+ * kernel source and compiles it with NVRTC while the program runs.  Here the
+ * user gives two CUDA C++ expressions of type double in the variables x, y, z
+ * (the physical point), the parameters p0..p3 (fea_coeffs.f_param at
+ * assembly time) and the constant pi, using CUDA's device math functions
+ * (sin, exp, pow, sinpi, ...) and the library's sinpi_fp64:
+ *   kappa_expr : k(x) inside the stiffness integral, -div(kappa_T k(x) grad u)
+ *                with kappa_T from fea_coeffs (per element or constant);
+ *                NULL means k = 1;
+ *   f_expr     : the load f(x); NULL means no load vector.
+ * Expressions may not contain ; { } # quotes, backslashes or comments.
+ * Integrals use the rule quad->npts: the stiffness as
+ * sum_q w_q |T| kappa_T k(x_q) grad phi_a . grad phi_b (exact, whatever the
+ * rule, when k is NULL), the load as sum_q w_q |T| f(x_q) phi_a; the mass
+ * term (FEA_DIFFUSION_MASS, form->mass_coef) is exact.  quad->prec selects
+ * FP64 or the mixed split (quadrature products in FP32).  Scalar forms only
+ * (FEA_POISSON, FEA_DIFFUSION_MASS), P1 or P2 tetrahedra. */
+typedef struct fea_jit fea_jit;
+
+/* Compile (NVRTC, host only: no GPU needed) the element kernel for the
+ * expressions and return a handle owning its sm_103a cubin.  Compiled
+ * sources are cached per process: the same specialisation compiles once.
+ * FEA_ERR_ARG with the compiler log in fea_last_error if they do not compile. */
+fea_status fea_jit_compile(const fea_form* form, const fea_quadrature* quad, const char* kappa_expr,
+                           const char* f_expr, fea_jit** out);
+
+/* Wall time of the fea_jit_compile call (ms), cubin size, and whether it was
+ * served from the process cache (1) or compiled (0).  NULL outputs skipped. */
+fea_status fea_jit_info(const fea_jit* jit, double* compile_ms, int64_t* cubin_bytes, int32_t* cache_hit);
+
+/* Generated kernel source and NVRTC log of a handle (owned by the handle). */
+const char* fea_jit_source(const fea_jit* jit);
+const char* fea_jit_log(const fea_jit* jit);
+
+/* Assemble with a compiled handle: CSR values [nnz] and, iff the handle has
+ * an f expression, the load rhs [ndof] (both FP64, device, overwritten).
+ * The pattern of (order, 1) must be built.  The first call loads the cubin
+ * (synchronises once); later calls are asynchronous. */
+fea_status fea_jit_assemble(fea_mesh* mesh, fea_jit* jit, const fea_coeffs* coeffs, double* values, double* rhs,
+                            void* stream);
+
+/* Release a handle (and its loaded module). */
+fea_status fea_jit_destroy(fea_jit* jit);
+
 /* Message for the last error on the calling thread ("" if none). */
 const char* fea_last_error(void);
 

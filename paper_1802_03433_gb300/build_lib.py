@@ -29,6 +29,41 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
+def cuda_lib_dir() -> str:
+    root = os.path.dirname(os.path.dirname(os.path.realpath(nvcc())))
+    for d in (os.path.join(root, "lib64"), os.path.join(root, "lib")):
+        if os.path.exists(os.path.join(d, "libnvrtc.so")):
+            return d
+    raise RuntimeError(f"libnvrtc.so not found under {root}")
+
+
+# Headers the runtime-compiled kernels include (NVRTC has no file system view
+# of csrc/, so jit.cu carries their text).
+JIT_HEADERS = ["devcommon.cuh", "element.cuh", "vecmem.cuh", "elem_user.cuh"]
+
+
+def gen_jit_headers() -> str:
+    out = os.path.join(OUT, "jit_headers.inc")
+    texts = []
+    for h in JIT_HEADERS:
+        with open(os.path.join(CSRC, h)) as f:
+            t = f.read()
+        if ')FEAJIT"' in t:
+            raise RuntimeError(f"{h} contains the raw-string delimiter")
+        texts.append(t)
+    body = ["// Generated by build_lib.py: the headers the runtime-compiled kernels include.",
+            f"static const int JIT_HEADER_COUNT = {len(JIT_HEADERS)};",
+            "static const char* const JIT_HEADER_NAMES[] = {" + ", ".join(f'"{h}"' for h in JIT_HEADERS) + "};",
+            "static const char* const JIT_HEADER_SOURCES[] = {"]
+    body.append(",\n".join(f'R"FEAJIT({t})FEAJIT"' for t in texts))
+    body.append("};\n")
+    new = "\n".join(body)
+    if not os.path.exists(out) or open(out).read() != new:
+        with open(out, "w") as f:
+            f.write(new)
+    return out
+
+
 def _stale(srcs, target) -> bool:
     if not os.path.exists(target):
         return True
@@ -44,12 +79,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     if not force and not _stale(cus + hdrs + [__file__], LIB):
         return LIB
     cc = nvcc()
+    gen_jit_headers()
     extra = ["-Xptxas", "-v"] if ptxas_info else []
 
     def compile_one(src):
         obj = os.path.join(OUT, os.path.basename(src) + ".o")
         if force or _stale([src] + hdrs + [__file__], obj):
-            cmd = [cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+            cmd = [cc, *ARCH, *FLAGS, *extra, "-I", OUT, "-c", src, "-o", obj]
             r = subprocess.run(cmd, capture_output=True, text=True)
             if r.returncode != 0:
                 raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stdout}\n{r.stderr}")
@@ -61,7 +97,9 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     with cf.ThreadPoolExecutor(workers) as ex:
         objs = list(ex.map(compile_one, cus))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [cc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs]
+    libdir = cuda_lib_dir()
+    cmd = [cc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-L", libdir, "-lnvrtc",
+           "-Xlinker", f"-rpath={libdir}"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

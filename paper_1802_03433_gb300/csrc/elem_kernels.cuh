@@ -8,8 +8,6 @@
 // local matrix come from the same upper-triangle value (bitwise symmetric).
 #pragma once
 
-#include <type_traits>
-
 #include "element.cuh"
 #include "internal.cuh"
 #include "vecmem.cuh"
@@ -55,28 +53,6 @@ __device__ __forceinline__ void atomic_add_entry(const ElemArgs& A, int64_t row,
     }
 }
 
-// Store one local row of NL values of type R at p (32-byte aligned) as whole
-// 32-byte sectors, zero padding included up to lstride.
-template <int NL>
-__device__ __forceinline__ void store_row(double* __restrict__ p, const double* v) {
-  constexpr int LS = lstride(NL, 8);
-#pragma unroll
-  for (int k = 0; k < LS / 4; ++k)
-    st_v4(p + 4 * k, 4 * k < NL ? v[4 * k] : 0.0, 4 * k + 1 < NL ? v[4 * k + 1] : 0.0,
-          4 * k + 2 < NL ? v[4 * k + 2] : 0.0, 4 * k + 3 < NL ? v[4 * k + 3] : 0.0);
-}
-template <int NL>
-__device__ __forceinline__ void store_row(float* __restrict__ p, const float* v) {
-  constexpr int LS = lstride(NL, 4);
-#pragma unroll
-  for (int k = 0; k < LS / 8; ++k) {
-    float w[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) w[j] = 8 * k + j < NL ? v[8 * k + j] : 0.f;
-    st_v8(p + 8 * k, w[0], w[1], w[2], w[3], w[4], w[5], w[6], w[7]);
-  }
-}
-
 constexpr int ELEM_T = 128;
 
 __device__ __forceinline__ void load_element(const ElemArgs& A, int64_t e, double X[4][3]) {
@@ -84,50 +60,6 @@ __device__ __forceinline__ void load_element(const ElemArgs& A, int64_t e, doubl
 #pragma unroll
   for (int a = 0; a < 4; ++a) v[a] = __ldg(A.tets + a * A.E + e);
   load_vertices(A.x, A.y, A.z, v, X);
-}
-
-__device__ __forceinline__ double dot3(const double* a, const double* b) {
-  return fma(a[0], b[0], fma(a[1], b[1], a[2] * b[2]));
-}
-__device__ __forceinline__ float dot3(const float* a, const float* b) {
-  return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2]));
-}
-
-// grad lambda_a in type R: FP64 path keeps the unscaled cofactors (the
-// 1/det scale is folded into the per-element factor); the mixed path forms
-// J^{-1} in FP64 and rounds it to FP32 once.
-template <typename R>
-__device__ __forceinline__ void grads(const Geo& g, R G[4][3]) {
-  if constexpr (std::is_same<R, double>::value) {
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int k = 0; k < 3; ++k) G[a][k] = g.c[a][k];
-  } else {
-    const double inv = 1.0 / g.det;
-#pragma unroll
-    for (int a = 1; a < 4; ++a)
-#pragma unroll
-      for (int k = 0; k < 3; ++k) G[a][k] = __double2float_rn(g.c[a][k] * inv);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) G[0][k] = -(G[1][k] + G[2][k] + G[3][k]);
-  }
-}
-
-// Scale that turns products of grads<R> into |T| grad . grad:
-// FP64: |T| / det^2 = 1 / (6 |det|); mixed: |T| = |det| / 6.
-template <typename R>
-__device__ __forceinline__ double grad_scale(double adet) {
-  if constexpr (std::is_same<R, double>::value) return 1.0 / (6.0 * adet);
-  else return adet * (1.0 / 6.0);
-}
-
-template <typename R>
-__device__ __forceinline__ void vertices_r(const double X[4][3], R Xr[4][3]) {
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) Xr[a][k] = to_r<R>(X[a][k]);
 }
 
 // ---------------------------------------------------------------- scalar forms

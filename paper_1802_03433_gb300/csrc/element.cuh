@@ -21,10 +21,7 @@
 // the Jacobian, det J and J^{-1} stay FP64).
 #pragma once
 
-#include <cuda_runtime.h>
-#include <stdint.h>
-
-#include <utility>
+#include "devcommon.cuh"
 
 namespace fea {
 
@@ -266,6 +263,59 @@ __device__ __forceinline__ double to_r<double>(double v) { return v; }
 template <>
 __device__ __forceinline__ float to_r<float>(double v) { return __double2float_rn(v); }
 
+template <typename R>
+struct IsDouble {
+  static constexpr bool value = false;
+};
+template <>
+struct IsDouble<double> {
+  static constexpr bool value = true;
+};
+
+__device__ __forceinline__ double dot3(const double* a, const double* b) {
+  return fma(a[0], b[0], fma(a[1], b[1], a[2] * b[2]));
+}
+__device__ __forceinline__ float dot3(const float* a, const float* b) {
+  return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2]));
+}
+
+// grad lambda_a in type R: FP64 path keeps the unscaled cofactors (the
+// 1/det scale is folded into the per-element factor); the mixed path forms
+// J^{-1} in FP64 and rounds it to FP32 once.
+template <typename R>
+__device__ __forceinline__ void grads(const Geo& g, R G[4][3]) {
+  if constexpr (IsDouble<R>::value) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) G[a][k] = g.c[a][k];
+  } else {
+    const double inv = 1.0 / g.det;
+#pragma unroll
+    for (int a = 1; a < 4; ++a)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) G[a][k] = __double2float_rn(g.c[a][k] * inv);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) G[0][k] = -(G[1][k] + G[2][k] + G[3][k]);
+  }
+}
+
+// Scale that turns products of grads<R> into |T| grad . grad:
+// FP64: |T| / det^2 = 1 / (6 |det|); mixed: |T| = |det| / 6.
+template <typename R>
+__device__ __forceinline__ double grad_scale(double adet) {
+  if constexpr (IsDouble<R>::value) return 1.0 / (6.0 * adet);
+  else return adet * (1.0 / 6.0);
+}
+
+template <typename R>
+__device__ __forceinline__ void vertices_r(const double X[4][3], R Xr[4][3]) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Xr[a][k] = to_r<R>(X[a][k]);
+}
+
 // Quadrature points of rule NPTS for one coordinate, from the vertex values
 // v[0..3]: x_q = sum_v bary(q, v) v[v], grouped by symmetry class.
 template <int NPTS, typename R>
@@ -288,14 +338,29 @@ __device__ __forceinline__ void quad_coord(const R v[4], R xq[NPTS]) {
   }
 }
 
-// Compile-time loop: f(std::integral_constant<int, I>) for I = 0..N-1.
-template <int... Is, typename F>
-__device__ __forceinline__ void static_for_impl(std::integer_sequence<int, Is...>, F&& f) {
-  (f(std::integral_constant<int, Is>{}), ...);
-}
+// Compile-time loop: f(Idx<I>{}) for I = 0..N-1, in ascending order.  Idx<I>
+// converts to the constant I, so the body can use it as a template argument.
+template <int I>
+struct Idx {
+  static constexpr int value = I;
+  __host__ __device__ constexpr operator int() const { return I; }
+};
+template <int I, int N>
+struct StaticFor {
+  template <typename F>
+  __device__ __forceinline__ static void run(F& f) {
+    f(Idx<I>{});
+    StaticFor<I + 1, N>::run(f);
+  }
+};
+template <int N>
+struct StaticFor<N, N> {
+  template <typename F>
+  __device__ __forceinline__ static void run(F&) {}
+};
 template <int N, typename F>
 __device__ __forceinline__ void static_for(F&& f) {
-  static_for_impl(std::make_integer_sequence<int, N>{}, f);
+  StaticFor<0, N>::run(f);
 }
 
 // Shape load  Fs_a = sum_q w_q s(x_q) phi_a(x_q)  (without the factor |T|),

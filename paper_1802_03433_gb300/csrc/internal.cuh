@@ -8,18 +8,11 @@
 #include <vector>
 
 #include "../../include/fea.h"
+#include "devcommon.cuh"
 
 namespace fea {
 
 // ------------------------------------------------------------------ errors
-// Bits of the device error word latched per mesh.
-enum : int {
-  DEV_ERR_INDEX = 1,
-  DEV_ERR_DEGENERATE = 2,
-  DEV_ERR_OVERFLOW = 4,
-  DEV_ERR_TIMEOUT = 8,
-};
-
 void set_error(const std::string& msg);
 fea_status fail(fea_status st, const std::string& msg);
 fea_status cuda_fail(cudaError_t e, const char* what);
@@ -58,10 +51,7 @@ struct Base {
 
 // Local rows are stored in incidence order: local row (e, a[, comp]) of the
 // element with incidence index i = ipos[a][e] lives at row i * ndpn + comp of
-// a buffer whose rows are lstride(nl, bytes) values apart: a whole number of
-// 32-byte DRAM sectors, written in full (padding included), so no sector is
-// ever left partly written (a partly written sector costs a DRAM read-fill).
-__host__ __device__ constexpr int lstride(int nl, int bytes) { return ((nl * bytes + 31) / 32) * 32 / bytes; }
+// a buffer whose rows are lstride(nl, bytes) values apart (devcommon.cuh).
 
 // The dof-level CSR pattern of (order, dofs per node).
 struct Pattern {

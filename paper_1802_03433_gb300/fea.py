@@ -102,6 +102,11 @@ def lib() -> C.CDLL:
         "fea_batch_assemble": [_vp, _vp],
         "fea_batch_tune": [_vp, _vp, C.POINTER(C.c_int32)],
         "fea_batch_destroy": [_vp],
+        "fea_jit_compile": [C.POINTER(fea_form), C.POINTER(fea_quadrature), C.c_char_p, C.c_char_p,
+                            C.POINTER(_vp)],
+        "fea_jit_info": [_vp, C.POINTER(C.c_double), i64p, C.POINTER(C.c_int32)],
+        "fea_jit_assemble": [_vp, _vp, C.POINTER(fea_coeffs), _vp, _vp, _vp],
+        "fea_jit_destroy": [_vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -109,6 +114,9 @@ def lib() -> C.CDLL:
         f.restype = C.c_int
     L.fea_last_error.restype = C.c_char_p
     L.fea_last_error.argtypes = []
+    for name in ("fea_jit_source", "fea_jit_log"):
+        getattr(L, name).restype = C.c_char_p
+        getattr(L, name).argtypes = [_vp]
     L.fea_status_string.restype = C.c_char_p
     L.fea_status_string.argtypes = [C.c_int]
     _lib = L
@@ -161,6 +169,40 @@ def fea_mesh_create_tri(x, y, tris, stream=None):
 
 def fea_assemble_2d(h, form2d, values, rhs=None, stream=None):
     _check(lib().fea_assemble_2d(h, C.byref(form2d), _ptr(values), _ptr(rhs), _stream(stream)), "fea_assemble_2d")
+
+
+def fea_jit_compile(form, quad, kappa_expr=None, f_expr=None):
+    """Compile (NVRTC, host side) the element kernel for the expressions;
+    returns the handle."""
+    out = C.c_void_p()
+    enc = lambda e: None if e is None else e.encode()  # noqa: E731
+    _check(lib().fea_jit_compile(C.byref(form), C.byref(quad), enc(kappa_expr), enc(f_expr), C.byref(out)),
+           "fea_jit_compile")
+    return out
+
+
+def fea_jit_info(jh):
+    """(compile_ms, cubin_bytes, cache_hit)."""
+    ms, nb, hit = C.c_double(), C.c_int64(), C.c_int32()
+    _check(lib().fea_jit_info(jh, C.byref(ms), C.byref(nb), C.byref(hit)), "fea_jit_info")
+    return ms.value, nb.value, bool(hit.value)
+
+
+def fea_jit_source(jh):
+    return lib().fea_jit_source(jh).decode()
+
+
+def fea_jit_log(jh):
+    return lib().fea_jit_log(jh).decode()
+
+
+def fea_jit_assemble(h, jh, coeffs, values, rhs=None, stream=None):
+    _check(lib().fea_jit_assemble(h, jh, C.byref(coeffs), _ptr(values), _ptr(rhs), _stream(stream)),
+           "fea_jit_assemble")
+
+
+def fea_jit_destroy(jh):
+    _check(lib().fea_jit_destroy(jh), "fea_jit_destroy")
 
 
 def fea_mesh_set_coords(h, x, y, z):
