@@ -42,12 +42,12 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP64_FLOP_PER_ELEM = {
     ("p2_diffmass_64", "fp64"): 1351.0,   # 518 DFMA + 140 DADD + 175 DMUL per element
     ("p1_kappa_96", "fp64"): 421.0,       # 143 DFMA + 60 DADD + 75 DMUL
-    ("p1_elast_128", "fp64"): 438.0,      # 144 DFMA + 15 DADD + 135 DMUL
+    ("p1_elast_128", "fp64"): 370.0,      # 114 DFMA + 16 DADD + 126 DMUL
 }
 DRAM_BYTES_PER_LAUNCH = {
-    ("p2_diffmass_64", "element"): 131.7e6 + 1599.5e6,
+    ("p2_diffmass_64", "element"): 107.6e6 + 1579.1e6,
     ("p1_kappa_96", "element"): 235.0e6 + 793.2e6,
-    ("p1_elast_128", "element"): 861.4e6 + 15709.9e6,
+    ("p1_elast_128", "element"): 705.8e6 + 15649.2e6,
 }
 
 WORKLOADS = {
