@@ -40,7 +40,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # captures are summarised under profiles/.  Absent where not captured for the
 # current kernels.
 FP64_FLOP_PER_ELEM = {
-    ("p2_diffmass_64", "fp64"): 1351.0,   # 518 DFMA + 140 DADD + 175 DMUL per element
+    ("p2_diffmass_64", "fp64"): 1248.0,   # 457 DFMA + 159 DADD + 175 DMUL per element
     ("p1_kappa_96", "fp64"): 421.0,       # 143 DFMA + 60 DADD + 75 DMUL
     ("p1_elast_128", "fp64"): 370.0,      # 114 DFMA + 16 DADD + 126 DMUL
 }

@@ -201,15 +201,10 @@ __device__ __forceinline__ void elem_user_body(const UserArgs& A, int64_t e) {
     static_for<NPTS>([&](auto Q) { fq[Q] = Spec::template f<R>(xq[0][Q], xq[1][Q], xq[2][Q], A.p[0], A.p[1], A.p[2], A.p[3]); });
     const R vol = R(adet * (1.0 / 6.0));
     R* __restrict__ Fl = static_cast<R*>(A.Fl);
-    static_for<NB>([&](auto Aa) {
-      constexpr int a = Aa;  // a constexpr local, usable in the nested lambda's constants
-      R acc = R(weight(NPTS, 0) * phi_at(ORDER, NPTS, 0, a)) * fq[0];
-      static_for<NPTS - 1>([&](auto Q) {
-        constexpr double c = weight(NPTS, Q + 1) * phi_at(ORDER, NPTS, Q + 1, a);
-        acc = fma(R(c), fq[Q + 1], acc);
-      });
-      Fl[pos[a]] = vol * acc;
-    });
+    R F[NB];
+    rule_sum<ORDER, NPTS, R>(fq, F);
+#pragma unroll
+    for (int a = 0; a < NB; ++a) Fl[pos[a]] = vol * F[a];
   }
 }
 

@@ -363,6 +363,104 @@ __device__ __forceinline__ void static_for(F&& f) {
   StaticFor<0, N>::run(f);
 }
 
+// ------------------------------------------------------------------ rule sums
+// wphi(q, a) = w_q phi_a(x_q) for the rule NPTS.
+template <int ORDER, int NPTS>
+__host__ __device__ constexpr double wphi(int q, int a) {
+  return weight(NPTS, q) * phi_at(ORDER, NPTS, q, a);
+}
+
+// The rules are symmetric, so w_q phi_a(x_q) takes few values.  Classes of
+// (point, basis function), with vertex-class point q = 1 + v and edge-class
+// point q = 5 + k (11 points) or point q = v (4 points):
+//   vertex function a:  centroid | own vertex point | other vertex point |
+//                       edge point on a | edge point off a
+//   edge function (i,j): centroid | vertex point on the edge | off it |
+//                       the same edge | an edge sharing one vertex | the
+//                       opposite edge (k <-> 5 - k)
+// rule_classes_ok checks every (q, a) against its class representative.
+__host__ __device__ constexpr bool on_edge(int k, int v) { return edge_p(k) == v || edge_q(k) == v; }
+template <int ORDER, int NPTS>
+__host__ __device__ constexpr bool rule_classes_ok() {
+  constexpr int NB = ORDER == 1 ? 4 : 10;
+  for (int a = 0; a < NB; ++a)
+    for (int q = 0; q < NPTS; ++q) {
+      double rep = 0.0;
+      if (NPTS == 1) continue;
+      const bool vpt = NPTS == 4 || (q >= 1 && q <= 4);
+      const int v = NPTS == 4 ? q : q - 1;  // vertex of a vertex-class point
+      const int k = q - 5;                 // edge of an edge-class point
+      if (a < 4) {
+        if (NPTS == 11 && q == 0) rep = wphi<ORDER, NPTS>(0, 0);
+        else if (vpt) rep = v == a ? wphi<ORDER, NPTS>(NPTS == 4 ? 0 : 1, 0) : wphi<ORDER, NPTS>(NPTS == 4 ? 1 : 2, 0);
+        else rep = on_edge(k, a) ? wphi<ORDER, NPTS>(5, 0) : wphi<ORDER, NPTS>(10, 0);
+      } else {
+        const int e = a - 4;
+        if (NPTS == 11 && q == 0) rep = wphi<ORDER, NPTS>(0, 4);
+        else if (vpt) rep = on_edge(e, v) ? wphi<ORDER, NPTS>(NPTS == 4 ? 0 : 1, 4) : wphi<ORDER, NPTS>(NPTS == 4 ? 2 : 3, 4);
+        else if (k == e) rep = wphi<ORDER, NPTS>(5, 4);
+        else if (k == 5 - e) rep = wphi<ORDER, NPTS>(10, 4);
+        else rep = wphi<ORDER, NPTS>(6, 4);
+      }
+      if (rep != wphi<ORDER, NPTS>(q, a)) return false;
+    }
+  return true;
+}
+
+// Fs_a = sum_q w_q phi_a(x_q) s_q for point values s, summed by classes:
+// the class sums S (vertex-class points), S6 (edge-class points) and E_a
+// (edge points on vertex a) are shared, so each Fs_a costs two or three FMAs
+// instead of one per point.
+template <int ORDER, int NPTS, typename R>
+__device__ __forceinline__ void rule_sum(const R s[NPTS], R Fs[ORDER == 1 ? 4 : 10]) {
+  static_assert(rule_classes_ok<ORDER, NPTS>(), "quadrature rule lost its symmetry classes");
+  using W = double;
+  if constexpr (NPTS == 1) {
+    Fs[0] = R(wphi<ORDER, 1>(0, 0)) * s[0];
+#pragma unroll
+    for (int a = 1; a < 4; ++a) Fs[a] = Fs[0];
+    if constexpr (ORDER == 2) {
+      Fs[4] = R(wphi<ORDER, 1>(0, 4)) * s[0];
+#pragma unroll
+      for (int a = 5; a < 10; ++a) Fs[a] = Fs[4];
+    }
+  } else if constexpr (NPTS == 4) {
+    const R S = (s[0] + s[1]) + (s[2] + s[3]);
+    constexpr W vs = wphi<ORDER, 4>(0, 0), vo = wphi<ORDER, 4>(1, 0);
+    const R Cv = R(vo) * S;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) Fs[a] = fma(R(vs - vo), s[a], Cv);
+    if constexpr (ORDER == 2) {
+      constexpr W ei = wphi<ORDER, 4>(0, 4), eo = wphi<ORDER, 4>(2, 4);
+      const R Ce = R(eo) * S;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) Fs[4 + k] = fma(R(ei - eo), s[edge_p(k)] + s[edge_q(k)], Ce);
+    }
+  } else {
+    const R S4 = (s[1] + s[2]) + (s[3] + s[4]);
+    const R S6 = ((s[5] + s[6]) + (s[7] + s[8])) + (s[9] + s[10]);
+    R E[4];  // edge points on vertex a: edges (a, .) among (0,1),(0,2),(0,3),(1,2),(1,3),(2,3)
+    E[0] = (s[5] + s[6]) + s[7];
+    E[1] = (s[5] + s[8]) + s[9];
+    E[2] = (s[6] + s[8]) + s[10];
+    E[3] = (s[7] + s[9]) + s[10];
+    constexpr W c0 = wphi<ORDER, 11>(0, 0), vs = wphi<ORDER, 11>(1, 0), vo = wphi<ORDER, 11>(2, 0);
+    constexpr W ei = wphi<ORDER, 11>(5, 0), eo = wphi<ORDER, 11>(10, 0);
+    const R Cv = fma(R(c0), s[0], fma(R(vo), S4, R(eo) * S6));
+#pragma unroll
+    for (int a = 0; a < 4; ++a) Fs[a] = fma(R(vs - vo), s[1 + a], fma(R(ei - eo), E[a], Cv));
+    if constexpr (ORDER == 2) {
+      constexpr W g0 = wphi<ORDER, 11>(0, 4), gi = wphi<ORDER, 11>(1, 4), go = wphi<ORDER, 11>(3, 4);
+      constexpr W ds = wphi<ORDER, 11>(5, 4), dh = wphi<ORDER, 11>(6, 4), dp = wphi<ORDER, 11>(10, 4);
+      const R Ce = fma(R(g0), s[0], fma(R(go), S4, R(dh) * S6));
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        Fs[4 + k] = fma(R(gi - go), s[1 + edge_p(k)] + s[1 + edge_q(k)],
+                        fma(R(ds - dh), s[5 + k], fma(R(dp - dh), s[10 - k], Ce)));
+    }
+  }
+}
+
 // Shape load  Fs_a = sum_q w_q s(x_q) phi_a(x_q)  (without the factor |T|),
 // s = 1 (LOAD_CONST) or sin(pi x) sin(pi y) sin(pi z) (LOAD_SIN).
 template <int ORDER, int NPTS, int LOAD, typename R>
@@ -376,24 +474,14 @@ __device__ __forceinline__ void shape_load(const R Xr[4][3], R Fs[ORDER == 1 ? 4
   } else {
     R sq[NPTS];
 #pragma unroll
-    for (int q = 0; q < NPTS; ++q) sq[q] = R(1);
-#pragma unroll
     for (int c = 0; c < 3; ++c) {
       const R v[4] = {Xr[0][c], Xr[1][c], Xr[2][c], Xr[3][c]};
       R xq[NPTS];
       quad_coord<NPTS, R>(v, xq);
 #pragma unroll
-      for (int q = 0; q < NPTS; ++q) sq[q] *= rsinpi<R>(xq[q]);
+      for (int q = 0; q < NPTS; ++q) sq[q] = c == 0 ? rsinpi<R>(xq[q]) : sq[q] * rsinpi<R>(xq[q]);
     }
-    static_for<NB>([&](auto A) {
-      constexpr double c0 = weight(NPTS, 0) * phi_at(ORDER, NPTS, 0, A);
-      R acc = R(c0) * sq[0];
-      static_for<NPTS - 1>([&](auto Q) {
-        constexpr double cq = weight(NPTS, Q + 1) * phi_at(ORDER, NPTS, Q + 1, A);
-        acc = fma(R(cq), sq[Q + 1], acc);
-      });
-      Fs[A] = acc;
-    });
+    rule_sum<ORDER, NPTS, R>(sq, Fs);
   }
 }
 
