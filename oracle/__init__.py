@@ -317,3 +317,18 @@ def local_user(X, order=1, mass=0.0, kfn=None, ffn=None, npts=11):
                          C.c_int(npts), Ke.ctypes.data_as(_dp), Fe.ctypes.data_as(_dp))
     del kkeep, fkeep
     return Ke, Fe
+
+
+# ---------------------------------------------------------------- Dirichlet conditions
+def dirichlet(row_ptr, col_idx, values, rhs, dofs, g=None):
+    """Copies of (values, rhs) with u = g imposed at dofs by symmetric elimination."""
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+    v = np.array(values, dtype=np.float64, copy=True)
+    r = np.array(rhs, dtype=np.float64, copy=True)
+    dofs = np.ascontiguousarray(dofs, dtype=np.int32)
+    (g,) = _keep(None if g is None else np.asarray(g, dtype=np.float64))
+    lib().orc_dirichlet(C.c_int64(row_ptr.size - 1), row_ptr.ctypes.data_as(_ip), col_idx.ctypes.data_as(_ip),
+                        v.ctypes.data_as(_dp), r.ctypes.data_as(_dp), C.c_int64(dofs.size),
+                        dofs.ctypes.data_as(_ip), _d(g))
+    return v, r

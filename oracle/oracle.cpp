@@ -868,3 +868,33 @@ void orc_local_user(const double* Xall /* n x 4 x 3 */, int64_t n, int order, do
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- Dirichlet conditions
+// Closing the loop to a solve (the paper assembles the pure Neumann operator
+// and leaves solving out): for every dof d of the list, row d becomes the
+// identity row with right-hand side g_d, and column d is eliminated from the
+// other rows, rhs_i -= A_id g_d, A_id = 0 (A stays symmetric).  The textbook
+// elimination, done literally: first the right-hand-side corrections with the
+// original values, then the zeroing.
+extern "C" void orc_dirichlet(int64_t ndof, const int32_t* row_ptr, const int32_t* col_idx, double* values,
+                              double* rhs, int64_t n, const int32_t* dofs, const double* g) {
+  std::vector<char> fixed(ndof, 0);
+  std::vector<double> gv(ndof, 0.0);
+  for (int64_t k = 0; k < n; ++k) {
+    fixed[dofs[k]] = 1;
+    gv[dofs[k]] = g ? g[k] : 0.0;
+  }
+  for (int64_t i = 0; i < ndof; ++i) {
+    if (fixed[i]) continue;
+    for (int32_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p)
+      if (fixed[col_idx[p]]) rhs[i] -= values[p] * gv[col_idx[p]];
+  }
+  for (int64_t i = 0; i < ndof; ++i)
+    for (int32_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
+      const int32_t c = col_idx[p];
+      if (fixed[i]) values[p] = (c == i) ? 1.0 : 0.0;
+      else if (fixed[c]) values[p] = 0.0;
+    }
+  for (int64_t i = 0; i < ndof; ++i)
+    if (fixed[i]) rhs[i] = gv[i];
+}

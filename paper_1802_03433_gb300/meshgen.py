@@ -192,3 +192,21 @@ def tri_square(n: int, perturb: float = 0.2, seed: int = 0):
     tris[:, :, 0] = np.stack([a, b, dd])
     tris[:, :, 1] = np.stack([a, dd, c])
     return np.ascontiguousarray(coords), np.ascontiguousarray(tris.reshape(3, -1).astype(np.int32))
+
+
+def cube_boundary_dofs(coords, edof, n_dofs):
+    """Dofs of a unit-cube mesh that lie on its boundary, from geometry only.
+    edof: (nb, E) element -> scalar dof table (nb = 4 P1, 10 P2 with the
+    local edge order (0,1),(0,2),(0,3),(1,2),(1,3),(2,3)); a dof's position is
+    its vertex, or the midpoint of its edge.  Returns (dofs int32 ascending,
+    positions (3, n_dofs))."""
+    edof = np.asarray(edof)
+    pos = np.zeros((3, n_dofs))
+    N = coords.shape[1]
+    pos[:, :N] = coords
+    if edof.shape[0] == 10:
+        pairs = ((0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3))
+        for k, (a, b) in enumerate(pairs):
+            pos[:, edof[4 + k]] = 0.5 * (coords[:, edof[a]] + coords[:, edof[b]])
+    on = np.any((np.abs(pos) < 1e-12) | (np.abs(pos - 1.0) < 1e-12), axis=0)
+    return np.nonzero(on)[0].astype(np.int32), pos
