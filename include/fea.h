@@ -149,12 +149,16 @@ fea_status fea_mesh_set_coords(fea_mesh* mesh, const double* x, const double* y,
  * bitwise identical for every setting. */
 fea_status fea_mesh_set_stages(fea_mesh* mesh, int32_t stages);
 
-/* Launch shape of fea_assemble's scatter when stages == 1: 0 = one launch of
- * the two-deep pipelined kernel over all row tiles; 1 = tiles whose CSR span
- * exceeds 60% of the widest in one such launch, the rest in a second launch
- * with a smaller shared-memory size and a one-deep kernel (fewer registers,
- * more CTAs per SM); 2 = one launch of the one-deep kernel; -1 (default) =
- * automatic: 2 when the pattern mixes long and short rows (P2), else 0.
+/* Scatter of fea_assemble (stages == 1), fea_assemble_noalloc,
+ * fea_assemble_2d and fea_jit_assemble.  3 = the bulk-copy scatter: local rows
+ * in the tile-interleaved layout, each row tile streamed into shared memory
+ * by cp.async.bulk copies through a three-stage mbarrier ring (scalar forms;
+ * elasticity falls back to 0).  The incidence-order scatters: 0 = one launch
+ * of the two-deep pipelined kernel over all row tiles; 1 = tiles whose CSR
+ * span exceeds 60% of the widest in one such launch, the rest in a second
+ * launch with a smaller shared-memory size and a one-deep kernel; 2 = one
+ * launch of the one-deep kernel.  -1 (default) = automatic: 3 for scalar
+ * forms, else 2 when the pattern mixes long and short rows, else 0.
  * Results are bitwise identical for every mode. */
 fea_status fea_mesh_set_scatter_classes(fea_mesh* mesh, int32_t mode);
 
@@ -358,6 +362,36 @@ fea_status fea_jit_assemble(fea_mesh* mesh, fea_jit* jit, const fea_coeffs* coef
 
 /* Release a handle (and its loaded module). */
 fea_status fea_jit_destroy(fea_jit* jit);
+
+/* ---------------------------------------------------------------- solving
+ * The step after assembly (the paper assembles the pure Neumann operator and
+ * leaves solving out, Sec. 2).  Both calls work on the CSR pattern of
+ * (order, dofs_per_node), which must be built. */
+
+/* Dirichlet conditions u_d = g_d by symmetric elimination, in place:
+ *   dofs   : [n] int32 dof ids (device), any order, repeats allowed; an id
+ *            outside [0, ndof) latches FEA_ERR_INDEX (fea_mesh_check);
+ *   g      : [n] FP64 values (device), or NULL for zero;
+ *   values : [nnz] CSR values (device): row d becomes the identity row,
+ *            column d of every other row is zeroed (A stays symmetric);
+ *   rhs    : [ndof] (device): rhs_d = g_d, rhs_i -= A_id g_d for the other
+ *            rows; may be NULL.
+ * Asynchronous.  Scratch (ndof doubles + bytes) is owned by the handle. */
+fea_status fea_dirichlet(fea_mesh* mesh, int32_t order, int32_t dofs_per_node, const int32_t* dofs, int64_t n,
+                         const double* g, double* values, double* rhs, void* stream);
+
+/* Solve A x = b with conjugate gradients and the Jacobi preconditioner
+ * (A symmetric positive definite, e.g. after fea_dirichlet).
+ *   values : [nnz] CSR values, b : [ndof], x : [ndof] (device, FP64); x holds
+ *            the initial guess and receives the solution;
+ *   stops at ||b - A x||_2 <= rtol ||b||_2 (rtol ||.|| of 1 when b = 0) or
+ *   after max_iter iterations; *iters and *rel_res (= ||r|| / ||b||) may be NULL.
+ * Every reduction has a fixed order: the same inputs give bitwise the same x.
+ * Runs on the handle's own stream after the work queued on `stream`, and
+ * synchronises (the host checks convergence every 16 iterations).
+ * FEA_ERR_ARG if p.Ap <= 0 occurs (A not positive definite). */
+fea_status fea_cg(fea_mesh* mesh, int32_t order, int32_t dofs_per_node, const double* values, const double* b,
+                  double* x, double rtol, int32_t max_iter, int32_t* iters, double* rel_res, void* stream);
 
 /* Message for the last error on the calling thread ("" if none). */
 const char* fea_last_error(void);

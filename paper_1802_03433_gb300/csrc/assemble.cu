@@ -6,6 +6,7 @@
 
 #include "elem_kernels.cuh"
 #include "gather.cuh"
+#include "gather_tiled.cuh"
 
 namespace fea {
 
@@ -77,8 +78,12 @@ fea_status assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* co, con
   const size_t rb = mixed ? sizeof(float) : sizeof(double);
   const int64_t E = m->n_elems;
   const int load = rhs ? co->f_kind : FEA_LOAD_NONE;
-  // local rows in incidence order: E * nb incidences x ndpn rows x lstride
-  const size_t nrows_local = (size_t)E * nb * ndpn;
+  const int stages = std::min(std::max(m->stages, 1), 16);
+  const bool sequential = stages == 1 || E < (int64_t)stages * ELEM_T;
+  // local rows in the tiled layout (bulk-copy scatter, scalar forms) or in
+  // incidence order (E * nb incidences x ndpn rows), lstride values apart
+  const bool tiled = sequential && use_tiled(m, P);
+  const size_t nrows_local = tiled ? (size_t)P->npos : (size_t)E * nb * ndpn;
   FEA_TRY(ensure_scratch(m->lm, nrows_local * lstride(nl, (int)rb) * rb));
   if (load != FEA_LOAD_NONE) FEA_TRY(ensure_scratch(m->fl, nrows_local * rb));
 
@@ -96,7 +101,7 @@ fea_status assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* co, con
   A.mu_const = co->mu_const;
   A.mass = form->mass_coef;
   for (int i = 0; i < 4; ++i) A.fp[i] = co->f_param[i];
-  A.ipos = B->ipos;
+  A.ipos = tiled ? P->tpos : B->ipos;
   A.Lm = m->lm.ptr;
   A.Fl = load != FEA_LOAD_NONE ? m->fl.ptr : nullptr;
   A.err = m->err;
@@ -112,8 +117,7 @@ fea_status assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* co, con
   G.values = values;
   G.rhs = rhs;
 
-  const int stages = std::min(std::max(m->stages, 1), 16);
-  if (stages == 1 || E < (int64_t)stages * ELEM_T) {
+  if (sequential) {
     // one element launch, then one scatter launch
     A.e0 = 0;
     A.e1 = E;
@@ -121,8 +125,12 @@ fea_status assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* co, con
     FEA_TRY(launch_elements(form, A, load, q->npts, prec, s));
     if (m->profile) FEA_CUDA(cudaEventRecord(m->ev[1], s));
     int mode = m->tile_classes;
-    if (mode < 0) mode = (P->n_heavy > 0 && P->n_light > 0) ? 2 : 0;
-    if (mode == 2) {
+    if (tiled) mode = 3;
+    // no tiled layout (vector dofs): mode 3 means the automatic incidence-order choice
+    if (mode < 0 || (mode == 3 && !tiled)) mode = (P->n_heavy > 0 && P->n_light > 0) ? 2 : 0;
+    if (mode == 3) {
+      FEA_TRY(scatter_tiled(m, P, B, mixed, A.Lm, A.Fl, values, rhs, s));
+    } else if (mode == 2) {
       FEA_TRY(launch_gather(nb, ndpn, mixed, G, P->rows_per_tile, P->max_tile_nnz, s, P->class_list,
                             P->n_heavy + P->n_light, false));
     } else if (mode == 1 && P->class_list) {

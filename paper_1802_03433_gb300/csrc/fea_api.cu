@@ -195,7 +195,7 @@ fea_status fea_mesh_set_stages(fea_mesh* m, int32_t stages) {
 
 fea_status fea_mesh_set_scatter_classes(fea_mesh* m, int32_t mode) {
   if (!m) return fail(FEA_ERR_ARG, "mesh is NULL");
-  if (mode < -1 || mode > 2) return fail(FEA_ERR_ARG, "mode must be -1, 0, 1 or 2");
+  if (mode < -1 || mode > 3) return fail(FEA_ERR_ARG, "mode must be -1, 0, 1, 2 or 3");
   m->tile_classes = mode;
   return FEA_OK;
 }
@@ -214,6 +214,10 @@ fea_status fea_mesh_destroy(fea_mesh* m) {
   if (m->lm.ptr) cudaFree(m->lm.ptr);
   if (m->fl.ptr) cudaFree(m->fl.ptr);
   if (m->gxs.ptr) cudaFree(m->gxs.ptr);
+  if (m->bc.ptr) cudaFree(m->bc.ptr);
+  if (m->cg.ptr) cudaFree(m->cg.ptr);
+  if (m->solve_ev) cudaEventDestroy(m->solve_ev);
+  if (m->solve_stream) cudaStreamDestroy(m->solve_stream);
   if (m->tets) cudaFree(m->tets);
   if (m->err) cudaFree(m->err);
   delete m;

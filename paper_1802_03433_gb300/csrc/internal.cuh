@@ -75,6 +75,17 @@ struct Pattern {
   int32_t* class_list = nullptr;   // heavy tiles, then light tiles
   int64_t n_heavy = 0, n_light = 0;
   int64_t heavy_span = 0, light_span = 0;
+  // Tile-interleaved local rows (scalar patterns, gather_tiled.cuh): row tile
+  // t owns positions tile_base[t] .. tile_base[t] + steps[t] * S_t, S_t = its
+  // row count rounded up to 4; the k-th contribution (incidence) of its row
+  // r0 + j sits at position tile_base[t] + k * S_t + j, so each step of a
+  // tile is one contiguous block that one bulk copy moves.  Positions of rows
+  // with fewer than steps[t] contributions stay unused (padding).
+  int32_t* tpos = nullptr;        // [nb][E] position of local row (e, a)
+  uint8_t* tslot = nullptr;       // [npos][SW] column slots at each position
+  int64_t* tile_base = nullptr;   // [ntiles]
+  int32_t* tile_steps = nullptr;  // [ntiles]
+  int64_t npos = 0;               // positions, padding included (0: layout not built)
 };
 
 struct Scratch {
@@ -97,6 +108,10 @@ struct fea_mesh {
   fea::Pattern* pat[3][4] = {{nullptr}};                     // by order, ndpn
   fea::Scratch lm, fl;      // local matrices / local loads of the last assembly
   fea::Scratch gxs;         // per-incidence vertex gradients of the last backward
+  fea::Scratch bc;          // Dirichlet marks and values (fea_dirichlet)
+  fea::Scratch cg;          // CG vectors, partial sums and state (fea_cg)
+  cudaStream_t solve_stream = nullptr;  // stream the CG iteration graph is captured on
+  cudaEvent_t solve_ev = nullptr;
   int stages = 1;           // element chunks overlapped with the scatter (1 = no overlap)
   int tile_classes = -1;    // sequential scatter: 0 one deep launch, 1 heavy/light split, 2 one light
                             // launch, -1 automatic (2 when the pattern mixes long and short rows, else 0)

@@ -27,6 +27,7 @@
 
 #include "elem_user.cuh"
 #include "gather.cuh"
+#include "gather_tiled.cuh"
 #include "jit_headers.inc"
 
 struct fea_jit {
@@ -243,8 +244,10 @@ fea_status fea_jit_assemble(fea_mesh* m, fea_jit* j, const fea_coeffs* co, doubl
   const bool mixed = j->prec == FEA_MIXED;
   const size_t rb = mixed ? sizeof(float) : sizeof(double);
   const int64_t E = m->n_elems;
-  FEA_TRY(ensure_scratch(m->lm, (size_t)E * nb * lstride(nb, (int)rb) * rb));
-  if (rhs) FEA_TRY(ensure_scratch(m->fl, (size_t)E * nb * rb));
+  const bool tiled = use_tiled(m, P);
+  const size_t npos = tiled ? (size_t)P->npos : (size_t)E * nb;
+  FEA_TRY(ensure_scratch(m->lm, npos * lstride(nb, (int)rb) * rb));
+  if (rhs) FEA_TRY(ensure_scratch(m->fl, npos * rb));
   UserArgs A{};
   A.x = m->x;
   A.y = m->y;
@@ -255,7 +258,7 @@ fea_status fea_jit_assemble(fea_mesh* m, fea_jit* j, const fea_coeffs* co, doubl
   A.kappa_const = co->kappa_const;
   A.mass = j->mass_coef;
   for (int k = 0; k < 4; ++k) A.p[k] = co->f_param[k];
-  A.ipos = B->ipos;
+  A.ipos = tiled ? P->tpos : B->ipos;
   A.Lm = m->lm.ptr;
   A.Fl = rhs ? m->fl.ptr : nullptr;
   A.err = m->err;
@@ -266,16 +269,20 @@ fea_status fea_jit_assemble(fea_mesh* m, fea_jit* j, const fea_coeffs* co, doubl
                               dim3(USER_T), args, 0, s));
   }
   if (m->profile) FEA_CUDA(cudaEventRecord(m->ev[1], s));
-  GatherArgs G{};
-  G.ndof = P->ndof;
-  G.row_ptr = P->row_ptr;
-  G.inc_ptr = B->inc_ptr;
-  G.slot = B->slot;
-  G.Lm = A.Lm;
-  G.Fl = A.Fl;
-  G.values = values;
-  G.rhs = rhs;
-  FEA_TRY(launch_gather(nb, 1, mixed, G, P->rows_per_tile, P->max_tile_nnz, s));
+  if (tiled) {
+    FEA_TRY(scatter_tiled(m, P, B, mixed, A.Lm, A.Fl, values, rhs, s));
+  } else {
+    GatherArgs G{};
+    G.ndof = P->ndof;
+    G.row_ptr = P->row_ptr;
+    G.inc_ptr = B->inc_ptr;
+    G.slot = B->slot;
+    G.Lm = A.Lm;
+    G.Fl = A.Fl;
+    G.values = values;
+    G.rhs = rhs;
+    FEA_TRY(launch_gather(nb, 1, mixed, G, P->rows_per_tile, P->max_tile_nnz, s));
+  }
   if (m->profile) {
     FEA_CUDA(cudaEventRecord(m->ev[2], s));
     m->profiled = true;

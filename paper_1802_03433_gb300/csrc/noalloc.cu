@@ -24,6 +24,7 @@
 
 #include "elem_kernels.cuh"
 #include "gather.cuh"
+#include "gather_tiled.cuh"
 
 namespace fea {
 namespace {
@@ -80,7 +81,8 @@ extern "C" fea_status fea_assemble_noalloc(fea_mesh* m, const fea_form* form, co
   const size_t rb = mixed ? sizeof(float) : sizeof(double);
   const int64_t E = m->n_elems;
   const int load = rhs ? co->f_kind : FEA_LOAD_NONE;
-  const size_t nrows_local = (size_t)E * nb * ndpn;
+  const bool tiled = use_tiled(m, P);
+  const size_t nrows_local = tiled ? (size_t)P->npos : (size_t)E * nb * ndpn;
   const size_t lm_bytes = (nrows_local * lstride(nl, (int)rb) * rb + 255) / 256 * 256;
   const size_t fl_bytes = load != FEA_LOAD_NONE ? nrows_local * rb : 0;
   if (lm_bytes + fl_bytes > NOALLOC_SCRATCH_BYTES)
@@ -107,7 +109,7 @@ extern "C" fea_status fea_assemble_noalloc(fea_mesh* m, const fea_form* form, co
   A.mu_const = co->mu_const;
   A.mass = form->mass_coef;
   for (int i = 0; i < 4; ++i) A.fp[i] = co->f_param[i];
-  A.ipos = B->ipos;
+  A.ipos = tiled ? P->tpos : B->ipos;
   A.Lm = base;
   A.Fl = load != FEA_LOAD_NONE ? static_cast<char*>(base) + lm_bytes : nullptr;
   A.err = m->err;
@@ -119,6 +121,7 @@ extern "C" fea_status fea_assemble_noalloc(fea_mesh* m, const fea_form* form, co
     if (order == 1) FEA_TRY(launch_elem_p1(A, mass, load, q->npts, prec, s));
     else FEA_TRY(launch_elem_p2(A, mass, load, q->npts, prec, s));
   }
+  if (tiled) return scatter_tiled(m, P, B, mixed, A.Lm, A.Fl, values, rhs, s);
   GatherArgs G{};
   G.ndof = P->ndof;
   G.row_ptr = P->row_ptr;

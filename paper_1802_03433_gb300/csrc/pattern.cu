@@ -432,6 +432,78 @@ __global__ void k_ipos(int64_t nI, int nb, int64_t E, const int32_t* __restrict_
   ipos[a * E + e] = (int32_t)i;
 }
 
+// ------------------------------------------------------------------ tiled layout
+// Steps of row tile t (the most contributions any of its rows has) and its
+// position count steps * S_t.
+__global__ void k_tile_steps(int64_t nrows, int rows, const int32_t* __restrict__ inc_ptr,
+                             int32_t* __restrict__ steps, int64_t* __restrict__ cnt) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t r0 = t * rows;
+  if (r0 >= nrows) return;
+  const int64_t r1 = r0 + rows < nrows ? r0 + rows : nrows;
+  int32_t K = 0;
+  for (int64_t r = r0; r < r1; ++r) K = max(K, inc_ptr[r + 1] - inc_ptr[r]);
+  steps[t] = K;
+  cnt[t] = (int64_t)K * (((r1 - r0) + 3) & ~int64_t(3));
+}
+
+// Position of every incidence in the tiled layout; its slots copied there.
+template <int SW>
+__global__ void k_tpos(int64_t nrows, int rows, int nb, int64_t E, const int32_t* __restrict__ inc_ptr,
+                       const int32_t* __restrict__ inc, const uint8_t* __restrict__ slot,
+                       const int64_t* __restrict__ tile_base, int32_t* __restrict__ tpos,
+                       uint8_t* __restrict__ tslot) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  const int64_t t = r / rows, j = r - t * rows;
+  const int64_t r1 = (t + 1) * rows < nrows ? (t + 1) * rows : nrows;
+  const int64_t S = ((r1 - t * rows) + 3) & ~int64_t(3);
+  const int64_t base = tile_base[t];
+  const int32_t i0 = inc_ptr[r];
+  for (int32_t i = i0; i < inc_ptr[r + 1]; ++i) {
+    const int64_t pos = base + (int64_t)(i - i0) * S + j;
+    const int64_t p = inc[i];
+    const int64_t e = p / nb, a = p - e * nb;
+    tpos[a * E + e] = (int32_t)pos;
+    const uint4* src = reinterpret_cast<const uint4*>(slot + (int64_t)i * SW);
+    if constexpr (SW == 16) {
+      *reinterpret_cast<uint4*>(tslot + pos * 16) = *src;
+    } else {
+      *reinterpret_cast<uint32_t*>(tslot + pos * 4) = *reinterpret_cast<const uint32_t*>(slot + (int64_t)i * 4);
+    }
+  }
+}
+
+fea_status build_tiled(fea_mesh* m, Pattern* P, const Base* B, cudaStream_t s) {
+  const int64_t nrows = P->ndof;
+  const int rows = P->rows_per_tile;
+  const int64_t ntiles = (nrows + rows - 1) / rows;
+  if (ntiles == 0) return FEA_OK;
+  FEA_TRY(dalloc(&P->tile_steps, ntiles));
+  FEA_TRY(dalloc(&P->tile_base, ntiles + 1));
+  Tmp<int64_t> cnt;
+  FEA_TRY(cnt.alloc(ntiles));
+  k_tile_steps<<<blocks_for(ntiles, 256), 256, 0, s>>>(nrows, rows, B->inc_ptr, P->tile_steps, cnt.p);
+  FEA_CUDA(cudaGetLastError());
+  FEA_TRY(scan(cnt.p, ntiles, P->tile_base, s));
+  int64_t npos = 0;
+  FEA_TRY(read_i64(P->tile_base + ntiles, &npos, s));
+  if (npos > (int64_t)INT32_MAX) return FEA_OK;  // positions must fit int32: keep the incidence layout
+  const int sw = B->slot_width;
+  FEA_TRY(dalloc(&P->tpos, (size_t)m->n_elems * B->nb));
+  FEA_TRY(dalloc(&P->tslot, (size_t)std::max<int64_t>(npos, 1) * sw));
+  if (sw == 16)
+    k_tpos<16><<<blocks_for(nrows, 128), 128, 0, s>>>(nrows, rows, B->nb, m->n_elems, B->inc_ptr, B->inc, B->slot,
+                                                      P->tile_base, P->tpos, P->tslot);
+  else
+    k_tpos<4><<<blocks_for(nrows, 128), 128, 0, s>>>(nrows, rows, B->nb, m->n_elems, B->inc_ptr, B->inc, B->slot,
+                                                     P->tile_base, P->tpos, P->tslot);
+  FEA_CUDA(cudaGetLastError());
+  FEA_CUDA(cudaStreamSynchronize(s));
+  P->npos = npos;
+  return FEA_OK;
+}
+
 // ------------------------------------------------------------------ stages
 // Stage of a row tile = chunk of the largest element id among its rows'
 // incidences (each incidence list is sorted, so its last entry).
@@ -550,6 +622,10 @@ void free_pattern(Pattern* p) {
   if (!p) return;
   dfree(p->tile_list);
   dfree(p->class_list);
+  dfree(p->tpos);
+  dfree(p->tslot);
+  dfree(p->tile_base);
+  dfree(p->tile_steps);
   if (p->own) {
     dfree(p->row_ptr);
     dfree(p->col_idx);
@@ -700,6 +776,8 @@ fea_status build_pattern(fea_mesh* m, int order, int ndpn, cudaStream_t s) {
       }
     }
   }
+  // the tiled local-row layout of the bulk-copy scatter (scalar patterns)
+  if (st == FEA_OK && ndpn == 1) st = build_tiled(m, P, B, s);
   if (st != FEA_OK) {
     free_pattern(P);
     return st;

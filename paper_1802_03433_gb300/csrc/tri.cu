@@ -21,6 +21,7 @@
 
 #include "elem_kernels.cuh"
 #include "gather.cuh"
+#include "gather_tiled.cuh"
 
 namespace fea {
 namespace {
@@ -148,8 +149,10 @@ extern "C" fea_status fea_assemble_2d(fea_mesh* m, const fea_form2d* form, doubl
   if (!P || !B) return fail(FEA_ERR_STATE, "fea_assemble_2d: build the pattern with fea_pattern(mesh, 1, 1) first");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int64_t E = m->n_elems;
-  FEA_TRY(ensure_scratch(m->lm, (size_t)E * 3 * 4 * sizeof(double)));
-  if (rhs) FEA_TRY(ensure_scratch(m->fl, (size_t)E * 3 * sizeof(double)));
+  const bool tiled = use_tiled(m, P);
+  const size_t npos = tiled ? (size_t)P->npos : (size_t)E * 3;
+  FEA_TRY(ensure_scratch(m->lm, npos * 4 * sizeof(double)));
+  if (rhs) FEA_TRY(ensure_scratch(m->fl, npos * sizeof(double)));
   TriArgs A{};
   A.x = m->x;
   A.y = m->y;
@@ -162,7 +165,7 @@ extern "C" fea_status fea_assemble_2d(fea_mesh* m, const fea_form2d* form, doubl
   }
   A.lam24 = form->lambda / 24.0;
   for (int k = 0; k < 6; ++k) A.f[k] = form->f[k];
-  A.ipos = B->ipos;
+  A.ipos = tiled ? P->tpos : B->ipos;
   A.Lm = static_cast<double*>(m->lm.ptr);
   A.Fl = rhs ? static_cast<double*>(m->fl.ptr) : nullptr;
   A.err = m->err;
@@ -173,16 +176,20 @@ extern "C" fea_status fea_assemble_2d(fea_mesh* m, const fea_form2d* form, doubl
     FEA_CUDA(cudaGetLastError());
   }
   if (m->profile) FEA_CUDA(cudaEventRecord(m->ev[1], s));
-  GatherArgs G{};
-  G.ndof = P->ndof;
-  G.row_ptr = P->row_ptr;
-  G.inc_ptr = B->inc_ptr;
-  G.slot = B->slot;
-  G.Lm = m->lm.ptr;
-  G.Fl = A.Fl;
-  G.values = values;
-  G.rhs = rhs;
-  FEA_TRY(launch_gather(3, 1, false, G, P->rows_per_tile, P->max_tile_nnz, s));
+  if (tiled) {
+    FEA_TRY(scatter_tiled(m, P, B, false, m->lm.ptr, A.Fl, values, rhs, s));
+  } else {
+    GatherArgs G{};
+    G.ndof = P->ndof;
+    G.row_ptr = P->row_ptr;
+    G.inc_ptr = B->inc_ptr;
+    G.slot = B->slot;
+    G.Lm = m->lm.ptr;
+    G.Fl = A.Fl;
+    G.values = values;
+    G.rhs = rhs;
+    FEA_TRY(launch_gather(3, 1, false, G, P->rows_per_tile, P->max_tile_nnz, s));
+  }
   if (m->profile) {
     FEA_CUDA(cudaEventRecord(m->ev[2], s));
     m->profiled = true;

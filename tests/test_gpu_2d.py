@@ -65,3 +65,18 @@ def test_paper_example_4m_nodes_properties():
     assert abs(v.sum() - 1.0) < 1e-9
     assert abs(r.sum() - (36 - 4 / 3)) < 1e-9 * 36
     m.close()
+
+
+def test_scatter_modes_bitwise_identical():
+    import torch
+    from paper_1802_03433_gb300 import fea
+    coords, tris = mg.tri_square(37, 0.2, 4)
+    m = fea.Mesh(coords, tris)
+    outs = []
+    for mode in (0, 3):
+        fea.fea_mesh_set_scatter_classes(m.h, mode)
+        v, r = m.assemble_2d(fea.make_form2d())
+        torch.cuda.synchronize()
+        outs.append((v.cpu().numpy().view(np.uint64), r.cpu().numpy().view(np.uint64)))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    m.close()

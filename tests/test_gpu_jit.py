@@ -147,3 +147,26 @@ def test_argument_errors():
         fea.fea_jit_assemble(m.h, j, co, v, None)
     fea.fea_jit_destroy(j)
     m.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_scatter_modes_bitwise_identical(prec):
+    import torch
+    from paper_1802_03433_gb300 import fea
+    coords, tets, _ = mg.make_cube(9, 0.2, 8)
+    m = fea.Mesh(coords, tets)
+    ndof, nnz = m.pattern(2, 1)
+    j = fea.fea_jit_compile(fea.make_form(fea.FEA_DIFFUSION_MASS, 2, 1.0), fea.make_quadrature(11, prec),
+                            CASES["smooth_k"][0], CASES["exp_f"][0])
+    co = fea.make_coeffs(f_param=P)
+    outs = []
+    for mode in (2, 3):
+        fea.fea_mesh_set_scatter_classes(m.h, mode)
+        v = torch.empty(nnz, dtype=torch.float64, device="cuda")
+        r = torch.empty(ndof, dtype=torch.float64, device="cuda")
+        fea.fea_jit_assemble(m.h, j, co, v, r)
+        torch.cuda.synchronize()
+        outs.append((v.cpu().numpy().view(np.uint64), r.cpu().numpy().view(np.uint64)))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    fea.fea_jit_destroy(j)
+    m.close()

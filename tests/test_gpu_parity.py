@@ -273,12 +273,13 @@ def test_atomic_comparison_path_matches_oracle(torch_cuda, kind, n):
 @pytest.mark.parametrize("kind,n", [("p1_kappa", 12), ("p2_diffmass", 9), ("elasticity", 8)])
 @pytest.mark.parametrize("prec", [0, 1])
 def test_scatter_launch_shapes_bitwise_identical(torch_cuda, kind, n, prec):
-    """One deep launch, heavy/light split, one light launch: same bits."""
+    """One deep launch, heavy/light split, one light launch, the bulk-copy
+    scatter over the tiled layout (scalar forms), automatic: same bits."""
     from paper_1802_03433_gb300 import fea
     c = case(kind, n, seed=23)
     m = fea.Mesh(c["coords"], c["tets"])
     ref = None
-    for mode in (0, 1, 2):
+    for mode in (0, 1, 2, 3, -1):
         fea.fea_mesh_set_scatter_classes(m.h, mode)
         g = gpu_system(c, prec=prec, mesh=m)
         if ref is None:
