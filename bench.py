@@ -288,6 +288,8 @@ def run_ours(args):
         forms["p1_kappa_96"] = bench_plain(fea, torch, dev, "p1_kappa", 96, small, args.warmup, flush)
     if want("jit"):
         forms["jit"] = bench_jit(fea, torch, dev, small, args.warmup, flush)
+    if want("solve"):
+        forms["solve"] = bench_solve(fea, torch, dev)
     if want("paper_2d"):
         forms["paper_2d"] = bench_paper_2d(fea, torch, dev, small, args.warmup, flush)
 
@@ -625,6 +627,51 @@ def bench_jit(fea, torch, dev, steps, warmup, flush, n=64):
     return out
 
 
+def bench_solve(fea, torch, dev, n=64, rtol=1e-8, max_iter=3000):
+    """The step after assembly on the headline system (P2 diffusion + mass,
+    64^3, log-normal kappa): Dirichlet u = 0 on the cube boundary, then
+    Jacobi-preconditioned CG to ||r|| <= rtol ||b||.  One solve, timed with
+    CUDA events; bytes per iteration = 12 nnz (values, columns) + 108 ndof
+    (row pointers and the vectors the five kernels read and write)."""
+    d = make_inputs("p2_diffmass", n, seed=0)
+    m = fea.Mesh(d["coords"], d["tets"], device=dev)
+    ndof, nnz = m.pattern(2, 1)
+    kap = torch.as_tensor(d["kappa"], device=dev)
+    co = fea.make_coeffs(kappa=kap, f_kind=fea.FEA_LOAD_SINPROD, f_param=(mg.SIN_AMP,))
+    form = fea.make_form(fea.FEA_DIFFUSION_MASS, 2, 1.0)
+    q = fea.make_quadrature(11)
+    ed = m.dof_table(2).cpu().numpy()
+    bd, _ = mg.cube_boundary_dofs(d["coords"], ed, ndof)
+    bdt = torch.as_tensor(bd, device=dev)
+    vals = torch.empty(nnz, dtype=torch.float64, device=dev)
+    rhs = torch.empty(ndof, dtype=torch.float64, device=dev)
+    x = torch.zeros(ndof, dtype=torch.float64, device=dev)
+    fea.fea_assemble(m.h, form, co, q, vals, rhs)
+    fea.fea_dirichlet(m.h, 2, 1, bdt, None, vals, rhs)
+    fea.fea_cg(m.h, 2, 1, vals, rhs, x, rtol=rtol, max_iter=20)  # warm-up: scratch, graph path
+    torch.cuda.synchronize()
+    a, b, c, e = (torch.cuda.Event(enable_timing=True) for _ in range(4))
+    a.record()
+    fea.fea_assemble(m.h, form, co, q, vals, rhs)
+    b.record()
+    fea.fea_dirichlet(m.h, 2, 1, bdt, None, vals, rhs)
+    c.record()
+    x.zero_()
+    it, rel = fea.fea_cg(m.h, 2, 1, vals, rhs, x, rtol=rtol, max_iter=max_iter)
+    e.record()
+    torch.cuda.synchronize()
+    m.check()
+    m.close()
+    cg_ms = c.elapsed_time(e)
+    per_it = cg_ms / max(it, 1)
+    bytes_it = 12 * nnz + 108 * ndof
+    return {"unit": "ms", "assemble_ms": a.elapsed_time(b), "dirichlet_ms": b.elapsed_time(c), "cg_ms": cg_ms,
+            "iterations": it, "rel_residual": rel, "ms_per_iteration": per_it,
+            "gbs_per_iteration": bytes_it / (per_it / 1e3) / 1e9,
+            "config": f"P2 diffusion + mass {n}^3 (ndof {ndof}, nnz {nnz}), u = 0 on the boundary, Jacobi PCG to "
+                      f"rtol {rtol}"}
+
+
 # ---------------------------------------------------------------- CPU oracle
 CPU_SAMPLE_N = {"p2_diffmass": 40, "p1_poisson": 64, "p1_kappa": 64, "elasticity": 32}
 
@@ -703,7 +750,7 @@ def main():
     p.add_argument("--no-forms", action="store_true")
     p.add_argument("--forms", default="all",
                    help="comma list of extra forms to time: mixed, atomic_alg1, batched, adjoint, elasticity_128, "
-                        "p1_kappa_96, paper_2d, jit (default all)")
+                        "p1_kappa_96, paper_2d, jit, solve (default all)")
     args = p.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -107,6 +107,9 @@ def lib() -> C.CDLL:
         "fea_jit_info": [_vp, C.POINTER(C.c_double), i64p, C.POINTER(C.c_int32)],
         "fea_jit_assemble": [_vp, _vp, C.POINTER(fea_coeffs), _vp, _vp, _vp],
         "fea_jit_destroy": [_vp],
+        "fea_dirichlet": [_vp, C.c_int32, C.c_int32, _vp, C.c_int64, _vp, _vp, _vp, _vp],
+        "fea_cg": [_vp, C.c_int32, C.c_int32, _vp, _vp, _vp, C.c_double, C.c_int32, C.POINTER(C.c_int32),
+                   C.POINTER(C.c_double), _vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -203,6 +206,21 @@ def fea_jit_assemble(h, jh, coeffs, values, rhs=None, stream=None):
 
 def fea_jit_destroy(jh):
     _check(lib().fea_jit_destroy(jh), "fea_jit_destroy")
+
+
+def fea_dirichlet(h, order, dofs_per_node, dofs, g, values, rhs=None, stream=None):
+    """Impose u = g at dofs (int32 CUDA tensor; g FP64 CUDA tensor or None)."""
+    n = 0 if dofs is None else dofs.numel()
+    _check(lib().fea_dirichlet(h, order, dofs_per_node, _ptr(dofs), n, _ptr(g), _ptr(values), _ptr(rhs),
+                               _stream(stream)), "fea_dirichlet")
+
+
+def fea_cg(h, order, dofs_per_node, values, b, x, rtol=1e-10, max_iter=10000, stream=None):
+    """Jacobi-preconditioned CG in place on x; returns (iterations, ||r|| / ||b||)."""
+    it, rr = C.c_int32(), C.c_double()
+    _check(lib().fea_cg(h, order, dofs_per_node, _ptr(values), _ptr(b), _ptr(x), rtol, max_iter, C.byref(it),
+                        C.byref(rr), _stream(stream)), "fea_cg")
+    return it.value, rr.value
 
 
 def fea_mesh_set_coords(h, x, y, z):
