@@ -155,7 +155,7 @@ fea_status fea_mesh_set_stages(fea_mesh* mesh, int32_t stages);
  * by cp.async.bulk copies through a three-stage mbarrier ring (scalar forms;
  * elasticity falls back to 0).  The incidence-order scatters: 0 = one launch
  * of the two-deep pipelined kernel over all row tiles; 1 = tiles whose CSR
- * span exceeds 60% of the widest in one such launch, the rest in a second
+ * span exceeds half the widest in one such launch, the rest in a second
  * launch with a smaller shared-memory size and a one-deep kernel; 2 = one
  * launch of the one-deep kernel.  -1 (default) = automatic: 3 for scalar
  * forms, else 2 when the pattern mixes long and short rows, else 0.

@@ -81,12 +81,17 @@ __device__ __forceinline__ void elem_scalar_body(const ElemArgs& A, int64_t e) {
   if constexpr (ORDER == 1) {
     // K_ab = kappa |T| grad lambda_a . grad lambda_b ; M_ab = |T| (1 + delta_ab) / 20
     const R s = R(kap * grad_scale<R>(adet));
-    [[maybe_unused]] R t = R(0);
-    if constexpr (MASS) t = R(A.mass * adet * (1.0 / 120.0));
+    [[maybe_unused]] R t1 = R(0), t2 = R(0);  // mass entries |T| / 20 and 2 |T| / 20
+    if constexpr (MASS) {
+      t1 = R(A.mass * adet * (1.0 / 120.0));
+      t2 = t1 + t1;
+    }
     static_for<10>([&](auto K) {
       constexpr int a = upper_a(4, K), b = upper_b(4, K);
-      R v = s * dot3(Gr[a], Gr[b]);
-      if constexpr (MASS) v = fma(t, R(a == b ? 2 : 1), v);
+      R v;
+      if constexpr (MASS && IsDouble<R>::value) v = fma(s, dot3(Gr[a], Gr[b]), a == b ? t2 : t1);
+      else if constexpr (MASS) v = fma(t1, R(a == b ? 2 : 1), s * dot3(Gr[a], Gr[b]));
+      else v = s * dot3(Gr[a], Gr[b]);
       Kl[a][b] = v;
       Kl[b][a] = v;
     });
@@ -100,12 +105,26 @@ __device__ __forceinline__ void elem_scalar_body(const ElemArgs& A, int64_t e) {
       G[i][j] = s * dot3(Gr[i], Gr[j]);
       if constexpr (i != j) G[j][i] = G[i][j];
     });
+    // FP64: |T| / 420 times each of the seven values of the P2 mass pattern
+    // starts the entry's FMA chain (one FP64 operation less per entry); the
+    // FP32 products of the mixed path add the mass term last
+    constexpr bool FOLD = MASS && IsDouble<R>::value;
+    [[maybe_unused]] R tm[7];
     [[maybe_unused]] R t = R(0);
     if constexpr (MASS) t = R(A.mass * adet * (1.0 / 2520.0));
+    if constexpr (FOLD) {
+#pragma unroll
+      for (int c = 0; c < 7; ++c) tm[c] = c == 1 ? t : R(p2_mass_value(c)) * t;
+    }
     static_for<55>([&](auto K) {
       constexpr int a = upper_a(10, K), b = upper_b(10, K);
-      R v = p2_stiff<K, R>(G);
-      if constexpr (MASS) v = fma(t, R(p2_mass420(a, b)), v);
+      R v;
+      if constexpr (FOLD) {
+        v = p2_stiff<K, R>(G, tm[p2_mass_class(a, b)]);
+      } else {
+        v = p2_stiff<K, R>(G);
+        if constexpr (MASS) v = fma(t, R(p2_mass420(a, b)), v);
+      }
       Kl[a][b] = v;
       Kl[b][a] = v;
     });

@@ -140,12 +140,26 @@ __device__ __forceinline__ void elem_user_body(const UserArgs& A, int64_t e) {
       G[i][j] = L[i][j];
       if constexpr (i != j) G[j][i] = G[i][j];
     });
+    // FP64: |T| / 420 times each of the seven values of the P2 mass pattern
+    // starts the entry's FMA chain (one FP64 operation less per entry); the
+    // FP32 products of the mixed path add the mass term last
+    constexpr bool FOLD = MASS && IsDouble<R>::value;
+    [[maybe_unused]] R tm[7];
     [[maybe_unused]] R t = R(0);
     if constexpr (MASS) t = R(A.mass * adet * (1.0 / 2520.0));
+    if constexpr (FOLD) {
+#pragma unroll
+      for (int c = 0; c < 7; ++c) tm[c] = c == 1 ? t : R(p2_mass_value(c)) * t;
+    }
     static_for<55>([&](auto K) {
       constexpr int a = upper_a(10, K), b = upper_b(10, K);
-      R v = p2_stiff<K, R>(G);
-      if constexpr (MASS) v = fma(t, R(p2_mass420(a, b)), v);
+      R v;
+      if constexpr (FOLD) {
+        v = p2_stiff<K, R>(G, tm[p2_mass_class(a, b)]);
+      } else {
+        v = p2_stiff<K, R>(G);
+        if constexpr (MASS) v = fma(t, R(p2_mass420(a, b)), v);
+      }
       Kl[a][b] = v;
       Kl[b][a] = v;
     });

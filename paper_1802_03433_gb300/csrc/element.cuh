@@ -486,7 +486,8 @@ __device__ __forceinline__ void shape_load(const R Xr[4][3], R Fs[ORDER == 1 ? 4
 }
 
 // ------------------------------------------------------------------ P2 stiffness entries
-// K_ab (upper pair number K) = sum_t num_t * G[i_t][j_t] (G already scaled).
+// K_ab (upper pair number K) = [c +] sum_t num_t * G[i_t][j_t] (G already
+// scaled); c, when given, starts the FMA chain (the entry's mass term).
 template <int K, typename R>
 __device__ __forceinline__ R p2_stiff(const R G[4][4]) {
   constexpr int A = upper_a(10, K), B = upper_b(10, K);
@@ -496,6 +497,27 @@ __device__ __forceinline__ R p2_stiff(const R G[4][4]) {
   if constexpr (t.n > 2) v = fma(R(t.num[2]), G[t.i[2]][t.j[2]], v);
   if constexpr (t.n > 3) v = fma(R(t.num[3]), G[t.i[3]][t.j[3]], v);
   return v;
+}
+template <int K, typename R>
+__device__ __forceinline__ R p2_stiff(const R G[4][4], R c) {
+  constexpr int A = upper_a(10, K), B = upper_b(10, K);
+  constexpr Terms t = p2_terms(A, B);
+  R v = fma(R(t.num[0]), G[t.i[0]][t.j[0]], c);
+  if constexpr (t.n > 1) v = fma(R(t.num[1]), G[t.i[1]][t.j[1]], v);
+  if constexpr (t.n > 2) v = fma(R(t.num[2]), G[t.i[2]][t.j[2]], v);
+  if constexpr (t.n > 3) v = fma(R(t.num[3]), G[t.i[3]][t.j[3]], v);
+  return v;
+}
+
+// The P2 mass pattern 420 |T|^{-1} M_ab takes seven values; mass_class(a, b)
+// numbers them, so the element kernels form t * value once per class and
+// start each entry's stiffness FMA chain from it.
+__host__ __device__ constexpr int p2_mass_value(int c) {
+  return c == 0 ? 6 : c == 1 ? 1 : c == 2 ? -4 : c == 3 ? -6 : c == 4 ? 32 : c == 5 ? 16 : 8;
+}
+__host__ __device__ constexpr int p2_mass_class(int a, int b) {
+  const int v = p2_mass420(a, b);
+  return v == 6 ? 0 : v == 1 ? 1 : v == -4 ? 2 : v == -6 ? 3 : v == 32 ? 4 : v == 16 ? 5 : 6;
 }
 
 }  // namespace fea

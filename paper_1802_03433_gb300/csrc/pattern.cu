@@ -742,7 +742,9 @@ fea_status build_pattern(fea_mesh* m, int order, int ndpn, cudaStream_t s) {
   if (st == FEA_OK && (int64_t)P->max_tile_nnz * 8 > 220 * 1024)
     st = fail(FEA_ERR_OVERFLOW, "a single row is too long for the shared-memory scatter");
   if (st == FEA_OK) {
-    // two tile classes: spans up to 60% of the widest go to the light launch
+    // two tile classes: spans up to half the widest go to the light launch
+    // (for P2 that separates the vertex-dof tiles from the edge-dof tiles,
+    // whose accumulator then leaves room for three CTAs per SM)
     const int64_t ntiles = (P->ndof + P->rows_per_tile - 1) / P->rows_per_tile;
     std::vector<int32_t> span(std::max<int64_t>(ntiles, 1));
     if (ntiles > 0) {
@@ -755,7 +757,7 @@ fea_status build_pattern(fea_mesh* m, int order, int ndpn, cudaStream_t s) {
       }
     }
     if (st == FEA_OK) {
-      const int64_t cut = P->max_tile_nnz * 6 / 10;
+      const int64_t cut = P->max_tile_nnz / 2;
       std::vector<int32_t> list;
       list.reserve(ntiles);
       for (int64_t t = 0; t < ntiles; ++t)
