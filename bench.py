@@ -41,12 +41,12 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # current kernels.
 FP64_FLOP_PER_ELEM = {
     ("p2_diffmass_64", "fp64"): 1194.0,   # 444 DFMA + 154 DADD + 152 DMUL per element
-    ("p1_kappa_96", "fp64"): 421.0,       # 143 DFMA + 60 DADD + 75 DMUL
+    ("p1_kappa_96", "fp64"): 409.0,       # 136 DFMA + 63 DADD + 74 DMUL
     ("p1_elast_128", "fp64"): 370.0,      # 114 DFMA + 16 DADD + 126 DMUL
 }
 DRAM_BYTES_PER_LAUNCH = {
-    ("p2_diffmass_64", "element"): 138.8e6 + 1594.8e6,
-    ("p1_kappa_96", "element"): 235.0e6 + 793.2e6,
+    ("p2_diffmass_64", "element"): 138.9e6 + 1595.5e6,
+    ("p1_kappa_96", "element"): 238.4e6 + 793.2e6,
     ("p1_elast_128", "element"): 705.8e6 + 15649.2e6,
 }
 
