@@ -249,10 +249,72 @@ __device__ __forceinline__ double sinpi_fp64(double x) {
   return __hiloint2double(__double2hiint(sv) ^ flip, __double2loint(sv));
 }
 
+// sin(pi x) to FP64 accuracy with the polynomial on the integer pipes (the
+// FP64 pipe retires two operations per SM and clock on this part, the
+// integer multiply-add path 64).  For 2^-10 <= |x| < 2^51:
+//   * reduction from the bits of x: x = m 2^(e-1075), so the fraction of x in
+//     units of 2^-64 is (m << (e - 1011)) mod 2^64 and the parity of the
+//     integer part is bit (64 - (e - 1011)) of m; rounding to the nearest
+//     integer n leaves r = x - n with |r| <= 1/2 exactly (ra = |r| 2^64);
+//   * u = r^2 and the degree-8 interpolant P(u) of sin(pi r)/r (9 Chebyshev
+//     nodes on [0, 1/4], relative error 3.2e-19, gen_sinpi.py) by Horner in
+//     signed fixed point with 60 fractional bits (64 x 64 -> high 64-bit
+//     products);
+//   * s = |r| P as the exact 128-bit product, rounded once to the nearest
+//     double (ties to even) by integer normalisation;
+//   * sign (-1)^n sign(r) sign(x).
+// Within 0.51 ulp of sin(pi x) (exact-arithmetic model of these steps against
+// 50-digit sin).  In the fast path |r| >= 2^-53, so the product's high word
+// is at least 2^8 and every shift below is by 9 to 61 bits.  Other arguments
+// (tiny, huge, zero, subnormal, infinite, NaN) take sinpi_fp64.
+constexpr long long SINPI_Q0 = 3622009729038561420LL;
+constexpr long long SINPI_Q1 = -5957967193751243029LL;
+constexpr long long SINPI_Q2 = 2940138961849612574LL;
+constexpr long long SINPI_Q3 = -690904962799911665LL;
+constexpr long long SINPI_Q4 = 94707759145125179LL;
+constexpr long long SINPI_Q5 = -8497527828481967LL;
+constexpr long long SINPI_Q6 = 537607085679486LL;
+constexpr long long SINPI_Q7 = -25253012803429LL;
+constexpr long long SINPI_Q8 = 887499001982LL;
+
+__device__ __forceinline__ double sinpi_fx(double x) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const unsigned e = static_cast<unsigned>(b >> 52) & 0x7FFu;
+  if (e - 1013u > 60u) return sinpi_fp64(x);
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const unsigned sh = e - 1011u;  // 2 .. 62
+  const unsigned long long f = m << sh;
+  const unsigned rneg = static_cast<unsigned>(f >> 63);
+  const unsigned par = (sh > 11u ? static_cast<unsigned>(m >> (64u - sh)) & 1u : 0u) ^ rneg;
+  const unsigned long long ra = rneg ? 0ull - f : f;
+  if (ra == 0ull) return __longlong_as_double(static_cast<long long>(b & 0x8000000000000000ull));
+  const long long u = static_cast<long long>(__umul64hi(ra, ra));
+  long long p = SINPI_Q8;
+  p = __mul64hi(p, u) + SINPI_Q7;
+  p = __mul64hi(p, u) + SINPI_Q6;
+  p = __mul64hi(p, u) + SINPI_Q5;
+  p = __mul64hi(p, u) + SINPI_Q4;
+  p = __mul64hi(p, u) + SINPI_Q3;
+  p = __mul64hi(p, u) + SINPI_Q2;
+  p = __mul64hi(p, u) + SINPI_Q1;
+  p = __mul64hi(p, u) + SINPI_Q0;
+  const unsigned long long up = static_cast<unsigned long long>(p);
+  const unsigned long long hi = __umul64hi(ra, up), lo = ra * up;
+  const int lz = __clzll(static_cast<long long>(hi));
+  const unsigned long long top = (hi << lz) | (lo >> (64 - lz));
+  const bool sticky = (lo << lz) != 0ull;
+  unsigned long long mant = top >> 11;
+  const unsigned rb = static_cast<unsigned>(top) & 0x7FFu;
+  mant += (rb > 0x400u || (rb == 0x400u && (sticky || (mant & 1ull)))) ? 1ull : 0ull;
+  const unsigned long long sign = ((b >> 63) ^ par ^ rneg) << 63;
+  const unsigned long long bits = (static_cast<unsigned long long>(1025 - lz) << 52) + mant;
+  return __longlong_as_double(static_cast<long long>(bits | sign));
+}
+
 template <typename R>
 __device__ __forceinline__ R rsinpi(R v);
 template <>
-__device__ __forceinline__ double rsinpi<double>(double v) { return sinpi_fp64(v); }
+__device__ __forceinline__ double rsinpi<double>(double v) { return sinpi_fx(v); }
 template <>
 __device__ __forceinline__ float rsinpi<float>(float v) { return sinpif(v); }
 

@@ -94,7 +94,7 @@ def lib() -> C.CDLL:
                                   C.POINTER(fea_quadrature), _vp, _vp, _vp, _vp, _vp],
         "fea_profile_enable": [_vp, C.c_int32],
         "fea_profile_last": [_vp, C.POINTER(C.c_float), C.POINTER(C.c_float)],
-        "fea_diag_sinpi": [_vp, C.c_int64, _vp, _vp, _vp],
+        "fea_diag_sinpi": [_vp, C.c_int64, C.c_int32, _vp, _vp, _vp],
         "fea_diag_fp64_rate": [C.POINTER(C.c_double), _vp],
         "fea_batch_create": [C.POINTER(_vp), C.c_int32, C.POINTER(fea_form), C.POINTER(fea_quadrature),
                              C.c_int32, _vp, C.POINTER(_vp)],
@@ -309,11 +309,13 @@ def fea_profile_last(h):
     return a.value, b.value
 
 
-def fea_diag_sinpi(x, stream=None):
-    """(kernel helper sin(pi x), CUDA sinpi(x)) for a CUDA float64 tensor x."""
+def fea_diag_sinpi(x, variant=0, stream=None):
+    """(helper sin(pi x), CUDA sinpi(x)) for a CUDA float64 tensor x; variant 0
+    = the element kernels' fixed-point evaluation, 1 = the FP64 polynomial."""
     _dev(x, torch.float64, "x")
     mine, ref = torch.empty_like(x), torch.empty_like(x)
-    _check(lib().fea_diag_sinpi(_ptr(x), x.numel(), _ptr(mine), _ptr(ref), _stream(stream)), "fea_diag_sinpi")
+    _check(lib().fea_diag_sinpi(_ptr(x), x.numel(), variant, _ptr(mine), _ptr(ref), _stream(stream)),
+           "fea_diag_sinpi")
     return mine, ref
 
 

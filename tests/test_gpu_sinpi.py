@@ -1,28 +1,46 @@
-"""The element kernels' FP64 sin(pi x) against CUDA's sinpi (GPU)."""
+"""The element kernels' FP64-accurate sin(pi x) helpers against CUDA's sinpi
+(GPU): the fixed-point evaluation the kernels use (variant 0) and the
+FP64-pipe polynomial (variant 1, its fallback)."""
 import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
 
 
-def test_sinpi_matches_cuda_library():
-    import torch
-    from paper_1802_03433_gb300 import fea
+def _args():
     rng = np.random.default_rng(0)
-    x = np.concatenate([
+    ints = np.arange(-8, 9, dtype=np.float64)
+    near = np.concatenate([ints + d for d in (2.0 ** -40, -2.0 ** -40, 1e-3, -1e-3, 1e-9, -1e-9)])
+    return np.concatenate([
         rng.uniform(-4, 4, 1 << 20), rng.uniform(0, 1, 1 << 18),
         np.arange(-8, 8.5, 0.5), np.arange(-8, 8.5, 0.25), [0.0, -0.0, 1e-300, -1e-300, 5e-324],
         [2.0 ** 51 - 0.5, 2.0 ** 51, 2.0 ** 53 + 2, 1e300, -1e300, np.inf, -np.inf, np.nan],
-        np.nextafter(0.5, 1) + np.arange(16) * 1e-16, rng.uniform(-1e6, 1e6, 4096)])
+        np.nextafter(0.5, 1) + np.arange(16) * 1e-16, rng.uniform(-1e6, 1e6, 4096), near,
+        # both sides of the fixed-point path's lower bound 2^-10 and upper bound 2^51
+        2.0 ** -10 * np.array([0.999999, 1.0, 1.000001]), -(2.0 ** -10) * np.array([0.999999, 1.0, 1.000001]),
+        np.nextafter(2.0 ** 51, 0) - np.arange(4), rng.uniform(2.0 ** 40, 2.0 ** 51, 256)])
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_sinpi_matches_cuda_library(variant):
+    import torch
+    from paper_1802_03433_gb300 import fea
+    x = _args()
     xt = torch.as_tensor(x, device="cuda")
-    mine, ref = (t.cpu().numpy() for t in fea.fea_diag_sinpi(xt))
+    mine, ref = (t.cpu().numpy() for t in fea.fea_diag_sinpi(xt, variant))
     finite = np.isfinite(x)
     assert np.array_equal(np.isnan(mine), np.isnan(ref))
     err = np.abs(mine[finite] - ref[finite])
     assert err.max() <= 4.5e-16, err.max()
+    # relative accuracy where the value is small (near the zeros of sin(pi x))
+    small = finite & (np.abs(ref) > 0) & (np.abs(ref) < 1e-2)
+    rel = np.abs(mine[small] - ref[small]) / np.abs(ref[small])
+    assert rel.max() <= 6e-16, rel.max()
     # odd symmetry and exact values at half-integers and zeros
     half = np.arange(-8, 8.5, 0.5)
-    m = fea.fea_diag_sinpi(torch.as_tensor(half, device="cuda"))[0].cpu().numpy()
+    m = fea.fea_diag_sinpi(torch.as_tensor(half, device="cuda"), variant)[0].cpu().numpy()
     np.testing.assert_array_equal(np.abs(m[(half * 2) % 2 == 0]), 0.0)
     np.testing.assert_allclose(np.abs(m[(half * 2) % 2 == 1]), 1.0, rtol=0, atol=4.5e-16)
-    assert np.signbit(fea.fea_diag_sinpi(torch.tensor([-0.0], device="cuda", dtype=torch.float64))[0].item())
+    assert np.signbit(fea.fea_diag_sinpi(torch.tensor([-0.0], device="cuda", dtype=torch.float64), variant)[0].item())
+    sym = fea.fea_diag_sinpi(torch.as_tensor(-x[finite], device="cuda"), variant)[0].cpu().numpy()
+    np.testing.assert_array_equal(sym, -mine[finite])
