@@ -82,7 +82,7 @@ fea_status assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* co, con
   const bool sequential = stages == 1 || E < (int64_t)stages * ELEM_T;
   // local rows in the tiled layout (bulk-copy scatter, scalar forms) or in
   // incidence order (E * nb incidences x ndpn rows), lstride values apart
-  const bool tiled = sequential && use_tiled(m, P);
+  const bool tiled = use_tiled(m, P);
   const size_t nrows_local = tiled ? (size_t)P->npos : (size_t)E * nb * ndpn;
   FEA_TRY(ensure_scratch(m->lm, nrows_local * lstride(nl, (int)rb) * rb));
   if (load != FEA_LOAD_NONE) FEA_TRY(ensure_scratch(m->fl, nrows_local * rb));
@@ -160,8 +160,11 @@ fea_status assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* co, con
       FEA_CUDA(cudaEventRecord(m->chunk_ev[k], s));
       FEA_CUDA(cudaStreamWaitEvent(m->side, m->chunk_ev[k], 0));
       const int64_t t0 = P->stage_ptr[k], t1 = P->stage_ptr[k + 1];
-      FEA_TRY(launch_gather(nb, ndpn, mixed, G, P->rows_per_tile, P->max_tile_nnz, m->side, P->tile_list + t0,
-                            t1 - t0));
+      if (tiled)
+        FEA_TRY(scatter_tiled_list(m, P, B, mixed, A.Lm, A.Fl, values, rhs, P->tile_list + t0, t1 - t0, m->side));
+      else
+        FEA_TRY(launch_gather(nb, ndpn, mixed, G, P->rows_per_tile, P->max_tile_nnz, m->side, P->tile_list + t0,
+                              t1 - t0));
     }
     if (m->profile) FEA_CUDA(cudaEventRecord(m->ev[1], s));
     FEA_CUDA(cudaEventRecord(m->chunk_ev[16], m->side));

@@ -34,10 +34,9 @@ bool use_tiled(const fea_mesh* m, const Pattern* P) {
   return P && P->npos > 0 && P->ndpn == 1 && (m->tile_classes == -1 || m->tile_classes == 3);
 }
 
-fea_status scatter_tiled(const fea_mesh* m, const Pattern* P, const Base* B, bool mixed, const void* Lm,
-                         const void* Fl, double* values, double* rhs, cudaStream_t s) {
-  if (!P->tpos || !P->tslot || !P->tile_base || !P->tile_steps || P->npos <= 0)
-    return fail(FEA_ERR_STATE, "bulk-copy scatter without a tiled layout");
+namespace {
+TiledArgs tiled_args(const fea_mesh* m, const Pattern* P, const Base* B, const void* Lm, const void* Fl,
+                     double* values, double* rhs) {
   TiledArgs G{};
   G.ndof = P->ndof;
   G.rows = P->rows_per_tile;
@@ -51,6 +50,15 @@ fea_status scatter_tiled(const fea_mesh* m, const Pattern* P, const Base* B, boo
   G.values = values;
   G.rhs = rhs;
   G.err = m->err;
+  return G;
+}
+}  // namespace
+
+fea_status scatter_tiled(const fea_mesh* m, const Pattern* P, const Base* B, bool mixed, const void* Lm,
+                         const void* Fl, double* values, double* rhs, cudaStream_t s) {
+  if (!P->tpos || !P->tslot || !P->tile_base || !P->tile_steps || P->npos <= 0)
+    return fail(FEA_ERR_STATE, "bulk-copy scatter without a tiled layout");
+  TiledArgs G = tiled_args(m, P, B, Lm, Fl, values, rhs);
   if (P->class_list && P->n_heavy > 0 && P->n_light > 0) {
     // long-row tiles, then short-row tiles with a smaller accumulator (more CTAs per SM)
     G.span_cap = P->heavy_span;
@@ -60,6 +68,16 @@ fea_status scatter_tiled(const fea_mesh* m, const Pattern* P, const Base* B, boo
   }
   G.span_cap = P->max_tile_nnz;
   return launch_gather_tiled(B->nb, mixed, G, s, nullptr, (P->ndof + G.rows - 1) / G.rows);
+}
+
+fea_status scatter_tiled_list(const fea_mesh* m, const Pattern* P, const Base* B, bool mixed, const void* Lm,
+                              const void* Fl, double* values, double* rhs, const int32_t* tiles, int64_t ntiles,
+                              cudaStream_t s) {
+  if (!P->tpos || !P->tslot || !P->tile_base || !P->tile_steps || P->npos <= 0)
+    return fail(FEA_ERR_STATE, "bulk-copy scatter without a tiled layout");
+  TiledArgs G = tiled_args(m, P, B, Lm, Fl, values, rhs);
+  G.span_cap = P->max_tile_nnz;
+  return launch_gather_tiled(B->nb, mixed, G, s, tiles, ntiles);
 }
 
 }  // namespace fea

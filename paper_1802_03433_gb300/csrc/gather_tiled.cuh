@@ -278,4 +278,9 @@ bool use_tiled(const fea_mesh* m, const Pattern* P);
 fea_status scatter_tiled(const fea_mesh* m, const Pattern* P, const Base* B, bool mixed, const void* Lm,
                          const void* Fl, double* values, double* rhs, cudaStream_t s);
 
+// The tiles tiles[0 .. ntiles) only (one stage of the overlapped assembly).
+fea_status scatter_tiled_list(const fea_mesh* m, const Pattern* P, const Base* B, bool mixed, const void* Lm,
+                              const void* Fl, double* values, double* rhs, const int32_t* tiles, int64_t ntiles,
+                              cudaStream_t s);
+
 }  // namespace fea
