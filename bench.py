@@ -185,6 +185,8 @@ def run_ours(args):
     fea.fea_mesh_set_stages(mesh.h, args.stages)
     if args.scatter_classes >= 0:
         fea.fea_mesh_set_scatter_classes(mesh.h, args.scatter_classes)
+    if args.load_split >= 0:
+        fea.fea_mesh_set_load_split(mesh.h, args.load_split)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ndof, nnz = mesh.pattern(d["order"], d["ndpn"])
@@ -744,7 +746,10 @@ def main():
     p.add_argument("--workload", default="p2_diffmass_64", choices=sorted(WORKLOADS))
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--stages", type=int, default=1, help="element chunks overlapped with the scatter (1 = none)")
-    p.add_argument("--scatter-classes", type=int, default=-1, help="scatter launch shape 0/1/2 (-1 = library default)")
+    p.add_argument("--scatter-classes", type=int, default=-1, help="scatter launch shape 0-3 (-1 = library default)")
+    p.add_argument("--load-split", type=int, default=-1, help="element launch: 0 fused, 1 matrix then load, "
+                                                               "2 load kernel concurrent with the matrix kernel "
+                                                               "(-1 = library default)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-forms", action="store_true")

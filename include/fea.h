@@ -162,6 +162,14 @@ fea_status fea_mesh_set_stages(fea_mesh* mesh, int32_t stages);
  * Results are bitwise identical for every mode. */
 fea_status fea_mesh_set_scatter_classes(fea_mesh* mesh, int32_t mode);
 
+/* Element launch of fea_assemble for scalar forms with a load vector (stages
+ * == 1): 0 = one kernel computes the local matrix and the local load; 1 = a
+ * matrix kernel, then a load kernel; 2 = the load kernel on a stream owned
+ * by the handle, concurrent with the matrix kernel (joined back to
+ * `stream`); -1 (default) = automatic: 2 for FP64 P2, else 0.  Results are
+ * bitwise identical for every mode. */
+fea_status fea_mesh_set_load_split(fea_mesh* mesh, int32_t mode);
+
 /* Release the handle and everything it owns.  Synchronises the device. */
 fea_status fea_mesh_destroy(fea_mesh* mesh);
 

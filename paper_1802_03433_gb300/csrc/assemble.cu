@@ -122,7 +122,28 @@ fea_status assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* co, con
     A.e0 = 0;
     A.e1 = E;
     if (m->profile) FEA_CUDA(cudaEventRecord(m->ev[0], s));
-    FEA_TRY(launch_elements(form, A, load, q->npts, prec, s));
+    // FP64 P2: the matrix part is FP64-bound and the load part bound by the
+    // integer-pipe sines, so they run as two concurrent kernels; for P1 the
+    // matrix part is small and one fused kernel is faster
+    const int split_mode = m->load_split >= 0 ? m->load_split : (order == 2 && !mixed ? 2 : 0);
+    const bool split = split_mode > 0 && load != FEA_LOAD_NONE && form->kind != FEA_ELASTICITY;
+    if (!split) {
+      FEA_TRY(launch_elements(form, A, load, q->npts, prec, s));
+    } else if (split_mode == 1) {
+      FEA_TRY(launch_elements(form, A, FEA_LOAD_NONE, q->npts, prec, s));
+      FEA_TRY(launch_elem_load(order, A, load, q->npts, prec, s));
+    } else {
+      // the load kernel on the side stream, concurrent with the matrix kernel
+      if (!m->side) FEA_CUDA(cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking));
+      for (int k : {15, 16})
+        if (!m->chunk_ev[k]) FEA_CUDA(cudaEventCreateWithFlags(&m->chunk_ev[k], cudaEventDisableTiming));
+      FEA_CUDA(cudaEventRecord(m->chunk_ev[16], s));
+      FEA_CUDA(cudaStreamWaitEvent(m->side, m->chunk_ev[16], 0));
+      FEA_TRY(launch_elem_load(order, A, load, q->npts, prec, m->side));
+      FEA_TRY(launch_elements(form, A, FEA_LOAD_NONE, q->npts, prec, s));
+      FEA_CUDA(cudaEventRecord(m->chunk_ev[15], m->side));
+      FEA_CUDA(cudaStreamWaitEvent(s, m->chunk_ev[15], 0));
+    }
     if (m->profile) FEA_CUDA(cudaEventRecord(m->ev[1], s));
     int mode = m->tile_classes;
     if (tiled) mode = 3;

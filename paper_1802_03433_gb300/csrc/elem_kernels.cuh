@@ -173,6 +173,29 @@ __global__ void __launch_bounds__(ELEM_T) k_elem_scalar(ElemArgs A) {
   if (e < A.e1) elem_scalar_body<ORDER, MASS, LOAD, NPTS, R, ATOMIC>(A, e);
 }
 
+// The load vector alone (F_a of Eq. 3 on one element), for running the load
+// as its own kernel beside the matrix kernel (launched with LOAD_NONE): the
+// matrix part is FP64-bound, the load part bound by the integer-pipe sines.
+// |det J| comes from det_only(), the same operations as geometry() in the
+// fused kernel, so the loads are bitwise the same.
+template <int ORDER, int LOAD, int NPTS, typename R>
+__global__ void __launch_bounds__(ELEM_T) k_elem_load(ElemArgs A) {
+  constexpr int NB = ORDER == 1 ? 4 : 10;
+  const int64_t e = A.e0 + (int64_t)blockIdx.x * ELEM_T + threadIdx.x;
+  if (e >= A.e1) return;
+  double X[4][3];
+  load_element(A, e, X);
+  const double adet = fabs(det_only(X));
+  R Xr[4][3];
+  vertices_r<R>(X, Xr);
+  R Fs[NB];
+  shape_load<ORDER, NPTS, LOAD, R>(Xr, Fs);
+  const R amp = R(A.fp[0] * adet * (1.0 / 6.0));
+  R* __restrict__ Fl = static_cast<R*>(A.Fl);
+#pragma unroll
+  for (int a = 0; a < NB; ++a) Fl[__ldg(A.ipos + a * A.E + e)] = amp * Fs[a];
+}
+
 // Deterministic-path output of the elasticity kernel: local rows in
 // incidence order (whole sectors) and local loads.
 template <int LOAD, int NPTS, typename R>
@@ -274,6 +297,7 @@ __global__ void __launch_bounds__(ELEM_T) k_elem_elast(ElemArgs A) {
 // Launchers (one translation unit per element family).
 fea_status launch_elem_p1(const ElemArgs& A, bool mass, int load, int npts, int prec, cudaStream_t s);
 fea_status launch_elem_p2(const ElemArgs& A, bool mass, int load, int npts, int prec, cudaStream_t s);
+fea_status launch_elem_load(int order, const ElemArgs& A, int load, int npts, int prec, cudaStream_t s);
 fea_status launch_elem_elast(const ElemArgs& A, int load, int npts, int prec, cudaStream_t s);
 
 }  // namespace fea

@@ -33,6 +33,30 @@ struct ScalarLauncher {
   }
 };
 
+template <int ORDER>
+struct LoadLauncher {
+  template <int LOAD, int NPTS>
+  static void go(const ElemArgs& A, int prec, cudaStream_t s) {
+    if (prec == FEA_FP64)
+      k_elem_load<ORDER, LOAD, NPTS, double><<<elem_blocks(A), ELEM_T, 0, s>>>(A);
+    else
+      k_elem_load<ORDER, LOAD, NPTS, float><<<elem_blocks(A), ELEM_T, 0, s>>>(A);
+  }
+  template <int NPTS>
+  static void by_load(const ElemArgs& A, int load, int prec, cudaStream_t s) {
+    if (load == LOAD_CONST) go<LOAD_CONST, NPTS>(A, prec, s);
+    else go<LOAD_SIN, NPTS>(A, prec, s);
+  }
+  static fea_status run(const ElemArgs& A, int load, int npts, int prec, cudaStream_t s) {
+    if (A.e1 <= A.e0 || load == LOAD_NONE) return FEA_OK;
+    if (npts == 1) by_load<1>(A, load, prec, s);
+    else if (npts == 4) by_load<4>(A, load, prec, s);
+    else by_load<11>(A, load, prec, s);
+    FEA_CUDA(cudaGetLastError());
+    return FEA_OK;
+  }
+};
+
 struct ElastLauncher {
   template <int LOAD, int NPTS>
   static void go(const ElemArgs& A, int prec, cudaStream_t s) {

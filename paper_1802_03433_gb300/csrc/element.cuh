@@ -212,6 +212,22 @@ __device__ __forceinline__ void geometry(const double X[4][3], Geo& g) {
   for (int k = 0; k < 3; ++k) g.c[0][k] = -(g.c[1][k] + g.c[2][k] + g.c[3][k]);
 }
 
+// det J alone, by exactly the operations geometry() uses for it (bitwise the
+// same value): e_i = x_i - x_0, c_1 = e_2 x e_3, det = e_1 . c_1.
+__device__ __forceinline__ double det_only(const double X[4][3]) {
+  double e[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) e[i][k] = X[i + 1][k] - X[0][k];
+  const double* u = e[1];
+  const double* w = e[2];
+  const double c0 = fma(u[1], w[2], -u[2] * w[1]);
+  const double c1 = fma(u[2], w[0], -u[0] * w[2]);
+  const double c2 = fma(u[0], w[1], -u[1] * w[0]);
+  return fma(e[0][0], c0, fma(e[0][1], c1, e[0][2] * c2));
+}
+
 // sin(pi x) in FP64 with 11 FP64 operations (the library sinpi costs about
 // 18 FP64-pipe operations on this part).  Range reduction: adding
 // 1.5 * 2^52 rounds x to the nearest integer n (ties to even) and leaves the

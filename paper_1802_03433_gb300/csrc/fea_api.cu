@@ -193,6 +193,13 @@ fea_status fea_mesh_set_stages(fea_mesh* m, int32_t stages) {
   return FEA_OK;
 }
 
+fea_status fea_mesh_set_load_split(fea_mesh* m, int32_t mode) {
+  if (!m) return fail(FEA_ERR_ARG, "mesh is NULL");
+  if (mode < -1 || mode > 2) return fail(FEA_ERR_ARG, "mode must be -1, 0, 1 or 2");
+  m->load_split = mode;
+  return FEA_OK;
+}
+
 fea_status fea_mesh_set_scatter_classes(fea_mesh* m, int32_t mode) {
   if (!m) return fail(FEA_ERR_ARG, "mesh is NULL");
   if (mode < -1 || mode > 3) return fail(FEA_ERR_ARG, "mode must be -1, 0, 1, 2 or 3");

@@ -80,6 +80,7 @@ def lib() -> C.CDLL:
         "fea_mesh_destroy": [_vp],
         "fea_mesh_set_stages": [_vp, C.c_int32],
         "fea_mesh_set_scatter_classes": [_vp, C.c_int32],
+        "fea_mesh_set_load_split": [_vp, C.c_int32],
         "fea_mesh_check": [_vp, _vp],
         "fea_pattern": [_vp, C.c_int32, C.c_int32, i64p, i64p, _vp],
         "fea_pattern_copy": [_vp, C.c_int32, C.c_int32, _vp, _vp, _vp],
@@ -229,6 +230,10 @@ def fea_mesh_set_coords(h, x, y, z):
 
 def fea_mesh_set_stages(h, stages):
     _check(lib().fea_mesh_set_stages(h, stages), "fea_mesh_set_stages")
+
+
+def fea_mesh_set_load_split(h, mode):
+    _check(lib().fea_mesh_set_load_split(h, mode), "fea_mesh_set_load_split")
 
 
 def fea_mesh_set_scatter_classes(h, mode):

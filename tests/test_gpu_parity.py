@@ -289,3 +289,22 @@ def test_scatter_launch_shapes_bitwise_identical(torch_cuda, kind, n, prec):
         assert np.array_equal(g["rhs"].view(np.uint64), ref["rhs"].view(np.uint64)), mode
     o = oracle_system(c)
     assert row_scaled_error(o["rp"], o["vals"], ref["vals"]) <= (TOL_FP64 if prec == 0 else TOL_MIXED)
+
+
+@pytest.mark.parametrize("kind,n", [("p1_kappa", 10), ("p2_diffmass", 7)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_load_split_modes_bitwise_identical(torch_cuda, kind, n, prec):
+    """Fused element kernel, matrix kernel then load kernel, load kernel on a
+    concurrent stream: same bits."""
+    from paper_1802_03433_gb300 import fea
+    c = case(kind, n, seed=31)
+    m = fea.Mesh(c["coords"], c["tets"])
+    ref = None
+    for mode in (0, 1, 2, -1):
+        fea.fea_mesh_set_load_split(m.h, mode)
+        g = gpu_system(c, prec=prec, mesh=m)
+        if ref is None:
+            ref = g
+            continue
+        assert np.array_equal(g["vals"].view(np.uint64), ref["vals"].view(np.uint64)), mode
+        assert np.array_equal(g["rhs"].view(np.uint64), ref["rhs"].view(np.uint64)), mode
