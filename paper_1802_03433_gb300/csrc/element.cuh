@@ -327,12 +327,23 @@ __device__ __forceinline__ double sinpi_fx(double x) {
   return __longlong_as_double(static_cast<long long>(bits | sign));
 }
 
-template <typename R>
+// One out-of-line copy of sinpi_fx for kernels with many sines: 33 inlined
+// copies of its ~165 instructions overflow the instruction cache (ncu: the
+// P2 load kernel stalled on instruction fetch), one copy called 33 times
+// does not.
+static __device__ __noinline__ double sinpi_fx_call(double x) { return sinpi_fx(x); }
+
+// sin(pi v) in the precision of R; OUTLINE calls the out-of-line copy.
+template <typename R, bool OUTLINE = false>
 __device__ __forceinline__ R rsinpi(R v);
 template <>
-__device__ __forceinline__ double rsinpi<double>(double v) { return sinpi_fx(v); }
+__device__ __forceinline__ double rsinpi<double, false>(double v) { return sinpi_fx(v); }
 template <>
-__device__ __forceinline__ float rsinpi<float>(float v) { return sinpif(v); }
+__device__ __forceinline__ double rsinpi<double, true>(double v) { return sinpi_fx_call(v); }
+template <>
+__device__ __forceinline__ float rsinpi<float, false>(float v) { return sinpif(v); }
+template <>
+__device__ __forceinline__ float rsinpi<float, true>(float v) { return sinpif(v); }
 
 template <typename R>
 __device__ __forceinline__ R to_r(double v);
@@ -541,7 +552,7 @@ __device__ __forceinline__ void rule_sum(const R s[NPTS], R Fs[ORDER == 1 ? 4 : 
 
 // Shape load  Fs_a = sum_q w_q s(x_q) phi_a(x_q)  (without the factor |T|),
 // s = 1 (LOAD_CONST) or sin(pi x) sin(pi y) sin(pi z) (LOAD_SIN).
-template <int ORDER, int NPTS, int LOAD, typename R>
+template <int ORDER, int NPTS, int LOAD, typename R, bool OUTLINE = (ORDER == 2)>
 __device__ __forceinline__ void shape_load(const R Xr[4][3], R Fs[ORDER == 1 ? 4 : 10]) {
   constexpr int NB = ORDER == 1 ? 4 : 10;
   if constexpr (LOAD == LOAD_CONST) {
@@ -557,7 +568,7 @@ __device__ __forceinline__ void shape_load(const R Xr[4][3], R Fs[ORDER == 1 ? 4
       R xq[NPTS];
       quad_coord<NPTS, R>(v, xq);
 #pragma unroll
-      for (int q = 0; q < NPTS; ++q) sq[q] = c == 0 ? rsinpi<R>(xq[q]) : sq[q] * rsinpi<R>(xq[q]);
+      for (int q = 0; q < NPTS; ++q) sq[q] = c == 0 ? rsinpi<R, OUTLINE>(xq[q]) : sq[q] * rsinpi<R, OUTLINE>(xq[q]);
     }
     rule_sum<ORDER, NPTS, R>(sq, Fs);
   }
