@@ -182,8 +182,8 @@ __global__ void __launch_bounds__(ADJ_T) k_adjoint(AdjArgs A) {
 #pragma unroll
             for (int c = 0; c < 4; ++c) v = fma(bary(NPTS, q, c), X[c][k], v);
             xq[k] = v;
-            sn[k] = sinpi_fp64(v);
-            cs[k] = sinpi_fp64(v + 0.5);
+            sn[k] = rsinpi<double, true>(v);        // sin(pi v), integer pipes, one out-of-line copy
+            cs[k] = rsinpi<double, true>(v + 0.5);  // cos(pi v)
           }
           const double f = A.fp0 * sn[0] * sn[1] * sn[2];
           sF = fma(f, wPhi, sF);
