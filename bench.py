@@ -598,7 +598,7 @@ def bench_jit(fea, torch, dev, steps, warmup, flush, n=64):
     q = fea.make_quadrature(11, fea.FEA_FP64)
     vals = torch.empty(nnz, dtype=torch.float64, device=dev)
     rhs = torch.empty(ndof, dtype=torch.float64, device=dev)
-    fexpr = "p0*sinpi_fp64(x)*sinpi_fp64(y)*sinpi_fp64(z)"
+    fexpr = "p0*sinpi_fx(x)*sinpi_fx(y)*sinpi_fx(z)"
     E = d["tets"].shape[1]
     fea.fea_profile_enable(m.h, True)
     out = {}

@@ -335,7 +335,8 @@ fea_status fea_diag_fp64_rate(double* flops_per_s, void* stream);
  * user gives two CUDA C++ expressions of type double in the variables x, y, z
  * (the physical point), the parameters p0..p3 (fea_coeffs.f_param at
  * assembly time) and the constant pi, using CUDA's device math functions
- * (sin, exp, pow, sinpi, ...) and the library's sinpi_fp64:
+ * (sin, exp, pow, sinpi, ...) and the library's sin(pi v) helpers sinpi_fx (on
+ * the integer pipes, within 0.51 ulp) and sinpi_fp64 (on the FP64 pipe):
  *   kappa_expr : k(x) inside the stiffness integral, -div(kappa_T k(x) grad u)
  *                with kappa_T from fea_coeffs (per element or constant);
  *                NULL means k = 1;

@@ -93,7 +93,8 @@ std::string point_fn(const char* name, const char* expr) {
   std::string b = "  template <typename R>\n  static __device__ __forceinline__ R " + std::string(name) +
                   "(R x, R y, R z, double p0, double p1, double p2, double p3) {\n";
   b += "    constexpr double pi = 3.141592653589793238462643383279502884;\n";
-  b += "    (void)x; (void)y; (void)z; (void)p0; (void)p1; (void)p2; (void)p3; (void)pi;\n";
+  b += "    auto sinpi_fx = [](double v) { return fea::sinpi_fx_call(v); };\n";
+  b += "    (void)x; (void)y; (void)z; (void)p0; (void)p1; (void)p2; (void)p3; (void)pi; (void)sinpi_fx;\n";
   b += "    return R(" + std::string(expr ? expr : "1") + ");\n  }\n";
   return b;
 }

@@ -22,6 +22,8 @@ CASES = {
     "sin_f": ("p0*sinpi_fp64(x)*sinpi_fp64(y)*sinpi_fp64(z)",
               lambda x, y, z: P[0] * math.sin(math.pi * x) * math.sin(math.pi * y) * math.sin(math.pi * z)),
     "exp_f": ("exp(-x)*(1 + y*z) + p1", lambda x, y, z: math.exp(-x) * (1 + y * z) + P[1]),
+    "sinx_f": ("p0*sinpi_fx(x)*sinpi_fx(y)*sinpi_fx(z)",
+               lambda x, y, z: P[0] * math.sin(math.pi * x) * math.sin(math.pi * y) * math.sin(math.pi * z)),
 }
 
 
@@ -56,7 +58,8 @@ def _run(order, n, npts, prec, k, f, mass, seed=0, kappa_per_elem=True):
 
 
 @pytest.mark.parametrize("order,npts,mass", [(1, 1, 0.0), (1, 4, 0.0), (1, 11, 1.0), (2, 4, 0.0), (2, 11, 1.0)])
-@pytest.mark.parametrize("k,f", [("smooth_k", "sin_f"), ("param_k", "exp_f"), (None, "exp_f"), ("smooth_k", None)])
+@pytest.mark.parametrize("k,f", [("smooth_k", "sin_f"), ("param_k", "exp_f"), (None, "exp_f"), ("smooth_k", None),
+                                 (None, "sinx_f")])
 def test_fp64_matches_oracle(order, npts, mass, k, f):
     rp, v, ov, r, orr = _run(order, 6, npts, 0, k, f, mass)
     assert row_scaled_error(rp, ov, v) <= TOL_FP64
