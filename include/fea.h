@@ -320,9 +320,11 @@ fea_status fea_profile_last(fea_mesh* mesh, float* elem_ms, float* scatter_ms);
 /* Self-check of the FP64-accurate sin(pi x) helpers (no counterpart in the
  * paper): for x [n] (device) writes the helper's value to mine [n] and CUDA's
  * sinpi to lib [n].  variant 0: the fixed-point evaluation the element
- * kernels use for the load vector; 1: the FP64-pipe polynomial (its fallback
- * for tiny, huge and non-finite arguments, and the sinpi_fp64 of
- * runtime-compiled expressions).  Asynchronous. */
+ * kernels use (sinpi_fx); 1: the FP64-pipe polynomial (its fallback for tiny,
+ * huge and non-finite arguments, and the sinpi_fp64 of runtime-compiled
+ * expressions); 2: the fixed-point value with 62 fractional bits the FP64
+ * load vectors multiply and sum on the integer pipes (sinpi_q62), converted.
+ * Asynchronous. */
 fea_status fea_diag_sinpi(const double* x, int64_t n, int32_t variant, double* mine, double* lib, void* stream);
 
 /* Measure the device's sustained FP64 FMA throughput (flop/s, FMA = 2)

@@ -327,6 +327,60 @@ __device__ __forceinline__ double sinpi_fx(double x) {
   return __longlong_as_double(static_cast<long long>(bits | sign));
 }
 
+// sin(pi x) 2^62 as a signed 64-bit integer (|value| <= 2^62), for products
+// and sums on the integer pipes: the reduction and polynomial of sinpi_fx,
+// then the 128-bit product |r| P shifted to 62 fractional bits (truncated,
+// error below 2^-62).  Arguments outside 2^-10 <= |x| < 2^51 take
+// sinpi_fp64, scaled exactly and rounded; a non-finite argument gives an
+// arbitrary value (an element with such a coordinate has a NaN det J and is
+// reported as degenerate).
+__device__ __forceinline__ long long sinpi_q62(double x) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const unsigned e = static_cast<unsigned>(b >> 52) & 0x7FFu;
+  if (e - 1013u > 60u) return __double2ll_rn(sinpi_fp64(x) * 4611686018427387904.0);
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const unsigned sh = e - 1011u;
+  const unsigned long long f = m << sh;
+  const unsigned rneg = static_cast<unsigned>(f >> 63);
+  const unsigned par = (sh > 11u ? static_cast<unsigned>(m >> (64u - sh)) & 1u : 0u) ^ rneg;
+  const unsigned long long ra = rneg ? 0ull - f : f;
+  const long long u = static_cast<long long>(__umul64hi(ra, ra));
+  long long p = SINPI_Q8;
+  p = __mul64hi(p, u) + SINPI_Q7;
+  p = __mul64hi(p, u) + SINPI_Q6;
+  p = __mul64hi(p, u) + SINPI_Q5;
+  p = __mul64hi(p, u) + SINPI_Q4;
+  p = __mul64hi(p, u) + SINPI_Q3;
+  p = __mul64hi(p, u) + SINPI_Q2;
+  p = __mul64hi(p, u) + SINPI_Q1;
+  p = __mul64hi(p, u) + SINPI_Q0;
+  const unsigned long long up = static_cast<unsigned long long>(p);
+  const unsigned long long hi = __umul64hi(ra, up), lo = ra * up;
+  const long long mag = static_cast<long long>((hi << 2) | (lo >> 62));
+  return ((b >> 63) ^ par ^ rneg) ? -mag : mag;
+}
+static __device__ __noinline__ long long sinpi_q62_call(double x) { return sinpi_q62(x); }
+template <bool OUTLINE>
+__device__ __forceinline__ long long sinpi_q62_sel(double x) {
+  if constexpr (OUTLINE) return sinpi_q62_call(x);
+  else return sinpi_q62(x);
+}
+
+// floor(a b / 2^62) for |a|, |b| <= 2^62 (the 128-bit product shifted).
+__device__ __forceinline__ long long mul_q62(long long a, long long b) {
+  const unsigned long long hi = static_cast<unsigned long long>(__mul64hi(a, b));
+  const unsigned long long lo = static_cast<unsigned long long>(a) * static_cast<unsigned long long>(b);
+  return static_cast<long long>((hi << 2) | (lo >> 62));
+}
+// A constant in 62 fractional bits (|c| < 2).
+__host__ __device__ constexpr long long q62(double c) { return static_cast<long long>(c * 4611686018427387904.0); }
+// v 2^-59 as a double: one correctly rounded conversion, then an exact
+// exponent shift (|v| >= 1 gives a normal result).
+__device__ __forceinline__ double q59_to_double(long long v) {
+  const double d = __ll2double_rn(v);
+  return v == 0 ? 0.0 : __longlong_as_double(__double_as_longlong(d) - (59LL << 52));
+}
+
 // One out-of-line copy of sinpi_fx for kernels with many sines: 33 inlined
 // copies of its ~165 instructions overflow the instruction cache (ncu: the
 // P2 load kernel stalled on instruction fetch), one copy called 33 times
@@ -550,6 +604,69 @@ __device__ __forceinline__ void rule_sum(const R s[NPTS], R Fs[ORDER == 1 ? 4 : 
   }
 }
 
+// rule_sum on the integer pipes: the point values S_q carry 62 fractional
+// bits; they are shifted to 59 (so class sums of up to six stay in range),
+// multiplied by the class coefficients in 62 fractional bits, and the sums
+// F_a carry 59 fractional bits.  Same classes and operations as rule_sum.
+template <int ORDER, int NPTS>
+__device__ __forceinline__ void rule_sum_q(const long long Sq[NPTS], long long F[ORDER == 1 ? 4 : 10]) {
+  static_assert(rule_classes_ok<ORDER, NPTS>(), "quadrature rule lost its symmetry classes");
+  long long s[NPTS];
+#pragma unroll
+  for (int q = 0; q < NPTS; ++q) s[q] = Sq[q] >> 3;
+  if constexpr (NPTS == 1) {
+    constexpr long long cv = q62(wphi<ORDER, 1>(0, 0));
+    F[0] = mul_q62(cv, s[0]);
+#pragma unroll
+    for (int a = 1; a < 4; ++a) F[a] = F[0];
+    if constexpr (ORDER == 2) {
+      constexpr long long ce = q62(wphi<ORDER, 1>(0, 4));
+      F[4] = mul_q62(ce, s[0]);
+#pragma unroll
+      for (int a = 5; a < 10; ++a) F[a] = F[4];
+    }
+  } else if constexpr (NPTS == 4) {
+    const long long S = (s[0] + s[1]) + (s[2] + s[3]);
+    constexpr long long vo = q62(wphi<ORDER, 4>(1, 0)), dv = q62(wphi<ORDER, 4>(0, 0) - wphi<ORDER, 4>(1, 0));
+    const long long Cv = mul_q62(vo, S);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) F[a] = Cv + mul_q62(dv, s[a]);
+    if constexpr (ORDER == 2) {
+      constexpr long long eo = q62(wphi<ORDER, 4>(2, 4)), de = q62(wphi<ORDER, 4>(0, 4) - wphi<ORDER, 4>(2, 4));
+      const long long Ce = mul_q62(eo, S);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) F[4 + k] = Ce + mul_q62(de, s[edge_p(k)] + s[edge_q(k)]);
+    }
+  } else {
+    const long long S4 = (s[1] + s[2]) + (s[3] + s[4]);
+    const long long S6 = ((s[5] + s[6]) + (s[7] + s[8])) + (s[9] + s[10]);
+    long long E[4];
+    E[0] = (s[5] + s[6]) + s[7];
+    E[1] = (s[5] + s[8]) + s[9];
+    E[2] = (s[6] + s[8]) + s[10];
+    E[3] = (s[7] + s[9]) + s[10];
+    constexpr long long c0 = q62(wphi<ORDER, 11>(0, 0)), vo = q62(wphi<ORDER, 11>(2, 0)),
+                        eo = q62(wphi<ORDER, 11>(10, 0));
+    constexpr long long dv = q62(wphi<ORDER, 11>(1, 0) - wphi<ORDER, 11>(2, 0)),
+                        de = q62(wphi<ORDER, 11>(5, 0) - wphi<ORDER, 11>(10, 0));
+    const long long Cv = mul_q62(c0, s[0]) + mul_q62(vo, S4) + mul_q62(eo, S6);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) F[a] = Cv + mul_q62(dv, s[1 + a]) + mul_q62(de, E[a]);
+    if constexpr (ORDER == 2) {
+      constexpr long long g0 = q62(wphi<ORDER, 11>(0, 4)), go = q62(wphi<ORDER, 11>(3, 4)),
+                          dh = q62(wphi<ORDER, 11>(6, 4));
+      constexpr long long dg = q62(wphi<ORDER, 11>(1, 4) - wphi<ORDER, 11>(3, 4)),
+                          dsm = q62(wphi<ORDER, 11>(5, 4) - wphi<ORDER, 11>(6, 4)),
+                          dp = q62(wphi<ORDER, 11>(10, 4) - wphi<ORDER, 11>(6, 4));
+      const long long Ce = mul_q62(g0, s[0]) + mul_q62(go, S4) + mul_q62(dh, S6);
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        F[4 + k] = Ce + mul_q62(dg, s[1 + edge_p(k)] + s[1 + edge_q(k)]) + mul_q62(dsm, s[5 + k]) +
+                   mul_q62(dp, s[10 - k]);
+    }
+  }
+}
+
 // Shape load  Fs_a = sum_q w_q s(x_q) phi_a(x_q)  (without the factor |T|),
 // s = 1 (LOAD_CONST) or sin(pi x) sin(pi y) sin(pi z) (LOAD_SIN).
 template <int ORDER, int NPTS, int LOAD, typename R, bool OUTLINE = (ORDER == 2)>
@@ -560,6 +677,25 @@ __device__ __forceinline__ void shape_load(const R Xr[4][3], R Fs[ORDER == 1 ? 4
       constexpr double c = wphi_sum(ORDER, NPTS, A);
       Fs[A] = R(c);
     });
+  } else if constexpr (IsDouble<R>::value) {
+    // FP64: the sines, their products and the rule sums in fixed point on the
+    // integer pipes; one conversion per output
+    long long sq[NPTS];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const R v[4] = {Xr[0][c], Xr[1][c], Xr[2][c], Xr[3][c]};
+      R xq[NPTS];
+      quad_coord<NPTS, R>(v, xq);
+#pragma unroll
+      for (int q = 0; q < NPTS; ++q) {
+        const long long t = sinpi_q62_sel<OUTLINE>(xq[q]);
+        sq[q] = c == 0 ? t : mul_q62(sq[q], t);
+      }
+    }
+    long long F[NB];
+    rule_sum_q<ORDER, NPTS>(sq, F);
+#pragma unroll
+    for (int a = 0; a < NB; ++a) Fs[a] = q59_to_double(F[a]);
   } else {
     R sq[NPTS];
 #pragma unroll
