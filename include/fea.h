@@ -166,7 +166,9 @@ fea_status fea_mesh_set_scatter_classes(fea_mesh* mesh, int32_t mode);
  * == 1): 0 = one kernel computes the local matrix and the local load; 1 = a
  * matrix kernel, then a load kernel; 2 = the load kernel on a stream owned
  * by the handle, concurrent with the matrix kernel (joined back to
- * `stream`); -1 (default) = automatic: 2 for FP64 P2, else 0.  Results are
+ * `stream`); 3 = one kernel whose blocks hold matrix warps and load warps of
+ * the same elements (FP64; the mixed path takes 0); -1 (default) =
+ * automatic, currently 0 everywhere (the fastest measured).  Results are
  * bitwise identical for every mode. */
 fea_status fea_mesh_set_load_split(fea_mesh* mesh, int32_t mode);
 

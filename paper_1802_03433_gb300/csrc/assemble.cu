@@ -122,13 +122,17 @@ fea_status assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* co, con
     A.e0 = 0;
     A.e1 = E;
     if (m->profile) FEA_CUDA(cudaEventRecord(m->ev[0], s));
-    // FP64 P2: the matrix part is FP64-bound and the load part bound by the
-    // integer-pipe sines, so they run as two concurrent kernels; for P1 the
-    // matrix part is small and one fused kernel is faster
-    const int split_mode = m->load_split >= 0 ? m->load_split : (order == 2 && !mixed ? 2 : 0);
-    const bool split = split_mode > 0 && load != FEA_LOAD_NONE && form->kind != FEA_ELASTICITY;
+    // the matrix part is FP64-bound and the load part runs mostly on the
+    // integer pipes; measured on P2 64^3 and P1 96^3, one fused kernel is
+    // still the fastest launch (the split modes stay selectable)
+    const int split_mode = m->load_split >= 0 ? m->load_split : 0;
+    const bool split = split_mode > 0 && load != FEA_LOAD_NONE && form->kind != FEA_ELASTICITY &&
+                       !(split_mode == 3 && mixed);
     if (!split) {
       FEA_TRY(launch_elements(form, A, load, q->npts, prec, s));
+    } else if (split_mode == 3) {
+      const bool mass = form->kind == FEA_DIFFUSION_MASS && form->mass_coef != 0.0;
+      FEA_TRY(launch_elem_roles(order, mass, A, load, q->npts, s));
     } else if (split_mode == 1) {
       FEA_TRY(launch_elements(form, A, FEA_LOAD_NONE, q->npts, prec, s));
       FEA_TRY(launch_elem_load(order, A, load, q->npts, prec, s));

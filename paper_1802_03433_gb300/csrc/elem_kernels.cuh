@@ -196,6 +196,31 @@ __global__ void __launch_bounds__(ELEM_T) k_elem_load(ElemArgs A) {
   for (int a = 0; a < NB; ++a) Fl[__ldg(A.ipos + a * A.E + e)] = amp * Fs[a];
 }
 
+// Matrix and load of the same elements in one kernel, by warp role: in a
+// block of 2 * ELEM_T threads the first ELEM_T threads compute the local
+// matrices of ELEM_T elements (FP64-bound) and the other ELEM_T threads their
+// loads (integer-pipe sines), so both kinds of work share every SM.  The
+// role is uniform per warp; the results are those of the separate kernels.
+template <int ORDER, bool MASS, int LOAD, int NPTS>
+__global__ void __launch_bounds__(2 * ELEM_T) k_elem_roles(ElemArgs A) {
+  const int64_t e = A.e0 + (int64_t)blockIdx.x * ELEM_T + (threadIdx.x % ELEM_T);
+  if (e >= A.e1) return;
+  if (threadIdx.x < ELEM_T) {
+    elem_scalar_body<ORDER, MASS, LOAD_NONE, 1, double>(A, e);
+  } else {
+    constexpr int NB = ORDER == 1 ? 4 : 10;
+    double X[4][3];
+    load_element(A, e, X);
+    const double adet = fabs(det_only(X));
+    double Fs[NB];
+    shape_load<ORDER, NPTS, LOAD, double>(X, Fs);
+    const double amp = A.fp[0] * adet * (1.0 / 6.0);
+    double* __restrict__ Fl = static_cast<double*>(A.Fl);
+#pragma unroll
+    for (int a = 0; a < NB; ++a) Fl[__ldg(A.ipos + a * A.E + e)] = amp * Fs[a];
+  }
+}
+
 // Deterministic-path output of the elasticity kernel: local rows in
 // incidence order (whole sectors) and local loads.
 template <int LOAD, int NPTS, typename R>
@@ -298,6 +323,7 @@ __global__ void __launch_bounds__(ELEM_T) k_elem_elast(ElemArgs A) {
 fea_status launch_elem_p1(const ElemArgs& A, bool mass, int load, int npts, int prec, cudaStream_t s);
 fea_status launch_elem_p2(const ElemArgs& A, bool mass, int load, int npts, int prec, cudaStream_t s);
 fea_status launch_elem_load(int order, const ElemArgs& A, int load, int npts, int prec, cudaStream_t s);
+fea_status launch_elem_roles(int order, bool mass, const ElemArgs& A, int load, int npts, cudaStream_t s);
 fea_status launch_elem_elast(const ElemArgs& A, int load, int npts, int prec, cudaStream_t s);
 
 }  // namespace fea

@@ -57,6 +57,28 @@ struct LoadLauncher {
   }
 };
 
+// FP64 only: matrix and load warps of the same elements in one kernel.
+template <int ORDER, bool MASS>
+struct RolesLauncher {
+  template <int LOAD, int NPTS>
+  static void go(const ElemArgs& A, cudaStream_t s) {
+    k_elem_roles<ORDER, MASS, LOAD, NPTS><<<elem_blocks(A), 2 * ELEM_T, 0, s>>>(A);
+  }
+  template <int NPTS>
+  static void by_load(const ElemArgs& A, int load, cudaStream_t s) {
+    if (load == LOAD_CONST) go<LOAD_CONST, NPTS>(A, s);
+    else go<LOAD_SIN, NPTS>(A, s);
+  }
+  static fea_status run(const ElemArgs& A, int load, int npts, cudaStream_t s) {
+    if (A.e1 <= A.e0 || load == LOAD_NONE) return FEA_OK;
+    if (npts == 1) by_load<1>(A, load, s);
+    else if (npts == 4) by_load<4>(A, load, s);
+    else by_load<11>(A, load, s);
+    FEA_CUDA(cudaGetLastError());
+    return FEA_OK;
+  }
+};
+
 struct ElastLauncher {
   template <int LOAD, int NPTS>
   static void go(const ElemArgs& A, int prec, cudaStream_t s) {

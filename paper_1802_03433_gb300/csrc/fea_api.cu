@@ -195,7 +195,7 @@ fea_status fea_mesh_set_stages(fea_mesh* m, int32_t stages) {
 
 fea_status fea_mesh_set_load_split(fea_mesh* m, int32_t mode) {
   if (!m) return fail(FEA_ERR_ARG, "mesh is NULL");
-  if (mode < -1 || mode > 2) return fail(FEA_ERR_ARG, "mode must be -1, 0, 1 or 2");
+  if (mode < -1 || mode > 3) return fail(FEA_ERR_ARG, "mode must be -1, 0, 1, 2 or 3");
   m->load_split = mode;
   return FEA_OK;
 }

@@ -119,7 +119,7 @@ struct fea_mesh {
   cudaEvent_t chunk_ev[17] = {nullptr};    // chunk done (<= 16 stages) + join
   int load_split = -1;      // scalar forms: 0 fused element kernel; 1 matrix kernel then load kernel;
                             // 2 load kernel on the side stream, concurrent with the matrix kernel;
-                            // -1 automatic: 2 for FP64 P2, else 0
+                            // 3 one kernel with matrix warps and load warps; -1 automatic (0)
   bool profile = false;     // record phase events in fea_assemble
   bool profiled = false;    // events of a call are pending
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};

@@ -300,7 +300,7 @@ def test_load_split_modes_bitwise_identical(torch_cuda, kind, n, prec):
     c = case(kind, n, seed=31)
     m = fea.Mesh(c["coords"], c["tets"])
     ref = None
-    for mode in (0, 1, 2, -1):
+    for mode in (0, 1, 2, 3, -1):
         fea.fea_mesh_set_load_split(m.h, mode)
         g = gpu_system(c, prec=prec, mesh=m)
         if ref is None:
