@@ -40,13 +40,13 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # captures are summarised under profiles/.  Absent where not captured for the
 # current kernels.
 FP64_FLOP_PER_ELEM = {
-    ("p2_diffmass_64", "fp64"): 499.0,    # fused element kernel, flop counted as matrix 362 + load 137 (recount)
-    ("p1_kappa_96", "fp64"): 409.0,       # 136 DFMA + 63 DADD + 74 DMUL
+    ("p2_diffmass_64", "fp64"): 476.0,    # 183 DFMA + 45 DADD + 65 DMUL per element (+ ~5,650 integer instructions)
+    ("p1_kappa_96", "fp64"): 161.0,       # 48 DFMA + 24 DADD + 41 DMUL (+ ~1,900 integer instructions)
     ("p1_elast_128", "fp64"): 370.0,      # 114 DFMA + 16 DADD + 126 DMUL
 }
 DRAM_BYTES_PER_LAUNCH = {
-    ("p2_diffmass_64", "element"): (107.3e6 + 1459.0e6) + (122.4e6 + 89.8e6),
-    ("p1_kappa_96", "element"): 238.4e6 + 793.2e6,
+    ("p2_diffmass_64", "element"): 138.9e6 + 1596.1e6,
+    ("p1_kappa_96", "element"): 238.4e6 + 793.6e6,
     ("p1_elast_128", "element"): 705.8e6 + 15649.2e6,
 }
 
