@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(ELEM_T) k_elem_elast(ElemArgs A) {
     }
   static_for<10>([&](auto K) {
     constexpr int a = upper_a(4, K), b = upper_b(4, K);
-    D[a][b] = Ms * dot3(Gr[a], Gr[b]);
+    D[a][b] = dot3(Mc[a], Gr[b]);  // mu |T| grad phi_a . grad phi_b
     if constexpr (a != b) D[b][a] = D[a][b];
   });
   R Kl[12][12];
@@ -290,6 +290,7 @@ __global__ void __launch_bounds__(ELEM_T) k_elem_elast(ElemArgs A) {
     constexpr int a = r / 3, i = r % 3, b = c / 3, j = c % 3;
     R v;
     if constexpr (i == j) v = fma(LMc[a][i], Gr[b][i], D[a][b]);
+    else if constexpr (a == b) v = LMc[a][i] * Gr[a][j];  // (lam + mu) d_i phi_a d_j phi_a
     else v = fma(Lc[a][i], Gr[b][j], Mc[a][j] * Gr[b][i]);
     Kl[r][c] = v;
     Kl[c][r] = v;
