@@ -482,7 +482,8 @@ def bench_batched(fea, torch, dev, steps, warmup, flush):
     return {"value": E / (res["graph"] / 1e3), "unit": "elements/s", "ms_per_step": res["graph"],
             "separate_value": E / (res["separate"] / 1e3), "separate_ms_per_step": res["separate"],
             "launches": {"graph": 1, "separate": 2 * len(specs)},
-            "tuned": {"elements_per_item": params[0], "element_ctas": params[1], "scatter_ctas": params[2]},
+            "tuned": {"elements_per_item": params[0], "p2_element_ctas": params[1], "p1_element_ctas": params[2],
+                      "scatter_ctas": params[3], "p2_register_variant": params[4], "p1_register_variant": params[5]},
             "meshes": len(specs), "elements": E,
             "config": "256 Kuhn cubes, n ~ U{4..32} (seed 0), even P1 (4-pt) / odd P2 (11-pt) Poisson, "
                       "log-normal kappa, sin load, FP64"}

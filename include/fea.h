@@ -293,15 +293,20 @@ fea_status fea_batch_bind(fea_batch* batch, const fea_coeffs* coeffs, double* co
                           double* const* rhs);
 
 /* Assemble every mesh of the batch: one launch of an internal CUDA graph
- * holding one persistent element kernel and one persistent scatter kernel
- * over all meshes.  Asynchronous on `stream`; allocates nothing.  Each
- * mesh's values and rhs are bitwise those of fea_assemble. */
+ * with two branches that may run concurrently, one for the P2 meshes and one
+ * for the P1 meshes, each a persistent element kernel over all of its meshes
+ * followed by the row-tile scatter kernels.  Asynchronous on `stream`;
+ * allocates nothing.  Each mesh's values and rhs are bitwise those of
+ * fea_assemble. */
 fea_status fea_batch_assemble(fea_batch* batch, void* stream);
 
 /* Autotune the batch's launch: times candidate (elements per work item,
- * persistent element-kernel CTAs) pairs on the device, keeps the fastest and
- * rebuilds the graph.  params (may be NULL) receives the chosen elements per
- * item, element-kernel CTAs and the scatter CTA count (one per row tile).
+ * P2 element-kernel CTAs) pairs on the device, then, per order, the element
+ * kernel's register variant (the compiler's register count, or capped for
+ * the single-mesh kernel's residency) with its CTA count; keeps the fastest
+ * and rebuilds the graph.  params (may be NULL) receives int32_t[6]: the
+ * chosen elements per item, P2 and P1 element-kernel CTAs, the scatter CTA
+ * count (one per row tile), and the P2 and P1 register variants (0 or 1).
  * Synchronises; overwrites the bound outputs. */
 fea_status fea_batch_tune(fea_batch* batch, void* stream, int32_t* params);
 

@@ -1,17 +1,20 @@
 // Batched assembly: many independent meshes (uneven sizes, P1 and P2) in one
 // CUDA-graph launch.
 //
-// The graph holds two persistent kernels.  The element kernel walks a static
-// list of (mesh, element tile) work items and the scatter kernel a list of
-// (mesh, row tile) items, each CTA taking items b, b + grid, b + 2 grid, ...
-// Items are sorted by estimated cost, largest first (longest-processing-time
-// order), so the long P2 tiles start early and the short P1 tiles fill the
-// tail.  Each work item runs the same per-element and per-row-tile device
-// code as the single-mesh path, so every mesh's values are bitwise those of
-// fea_assemble.  The elements per work item and both grid sizes are chosen by
-// an autotuner (fea_batch_tune) that times candidate configurations on the
-// device.  Every pattern, map and scratch buffer is built before the graph is
-// captured: a replay allocates nothing and never synchronises.
+// The graph holds two branches, one per element order, that may run at the
+// same time.  Each branch is a persistent element kernel walking a static
+// list of (mesh, element tile) work items, each CTA taking items b, b + grid,
+// b + 2 grid, ..., followed by the scatter kernels, one CTA per (mesh, row
+// tile) item.  Element items are sorted longest first
+// (longest-processing-time order); the P2 branch is issued first, and the P1
+// kernels take the SMs that the P2 element kernel's tail leaves idle.  Each
+// work item runs the same per-element and per-row-tile device code as the
+// single-mesh path (including the bulk-copy scatter over the tiled layout),
+// so every mesh's values are bitwise those of fea_assemble.  The elements per
+// work item and the grid of each element kernel are chosen by an autotuner
+// (fea_batch_tune) that times candidate configurations on the device.  Every
+// pattern, map and scratch buffer is built before the graph is captured: a
+// replay allocates nothing and never synchronises.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -20,13 +23,16 @@
 
 #include "elem_kernels.cuh"
 #include "gather.cuh"
+#include "gather_tiled.cuh"
 
 namespace fea {
 namespace {
 
 struct BMesh {
   ElemArgs el;
-  GatherArgs ga;
+  GatherArgs ga;   // incidence-order scatter
+  TiledArgs tg;    // bulk-copy scatter over the tiled layout (tiled != 0)
+  int32_t tiled;
   int32_t order;
   int32_t mass;
   int32_t rows_per_tile;
@@ -40,48 +46,103 @@ struct BItem {
 
 constexpr int BT = 128;
 
-template <int LOAD, int NP1, int NP2>
-__global__ void __launch_bounds__(BT) k_batch_elem(const BMesh* __restrict__ M, const BItem* __restrict__ items,
+// One element kernel per order: a P1 body compiled beside the P2 body would
+// run at the P2 body's register count (168 against 72 per thread, 3 against
+// 7 resident CTAs per SM).  The mesh's arguments come from global memory and
+// stay in registers across the element loop (the single-mesh kernels read
+// theirs from the constant bank), which costs 20-40 registers per thread.
+// Each kernel is built twice: with the compiler's register count (variant 0;
+// P2 with the sine load: 180, two resident CTAs per SM) and capped to keep
+// the residency of the single-mesh kernel (variant 1: three CTAs per SM for
+// P2, six for P1, at the price of a few spilled bytes); the autotuner picks.
+template <int ORDER, int VARIANT>
+constexpr int batch_elem_min_blocks() { return VARIANT == 0 ? 1 : ORDER == 2 ? 3 : 6; }
+
+template <int ORDER, int LOAD, int NP, int VARIANT>
+__global__ void __launch_bounds__(BT, batch_elem_min_blocks<ORDER, VARIANT>()) k_batch_elem(const BMesh* __restrict__ M, const BItem* __restrict__ items,
                                                    int nitems) {
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const BItem w = items[it];
     const BMesh& m = M[w.mesh];
     const int64_t end = (int64_t)w.first + w.count;
-    if (m.order == 1) {
-      for (int64_t e = w.first + threadIdx.x; e < end; e += BT) {
-        if (m.mass) elem_scalar_body<1, true, LOAD, NP1, double>(m.el, e);
-        else elem_scalar_body<1, false, LOAD, NP1, double>(m.el, e);
-      }
+    if (m.mass) {
+      for (int64_t e = w.first + threadIdx.x; e < end; e += BT) elem_scalar_body<ORDER, true, LOAD, NP, double>(m.el, e);
     } else {
-      for (int64_t e = w.first + threadIdx.x; e < end; e += BT) {
-        if (m.mass) elem_scalar_body<2, true, LOAD, NP2, double>(m.el, e);
-        else elem_scalar_body<2, false, LOAD, NP2, double>(m.el, e);
-      }
+      for (int64_t e = w.first + threadIdx.x; e < end; e += BT)
+        elem_scalar_body<ORDER, false, LOAD, NP, double>(m.el, e);
     }
   }
 }
 
-// One scatter kernel per element order (NB = 4 or 10), one CTA per row-tile
+// Scatter kernels per element order (NB = 4 or 10), one CTA per row-tile
 // item (a persistent loop here costs ~60 registers per thread, i.e. a third
-// of the resident CTAs, for no gain: the tiles are already uniform).
+// of the resident CTAs, for no gain: the tiles are already uniform).  Meshes
+// whose pattern has the tiled layout take the bulk-copy scatter of
+// gather_tiled.cuh, the others the incidence-order one of gather.cuh (two
+// kernels, as one kernel holding both bodies needs the registers of the
+// larger); both give the same bits.
 template <int NB>
 __global__ void __launch_bounds__(BT) k_batch_gather(const BMesh* __restrict__ M, const BItem* __restrict__ items,
-                                                     int nitems) {
+                                                     int nitems, int64_t) {
   extern __shared__ double acc[];
   if ((int)blockIdx.x >= nitems) return;
   const BItem w = items[blockIdx.x];
   gather_tile<NB, 1, double>(M[w.mesh].ga, w.first, M[w.mesh].rows_per_tile, acc);
 }
 
+// span_cap: the accumulator capacity (doubles) of this launch's shared-memory
+// layout, at least the CSR span of every tile it is given.
+template <int NB>
+__global__ void __launch_bounds__(BT) k_batch_gather_tiled(const BMesh* __restrict__ M,
+                                                           const BItem* __restrict__ items, int nitems,
+                                                           int64_t span_cap) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  if ((int)blockIdx.x >= nitems) return;
+  const BItem w = items[blockIdx.x];
+  TiledArgs G = M[w.mesh].tg;
+  G.span_cap = span_cap;
+  gather_tiled_tile<NB, double>(G, w.first, sm);
+}
+
+// Scatter item groups, in launch order, per order (P2, then P1): tiled tiles
+// of the heavy class (CSR span above half the mesh's widest), tiled tiles of
+// the light class, incidence-order tiles.  The light class's accumulator is
+// about half the heavy one's, which leaves room for one more resident CTA
+// per SM (as in the single-mesh scatter).
+constexpr int NGROUPS = 6;
+enum { CLS_HEAVY = 0, CLS_LIGHT = 1, CLS_INCIDENCE = 2 };
+inline int gather_group(int order, int cls) { return (order == 2 ? 0 : 3) + cls; }
+
+using GatherKernel = void (*)(const BMesh*, const BItem*, int, int64_t);
+const GatherKernel GATHER_KERNELS[NGROUPS] = {k_batch_gather_tiled<10>, k_batch_gather_tiled<10>, k_batch_gather<10>,
+                                              k_batch_gather_tiled<4>,  k_batch_gather_tiled<4>,  k_batch_gather<4>};
+
 using ElemKernel = void (*)(const BMesh*, const BItem*, int);
 
-ElemKernel pick_elem_kernel(int load, int np1, int np2) {
-  if (load == LOAD_NONE) return k_batch_elem<LOAD_NONE, 1, 1>;
-  const bool sin = load == LOAD_SIN;
-  if (np1 == 4 && np2 == 11) return sin ? k_batch_elem<LOAD_SIN, 4, 11> : k_batch_elem<LOAD_CONST, 4, 11>;
-  if (np1 == 11 && np2 == 11) return sin ? k_batch_elem<LOAD_SIN, 11, 11> : k_batch_elem<LOAD_CONST, 11, 11>;
-  if (np1 == 4 && np2 == 4) return sin ? k_batch_elem<LOAD_SIN, 4, 4> : k_batch_elem<LOAD_CONST, 4, 4>;
-  return nullptr;
+constexpr int ELEM_VARIANTS = 2;
+
+template <int ORDER, int NP, int VARIANT>
+ElemKernel elem_kernel_for(int load) {
+  if (load == LOAD_NONE) return k_batch_elem<ORDER, LOAD_NONE, 1, VARIANT>;
+  return load == LOAD_SIN ? k_batch_elem<ORDER, LOAD_SIN, NP, VARIANT> : k_batch_elem<ORDER, LOAD_CONST, NP, VARIANT>;
+}
+
+template <int ORDER, int NP>
+void elem_kernels_for(int load, ElemKernel ek[ELEM_VARIANTS]) {
+  ek[0] = elem_kernel_for<ORDER, NP, 0>(load);
+  ek[1] = elem_kernel_for<ORDER, NP, 1>(load);
+}
+
+// Element kernels of the supported (P1, P2) rules, indexed by order and variant.
+bool pick_elem_kernels(int load, int np1, int np2, ElemKernel ek[3][ELEM_VARIANTS]) {
+  ek[0][0] = ek[0][1] = nullptr;
+  if (np1 == 4) elem_kernels_for<1, 4>(load, ek[1]);
+  else if (np1 == 11) elem_kernels_for<1, 11>(load, ek[1]);
+  else return false;
+  if (np2 == 4) elem_kernels_for<2, 4>(load, ek[2]);
+  else if (np2 == 11) elem_kernels_for<2, 11>(load, ek[2]);
+  else return false;
+  return (np1 == 4 && np2 == 11) || (np1 == 11 && np2 == 11) || (np1 == 4 && np2 == 4);
 }
 
 }  // namespace
@@ -95,17 +156,25 @@ struct fea_batch {
   std::vector<fea_form> forms;
   std::vector<BMesh> host;
   BMesh* d_mesh = nullptr;
-  BItem* d_eitems = nullptr;
-  BItem* d_gitems = nullptr;     // P2 row tiles first, then P1 row tiles
-  int n_eitems = 0, n_gitems = 0, n_gitems2 = 0;
+  BItem* d_eitems = nullptr;     // element tiles, P2 first, then P1
+  BItem* d_gitems = nullptr;     // row tiles by scatter group (gather_group)
+  int n_eitems = 0, n_gitems = 0;
+  int ecount[3] = {0, 0, 0};           // element items per order
+  int gcount[NGROUPS] = {};           // row-tile items per group
   void* pool = nullptr;  // local rows and loads of every mesh
-  size_t smem[3] = {0, 0, 0};  // scatter shared memory per CTA, by order
+  size_t smem[NGROUPS] = {};          // scatter shared memory per CTA, by group
+  int64_t span_cap[NGROUPS] = {};     // accumulator capacity of the tiled groups
+  std::vector<std::vector<uint8_t>> heavy;  // per mesh: tile -> heavy class (tiled meshes)
   int load = 0, np1 = 4, np2 = 11;
-  ElemKernel ek = nullptr;
-  int elem_tile = 256, elem_grid = 0, gather_grid = 0;
+  ElemKernel ek[3][ELEM_VARIANTS] = {};  // by order and register variant
+  int variant[3] = {1, 1, 1};          // the variant launched, by order
+  int elem_tile = 256, gather_grid = 0;
+  int elem_grid[3] = {0, 0, 0};        // persistent element-kernel CTAs, by order (0: one CTA per item)
   int sms = 0;
   bool bound = false;
   cudaStream_t cap = nullptr;
+  cudaStream_t side = nullptr;         // the P1 branch (P2 runs on the launch stream)
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
 
@@ -117,14 +186,19 @@ fea_status build_items(fea_batch* b) {
     const fea_mesh* m = b->meshes[k];
     const int order = b->forms[k].order;
     const int64_t E = m->n_elems;
-    const int64_t cost = order == 2 ? 8 : 1;  // P2 element ~8x a P1 element
+    // P2 items first (a P2 element costs ~3x a P1 element), each order's
+    // items longest first
+    const int64_t key = order == 2 ? (int64_t(1) << 40) : 0;
     for (int64_t f = 0; f < E; f += b->elem_tile) {
       const int32_t cnt = (int32_t)std::min<int64_t>(b->elem_tile, E - f);
-      ei.push_back({cost * cnt, BItem{k, (int32_t)f, cnt}});
+      ei.push_back({key + cnt, BItem{k, (int32_t)f, cnt}});
     }
     const Pattern* P = m->pat[order][1];
     const int64_t tiles = (P->ndof + P->rows_per_tile - 1) / P->rows_per_tile;
-    for (int64_t t = 0; t < tiles; ++t) gi.push_back({order == 2 ? 10 : 4, BItem{k, (int32_t)t, 0}});
+    for (int64_t t = 0; t < tiles; ++t) {
+      const int cls = !b->host[k].tiled ? CLS_INCIDENCE : b->heavy[k][t] ? CLS_HEAVY : CLS_LIGHT;
+      gi.push_back({NGROUPS - gather_group(order, cls), BItem{k, (int32_t)t, cls}});
+    }
   }
   auto by_cost = [](const std::pair<int64_t, BItem>& a, const std::pair<int64_t, BItem>& c) {
     return a.first > c.first;
@@ -143,17 +217,39 @@ fea_status build_items(fea_batch* b) {
   if (!hg.empty()) FEA_CUDA(cudaMemcpy(b->d_gitems, hg.data(), sizeof(BItem) * hg.size(), cudaMemcpyHostToDevice));
   b->n_eitems = (int)he.size();
   b->n_gitems = (int)hg.size();
-  b->n_gitems2 = 0;
-  for (const BItem& w : hg) b->n_gitems2 += b->forms[w.mesh].order == 2;
+  b->ecount[0] = b->ecount[1] = b->ecount[2] = 0;
+  for (const BItem& w : he) ++b->ecount[b->forms[w.mesh].order];
+  for (int g = 0; g < NGROUPS; ++g) b->gcount[g] = 0;
+  for (const BItem& w : hg) ++b->gcount[gather_group(b->forms[w.mesh].order, w.count)];
   return FEA_OK;
 }
 
+// Two independent branches: the P2 meshes (element kernel, then their
+// scatter) on s and the P1 meshes on the side stream, forked from and joined
+// back into s.  The meshes of the two branches share no output, so the
+// branches may overlap: the P1 kernels fill the SMs the P2 element kernel's
+// tail leaves idle.
 fea_status launch_phases(fea_batch* b, cudaStream_t s) {
-  if (b->n_eitems > 0) b->ek<<<b->elem_grid, BT, 0, s>>>(b->d_mesh, b->d_eitems, b->n_eitems);
-  const int n1 = b->n_gitems - b->n_gitems2;
-  if (b->n_gitems2 > 0) k_batch_gather<10><<<b->n_gitems2, BT, b->smem[2], s>>>(b->d_mesh, b->d_gitems, b->n_gitems2);
-  if (n1 > 0) k_batch_gather<4><<<n1, BT, b->smem[1], s>>>(b->d_mesh, b->d_gitems + b->n_gitems2, n1);
+  FEA_CUDA(cudaEventRecord(b->fork_ev, s));
+  FEA_CUDA(cudaStreamWaitEvent(b->side, b->fork_ev, 0));
+  int first = 0;  // items of group g start after those of groups 0 .. g-1
+  for (int order = 2; order >= 1; --order) {
+    cudaStream_t st = order == 2 ? s : b->side;
+    const int e_first = order == 2 ? 0 : b->ecount[2];
+    if (b->ecount[order] > 0) {
+      const int grid = b->elem_grid[order] > 0 ? b->elem_grid[order] : b->ecount[order];
+      b->ek[order][b->variant[order]]<<<grid, BT, 0, st>>>(b->d_mesh, b->d_eitems + e_first, b->ecount[order]);
+    }
+    for (int g = gather_group(order, 0), ge = g + 3; g < ge; ++g) {
+      if (b->gcount[g] > 0)
+        GATHER_KERNELS[g]<<<b->gcount[g], BT, b->smem[g], st>>>(b->d_mesh, b->d_gitems + first, b->gcount[g],
+                                                                 b->span_cap[g]);
+      first += b->gcount[g];
+    }
+  }
   FEA_CUDA(cudaGetLastError());
+  FEA_CUDA(cudaEventRecord(b->join_ev, b->side));
+  FEA_CUDA(cudaStreamWaitEvent(s, b->join_ev, 0));
   return FEA_OK;
 }
 
@@ -198,12 +294,14 @@ fea_status fea_batch_create(fea_mesh* const* meshes, int32_t n, const fea_form* 
   }
   np1 = np1 ? np1 : 4;
   np2 = np2 ? np2 : 11;
-  ElemKernel ek = pick_elem_kernel(f_kind, np1, np2);
-  if (!ek) return fail(FEA_ERR_ARG, "supported (P1, P2) rules: (4, 11), (11, 11), (4, 4)");
+  ElemKernel ek[3][ELEM_VARIANTS];
+  if (!pick_elem_kernels(f_kind, np1, np2, ek))
+    return fail(FEA_ERR_ARG, "supported (P1, P2) rules: (4, 11), (11, 11), (4, 4)");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   fea_batch* b = new fea_batch();
   b->n = n;
-  b->ek = ek;
+  for (int o = 0; o < 3; ++o)
+    for (int v = 0; v < ELEM_VARIANTS; ++v) b->ek[o][v] = ek[o][v];
   b->load = f_kind;
   b->np1 = np1;
   b->np2 = np2;
@@ -216,17 +314,55 @@ fea_status fea_batch_create(fea_mesh* const* meshes, int32_t n, const fea_form* 
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
     size_t bytes = 0;
     std::vector<size_t> lm_off(n), fl_off(n);
+    int max_rows[NGROUPS] = {};
+    b->heavy.assign(n, {});
     for (int k = 0; k < n && st == FEA_OK; ++k) {
       const int order = forms[k].order;
       if ((st = build_pattern(meshes[k], order, 1, s)) != FEA_OK) break;
       const Pattern* P = meshes[k]->pat[order][1];
       const int nb = order == 1 ? 4 : 10;
+      const bool tiled = use_tiled(meshes[k], P);
+      // local rows at tiled positions (npos, padding included) or incidence order
+      const size_t nrows = tiled ? (size_t)P->npos : (size_t)meshes[k]->n_elems * nb;
       lm_off[k] = bytes;
-      bytes += (size_t)meshes[k]->n_elems * nb * lstride(nb, 8) * 8;
+      bytes += (nrows * lstride(nb, 8) * 8 + 255) / 256 * 256;
       fl_off[k] = bytes;
-      bytes += ((size_t)meshes[k]->n_elems * nb * 8 + 255) / 256 * 256;
-      b->smem[order] = std::max<size_t>(b->smem[order], (size_t)P->max_tile_nnz * 8);
+      bytes += (nrows * 8 + 255) / 256 * 256;
       if (P->rows_per_tile > BT) st = fail(FEA_ERR_ARG, "row tile taller than the batch CTA");
+      if (!tiled) {
+        const int g = gather_group(order, CLS_INCIDENCE);
+        b->smem[g] = std::max(b->smem[g], (size_t)P->max_tile_nnz * 8);
+        continue;
+      }
+      // the pattern's tile classes (heavy tiles first in class_list); one
+      // class (heavy) when the pattern has no split
+      const int64_t ntiles = (P->ndof + P->rows_per_tile - 1) / P->rows_per_tile;
+      std::vector<uint8_t>& hv = b->heavy[k];
+      const bool split = P->class_list && P->n_heavy > 0 && P->n_light > 0;
+      hv.assign(ntiles, split ? 0 : 1);
+      if (split) {
+        std::vector<int32_t> list(P->n_heavy);
+        cudaError_t ce = cudaMemcpy(list.data(), P->class_list, P->n_heavy * sizeof(int32_t), cudaMemcpyDeviceToHost);
+        if (ce != cudaSuccess) {
+          st = cuda_fail(ce, "tile classes");
+          break;
+        }
+        for (int32_t t : list) hv[t] = 1;
+      }
+      const int gh = gather_group(order, CLS_HEAVY), gl = gather_group(order, CLS_LIGHT);
+      b->span_cap[gh] = std::max<int64_t>(b->span_cap[gh], split ? P->heavy_span : P->max_tile_nnz);
+      max_rows[gh] = std::max(max_rows[gh], P->rows_per_tile);
+      if (split) {
+        b->span_cap[gl] = std::max<int64_t>(b->span_cap[gl], P->light_span);
+        max_rows[gl] = std::max(max_rows[gl], P->rows_per_tile);
+      }
+    }
+    if (st != FEA_OK) break;
+    for (int g = 0; g < NGROUPS; ++g) {
+      if (g % 3 != CLS_INCIDENCE && max_rows[g] > 0)
+        b->smem[g] = g < 3 ? Tiled<10, double>::smem_bytes(max_rows[g], b->span_cap[g])
+                           : Tiled<4, double>::smem_bytes(max_rows[g], b->span_cap[g]);
+      if (b->smem[g] > 227 * 1024) st = fail(FEA_ERR_OVERFLOW, "row tile too large for the batch scatter");
     }
     if (st != FEA_OK) break;
     if (cudaMalloc(&b->pool, std::max<size_t>(bytes, 256)) != cudaSuccess) {
@@ -254,7 +390,8 @@ fea_status fea_batch_create(fea_mesh* const* meshes, int32_t n, const fea_form* 
       d.el.e1 = m->n_elems;
       d.el.kappa_const = 1.0;
       d.el.mass = forms[k].mass_coef;
-      d.el.ipos = B->ipos;
+      d.tiled = use_tiled(m, P);
+      d.el.ipos = d.tiled ? P->tpos : B->ipos;
       d.el.Lm = static_cast<char*>(b->pool) + lm_off[k];
       d.el.Fl = f_kind != FEA_LOAD_NONE ? static_cast<char*>(b->pool) + fl_off[k] : nullptr;
       d.el.err = m->err;
@@ -264,6 +401,17 @@ fea_status fea_batch_create(fea_mesh* const* meshes, int32_t n, const fea_form* 
       d.ga.slot = B->slot;
       d.ga.Lm = d.el.Lm;
       d.ga.Fl = d.el.Fl;
+      d.tg.ndof = P->ndof;
+      d.tg.rows = P->rows_per_tile;
+      d.tg.span_cap = P->max_tile_nnz;
+      d.tg.row_ptr = P->row_ptr;
+      d.tg.inc_ptr = B->inc_ptr;
+      d.tg.tile_base = P->tile_base;
+      d.tg.tile_steps = P->tile_steps;
+      d.tg.tslot = P->tslot;
+      d.tg.Lm = d.el.Lm;
+      d.tg.Fl = d.el.Fl;
+      d.tg.err = m->err;
     }
     if (cudaMalloc(&b->d_mesh, sizeof(BMesh) * n) != cudaSuccess) {
       cudaGetLastError();
@@ -271,19 +419,35 @@ fea_status fea_batch_create(fea_mesh* const* meshes, int32_t n, const fea_form* 
       break;
     }
     cudaError_t ea = cudaSuccess;
-    if (b->smem[1] > 48 * 1024)
-      ea = cudaFuncSetAttribute(k_batch_gather<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem[1]);
-    if (ea == cudaSuccess && b->smem[2] > 48 * 1024)
-      ea = cudaFuncSetAttribute(k_batch_gather<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem[2]);
+    // groups that share a kernel (heavy and light) opt in to the larger size
+    for (int g = 0; g < NGROUPS && ea == cudaSuccess; ++g) {
+      size_t need = 0;
+      for (int h = 0; h < NGROUPS; ++h)
+        if (GATHER_KERNELS[h] == GATHER_KERNELS[g]) need = std::max(need, b->smem[h]);
+      if (need > 48 * 1024)
+        ea = cudaFuncSetAttribute(GATHER_KERNELS[g], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+    }
     if (ea != cudaSuccess) {
       st = cuda_fail(ea, "batch scatter shared memory");
       break;
     }
-    b->elem_grid = b->sms * 4;
-    b->gather_grid = b->sms * 3;
+    // persistent grids: every CTA of each element kernel resident at once
+    for (int o = 1; o <= 2 && ea == cudaSuccess; ++o) {
+      int per_sm = 0;
+      ea = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b->ek[o][b->variant[o]], BT, 0);
+      b->elem_grid[o] = std::max(1, per_sm) * b->sms;
+    }
+    if (ea != cudaSuccess) {
+      st = cuda_fail(ea, "element kernel occupancy");
+      break;
+    }
     if ((st = build_items(b)) != FEA_OK) break;
+    b->gather_grid = b->n_gitems;
     cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
-    if (e != cudaSuccess) st = cuda_fail(e, "capture stream");
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) st = cuda_fail(e, "batch streams and events");
   } while (0);
   if (st != FEA_OK) {
     fea_batch_destroy(b);
@@ -306,6 +470,9 @@ fea_status fea_batch_bind(fea_batch* b, const fea_coeffs* coeffs, double* const*
     d.ga.rhs = rhs ? rhs[k] : nullptr;
     if (!d.ga.rhs) d.ga.Fl = nullptr;
     else d.ga.Fl = d.el.Fl;
+    d.tg.values = d.ga.values;
+    d.tg.rhs = d.ga.rhs;
+    d.tg.Fl = d.ga.Fl;
   }
   FEA_CUDA(cudaMemcpy(b->d_mesh, b->host.data(), sizeof(BMesh) * b->n, cudaMemcpyHostToDevice));
   b->bound = true;
@@ -325,7 +492,7 @@ fea_status fea_batch_tune(fea_batch* b, void* stream, int32_t* params) {
   if (!b->bound) return fail(FEA_ERR_STATE, "fea_batch_bind first");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int tiles[] = {128, 256, 512, 1024, 2048};
-  const int egrid[] = {2, 3, 4, 6, 8, 16};
+  const int egrid[] = {0, 2, 3, 4, 6, 8, 16};  // x SMs
   cudaEvent_t a, c;
   FEA_CUDA(cudaEventCreate(&a));
   FEA_CUDA(cudaEventCreate(&c));
@@ -343,34 +510,64 @@ fea_status fea_batch_tune(fea_batch* b, void* stream, int32_t* params) {
     }
     return FEA_OK;
   };
-  int bt = b->elem_tile, be = b->elem_grid;
-  float best = 1e30f;
-  // elements per work item x persistent element-kernel CTAs
+  // Coordinate search: elements per work item x P2 element-kernel CTAs (P1
+  // at full residency), then the P2 register variant x its CTAs, then the P1
+  // variant x its CTAs.  A grid of 0 launches one CTA per work item.
+  fea_status st = FEA_OK;
+  float best = 1e30f, ms = 0.f;
+  auto try_config = [&](bool* better) -> fea_status {
+    FEA_TRY(time_it(&ms));
+    *better = ms < best;
+    if (*better) best = ms;
+    return FEA_OK;
+  };
+  int bt = b->elem_tile, bg[3] = {0, b->elem_grid[1], b->elem_grid[2]}, bv[3] = {0, b->variant[1], b->variant[2]};
+  bool better = false;
   for (int t : tiles) {
     b->elem_tile = t;
-    FEA_TRY(build_items(b));
+    if ((st = build_items(b)) != FEA_OK) break;
     for (int g : egrid) {
-      b->elem_grid = g * b->sms;
-      float ms;
-      FEA_TRY(time_it(&ms));
-      if (ms < best) {
-        best = ms;
+      b->elem_grid[2] = g * b->sms;
+      if ((st = try_config(&better)) != FEA_OK) break;
+      if (better) {
         bt = t;
-        be = b->elem_grid;
+        bg[2] = b->elem_grid[2];
       }
     }
+    if (st != FEA_OK) break;
   }
-  b->elem_tile = bt;
-  b->elem_grid = be;
-  FEA_TRY(build_items(b));
-  b->gather_grid = b->n_gitems;
+  if (st == FEA_OK) {
+    b->elem_tile = bt;
+    b->elem_grid[2] = bg[2];
+    st = build_items(b);
+  }
+  for (int order = 2; order >= 1 && st == FEA_OK; --order) {
+    for (int v = 0; v < ELEM_VARIANTS && st == FEA_OK; ++v) {
+      b->variant[order] = v;
+      for (int g : egrid) {
+        b->elem_grid[order] = g * b->sms;
+        if ((st = try_config(&better)) != FEA_OK) break;
+        if (better) {
+          bv[order] = v;
+          bg[order] = b->elem_grid[order];
+        }
+      }
+    }
+    b->variant[order] = bv[order];
+    b->elem_grid[order] = bg[order];
+  }
   cudaEventDestroy(a);
   cudaEventDestroy(c);
+  FEA_TRY(st);
+  b->gather_grid = b->n_gitems;
   FEA_TRY(rebuild_graph(b));
   if (params) {
     params[0] = b->elem_tile;
-    params[1] = b->elem_grid;
-    params[2] = b->gather_grid;
+    params[1] = b->elem_grid[2] > 0 ? b->elem_grid[2] : b->ecount[2];
+    params[2] = b->elem_grid[1] > 0 ? b->elem_grid[1] : b->ecount[1];
+    params[3] = b->gather_grid;
+    params[4] = b->variant[2];
+    params[5] = b->variant[1];
   }
   return FEA_OK;
 }
@@ -380,6 +577,9 @@ fea_status fea_batch_destroy(fea_batch* b) {
   cudaDeviceSynchronize();
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->side) cudaStreamDestroy(b->side);
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+  if (b->join_ev) cudaEventDestroy(b->join_ev);
   if (b->d_mesh) cudaFree(b->d_mesh);
   if (b->d_eitems) cudaFree(b->d_eitems);
   if (b->d_gitems) cudaFree(b->d_gitems);

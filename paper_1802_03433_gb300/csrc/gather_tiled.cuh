@@ -174,17 +174,18 @@ __device__ __forceinline__ void smem_slots(const uint8_t* __restrict__ p, int s[
   }
 }
 
-// One CTA per row tile (tiles[blockIdx.x], or blockIdx.x), blockDim.x == rows.
+// The scatter of row tile `tile` by the whole CTA (blockDim.x >= G.rows;
+// threads past the tile's rows only help with the accumulator), with `sm`
+// the 128-byte aligned dynamic shared memory of Tiled<NB, LT>::smem_bytes.
+// A CTA runs this once: its mbarriers are initialised here.
 template <int NB, typename LT>
-__global__ void __launch_bounds__(128) k_gather_tiled(TiledArgs G, const int32_t* __restrict__ tiles) {
+__device__ __forceinline__ void gather_tiled_tile(const TiledArgs& G, int64_t tile, unsigned char* sm) {
   using L = Tiled<NB, LT>;
-  extern __shared__ __align__(128) unsigned char sm[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm);
   double* acc = reinterpret_cast<double*>(sm + 128);
   unsigned char* stages = sm + 128 + (((size_t)G.span_cap * 8 + 127) & ~size_t(127));
   const uint32_t stride = L::stage_stride(G.rows);
 
-  const int64_t tile = tiles ? (int64_t)__ldg(tiles + blockIdx.x) : (int64_t)blockIdx.x;
   const int64_t r0 = tile * G.rows;
   const int64_t r1 = r0 + G.rows < G.ndof ? r0 + G.rows : G.ndof;
   const int R = (int)(r1 - r0);
@@ -264,6 +265,14 @@ __global__ void __launch_bounds__(128) k_gather_tiled(TiledArgs G, const int32_t
   if (mine && G.rhs) G.rhs[r] = f;
   __syncthreads();
   for (int j = tid; j < span; j += blockDim.x) G.values[base + j] = acc[j];
+}
+
+// One CTA per row tile (tiles[blockIdx.x], or blockIdx.x), blockDim.x == rows.
+template <int NB, typename LT>
+__global__ void __launch_bounds__(128) k_gather_tiled(TiledArgs G, const int32_t* __restrict__ tiles) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  const int64_t tile = tiles ? (int64_t)__ldg(tiles + blockIdx.x) : (int64_t)blockIdx.x;
+  gather_tiled_tile<NB, LT>(G, tile, sm);
 }
 
 fea_status launch_gather_tiled(int nb, bool mixed, const TiledArgs& G, cudaStream_t s, const int32_t* tiles,

@@ -354,7 +354,7 @@ def fea_batch_assemble(b, stream=None):
 
 
 def fea_batch_tune(b, stream=None):
-    p = (C.c_int32 * 3)()
+    p = (C.c_int32 * 6)()
     _check(lib().fea_batch_tune(b, _stream(stream), p), "fea_batch_tune")
     return tuple(p)
 

@@ -74,13 +74,45 @@ def test_tuned_batch_still_bitwise():
     single = _single(meshes, forms, quads, coeffs)
     b = fea.Batch(meshes, forms, quads, coeffs, fea.FEA_LOAD_SINPROD)
     params = b.tune()
-    assert params[0] in (128, 256, 512, 1024, 2048) and params[1] > 0 and params[2] > 0
+    assert params[0] in (128, 256, 512, 1024, 2048) and min(params[1:4]) > 0
+    assert params[4] in (0, 1) and params[5] in (0, 1)
     b.assemble()
     torch.cuda.synchronize()
     for k in range(len(meshes)):
         nnz = meshes[k].pattern(forms[k].order)[1]
         assert _bitwise_equal(b.values[k][:nnz], single[k][0])
         assert _bitwise_equal(b.rhs[k], single[k][1])
+    b.close()
+
+
+@pytest.mark.parametrize("orders", ["mixed_layouts", "p2_only", "p1_only"])
+def test_batch_layouts_and_single_order(orders):
+    """Meshes whose scatter is forced to the incidence-order layout (scatter
+    classes 0) beside meshes on the tiled layout, and batches with one of the
+    two order branches empty: still bitwise the single-mesh results."""
+    import torch
+    from paper_1802_03433_gb300 import fea
+    specs = mg.batch(n_meshes=8, lo=2, hi=7, seed=6)
+    if orders != "mixed_layouts":
+        want = 2 if orders == "p2_only" else 1
+        for d in specs:
+            d["order"], d["npts"] = want, 4 if want == 1 else 11
+    meshes, forms, quads, coeffs, keep = _build(specs)
+    if orders == "mixed_layouts":
+        for k in (0, 3, 5):
+            fea.fea_mesh_set_scatter_classes(meshes[k].h, 0)
+    single = _single(meshes, forms, quads, coeffs)
+    b = fea.Batch(meshes, forms, quads, coeffs, fea.FEA_LOAD_SINPROD)
+    for rep in range(2):
+        if rep == 1:
+            b.tune()
+        b.assemble()
+        torch.cuda.synchronize()
+        for k in range(len(meshes)):
+            meshes[k].check()
+            nnz = meshes[k].pattern(forms[k].order)[1]
+            assert _bitwise_equal(b.values[k][:nnz], single[k][0]), (k, rep)
+            assert _bitwise_equal(b.rhs[k], single[k][1]), (k, rep)
     b.close()
 
 
