@@ -54,6 +54,7 @@ WORKLOADS = {
     "p2_diffmass_64": dict(kind="p2_diffmass", n=64),
     "p1_poisson_8": dict(kind="p1_poisson", n=8),
     "p1_elast_128": dict(kind="elasticity", n=128),
+    "p1_elast_64": dict(kind="elasticity", n=64),     # small case of the same kernel, for multi-pass captures
     "p1_kappa_96": dict(kind="p1_kappa", n=96),
 }
 
@@ -187,6 +188,8 @@ def run_ours(args):
         fea.fea_mesh_set_scatter_classes(mesh.h, args.scatter_classes)
     if args.load_split >= 0:
         fea.fea_mesh_set_load_split(mesh.h, args.load_split)
+    if args.scatter_stages > 0:
+        fea.fea_mesh_set_scatter_stages(mesh.h, args.scatter_stages)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ndof, nnz = mesh.pattern(d["order"], d["ndpn"])
@@ -315,6 +318,8 @@ def run_ours(args):
                     fea.fea_mesh_set_scatter_classes(mi.h, args.scatter_classes)
                 if args.load_split >= 0:
                     fea.fea_mesh_set_load_split(mi.h, args.load_split)
+                if args.scatter_stages > 0:
+                    fea.fea_mesh_set_scatter_stages(mi.h, args.scatter_stages)
                 mi.pattern(d["order"], d["ndpn"])
             dev_coef = [torch.empty_like(t) for t in keep if t is not None]
             if d["form"] == 2:
@@ -779,6 +784,8 @@ def main():
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--stages", type=int, default=1, help="element chunks overlapped with the scatter (1 = none)")
     p.add_argument("--scatter-classes", type=int, default=-1, help="scatter launch shape 0-3 (-1 = library default)")
+    p.add_argument("--scatter-stages", type=int, default=0,
+                   help="bulk-copy scatter stages per CTA, 2-4 (0 = library default)")
     p.add_argument("--load-split", type=int, default=-1, help="element launch: 0 fused, 1 matrix then load, "
                                                                "2 load kernel concurrent with the matrix kernel "
                                                                "(-1 = library default)")

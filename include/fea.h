@@ -152,7 +152,7 @@ fea_status fea_mesh_set_stages(fea_mesh* mesh, int32_t stages);
 /* Scatter of fea_assemble (stages == 1), fea_assemble_noalloc,
  * fea_assemble_2d and fea_jit_assemble.  3 = the bulk-copy scatter: local rows
  * in the tile-interleaved layout, each row tile streamed into shared memory
- * by cp.async.bulk copies through a three-stage mbarrier ring (scalar forms;
+ * by cp.async.bulk copies through a ring of mbarrier-completed stages (scalar forms;
  * elasticity falls back to 0).  The incidence-order scatters: 0 = one launch
  * of the two-deep pipelined kernel over all row tiles; 1 = tiles whose CSR
  * span exceeds half the widest in one such launch, the rest in a second
@@ -161,6 +161,13 @@ fea_status fea_mesh_set_stages(fea_mesh* mesh, int32_t stages);
  * forms, else 2 when the pattern mixes long and short rows, else 0.
  * Results are bitwise identical for every mode. */
 fea_status fea_mesh_set_scatter_classes(fea_mesh* mesh, int32_t mode);
+
+/* Shared-memory stages per CTA of the bulk-copy scatter (scatter mode 3):
+ * 2, 3 or 4 steps of the row tile in flight per CTA; 0 (default) =
+ * automatic, per launch the most resident CTAs per SM given the
+ * accumulator's shared memory, then the most stages that keep that count.
+ * Results are bitwise identical for every count. */
+fea_status fea_mesh_set_scatter_stages(fea_mesh* mesh, int32_t stages);
 
 /* Element launch of fea_assemble for scalar forms with a load vector (stages
  * == 1): 0 = one kernel computes the local matrix and the local load; 1 = a
@@ -330,8 +337,10 @@ fea_status fea_profile_last(fea_mesh* mesh, float* elem_ms, float* scatter_ms);
  * kernels use (sinpi_fx); 1: the FP64-pipe polynomial (its fallback for tiny,
  * huge and non-finite arguments, and the sinpi_fp64 of runtime-compiled
  * expressions); 2: the fixed-point value with 62 fractional bits the FP64
- * load vectors multiply and sum on the integer pipes (sinpi_q62), converted.
- * Asynchronous. */
+ * load vectors multiply and sum on the integer pipes (sinpi_q62), converted;
+ * 3: the same value from x in fixed point, x 2^(61 - s) with s set by |x|
+ * (to_fx, sinpi_q62_fx: the path of the FP64 sine loads, whose quadrature
+ * points are formed in fixed point), for |x| < 2^58.  Asynchronous. */
 fea_status fea_diag_sinpi(const double* x, int64_t n, int32_t variant, double* mine, double* lib, void* stream);
 
 /* Measure the device's sustained FP64 FMA throughput (flop/s, FMA = 2)

@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(BT) k_batch_gather(const BMesh* __restrict__ M
 
 // span_cap: the accumulator capacity (doubles) of this launch's shared-memory
 // layout, at least the CSR span of every tile it is given.
-template <int NB>
+template <int NB, int STAGES>
 __global__ void __launch_bounds__(BT) k_batch_gather_tiled(const BMesh* __restrict__ M,
                                                            const BItem* __restrict__ items, int nitems,
                                                            int64_t span_cap) {
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(BT) k_batch_gather_tiled(const BMesh* __restri
   const BItem w = items[blockIdx.x];
   TiledArgs G = M[w.mesh].tg;
   G.span_cap = span_cap;
-  gather_tiled_tile<NB, double>(G, w.first, sm);
+  gather_tiled_tile<NB, double, STAGES>(G, w.first, sm);
 }
 
 // Scatter item groups, in launch order, per order (P2, then P1): tiled tiles
@@ -114,8 +114,13 @@ enum { CLS_HEAVY = 0, CLS_LIGHT = 1, CLS_INCIDENCE = 2 };
 inline int gather_group(int order, int cls) { return (order == 2 ? 0 : 3) + cls; }
 
 using GatherKernel = void (*)(const BMesh*, const BItem*, int, int64_t);
-const GatherKernel GATHER_KERNELS[NGROUPS] = {k_batch_gather_tiled<10>, k_batch_gather_tiled<10>, k_batch_gather<10>,
-                                              k_batch_gather_tiled<4>,  k_batch_gather_tiled<4>,  k_batch_gather<4>};
+
+template <int NB>
+GatherKernel tiled_kernel(int stages) {
+  if (stages == 2) return k_batch_gather_tiled<NB, 2>;
+  if (stages == 4) return k_batch_gather_tiled<NB, 4>;
+  return k_batch_gather_tiled<NB, 3>;
+}
 
 using ElemKernel = void (*)(const BMesh*, const BItem*, int);
 
@@ -163,6 +168,7 @@ struct fea_batch {
   int gcount[NGROUPS] = {};           // row-tile items per group
   void* pool = nullptr;  // local rows and loads of every mesh
   size_t smem[NGROUPS] = {};          // scatter shared memory per CTA, by group
+  GatherKernel gk[NGROUPS] = {};      // scatter kernel per group (stage count of the tiled groups)
   int64_t span_cap[NGROUPS] = {};     // accumulator capacity of the tiled groups
   std::vector<std::vector<uint8_t>> heavy;  // per mesh: tile -> heavy class (tiled meshes)
   int load = 0, np1 = 4, np2 = 11;
@@ -242,8 +248,8 @@ fea_status launch_phases(fea_batch* b, cudaStream_t s) {
     }
     for (int g = gather_group(order, 0), ge = g + 3; g < ge; ++g) {
       if (b->gcount[g] > 0)
-        GATHER_KERNELS[g]<<<b->gcount[g], BT, b->smem[g], st>>>(b->d_mesh, b->d_gitems + first, b->gcount[g],
-                                                                 b->span_cap[g]);
+        b->gk[g]<<<b->gcount[g], BT, b->smem[g], st>>>(b->d_mesh, b->d_gitems + first, b->gcount[g],
+                                                        b->span_cap[g]);
       first += b->gcount[g];
     }
   }
@@ -359,9 +365,17 @@ fea_status fea_batch_create(fea_mesh* const* meshes, int32_t n, const fea_form* 
     }
     if (st != FEA_OK) break;
     for (int g = 0; g < NGROUPS; ++g) {
-      if (g % 3 != CLS_INCIDENCE && max_rows[g] > 0)
-        b->smem[g] = g < 3 ? Tiled<10, double>::smem_bytes(max_rows[g], b->span_cap[g])
-                           : Tiled<4, double>::smem_bytes(max_rows[g], b->span_cap[g]);
+      const int nb = g < 3 ? 10 : 4;
+      if (g % 3 == CLS_INCIDENCE) {
+        b->gk[g] = nb == 10 ? k_batch_gather<10> : k_batch_gather<4>;
+      } else {
+        // the single-mesh scatter's stage choice, for the group's widest tile
+        const int stages = tiled_stages_auto(nb, false, std::max(max_rows[g], 1), b->span_cap[g]);
+        b->gk[g] = nb == 10 ? tiled_kernel<10>(stages) : tiled_kernel<4>(stages);
+        if (max_rows[g] > 0)
+          b->smem[g] = nb == 10 ? Tiled<10, double>::smem_bytes(max_rows[g], b->span_cap[g], stages)
+                                : Tiled<4, double>::smem_bytes(max_rows[g], b->span_cap[g], stages);
+      }
       if (b->smem[g] > 227 * 1024) st = fail(FEA_ERR_OVERFLOW, "row tile too large for the batch scatter");
     }
     if (st != FEA_OK) break;
@@ -423,9 +437,9 @@ fea_status fea_batch_create(fea_mesh* const* meshes, int32_t n, const fea_form* 
     for (int g = 0; g < NGROUPS && ea == cudaSuccess; ++g) {
       size_t need = 0;
       for (int h = 0; h < NGROUPS; ++h)
-        if (GATHER_KERNELS[h] == GATHER_KERNELS[g]) need = std::max(need, b->smem[h]);
+        if (b->gk[h] == b->gk[g]) need = std::max(need, b->smem[h]);
       if (need > 48 * 1024)
-        ea = cudaFuncSetAttribute(GATHER_KERNELS[g], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+        ea = cudaFuncSetAttribute(b->gk[g], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
     }
     if (ea != cudaSuccess) {
       st = cuda_fail(ea, "batch scatter shared memory");

@@ -9,9 +9,15 @@ __global__ void k_diag_sinpi(const double* __restrict__ x, int64_t n, int varian
                              double* __restrict__ lib) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  mine[i] = variant == 0   ? rsinpi<double>(x[i])
-            : variant == 1 ? sinpi_fp64(x[i])
-                           : __ll2double_rn(sinpi_q62(x[i])) * 0x1p-62;
+  if (variant == 3) {
+    const double v[4] = {x[i], x[i], x[i], x[i]};
+    const int s = fx_shift(v);
+    mine[i] = __ll2double_rn(sinpi_q62_fx(to_fx(x[i], s), s)) * 0x1p-62;
+  } else {
+    mine[i] = variant == 0   ? rsinpi<double>(x[i])
+              : variant == 1 ? sinpi_fp64(x[i])
+                             : __ll2double_rn(sinpi_q62(x[i])) * 0x1p-62;
+  }
   lib[i] = sinpi(x[i]);
 }
 // Eight independent DFMA chains per thread: the FP64 pipe's sustained FMA
@@ -60,7 +66,7 @@ extern "C" fea_status fea_diag_fp64_rate(double* flops_per_s, void* stream) {
 
 extern "C" fea_status fea_diag_sinpi(const double* x, int64_t n, int32_t variant, double* mine, double* lib,
                                       void* stream) {
-  if (n < 0 || (n > 0 && (!x || !mine || !lib)) || variant < 0 || variant > 2)
+  if (n < 0 || (n > 0 && (!x || !mine || !lib)) || variant < 0 || variant > 3)
     return fea::fail(FEA_ERR_ARG, "bad argument");
   if (n == 0) return FEA_OK;
   fea::k_diag_sinpi<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, n, variant, mine,

@@ -327,6 +327,25 @@ __device__ __forceinline__ double sinpi_fx(double x) {
   return __longlong_as_double(static_cast<long long>(bits | sign));
 }
 
+// |r| P(r^2) 2^62 for ra = |r| 2^64 (|r| <= 1/2): the Horner polynomial of
+// sinpi_fx in 60 fractional bits and the 128-bit product |r| P shifted to 62
+// fractional bits (truncated).
+__device__ __forceinline__ long long sinpi_q62_mag(unsigned long long ra) {
+  const long long u = static_cast<long long>(__umul64hi(ra, ra));
+  long long p = SINPI_Q8;
+  p = __mul64hi(p, u) + SINPI_Q7;
+  p = __mul64hi(p, u) + SINPI_Q6;
+  p = __mul64hi(p, u) + SINPI_Q5;
+  p = __mul64hi(p, u) + SINPI_Q4;
+  p = __mul64hi(p, u) + SINPI_Q3;
+  p = __mul64hi(p, u) + SINPI_Q2;
+  p = __mul64hi(p, u) + SINPI_Q1;
+  p = __mul64hi(p, u) + SINPI_Q0;
+  const unsigned long long up = static_cast<unsigned long long>(p);
+  const unsigned long long hi = __umul64hi(ra, up), lo = ra * up;
+  return static_cast<long long>((hi << 2) | (lo >> 62));
+}
+
 // sin(pi x) 2^62 as a signed 64-bit integer (|value| <= 2^62), for products
 // and sums on the integer pipes: the reduction and polynomial of sinpi_fx,
 // then the 128-bit product |r| P shifted to 62 fractional bits (truncated,
@@ -344,19 +363,7 @@ __device__ __forceinline__ long long sinpi_q62(double x) {
   const unsigned rneg = static_cast<unsigned>(f >> 63);
   const unsigned par = (sh > 11u ? static_cast<unsigned>(m >> (64u - sh)) & 1u : 0u) ^ rneg;
   const unsigned long long ra = rneg ? 0ull - f : f;
-  const long long u = static_cast<long long>(__umul64hi(ra, ra));
-  long long p = SINPI_Q8;
-  p = __mul64hi(p, u) + SINPI_Q7;
-  p = __mul64hi(p, u) + SINPI_Q6;
-  p = __mul64hi(p, u) + SINPI_Q5;
-  p = __mul64hi(p, u) + SINPI_Q4;
-  p = __mul64hi(p, u) + SINPI_Q3;
-  p = __mul64hi(p, u) + SINPI_Q2;
-  p = __mul64hi(p, u) + SINPI_Q1;
-  p = __mul64hi(p, u) + SINPI_Q0;
-  const unsigned long long up = static_cast<unsigned long long>(p);
-  const unsigned long long hi = __umul64hi(ra, up), lo = ra * up;
-  const long long mag = static_cast<long long>((hi << 2) | (lo >> 62));
+  const long long mag = sinpi_q62_mag(ra);
   return ((b >> 63) ^ par ^ rneg) ? -mag : mag;
 }
 static __device__ __noinline__ long long sinpi_q62_call(double x) { return sinpi_q62(x); }
@@ -364,6 +371,89 @@ template <bool OUTLINE>
 __device__ __forceinline__ long long sinpi_q62_sel(double x) {
   if constexpr (OUTLINE) return sinpi_q62_call(x);
   else return sinpi_q62(x);
+}
+
+// sin(pi x) 2^62 for x given in fixed point, t = x 2^(61 - s) (0 <= s <= 60,
+// two's complement): the fraction of x in units of 2^-64 is t << (3 + s) and
+// the parity of floor(x) is bit 61 - s of t.  With n the nearest integer to x
+// and r = x - n, sin(pi x) = (-1)^n sign(r) |r| P(r^2); when the fraction is
+// at least 1/2, n = floor(x) + 1 and r < 0, so both factors flip and the sign
+// of the result is the parity of floor(x) alone.  The polynomial and the
+// product are those of sinpi_q62.
+__device__ __forceinline__ long long sinpi_q62_fx(long long t, int s) {
+  const unsigned long long ut = static_cast<unsigned long long>(t);
+  const unsigned long long f = ut << (3 + s);
+  const unsigned pf = static_cast<unsigned>(ut >> (61 - s)) & 1u;
+  const unsigned long long ra = (f >> 63) ? 0ull - f : f;
+  const long long mag = sinpi_q62_mag(ra);
+  return pf ? -mag : mag;
+}
+static __device__ __noinline__ long long sinpi_q62_fx_call(long long t, int s) { return sinpi_q62_fx(t, s); }
+template <bool OUTLINE>
+__device__ __forceinline__ long long sinpi_q62_fx_sel(long long t, int s) {
+  if constexpr (OUTLINE) return sinpi_q62_fx_call(t, s);
+  else return sinpi_q62_fx(t, s);
+}
+
+// ---- quadrature-point coordinates in fixed point (the sine load in FP64)
+// A coordinate c of the four vertices, v_a, goes to t_a = round(v_a 2^(61 - s))
+// with s = max(0, E + 1) for |v_a| < 2^E (E from the largest exponent):
+// |t_a| < 2^60, their sum below 2^62, and every point of the rule (a convex
+// combination) as well, so nothing wraps.  The conversion shifts the
+// mantissa (integer pipes only); the resolution 2^(s - 61) is about 2^-62 of
+// max |v_a|, below the rounding of an FP64 evaluation of the point.
+// Coordinates of 2^59 and more (and non-finite ones) saturate s at 60 and
+// give meaningless sines (such an element has no FP64 fraction left, and a
+// non-finite one is reported through its det J).
+__device__ __forceinline__ int fx_shift(const double v[4]) {
+  int e = 0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) e = max(e, static_cast<int>(__double2hiint(v[a]) >> 20) & 0x7FF);
+  return min(max(e - 1021, 0), 60);
+}
+__device__ __forceinline__ long long to_fx(double v, int s) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+  const int e = static_cast<int>(b >> 52) & 0x7FF;
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (e ? (1ull << 52) : 0ull);
+  const int k = e - 1014 - s;  // v 2^(61 - s) = m 2^k; k <= 7 for s from fx_shift
+  const unsigned long long mag = k >= 0 ? (m << min(k, 63)) : (((m >> min(-k - 1, 62)) + 1ull) >> 1);
+  return (b >> 63) ? -static_cast<long long>(mag) : static_cast<long long>(mag);
+}
+// floor(L v / 2^63) for a rule constant L = l 2^63 (0 <= l < 1).
+__device__ __forceinline__ long long mul_q63(long long L, long long v) {
+  const unsigned long long hi = static_cast<unsigned long long>(__mul64hi(L, v));
+  const unsigned long long lo = static_cast<unsigned long long>(L) * static_cast<unsigned long long>(v);
+  return static_cast<long long>((hi << 1) | (lo >> 63));
+}
+__host__ __device__ constexpr long long q63(double c) { return static_cast<long long>(c * 9223372036854775808.0); }
+
+// The rule's points, coordinate c, in fixed point: the same symmetry-class
+// form as quad_coord (a point of a class is B S + (A - B) v_q, S the vertex
+// sum) with the same FP64 constants, scaled exactly by 2^63.
+template <int NPTS>
+__device__ __forceinline__ void quad_coord_fx(const double v[4], int s, long long xq[NPTS]) {
+  long long t[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) t[a] = to_fx(v[a], s);
+  const long long S = (t[0] + t[1]) + (t[2] + t[3]);
+  if constexpr (NPTS == 1) {
+    xq[0] = S >> 2;
+  } else if constexpr (NPTS == 4) {
+    const long long bS = mul_q63(q63(R4B), S);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) xq[q] = mul_q63(q63(R4A - R4B), t[q]) + bS;
+  } else {
+    xq[0] = S >> 2;
+    const long long bS = mul_q63(q63(K11B), S);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) xq[1 + q] = mul_q63(q63(K11A - K11B), t[q]) + bS;
+    const long long cS = mul_q63(q63(K11C2), S);
+    long long P[4];  // (C1 - C2) v_a, summed per edge
+#pragma unroll
+    for (int a = 0; a < 4; ++a) P[a] = mul_q63(q63(K11C1 - K11C2), t[a]);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) xq[5 + k] = P[edge_p(k)] + P[edge_q(k)] + cS;
+  }
 }
 
 // floor(a b / 2^62) for |a|, |b| <= 2^62 (the 128-bit product shifted).
@@ -678,17 +768,18 @@ __device__ __forceinline__ void shape_load(const R Xr[4][3], R Fs[ORDER == 1 ? 4
       Fs[A] = R(c);
     });
   } else if constexpr (IsDouble<R>::value) {
-    // FP64: the sines, their products and the rule sums in fixed point on the
-    // integer pipes; one conversion per output
+    // FP64: the points' coordinates, the sines, their products and the rule
+    // sums in fixed point on the integer pipes; one conversion per output
     long long sq[NPTS];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const R v[4] = {Xr[0][c], Xr[1][c], Xr[2][c], Xr[3][c]};
-      R xq[NPTS];
-      quad_coord<NPTS, R>(v, xq);
+      const double v[4] = {Xr[0][c], Xr[1][c], Xr[2][c], Xr[3][c]};
+      const int s = fx_shift(v);
+      long long xq[NPTS];
+      quad_coord_fx<NPTS>(v, s, xq);
 #pragma unroll
       for (int q = 0; q < NPTS; ++q) {
-        const long long t = sinpi_q62_sel<OUTLINE>(xq[q]);
+        const long long t = sinpi_q62_fx_sel<OUTLINE>(xq[q], s);
         sq[q] = c == 0 ? t : mul_q62(sq[q], t);
       }
     }

@@ -207,6 +207,13 @@ fea_status fea_mesh_set_scatter_classes(fea_mesh* m, int32_t mode) {
   return FEA_OK;
 }
 
+fea_status fea_mesh_set_scatter_stages(fea_mesh* m, int32_t stages) {
+  if (!m) return fail(FEA_ERR_ARG, "mesh is NULL");
+  if (stages != 0 && (stages < 2 || stages > 4)) return fail(FEA_ERR_ARG, "stages must be 0, 2, 3 or 4");
+  m->tiled_stages = stages;
+  return FEA_OK;
+}
+
 fea_status fea_mesh_destroy(fea_mesh* m) {
   if (!m) return FEA_OK;
   cudaDeviceSynchronize();

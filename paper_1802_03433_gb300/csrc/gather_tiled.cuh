@@ -12,9 +12,11 @@
 // k-th contribution of each of its rows) is one contiguous block of global
 // memory (the element kernel writes every local row to its tiled position,
 // Pattern::tpos).  Thread 0 streams the tile step by step with bulk copies
-// into TILED_STAGES shared-memory stages, each completed by an mbarrier
-// transaction count, so TILED_STAGES - 1 steps are in flight while the CTA
-// adds the current one; no thread waits on its own global loads.
+// into STAGES (2 to 4) shared-memory stages, each completed by an mbarrier
+// transaction count, so STAGES - 1 steps are in flight while the CTA adds the
+// current one; no thread waits on its own global loads.  The launcher picks
+// STAGES per launch from the shared memory that the accumulator leaves
+// (tiled_stages_auto).
 //
 // Every wait on an mbarrier is bounded (TILED_WAIT_LIMIT polls).  If a step
 // never completes, the CTA raises DEV_ERR_TIMEOUT in the mesh's error word,
@@ -29,7 +31,8 @@
 
 namespace fea {
 
-constexpr int TILED_STAGES = 3;
+constexpr int TILED_STAGES = 3;      // default stage count
+constexpr int TILED_MAX_STAGES = 4;
 constexpr uint32_t TILED_WAIT_LIMIT = 1u << 22;
 
 // ------------------------------------------------------------------ PTX
@@ -89,8 +92,8 @@ struct Tiled {
            ~127u;
   }
   // dynamic shared memory: mbarriers, the accumulator span, the stages
-  __host__ __device__ static constexpr size_t smem_bytes(int rows, int64_t span_cap) {
-    return 128 + (((size_t)span_cap * 8 + 127) & ~size_t(127)) + (size_t)TILED_STAGES * stage_stride(rows);
+  __host__ __device__ static constexpr size_t smem_bytes(int rows, int64_t span_cap, int stages = TILED_STAGES) {
+    return 128 + (((size_t)span_cap * 8 + 127) & ~size_t(127)) + (size_t)stages * stage_stride(rows);
   }
 };
 
@@ -176,10 +179,12 @@ __device__ __forceinline__ void smem_slots(const uint8_t* __restrict__ p, int s[
 
 // The scatter of row tile `tile` by the whole CTA (blockDim.x >= G.rows;
 // threads past the tile's rows only help with the accumulator), with `sm`
-// the 128-byte aligned dynamic shared memory of Tiled<NB, LT>::smem_bytes.
-// A CTA runs this once: its mbarriers are initialised here.
-template <int NB, typename LT>
+// the 128-byte aligned dynamic shared memory of
+// Tiled<NB, LT>::smem_bytes(rows, G.span_cap, STAGES).  A CTA runs this
+// once: its mbarriers are initialised here.
+template <int NB, typename LT, int STAGES = TILED_STAGES>
 __device__ __forceinline__ void gather_tiled_tile(const TiledArgs& G, int64_t tile, unsigned char* sm) {
+  static_assert(STAGES >= 2 && STAGES <= TILED_MAX_STAGES, "stage count");
   using L = Tiled<NB, LT>;
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm);
   double* acc = reinterpret_cast<double*>(sm + 128);
@@ -201,14 +206,14 @@ __device__ __forceinline__ void gather_tiled_tile(const TiledArgs& G, int64_t ti
   for (int k = tid; k < span; k += blockDim.x) acc[k] = 0.0;
   if (tid == 0) {
 #pragma unroll
-    for (int st = 0; st < TILED_STAGES; ++st) mbar_init(&bar[st], 1);
+    for (int st = 0; st < STAGES; ++st) mbar_init(&bar[st], 1);
     mbar_init_fence();
   }
   __syncthreads();
 
-  // thread 0: step k of the tile -> stage k % TILED_STAGES
+  // thread 0: step k of the tile -> stage k % STAGES
   auto issue = [&](int k) {
-    const int st = k % TILED_STAGES;
+    const int st = k % STAGES;
     unsigned char* dst = stages + (size_t)st * stride;
     const int64_t p = pbase + (int64_t)k * S;
     mbar_expect_tx(&bar[st], lm_b + sl_b + fl_b);
@@ -218,7 +223,7 @@ __device__ __forceinline__ void gather_tiled_tile(const TiledArgs& G, int64_t ti
   };
   int issued = 0;  // thread 0's count of issued steps
   if (tid == 0)
-    for (; issued < (K < TILED_STAGES ? K : TILED_STAGES); ++issued) issue(issued);
+    for (; issued < (K < STAGES ? K : STAGES); ++issued) issue(issued);
 
   const bool mine = tid < R;
   const int64_t r = r0 + tid;
@@ -232,8 +237,8 @@ __device__ __forceinline__ void gather_tiled_tile(const TiledArgs& G, int64_t ti
   int k = 0;
   bool failed = false;
   for (; k < K; ++k) {
-    const int st = k % TILED_STAGES;
-    const bool ok = mbar_wait(&bar[st], (uint32_t)(k / TILED_STAGES) & 1u);
+    const int st = k % STAGES;
+    const bool ok = mbar_wait(&bar[st], (uint32_t)(k / STAGES) & 1u);
     if (ok && mine && k < cnt) {
       const unsigned char* sp = stages + (size_t)st * stride;
       int sl[NB];
@@ -257,7 +262,7 @@ __device__ __forceinline__ void gather_tiled_tile(const TiledArgs& G, int64_t ti
     if (tid == 0) {
       atomicOr(G.err, DEV_ERR_TIMEOUT);
       // let the copies already issued land before the CTA's shared memory goes away
-      for (int j = k; j < issued; ++j) mbar_wait(&bar[j % TILED_STAGES], (uint32_t)(j / TILED_STAGES) & 1u);
+      for (int j = k; j < issued; ++j) mbar_wait(&bar[j % STAGES], (uint32_t)(j / STAGES) & 1u);
     }
     __syncthreads();
     return;
@@ -268,15 +273,25 @@ __device__ __forceinline__ void gather_tiled_tile(const TiledArgs& G, int64_t ti
 }
 
 // One CTA per row tile (tiles[blockIdx.x], or blockIdx.x), blockDim.x == rows.
-template <int NB, typename LT>
+template <int NB, typename LT, int STAGES>
 __global__ void __launch_bounds__(128) k_gather_tiled(TiledArgs G, const int32_t* __restrict__ tiles) {
   extern __shared__ __align__(128) unsigned char sm[];
   const int64_t tile = tiles ? (int64_t)__ldg(tiles + blockIdx.x) : (int64_t)blockIdx.x;
-  gather_tiled_tile<NB, LT>(G, tile, sm);
+  gather_tiled_tile<NB, LT, STAGES>(G, tile, sm);
 }
 
+// stages: 2 to TILED_MAX_STAGES, or 0 for the automatic choice
+// (tiled_stages_auto).
 fea_status launch_gather_tiled(int nb, bool mixed, const TiledArgs& G, cudaStream_t s, const int32_t* tiles,
-                               int64_t ntiles);
+                               int64_t ntiles, int stages = 0);
+
+// The stage count for a CTA whose accumulator holds span_cap doubles: the
+// most resident CTAs per SM first, then the most stages that keep that count.
+// (Measured on the P2 diffusion + mass scatter: two stages and three CTAs per
+// SM beat three stages and two CTAs by 14%, four stages and two CTAs lose a
+// further 15%: the CTAs' warps hide the shared-memory adds and the pipeline
+// fill of the short tiles, more stages do not.)
+int tiled_stages_auto(int nb, bool mixed, int rows, int64_t span_cap);
 
 // Whether a scalar pattern takes the bulk-copy scatter: its tiled layout is
 // built and the mesh's scatter mode is automatic (-1) or 3.

@@ -117,6 +117,7 @@ struct fea_mesh {
                             // launch, -1 automatic (2 when the pattern mixes long and short rows, else 0)
   cudaStream_t side = nullptr;             // scatter stream of the overlapped path
   cudaEvent_t chunk_ev[17] = {nullptr};    // chunk done (<= 16 stages) + join
+  int tiled_stages = 0;     // bulk-copy scatter stages per CTA (2..4), 0 automatic
   int load_split = -1;      // scalar forms: 0 fused element kernel; 1 matrix kernel then load kernel;
                             // 2 load kernel on the side stream, concurrent with the matrix kernel;
                             // 3 one kernel with matrix warps and load warps; -1 automatic (0)

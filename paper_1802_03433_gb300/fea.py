@@ -81,6 +81,7 @@ def lib() -> C.CDLL:
         "fea_mesh_set_stages": [_vp, C.c_int32],
         "fea_mesh_set_scatter_classes": [_vp, C.c_int32],
         "fea_mesh_set_load_split": [_vp, C.c_int32],
+        "fea_mesh_set_scatter_stages": [_vp, C.c_int32],
         "fea_mesh_check": [_vp, _vp],
         "fea_pattern": [_vp, C.c_int32, C.c_int32, i64p, i64p, _vp],
         "fea_pattern_copy": [_vp, C.c_int32, C.c_int32, _vp, _vp, _vp],
@@ -238,6 +239,10 @@ def fea_mesh_set_load_split(h, mode):
 
 def fea_mesh_set_scatter_classes(h, mode):
     _check(lib().fea_mesh_set_scatter_classes(h, mode), "fea_mesh_set_scatter_classes")
+
+
+def fea_mesh_set_scatter_stages(h, stages):
+    _check(lib().fea_mesh_set_scatter_stages(h, stages), "fea_mesh_set_scatter_stages")
 
 
 def fea_mesh_destroy(h):

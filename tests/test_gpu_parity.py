@@ -291,6 +291,28 @@ def test_scatter_launch_shapes_bitwise_identical(torch_cuda, kind, n, prec):
     assert row_scaled_error(o["rp"], o["vals"], ref["vals"]) <= (TOL_FP64 if prec == 0 else TOL_MIXED)
 
 
+@pytest.mark.parametrize("kind,n", [("p1_kappa", 12), ("p2_diffmass", 9)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_scatter_stage_counts_bitwise_identical(torch_cuda, kind, n, prec):
+    """The bulk-copy scatter with 2, 3 and 4 stages per CTA and the automatic
+    count: same bits."""
+    from paper_1802_03433_gb300 import fea
+    c = case(kind, n, seed=29)
+    m = fea.Mesh(c["coords"], c["tets"])
+    fea.fea_mesh_set_scatter_classes(m.h, 3)
+    ref = None
+    for st in (3, 2, 4, 0):
+        fea.fea_mesh_set_scatter_stages(m.h, st)
+        g = gpu_system(c, prec=prec, mesh=m)
+        if ref is None:
+            ref = g
+            continue
+        assert np.array_equal(g["vals"].view(np.uint64), ref["vals"].view(np.uint64)), st
+        assert np.array_equal(g["rhs"].view(np.uint64), ref["rhs"].view(np.uint64)), st
+    with pytest.raises(fea.FeaError):
+        fea.fea_mesh_set_scatter_stages(m.h, 5)
+
+
 @pytest.mark.parametrize("kind,n", [("p1_kappa", 10), ("p2_diffmass", 7)])
 @pytest.mark.parametrize("prec", [0, 1])
 def test_load_split_modes_bitwise_identical(torch_cuda, kind, n, prec):
