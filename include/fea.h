@@ -165,7 +165,7 @@ fea_status fea_mesh_set_scatter_classes(fea_mesh* mesh, int32_t mode);
 /* Shared-memory stages per CTA of the bulk-copy scatter (scatter mode 3):
  * 2, 3 or 4 steps of the row tile in flight per CTA; 0 (default) =
  * automatic, per launch the most resident CTAs per SM given the
- * accumulator's shared memory, then the most stages that keep that count.
+ * accumulator's shared memory, and the fewest stages at that count.
  * Results are bitwise identical for every count. */
 fea_status fea_mesh_set_scatter_stages(fea_mesh* mesh, int32_t stages);
 
@@ -175,8 +175,8 @@ fea_status fea_mesh_set_scatter_stages(fea_mesh* mesh, int32_t stages);
  * by the handle, concurrent with the matrix kernel (joined back to
  * `stream`); 3 = one kernel whose blocks hold matrix warps and load warps of
  * the same elements (FP64; the mixed path takes 0); -1 (default) =
- * automatic, currently 0 everywhere (the fastest measured).  Results are
- * bitwise identical for every mode. */
+ * automatic: 3 for FP64 P2 with the sine load, 0 elsewhere (the fastest
+ * measured).  Results are bitwise identical for every mode. */
 fea_status fea_mesh_set_load_split(fea_mesh* mesh, int32_t mode);
 
 /* Release the handle and everything it owns.  Synchronises the device. */
@@ -309,11 +309,12 @@ fea_status fea_batch_assemble(fea_batch* batch, void* stream);
 
 /* Autotune the batch's launch: times candidate (elements per work item,
  * P2 element-kernel CTAs) pairs on the device, then, per order, the element
- * kernel's register variant (the compiler's register count, or capped for
- * the single-mesh kernel's residency) with its CTA count; keeps the fastest
- * and rebuilds the graph.  params (may be NULL) receives int32_t[6]: the
+ * kernel's variant with its CTA count; keeps the fastest and rebuilds the
+ * graph.  params (may be NULL) receives int32_t[6]: the
  * chosen elements per item, P2 and P1 element-kernel CTAs, the scatter CTA
- * count (one per row tile), and the P2 and P1 register variants (0 or 1).
+ * count (one per row tile), and the P2 and P1 element-kernel variants (0: the
+ * compiler's register count; 1: capped for the single-mesh residency; 2, P2
+ * with the sine load only: matrix warps and load warps in one CTA).
  * Synchronises; overwrites the bound outputs. */
 fea_status fea_batch_tune(fea_batch* batch, void* stream, int32_t* params);
 

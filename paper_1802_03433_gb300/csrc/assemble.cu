@@ -122,10 +122,13 @@ fea_status assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* co, con
     A.e0 = 0;
     A.e1 = E;
     if (m->profile) FEA_CUDA(cudaEventRecord(m->ev[0], s));
-    // the matrix part is FP64-bound and the load part runs mostly on the
-    // integer pipes; measured on P2 64^3 and P1 96^3, one fused kernel is
-    // still the fastest launch (the split modes stay selectable)
-    const int split_mode = m->load_split >= 0 ? m->load_split : 0;
+    // automatic: matrix warps and load warps in one kernel for the FP64 P2 sine
+    // load (its sines run on the integer pipes beside the matrix's FP64 work:
+    // 0.80 against 0.85 ms fused at 64^3); the fused kernel elsewhere (P1: 0.95
+    // against 1.09 ms at 96^3)
+    const int split_mode = m->load_split >= 0 ? m->load_split
+                           : (order == 2 && load == FEA_LOAD_SINPROD && !mixed) ? 3
+                                                                                  : 0;
     const bool split = split_mode > 0 && load != FEA_LOAD_NONE && form->kind != FEA_ELASTICITY &&
                        !(split_mode == 3 && mixed);
     if (!split) {

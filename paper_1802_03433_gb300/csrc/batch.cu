@@ -54,7 +54,9 @@ constexpr int BT = 128;
 // Each kernel is built twice: with the compiler's register count (variant 0;
 // P2 with the sine load: 180, two resident CTAs per SM) and capped to keep
 // the residency of the single-mesh kernel (variant 1: three CTAs per SM for
-// P2, six for P1, at the price of a few spilled bytes); the autotuner picks.
+// P2, six for P1, at the price of a few spilled bytes).  P2 with the sine
+// load has a third form, k_batch_elem_roles (variant 2).  The autotuner
+// picks.
 template <int ORDER, int VARIANT>
 constexpr int batch_elem_min_blocks() { return VARIANT == 0 ? 1 : ORDER == 2 ? 3 : 6; }
 
@@ -124,7 +126,28 @@ GatherKernel tiled_kernel(int stages) {
 
 using ElemKernel = void (*)(const BMesh*, const BItem*, int);
 
-constexpr int ELEM_VARIANTS = 2;
+// Matrix warps and load warps (elem_roles_body) for the sine load: each item's
+// elements are taken twice, by the CTA's first BT threads for the local matrix
+// and by the next BT for the local load (variant 2, sine loads only).
+template <int ORDER, int LOAD, int NP>
+__global__ void __launch_bounds__(2 * BT, 2) k_batch_elem_roles(const BMesh* __restrict__ M,
+                                                              const BItem* __restrict__ items, int nitems) {
+  const bool matrix = threadIdx.x < BT;
+  const int lane = threadIdx.x % BT;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const BItem w = items[it];
+    const BMesh& m = M[w.mesh];
+    const int64_t end = (int64_t)w.first + w.count;
+    if (m.mass) {
+      for (int64_t e = w.first + lane; e < end; e += BT) elem_roles_body<ORDER, true, LOAD, NP>(m.el, e, matrix);
+    } else {
+      for (int64_t e = w.first + lane; e < end; e += BT) elem_roles_body<ORDER, false, LOAD, NP>(m.el, e, matrix);
+    }
+  }
+}
+
+constexpr int ELEM_VARIANTS = 3;
+inline int variant_threads(int v) { return v == 2 ? 2 * BT : BT; }
 
 template <int ORDER, int NP, int VARIANT>
 ElemKernel elem_kernel_for(int load) {
@@ -136,11 +159,16 @@ template <int ORDER, int NP>
 void elem_kernels_for(int load, ElemKernel ek[ELEM_VARIANTS]) {
   ek[0] = elem_kernel_for<ORDER, NP, 0>(load);
   ek[1] = elem_kernel_for<ORDER, NP, 1>(load);
+  // the roles kernel only where there is a sine load to split off (P2)
+  ek[2] = nullptr;
+  if constexpr (ORDER == 2)
+    if (load == LOAD_SIN) ek[2] = k_batch_elem_roles<ORDER, LOAD_SIN, NP>;
 }
 
-// Element kernels of the supported (P1, P2) rules, indexed by order and variant.
+// Element kernels of the supported (P1, P2) rules, indexed by order and variant
+// (NULL where a variant does not apply).
 bool pick_elem_kernels(int load, int np1, int np2, ElemKernel ek[3][ELEM_VARIANTS]) {
-  ek[0][0] = ek[0][1] = nullptr;
+  for (int v = 0; v < ELEM_VARIANTS; ++v) ek[0][v] = nullptr;
   if (np1 == 4) elem_kernels_for<1, 4>(load, ek[1]);
   else if (np1 == 11) elem_kernels_for<1, 11>(load, ek[1]);
   else return false;
@@ -244,7 +272,8 @@ fea_status launch_phases(fea_batch* b, cudaStream_t s) {
     const int e_first = order == 2 ? 0 : b->ecount[2];
     if (b->ecount[order] > 0) {
       const int grid = b->elem_grid[order] > 0 ? b->elem_grid[order] : b->ecount[order];
-      b->ek[order][b->variant[order]]<<<grid, BT, 0, st>>>(b->d_mesh, b->d_eitems + e_first, b->ecount[order]);
+      const int v = b->variant[order];
+      b->ek[order][v]<<<grid, variant_threads(v), 0, st>>>(b->d_mesh, b->d_eitems + e_first, b->ecount[order]);
     }
     for (int g = gather_group(order, 0), ge = g + 3; g < ge; ++g) {
       if (b->gcount[g] > 0)
@@ -448,7 +477,8 @@ fea_status fea_batch_create(fea_mesh* const* meshes, int32_t n, const fea_form* 
     // persistent grids: every CTA of each element kernel resident at once
     for (int o = 1; o <= 2 && ea == cudaSuccess; ++o) {
       int per_sm = 0;
-      ea = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b->ek[o][b->variant[o]], BT, 0);
+      ea = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b->ek[o][b->variant[o]],
+                                                         variant_threads(b->variant[o]), 0);
       b->elem_grid[o] = std::max(1, per_sm) * b->sms;
     }
     if (ea != cudaSuccess) {
@@ -557,6 +587,7 @@ fea_status fea_batch_tune(fea_batch* b, void* stream, int32_t* params) {
   }
   for (int order = 2; order >= 1 && st == FEA_OK; --order) {
     for (int v = 0; v < ELEM_VARIANTS && st == FEA_OK; ++v) {
+      if (!b->ek[order][v]) continue;
       b->variant[order] = v;
       for (int g : egrid) {
         b->elem_grid[order] = g * b->sms;

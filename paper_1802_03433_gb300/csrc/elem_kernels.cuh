@@ -201,11 +201,11 @@ __global__ void __launch_bounds__(ELEM_T) k_elem_load(ElemArgs A) {
 // matrices of ELEM_T elements (FP64-bound) and the other ELEM_T threads their
 // loads (integer-pipe sines), so both kinds of work share every SM.  The
 // role is uniform per warp; the results are those of the separate kernels.
+// Element e in one of the two roles: the local matrix (matrix warps) or the
+// local load (load warps).
 template <int ORDER, bool MASS, int LOAD, int NPTS>
-__global__ void __launch_bounds__(2 * ELEM_T) k_elem_roles(ElemArgs A) {
-  const int64_t e = A.e0 + (int64_t)blockIdx.x * ELEM_T + (threadIdx.x % ELEM_T);
-  if (e >= A.e1) return;
-  if (threadIdx.x < ELEM_T) {
+__device__ __forceinline__ void elem_roles_body(const ElemArgs& A, int64_t e, bool matrix) {
+  if (matrix) {
     elem_scalar_body<ORDER, MASS, LOAD_NONE, 1, double>(A, e);
   } else {
     constexpr int NB = ORDER == 1 ? 4 : 10;
@@ -219,6 +219,13 @@ __global__ void __launch_bounds__(2 * ELEM_T) k_elem_roles(ElemArgs A) {
 #pragma unroll
     for (int a = 0; a < NB; ++a) Fl[__ldg(A.ipos + a * A.E + e)] = amp * Fs[a];
   }
+}
+
+template <int ORDER, bool MASS, int LOAD, int NPTS>
+__global__ void __launch_bounds__(2 * ELEM_T) k_elem_roles(ElemArgs A) {
+  const int64_t e = A.e0 + (int64_t)blockIdx.x * ELEM_T + (threadIdx.x % ELEM_T);
+  if (e >= A.e1) return;
+  elem_roles_body<ORDER, MASS, LOAD, NPTS>(A, e, threadIdx.x < ELEM_T);
 }
 
 // Deterministic-path output of the elasticity kernel: local rows in

@@ -388,11 +388,24 @@ __device__ __forceinline__ long long sinpi_q62_fx(long long t, int s) {
   const long long mag = sinpi_q62_mag(ra);
   return pf ? -mag : mag;
 }
-static __device__ __noinline__ long long sinpi_q62_fx_call(long long t, int s) { return sinpi_q62_fx(t, s); }
+// Four at once: four independent dependency chains (the polynomial is a
+// chain of nine 64-bit high products) that the scheduler interleaves.  The
+// P2 kernels call it out of line (instruction-cache footprint), so a call
+// carries four chains rather than one.
+struct Q4 {
+  long long v[4];
+};
+__device__ __forceinline__ Q4 sinpi_q62_fx4(const Q4& t, int s) {
+  Q4 r;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) r.v[k] = sinpi_q62_fx(t.v[k], s);
+  return r;
+}
+static __device__ __noinline__ Q4 sinpi_q62_fx4_call(Q4 t, int s) { return sinpi_q62_fx4(t, s); }
 template <bool OUTLINE>
-__device__ __forceinline__ long long sinpi_q62_fx_sel(long long t, int s) {
-  if constexpr (OUTLINE) return sinpi_q62_fx_call(t, s);
-  else return sinpi_q62_fx(t, s);
+__device__ __forceinline__ Q4 sinpi_q62_fx4_sel(const Q4& t, int s) {
+  if constexpr (OUTLINE) return sinpi_q62_fx4_call(t, s);
+  else return sinpi_q62_fx4(t, s);
 }
 
 // ---- quadrature-point coordinates in fixed point (the sine load in FP64)
@@ -778,9 +791,14 @@ __device__ __forceinline__ void shape_load(const R Xr[4][3], R Fs[ORDER == 1 ? 4
       long long xq[NPTS];
       quad_coord_fx<NPTS>(v, s, xq);
 #pragma unroll
-      for (int q = 0; q < NPTS; ++q) {
-        const long long t = sinpi_q62_fx_sel<OUTLINE>(xq[q], s);
-        sq[q] = c == 0 ? t : mul_q62(sq[q], t);
+      for (int q0 = 0; q0 < NPTS; q0 += 4) {
+        Q4 in;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) in.v[k] = q0 + k < NPTS ? xq[q0 + k] : 0;
+        const Q4 o = sinpi_q62_fx4_sel<OUTLINE>(in, s);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (q0 + k < NPTS) sq[q0 + k] = c == 0 ? o.v[k] : mul_q62(sq[q0 + k], o.v[k]);
       }
     }
     long long F[NB];

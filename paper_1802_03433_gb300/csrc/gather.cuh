@@ -26,28 +26,77 @@
 
 namespace fea {
 
-// Exact float -> double conversion of a whole local row with integer
-// operations (keeps the widening off the scarce FP64 pipe): the IEEE-754
-// binary32 fields move into binary64 position with the exponent re-biased by
-// 1023 - 127 = 896; +-0 keeps only its sign.  A row holding a subnormal, an
-// infinity or a NaN (never produced by finite inputs of normal size) takes
-// the hardware conversion instead.
+// Exact float -> double conversion with integer operations only (the FP64
+// pipe is the scarce one on this part, and a hardware conversion kept as a
+// fallback branch is if-converted by the compiler into an unconditional one):
+// the IEEE-754 binary32 fields move into binary64 position; the exponent of a
+// normal number is re-biased by 1023 - 127 = 896, infinities and NaNs
+// (payload kept) get 2047, a subnormal is normalised from the position p of
+// its top mantissa bit (value m 2^-149 = 1.f 2^(p - 149)), and +-0 keeps only
+// its sign.  Bitwise equal to the hardware conversion for every input.
+__device__ __forceinline__ double widen_bits(float x) {
+  const uint32_t u = __float_as_uint(x);
+  const uint32_t sgn = u & 0x80000000u, ex = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+  uint32_t hi, lo;
+  if (ex - 1u < 0xFEu) {  // normal
+    hi = sgn | ((ex + 896u) << 20) | (m >> 3);
+    lo = m << 29;
+  } else if (ex == 0xFFu) {  // infinity, NaN
+    hi = sgn | (2047u << 20) | (m >> 3);
+    lo = m << 29;
+  } else {  // zero, subnormal
+    const uint32_t p = 31u - static_cast<uint32_t>(__clz(static_cast<int>(m | 1u)));
+    const unsigned long long f = (static_cast<unsigned long long>(m) << (52u - p)) & 0xFFFFFFFFFFFFFull;
+    hi = m ? (sgn | ((p + 874u) << 20) | static_cast<uint32_t>(f >> 32)) : sgn;
+    lo = m ? static_cast<uint32_t>(f) : 0u;
+  }
+  return __hiloint2double(static_cast<int>(hi), static_cast<int>(lo));
+}
+// Normal numbers and zeros only: the sign, exponent and top mantissa bits
+// shifted into place with the exponent re-biased by one add (896 << 20), the
+// low mantissa bits into the low word; +-0 keeps only its sign.
+__device__ __forceinline__ double widen_fast(uint32_t u) {
+  const uint32_t mag = u & 0x7FFFFFFFu;
+  const uint32_t hi = mag ? (((mag >> 3) + 0x38000000u) | (u & 0x80000000u)) : u;
+  return __hiloint2double(static_cast<int>(hi), static_cast<int>(u << 29));
+}
+// Subnormal, infinite or NaN (exponent field 0 with a nonzero mantissa, or 255).
+__device__ __forceinline__ bool widen_special(uint32_t u) {
+  return (((u + 0x00800000u) & 0x7F800000u) <= 0x00800000u) && (u & 0x7FFFFFFFu) != 0u;
+}
+template <int NL>
+struct FRow {
+  float v[NL];
+};
+template <int NL>
+struct DRow {
+  double v[NL];
+};
+// Out of line, so that the rare exact path is a real branch (by value: the
+// row stays in registers).
+template <int NL>
+static __device__ __noinline__ DRow<NL> widen_row_exact(FRow<NL> r) {
+  DRow<NL> o;
+#pragma unroll
+  for (int k = 0; k < NL; ++k) o.v[k] = widen_bits(r.v[k]);
+  return o;
+}
 template <int NL>
 __device__ __forceinline__ void widen_row(const float* v, double* out) {
   bool special = false;
 #pragma unroll
   for (int k = 0; k < NL; ++k) {
     const uint32_t u = __float_as_uint(v[k]);
-    const uint32_t ex = (u >> 23) & 0xFFu;
-    const bool zero = (u & 0x7FFFFFFFu) == 0u;
-    special |= !zero && (ex - 1u >= 0xFEu);
-    uint32_t hi = (u & 0x80000000u) | ((ex + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
-    hi = zero ? u : hi;
-    out[k] = __hiloint2double((int)hi, (int)(u << 29));
+    out[k] = widen_fast(u);
+    special |= widen_special(u);
   }
   if (special) {
+    FRow<NL> r;
 #pragma unroll
-    for (int k = 0; k < NL; ++k) out[k] = (double)v[k];
+    for (int k = 0; k < NL; ++k) r.v[k] = v[k];
+    const DRow<NL> o = widen_row_exact<NL>(r);
+#pragma unroll
+    for (int k = 0; k < NL; ++k) out[k] = o.v[k];
   }
 }
 template <int NL>

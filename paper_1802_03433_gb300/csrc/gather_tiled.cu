@@ -58,7 +58,7 @@ int tiled_stages_auto(int nb, bool mixed, int rows, int64_t span_cap) {
                                             : tiled_smem<10, double>(rows, span_cap, st));
     if (smem > 227 * 1024) break;
     const int ctas = std::min<int>(per_sm / (int)(smem + reserved), 2048 / std::max(rows, 32));
-    if (ctas >= best_ctas) {  // stages only where they cost no resident CTA
+    if (ctas > best_ctas) {  // ties keep the fewer stages
       best = st;
       best_ctas = ctas;
     }

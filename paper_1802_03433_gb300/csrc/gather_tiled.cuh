@@ -286,11 +286,13 @@ fea_status launch_gather_tiled(int nb, bool mixed, const TiledArgs& G, cudaStrea
                                int64_t ntiles, int stages = 0);
 
 // The stage count for a CTA whose accumulator holds span_cap doubles: the
-// most resident CTAs per SM first, then the most stages that keep that count.
+// most resident CTAs per SM, and of those counts the fewest stages.
 // (Measured on the P2 diffusion + mass scatter: two stages and three CTAs per
 // SM beat three stages and two CTAs by 14%, four stages and two CTAs lose a
-// further 15%: the CTAs' warps hide the shared-memory adds and the pipeline
-// fill of the short tiles, more stages do not.)
+// further 15%; at an equal CTA count three stages gain nothing over two and
+// four lose 20% (FP32 rows, long-row tiles): the CTAs' warps hide the
+// shared-memory adds and the pipeline fill of the short tiles, deeper rings
+// do not.)
 int tiled_stages_auto(int nb, bool mixed, int rows, int64_t span_cap);
 
 // Whether a scalar pattern takes the bulk-copy scatter: its tiled layout is

@@ -120,7 +120,8 @@ struct fea_mesh {
   int tiled_stages = 0;     // bulk-copy scatter stages per CTA (2..4), 0 automatic
   int load_split = -1;      // scalar forms: 0 fused element kernel; 1 matrix kernel then load kernel;
                             // 2 load kernel on the side stream, concurrent with the matrix kernel;
-                            // 3 one kernel with matrix warps and load warps; -1 automatic (0)
+                            // 3 one kernel with matrix warps and load warps; -1 automatic (3 for
+                            // FP64 P2 with the sine load, else 0)
   bool profile = false;     // record phase events in fea_assemble
   bool profiled = false;    // events of a call are pending
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
