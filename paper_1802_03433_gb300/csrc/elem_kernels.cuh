@@ -77,10 +77,15 @@ __device__ __forceinline__ void elem_scalar_body(const ElemArgs& A, int64_t e) {
   R Gr[4][3];
   grads<R>(g, Gr);
   R Kl[NB][NB];
+  // Gram matrix G_ij = s grad lambda_i . grad lambda_j; FP64 P1 with a mass
+  // term keeps it unscaled and applies s in the FMA that adds the mass
+  const R s = R(kap * grad_scale<R>(adet) * (ORDER == 2 ? 1.0 / 20.0 : 1.0));
+  constexpr bool SCALE_IN_FMA = ORDER == 1 && MASS && IsDouble<R>::value;
+  R G[4][4];
+  gram<R>(Gr, SCALE_IN_FMA ? R(1) : s, G);
 
   if constexpr (ORDER == 1) {
     // K_ab = kappa |T| grad lambda_a . grad lambda_b ; M_ab = |T| (1 + delta_ab) / 20
-    const R s = R(kap * grad_scale<R>(adet));
     [[maybe_unused]] R t1 = R(0), t2 = R(0);  // mass entries |T| / 20 and 2 |T| / 20
     if constexpr (MASS) {
       t1 = R(A.mass * adet * (1.0 / 120.0));
@@ -89,22 +94,15 @@ __device__ __forceinline__ void elem_scalar_body(const ElemArgs& A, int64_t e) {
     static_for<10>([&](auto K) {
       constexpr int a = upper_a(4, K), b = upper_b(4, K);
       R v;
-      if constexpr (MASS && IsDouble<R>::value) v = fma(s, dot3(Gr[a], Gr[b]), a == b ? t2 : t1);
-      else if constexpr (MASS) v = fma(t1, R(a == b ? 2 : 1), s * dot3(Gr[a], Gr[b]));
-      else v = s * dot3(Gr[a], Gr[b]);
+      if constexpr (SCALE_IN_FMA) v = fma(s, G[a][b], a == b ? t2 : t1);
+      else if constexpr (MASS) v = G[a][b] + (a == b ? t2 : t1);
+      else v = G[a][b];
       Kl[a][b] = v;
       Kl[b][a] = v;
     });
   } else {
     // K_ab = kappa |T| / 20 sum_t num_t (grad lambda_i . grad lambda_j);
     // M_ab = |T| / 420 * m420_ab
-    const R s = R(kap * grad_scale<R>(adet) * (1.0 / 20.0));
-    R G[4][4];  // kappa |T| / 20 * grad lambda_i . grad lambda_j
-    static_for<10>([&](auto K) {
-      constexpr int i = upper_a(4, K), j = upper_b(4, K);
-      G[i][j] = s * dot3(Gr[i], Gr[j]);
-      if constexpr (i != j) G[j][i] = G[i][j];
-    });
     // FP64: |T| / 420 times each of the seven values of the P2 mass pattern
     // starts the entry's FMA chain (one FP64 operation less per entry); the
     // FP32 products of the mixed path add the mass term last

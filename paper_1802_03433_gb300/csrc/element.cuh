@@ -546,6 +546,37 @@ __device__ __forceinline__ void grads(const Geo& g, R G[4][3]) {
   }
 }
 
+// G_ij = s grad_i . grad_j (symmetric).  FP64: the products of rows 1..3 only;
+// row 0 from the zero row sums (grad_0 = -(grad_1 + grad_2 + grad_3), so
+// G_0j = -(G_1j + G_2j + G_3j)): two adds instead of a dot product and a
+// scale, and grad_0 itself is never formed.  FP32: every product.
+template <typename R>
+__device__ __forceinline__ void gram(const R Gr[4][3], R s, R G[4][4]) {
+  if constexpr (IsDouble<R>::value) {
+#pragma unroll
+    for (int i = 1; i < 4; ++i)
+#pragma unroll
+      for (int j = i; j < 4; ++j) {
+        G[i][j] = s * dot3(Gr[i], Gr[j]);
+        G[j][i] = G[i][j];
+      }
+#pragma unroll
+    for (int j = 1; j < 4; ++j) {
+      G[0][j] = -((G[1][j] + G[2][j]) + G[3][j]);
+      G[j][0] = G[0][j];
+    }
+    G[0][0] = -((G[0][1] + G[0][2]) + G[0][3]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = i; j < 4; ++j) {
+        G[i][j] = s * dot3(Gr[i], Gr[j]);
+        G[j][i] = G[i][j];
+      }
+  }
+}
+
 // Scale that turns products of grads<R> into |T| grad . grad:
 // FP64: |T| / det^2 = 1 / (6 |det|); mixed: |T| = |det| / 6.
 template <typename R>
