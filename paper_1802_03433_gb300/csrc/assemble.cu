@@ -117,24 +117,25 @@ fea_status assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* co, con
   G.values = values;
   G.rhs = rhs;
 
+  // automatic: matrix warps and load warps in one kernel for the FP64 P2 sine
+  // load (its sines run on the integer pipes beside the matrix's FP64 work:
+  // 0.80 against 0.85 ms fused at 64^3); the fused kernel elsewhere (P1: 0.95
+  // against 1.09 ms at 96^3)
+  const int split_mode = m->load_split >= 0 ? m->load_split
+                         : (order == 2 && load == FEA_LOAD_SINPROD && !mixed) ? 3
+                                                                                : 0;
+  const bool split = split_mode > 0 && load != FEA_LOAD_NONE && form->kind != FEA_ELASTICITY &&
+                     !(split_mode == 3 && mixed);
+  const bool mass = form->kind == FEA_DIFFUSION_MASS && form->mass_coef != 0.0;
+
   if (sequential) {
     // one element launch, then one scatter launch
     A.e0 = 0;
     A.e1 = E;
     if (m->profile) FEA_CUDA(cudaEventRecord(m->ev[0], s));
-    // automatic: matrix warps and load warps in one kernel for the FP64 P2 sine
-    // load (its sines run on the integer pipes beside the matrix's FP64 work:
-    // 0.80 against 0.85 ms fused at 64^3); the fused kernel elsewhere (P1: 0.95
-    // against 1.09 ms at 96^3)
-    const int split_mode = m->load_split >= 0 ? m->load_split
-                           : (order == 2 && load == FEA_LOAD_SINPROD && !mixed) ? 3
-                                                                                  : 0;
-    const bool split = split_mode > 0 && load != FEA_LOAD_NONE && form->kind != FEA_ELASTICITY &&
-                       !(split_mode == 3 && mixed);
     if (!split) {
       FEA_TRY(launch_elements(form, A, load, q->npts, prec, s));
     } else if (split_mode == 3) {
-      const bool mass = form->kind == FEA_DIFFUSION_MASS && form->mass_coef != 0.0;
       FEA_TRY(launch_elem_roles(order, mass, A, load, q->npts, s));
     } else if (split_mode == 1) {
       FEA_TRY(launch_elements(form, A, FEA_LOAD_NONE, q->npts, prec, s));
@@ -184,7 +185,10 @@ fea_status assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* co, con
     for (int k = 0; k < stages; ++k) {
       A.e0 = std::min<int64_t>(E, (int64_t)k * P->chunk);
       A.e1 = std::min<int64_t>(E, (int64_t)(k + 1) * P->chunk);
-      FEA_TRY(launch_elements(form, A, load, q->npts, prec, s));
+      // the chunks take the fused kernel, or the matrix/load-warp kernel when
+      // that is the launch mode (the other split modes apply to one launch)
+      if (split && split_mode == 3) FEA_TRY(launch_elem_roles(order, mass, A, load, q->npts, s));
+      else FEA_TRY(launch_elements(form, A, load, q->npts, prec, s));
       FEA_CUDA(cudaEventRecord(m->chunk_ev[k], s));
       FEA_CUDA(cudaStreamWaitEvent(m->side, m->chunk_ev[k], 0));
       const int64_t t0 = P->stage_ptr[k], t1 = P->stage_ptr[k + 1];
