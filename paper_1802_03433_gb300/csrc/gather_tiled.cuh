@@ -31,7 +31,7 @@
 
 namespace fea {
 
-constexpr int TILED_STAGES = 3;      // default stage count
+constexpr int TILED_STAGES = 2;      // default stage count (tiled_stages_auto)
 constexpr int TILED_MAX_STAGES = 4;
 constexpr uint32_t TILED_WAIT_LIMIT = 1u << 22;
 
