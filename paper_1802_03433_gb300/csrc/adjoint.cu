@@ -119,8 +119,8 @@ __global__ void __launch_bounds__(ADJ_T) k_adjoint(AdjArgs A) {
       });
     }
   }
-  // S = sum_{i<=j} Hc_ij g_i . g_j;  dS/dg_a = sum_j Hsym_aj g_j (Hsym = Hc + Hc^T)
-  double S = 0.0;
+  // dS/dg_a = sum_j Hsym_aj g_j (Hsym = Hc + Hc^T), and, S being a quadratic
+  // form in the g_a, S = sum_{i<=j} Hc_ij g_i . g_j = 1/2 sum_a g_a . dS_a
   double dS[4][3];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -129,17 +129,20 @@ __global__ void __launch_bounds__(ADJ_T) k_adjoint(AdjArgs A) {
   static_for<10>([&](auto K) {
     constexpr int i = upper_a(4, K), j = upper_b(4, K);
     const double h = Hc[i][j];
-    S = fma(h, g[i][0] * g[j][0] + g[i][1] * g[j][1] + g[i][2] * g[j][2], S);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       if constexpr (i == j) {
-        dS[i][k] = fma(2.0 * h, g[i][k], dS[i][k]);
+        dS[i][k] = fma(h + h, g[i][k], dS[i][k]);
       } else {
         dS[i][k] = fma(h, g[j][k], dS[i][k]);
         dS[j][k] = fma(h, g[i][k], dS[j][k]);
       }
     }
   });
+  double S2 = 0.0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) S2 = fma(g[a][0], dS[a][0], fma(g[a][1], dS[a][1], fma(g[a][2], dS[a][2], S2)));
+  const double S = 0.5 * S2;
   // Q = sum_{i=1..3} g_i (dS_i - dS_0)^T
   double Q[3][3];
 #pragma unroll
@@ -164,6 +167,16 @@ __global__ void __launch_bounds__(ADJ_T) k_adjoint(AdjArgs A) {
       double gfl[NB];
 #pragma unroll
       for (int a = 0; a < NB; ++a) gfl[a] = __ldg(A.gf + __ldg(A.edof + a * A.E + e));
+      [[maybe_unused]] int sh[3];
+      [[maybe_unused]] long long xfx[3][NPTS];
+      if constexpr (LOAD == LOAD_SIN) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const double v[4] = {X[0][k], X[1][k], X[2][k], X[3][k]};
+          sh[k] = fx_shift(v);
+          quad_coord_fx<NPTS>(v, sh[k], xfx[k]);
+        }
+      }
       static_for<NPTS>([&](auto Qi) {
         constexpr int q = Qi;
         double Phi = 0.0;
@@ -174,6 +187,28 @@ __global__ void __launch_bounds__(ADJ_T) k_adjoint(AdjArgs A) {
         const double wPhi = weight(NPTS, q) * Phi;
         if constexpr (LOAD == LOAD_CONST) {
           sF = fma(A.fp0, wPhi, sF);
+        } else if constexpr (LOAD == LOAD_SIN) {
+          // the points, sin(pi x_k), cos(pi x_k) = sin(pi (x_k + 1/2)) and the
+          // products of f and grad f in fixed point (as the forward load);
+          // four conversions, then the w_q Phi_q weights in FP64
+          // lanes: sin x, sin y, sin z, cos x | cos y, cos z (each with its coordinate's shift)
+          const Q4 in0 = {{xfx[0][q], xfx[1][q], xfx[2][q], xfx[0][q] + (1LL << (60 - sh[0]))}};
+          const Q4 in1 = {{xfx[1][q] + (1LL << (60 - sh[1])), xfx[2][q] + (1LL << (60 - sh[2])), 0, 0}};
+          const Q4 o0 = sinpi_q62_fx4v_call(in0, S4{{sh[0], sh[1], sh[2], sh[0]}});
+          const Q4 o1 = sinpi_q62_fx4v_call(in1, S4{{sh[1], sh[2], 0, 0}});
+          const long long sn0 = o0.v[0], sn1 = o0.v[1], sn2 = o0.v[2], cs0 = o0.v[3], cs1 = o1.v[0], cs2 = o1.v[1];
+          const long long p01 = mul_q62(sn0, sn1), p12 = mul_q62(sn1, sn2);
+          const double f = q62_to_double(mul_q62(p01, sn2));
+          const double d0 = q62_to_double(mul_q62(cs0, p12));
+          const double d1 = q62_to_double(mul_q62(mul_q62(sn0, cs1), sn2));
+          const double d2 = q62_to_double(mul_q62(p01, cs2));
+          sF = fma(f, wPhi, sF);  // times fp0 below
+          const double pw = A.fp0 * 3.14159265358979323846 * wPhi;
+          const double df[3] = {pw * d0, pw * d1, pw * d2};
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) lg[c][k] = fma(bary(NPTS, q, c), df[k], lg[c][k]);
         } else {
           double xq[3], sn[3], cs[3];
 #pragma unroll
@@ -198,6 +233,7 @@ __global__ void __launch_bounds__(ADJ_T) k_adjoint(AdjArgs A) {
     }
   }
 
+  if constexpr (LOAD == LOAD_SIN) sF *= A.fp0;
   if (A.gk) A.gk[e] = vol * S;
   const double sigma = kap * S + (MASS ? A.mass * sM : 0.0) + sF;
 #pragma unroll

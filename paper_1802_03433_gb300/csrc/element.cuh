@@ -407,6 +407,16 @@ __device__ __forceinline__ Q4 sinpi_q62_fx4_sel(const Q4& t, int s) {
   if constexpr (OUTLINE) return sinpi_q62_fx4_call(t, s);
   else return sinpi_q62_fx4(t, s);
 }
+// The same with one shift per lane (arguments from different coordinates).
+struct S4 {
+  int v[4];
+};
+static __device__ __noinline__ Q4 sinpi_q62_fx4v_call(Q4 t, S4 s) {
+  Q4 r;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) r.v[k] = sinpi_q62_fx(t.v[k], s.v[k]);
+  return r;
+}
 
 // ---- quadrature-point coordinates in fixed point (the sine load in FP64)
 // A coordinate c of the four vertices, v_a, goes to t_a = round(v_a 2^(61 - s))
@@ -482,6 +492,13 @@ __host__ __device__ constexpr long long q62(double c) { return static_cast<long 
 __device__ __forceinline__ double q59_to_double(long long v) {
   const double d = __ll2double_rn(v);
   return v == 0 ? 0.0 : __longlong_as_double(__double_as_longlong(d) - (59LL << 52));
+}
+
+// v 2^-62 as a double (one correctly rounded conversion, then an exact
+// exponent shift; |v| >= 2^-960 2^62 gives a normal result).
+__device__ __forceinline__ double q62_to_double(long long v) {
+  const double d = __ll2double_rn(v);
+  return v == 0 ? 0.0 : __longlong_as_double(__double_as_longlong(d) - (62LL << 52));
 }
 
 // One out-of-line copy of sinpi_fx for kernels with many sines: 33 inlined
