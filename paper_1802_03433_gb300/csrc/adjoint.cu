@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(ADJ_T) k_adjoint(AdjArgs A) {
 
   // ---- load terms
   double sF = 0.0;
-  double lg[4][3];  // sum_q w_q Phi_q lambda_c(x_q) grad f(x_q), per vertex c
+  double lg[4][3];  // |T| sum_q w_q Phi_q lambda_c(x_q) grad f(x_q), per vertex c
 #pragma unroll
   for (int c = 0; c < 4; ++c)
 #pragma unroll
@@ -169,6 +169,9 @@ __global__ void __launch_bounds__(ADJ_T) k_adjoint(AdjArgs A) {
       for (int a = 0; a < NB; ++a) gfl[a] = __ldg(A.gf + __ldg(A.edof + a * A.E + e));
       [[maybe_unused]] int sh[3];
       [[maybe_unused]] long long xfx[3][NPTS];
+      [[maybe_unused]] double u[3][NPTS];  // sine load: |T| pi p0 Phi_q d f/d x_k at point q (unweighted)
+      [[maybe_unused]] const double vpf = vol * A.fp0 * 3.14159265358979323846;
+      [[maybe_unused]] double uf[NPTS];    // sine load: Phi_q f_q / p0
       if constexpr (LOAD == LOAD_SIN) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -184,13 +187,12 @@ __global__ void __launch_bounds__(ADJ_T) k_adjoint(AdjArgs A) {
           constexpr double ph = phi_at(ORDER, NPTS, q, Aa);
           Phi = fma(ph, gfl[Aa], Phi);
         });
-        const double wPhi = weight(NPTS, q) * Phi;
         if constexpr (LOAD == LOAD_CONST) {
-          sF = fma(A.fp0, wPhi, sF);
-        } else if constexpr (LOAD == LOAD_SIN) {
+          sF = fma(A.fp0, weight(NPTS, q) * Phi, sF);
+        } else {
           // the points, sin(pi x_k), cos(pi x_k) = sin(pi (x_k + 1/2)) and the
           // products of f and grad f in fixed point (as the forward load);
-          // four conversions, then the w_q Phi_q weights in FP64
+          // four conversions, then the Phi_q factors in FP64
           // lanes: sin x, sin y, sin z, cos x | cos y, cos z (each with its coordinate's shift)
           const Q4 in0 = {{xfx[0][q], xfx[1][q], xfx[2][q], xfx[0][q] + (1LL << (60 - sh[0]))}};
           const Q4 in1 = {{xfx[1][q] + (1LL << (60 - sh[1])), xfx[2][q] + (1LL << (60 - sh[2])), 0, 0}};
@@ -202,47 +204,41 @@ __global__ void __launch_bounds__(ADJ_T) k_adjoint(AdjArgs A) {
           const double d0 = q62_to_double(mul_q62(cs0, p12));
           const double d1 = q62_to_double(mul_q62(mul_q62(sn0, cs1), sn2));
           const double d2 = q62_to_double(mul_q62(p01, cs2));
-          sF = fma(f, wPhi, sF);  // times fp0 below
-          const double pw = A.fp0 * 3.14159265358979323846 * wPhi;
-          const double df[3] = {pw * d0, pw * d1, pw * d2};
-#pragma unroll
-          for (int c = 0; c < 4; ++c)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) lg[c][k] = fma(bary(NPTS, q, c), df[k], lg[c][k]);
-        } else {
-          double xq[3], sn[3], cs[3];
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            double v = 0.0;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) v = fma(bary(NPTS, q, c), X[c][k], v);
-            xq[k] = v;
-            sn[k] = rsinpi<double, true>(v);        // sin(pi v), integer pipes, one out-of-line copy
-            cs[k] = rsinpi<double, true>(v + 0.5);  // cos(pi v)
-          }
-          const double f = A.fp0 * sn[0] * sn[1] * sn[2];
-          sF = fma(f, wPhi, sF);
-          const double pw = A.fp0 * 3.14159265358979323846 * wPhi;
-          const double df[3] = {pw * cs[0] * sn[1] * sn[2], pw * sn[0] * cs[1] * sn[2], pw * sn[0] * sn[1] * cs[2]};
-#pragma unroll
-          for (int c = 0; c < 4; ++c)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) lg[c][k] = fma(bary(NPTS, q, c), df[k], lg[c][k]);
+          uf[q] = Phi * f;
+          const double pPhi = vpf * Phi;
+          u[0][q] = pPhi * d0;
+          u[1][q] = pPhi * d1;
+          u[2][q] = pPhi * d2;
         }
       });
+      if constexpr (LOAD == LOAD_SIN) {
+        // lg_ck = sum_q w_q lambda_c(x_q) u_kq and sF = p0 sum_q w_q Phi_q f_q, by
+        // the rule's symmetry classes (rule_sum with the P1 basis: lambda_c)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          double col[4];
+          rule_sum<1, NPTS, double>(u[k], col);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) lg[c][k] = col[c];
+        }
+        static_for<NPTS>([&](auto Qi) { sF = fma(weight(NPTS, Qi), uf[Qi], sF); });
+      }
     }
   }
 
   if constexpr (LOAD == LOAD_SIN) sF *= A.fp0;
   if (A.gk) A.gk[e] = vol * S;
   const double sigma = kap * S + (MASS ? A.mass * sM : 0.0) + sF;
+  // |T| [sigma grad lambda_c - kappa Q grad lambda_c + lg_c], with |T| folded
+  // into sigma, kappa and (through vpf) lg
+  const double vs = vol * sigma, vk = -vol * kap;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     double d[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const double qg = Q[k][0] * g[c][0] + Q[k][1] * g[c][1] + Q[k][2] * g[c][2];
-      d[k] = vol * (sigma * g[c][k] - kap * qg + lg[c][k]);
+      const double qg = fma(Q[k][0], g[c][0], fma(Q[k][1], g[c][1], Q[k][2] * g[c][2]));
+      d[k] = fma(vs, g[c][k], fma(vk, qg, lg[c][k]));
     }
     st_v4(A.gxs + (int64_t)pos[c] * 4, d[0], d[1], d[2], 0.0);
   }
