@@ -283,6 +283,11 @@ __device__ __forceinline__ double sinpi_fp64(double x) {
 // 50-digit sin).  In the fast path |r| >= 2^-53, so the product's high word
 // is at least 2^8 and every shift below is by 9 to 61 bits.  Other arguments
 // (tiny, huge, zero, subnormal, infinite, NaN) take sinpi_fp64.
+// The FP64 polynomial out of line, for the rare arguments the fixed-point
+// paths hand over: inline, the compiler if-converts the branch and every call
+// pays its FP64 operations.
+static __device__ __noinline__ double sinpi_fp64_call(double x) { return sinpi_fp64(x); }
+
 constexpr long long SINPI_Q0 = 3622009729038561420LL;
 constexpr long long SINPI_Q1 = -5957967193751243029LL;
 constexpr long long SINPI_Q2 = 2940138961849612574LL;
@@ -296,7 +301,7 @@ constexpr long long SINPI_Q8 = 887499001982LL;
 __device__ __forceinline__ double sinpi_fx(double x) {
   const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
   const unsigned e = static_cast<unsigned>(b >> 52) & 0x7FFu;
-  if (e - 1013u > 60u) return sinpi_fp64(x);
+  if (e - 1013u > 60u) return sinpi_fp64_call(x);
   const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
   const unsigned sh = e - 1011u;  // 2 .. 62
   const unsigned long long f = m << sh;
@@ -356,7 +361,7 @@ __device__ __forceinline__ long long sinpi_q62_mag(unsigned long long ra) {
 __device__ __forceinline__ long long sinpi_q62(double x) {
   const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
   const unsigned e = static_cast<unsigned>(b >> 52) & 0x7FFu;
-  if (e - 1013u > 60u) return __double2ll_rn(sinpi_fp64(x) * 4611686018427387904.0);
+  if (e - 1013u > 60u) return __double2ll_rn(sinpi_fp64_call(x) * 4611686018427387904.0);
   const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
   const unsigned sh = e - 1011u;
   const unsigned long long f = m << sh;
