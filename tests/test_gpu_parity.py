@@ -330,3 +330,41 @@ def test_load_split_modes_bitwise_identical(torch_cuda, kind, n, prec):
             continue
         assert np.array_equal(g["vals"].view(np.uint64), ref["vals"].view(np.uint64)), mode
         assert np.array_equal(g["rhs"].view(np.uint64), ref["rhs"].view(np.uint64)), mode
+
+
+@pytest.mark.parametrize("kind,n", [("p1_kappa", 6), ("p2_diffmass", 5)])
+def test_sine_load_under_integer_translation(torch_cuda, kind, n):
+    """The sine load's quadrature points and sines run in fixed point with a
+    shift set by the coordinates' size.  Translating the mesh by integers
+    changes the load exactly: sin(pi (x + 2)) = sin(pi x) and
+    sin(pi (x + 1)) = -sin(pi x), so a shift by (2, -4, 6) leaves every load
+    value unchanged and a shift by (1, 2, -3) flips its sign twice (odd x and
+    z), i.e. leaves it unchanged too, while (1, 0, 0) and (-37, 64, 1000)
+    negate it (the last with a fixed-point shift set by |z| ~ 1000).  The
+    translated coordinates carry a few FP64 roundings, hence the tolerance.
+    The matrix does not depend on the translation at all."""
+    from common import vec_scaled_error
+    c = case(kind, n, seed=41)
+    ref = gpu_system(c)
+    for shift, sign in (((2.0, -4.0, 6.0), 1.0), ((1.0, 2.0, -3.0), 1.0), ((1.0, 0.0, 0.0), -1.0),
+                        ((-37.0, 64.0, 1000.0), -1.0)):
+        ct = dict(c)
+        ct["coords"] = c["coords"] + np.asarray(shift)[:, None]
+        g = gpu_system(ct)
+        assert vec_scaled_error(sign * ref["rhs"], g["rhs"]) <= 1e-12, shift
+        assert row_scaled_error(ref["rp"], ref["vals"], g["vals"]) <= 1e-12, shift
+
+
+@pytest.mark.parametrize("kind,n", [("p1_kappa", 5), ("p2_diffmass", 4)])
+def test_sine_load_small_offset_mesh_matches_oracle(torch_cuda, kind, n):
+    """A mesh of tiny elements away from the origin (the cube scaled by 1e-3
+    and moved to x = 0.3 + ..., y = -0.7 + ..., z = 12.25 + ...), where the
+    fixed-point shift of each coordinate is set by its offset (resolution
+    2^-56 for z): matrix and load against the oracle."""
+    c = case(kind, n, seed=43)
+    c = dict(c)
+    c["coords"] = c["coords"] * 1e-3 + np.array([0.3, -0.7, 12.25])[:, None]
+    g = gpu_system(c)
+    o = oracle_system(c)
+    assert row_scaled_error(o["rp"], o["vals"], g["vals"]) <= TOL_FP64
+    assert vec_scaled_error(o["rhs"], g["rhs"]) <= TOL_FP64
