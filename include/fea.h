@@ -344,6 +344,14 @@ fea_status fea_profile_last(fea_mesh* mesh, float* elem_ms, float* scatter_ms);
  * points are formed in fixed point), for |x| < 2^58.  Asynchronous. */
 fea_status fea_diag_sinpi(const double* x, int64_t n, int32_t variant, double* mine, double* lib, void* stream);
 
+/* Failure-path check of the bounded device waits: one warp waits, with the
+ * bulk-copy scatter's bounded mbarrier wait, on a barrier whose expected
+ * arrival never comes, gives up after `polls` polls (1 to 2^20) and raises
+ * the timeout bit in the mesh's device error word; the next fea_mesh_check
+ * returns FEA_ERR_TIMEOUT and clears it.  Nothing else is touched and the
+ * context stays usable.  Asynchronous. */
+fea_status fea_diag_wait_timeout(fea_mesh* mesh, int32_t polls, void* stream);
+
 /* Measure the device's sustained FP64 FMA throughput (flop/s, FMA = 2)
  * with independent DFMA chains on every SM.  Synchronises. */
 fea_status fea_diag_fp64_rate(double* flops_per_s, void* stream);

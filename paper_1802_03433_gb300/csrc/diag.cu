@@ -1,6 +1,7 @@
 // Diagnostic entry points (self-checks of device helpers; no counterpart in
 // the paper).
 #include "element.cuh"
+#include "gather_tiled.cuh"
 #include "internal.cuh"
 
 namespace fea {
@@ -20,6 +21,21 @@ __global__ void k_diag_sinpi(const double* __restrict__ x, int64_t n, int varian
   }
   lib[i] = sinpi(x[i]);
 }
+// The bounded mbarrier wait of the bulk-copy scatter on a barrier whose one
+// expected arrival never comes (no copy is issued): every thread gives up
+// after `polls` polls and the kernel raises DEV_ERR_TIMEOUT in the error word,
+// as the scatter does when a copy never completes.
+__global__ void k_diag_wait_timeout(int* err, uint32_t polls) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  const bool ok = mbar_wait(&bar, 0, polls);
+  if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(err, DEV_ERR_TIMEOUT);
+}
+
 // Eight independent DFMA chains per thread: the FP64 pipe's sustained FMA
 // rate, the denominator of the element kernels' roofline.
 __global__ void k_diag_dfma(double* __restrict__ out, int iters, double s) {
@@ -71,6 +87,14 @@ extern "C" fea_status fea_diag_sinpi(const double* x, int64_t n, int32_t variant
   if (n == 0) return FEA_OK;
   fea::k_diag_sinpi<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, n, variant, mine,
                                                                                                lib);
+  FEA_CUDA(cudaGetLastError());
+  return FEA_OK;
+}
+
+extern "C" fea_status fea_diag_wait_timeout(fea_mesh* m, int32_t polls, void* stream) {
+  if (!m) return fea::fail(FEA_ERR_ARG, "mesh is NULL");
+  if (polls < 1 || polls > (1 << 20)) return fea::fail(FEA_ERR_ARG, "polls must be in [1, 2^20]");
+  fea::k_diag_wait_timeout<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(m->err, (uint32_t)polls);
   FEA_CUDA(cudaGetLastError());
   return FEA_OK;
 }

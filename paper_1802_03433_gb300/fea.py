@@ -97,6 +97,7 @@ def lib() -> C.CDLL:
         "fea_profile_enable": [_vp, C.c_int32],
         "fea_profile_last": [_vp, C.POINTER(C.c_float), C.POINTER(C.c_float)],
         "fea_diag_sinpi": [_vp, C.c_int64, C.c_int32, _vp, _vp, _vp],
+        "fea_diag_wait_timeout": [_vp, C.c_int32, _vp],
         "fea_diag_fp64_rate": [C.POINTER(C.c_double), _vp],
         "fea_batch_create": [C.POINTER(_vp), C.c_int32, C.POINTER(fea_form), C.POINTER(fea_quadrature),
                              C.c_int32, _vp, C.POINTER(_vp)],
@@ -317,6 +318,10 @@ def fea_profile_last(h):
     a, b = C.c_float(), C.c_float()
     _check(lib().fea_profile_last(h, C.byref(a), C.byref(b)), "fea_profile_last")
     return a.value, b.value
+
+
+def fea_diag_wait_timeout(h, polls=1024, stream=None):
+    _check(lib().fea_diag_wait_timeout(h, polls, _stream(stream)), "fea_diag_wait_timeout")
 
 
 def fea_diag_sinpi(x, variant=0, stream=None):

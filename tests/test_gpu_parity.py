@@ -368,3 +368,23 @@ def test_sine_load_small_offset_mesh_matches_oracle(torch_cuda, kind, n):
     o = oracle_system(c)
     assert row_scaled_error(o["rp"], o["vals"], g["vals"]) <= TOL_FP64
     assert vec_scaled_error(o["rhs"], g["rhs"]) <= TOL_FP64
+
+
+def test_bounded_wait_times_out_and_context_survives(torch_cuda):
+    """A device wait that never completes (the bulk-copy scatter's bounded
+    mbarrier wait on a barrier nobody arrives at) gives up, the host reads
+    FEA_ERR_TIMEOUT from the mesh's error word, the word is cleared, and the
+    same context then assembles correctly."""
+    from paper_1802_03433_gb300 import fea
+    c = case("p2_diffmass", 4, seed=47)
+    m = fea.Mesh(c["coords"], c["tets"])
+    fea.fea_diag_wait_timeout(m.h, 1024)
+    with pytest.raises(fea.FeaError) as ei:
+        m.check()
+    assert ei.value.status == 7  # FEA_ERR_TIMEOUT
+    m.check()  # cleared
+    g = gpu_system(c, mesh=m)
+    o = oracle_system(c)
+    assert row_scaled_error(o["rp"], o["vals"], g["vals"]) <= TOL_FP64
+    with pytest.raises(fea.FeaError):
+        fea.fea_diag_wait_timeout(m.h, 0)
