@@ -52,6 +52,8 @@ DRAM_BYTES_PER_LAUNCH = {
     ("p1_elast_128", "element"): 8 * (82.2e6 + 1907.8e6),
 }
 
+METRIC = "elements/s assembled into CSR and % of HBM roofline, plain vs chosen forms"
+
 WORKLOADS = {
     "p2_diffmass_64": dict(kind="p2_diffmass", n=64),
     "p1_poisson_8": dict(kind="p1_poisson", n=8),
@@ -400,7 +402,7 @@ def run_ours(args):
         if ws == 1 and not args.no_cpu_baseline:
             cpu = cpu_baseline(d["kind"])
         out = {
-            "metric": "elements/s assembled into CSR (plain FP64), with % of HBM roofline and the mixed form",
+            "metric": METRIC,
             "overlap_stages": args.stages,
             "value": value, "unit": "elements/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -762,7 +764,7 @@ def run_reference(args):
     dt = time.perf_counter() - t
     value = E * args.steps / dt
     out = {
-        "impl": "reference", "metric": "elements/s assembled into CSR (plain FP64), with % of HBM roofline and the mixed form",
+        "impl": "reference", "metric": METRIC,
         "value": value, "unit": "elements/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
