@@ -63,6 +63,25 @@ WORKLOADS = {
 }
 
 
+def mixed_error(torch, mesh, d, ref_vals, vals, ref_rhs, rhs):
+    """Row-scaled error of the mixed-precision result against the FP64 result
+    of the same run (max over rows of max |dA| / max |A_fp64| in the row; rhs
+    scaled by its max), computed on the device.  The FP64 path is within 1e-12
+    of the oracle, so this is the mixed path's error against the oracle to
+    that accuracy."""
+    rp, _ = mesh.pattern_tensors(d["order"], d["ndpn"])
+    counts = torch.diff(rp.long())
+    rows = torch.repeat_interleave(torch.arange(counts.numel(), device=rp.device), counts)
+    nnz = rows.numel()
+    diff = (vals[:nnz] - ref_vals[:nnz]).abs()
+    scale = torch.zeros(counts.numel(), dtype=torch.float64, device=rp.device)
+    scale.scatter_reduce_(0, rows, ref_vals[:nnz].abs(), reduce="amax")
+    worst = torch.zeros_like(scale).scatter_reduce_(0, rows, diff, reduce="amax")
+    row_err = torch.where(scale > 0, worst / torch.where(scale > 0, scale, torch.ones_like(scale)), worst)
+    rhs_err = (rhs - ref_rhs).abs().max() / ref_rhs.abs().max().clamp_min(1e-300)
+    return {"values_row_scaled": float(row_err.max()), "rhs_scaled": float(rhs_err)}
+
+
 def algorithmic_bytes(kind, E, N, ndof, nnz):
     """Inputs read once + outputs written once (coords 24 B/node, element->node
     table 16 B/element, coefficients 8 B per field per element, values 8 B/nnz,
@@ -255,11 +274,13 @@ def run_ours(args):
         return not args.no_forms and (args.forms == "all" or name in args.forms.split(","))
 
     if want("mixed"):
+        ref_vals, ref_rhs = values.clone(), rhs.clone()  # the FP64 result of the loop above
         m_total, _, m_phase, _ = timed_loop(fea.FEA_MIXED, max(3, args.steps // 2), args.warmup)
         ms = m_total / max(3, args.steps // 2)
         forms["mixed"] = {"value": ws * E / (ms / 1e3), "ms_per_step": ms,
                           "elem_ms": statistics.mean(p[0] for p in m_phase),
-                          "scatter_ms": statistics.mean(p[1] for p in m_phase)}
+                          "scatter_ms": statistics.mean(p[1] for p in m_phase),
+                          "error_vs_fp64": mixed_error(torch, mesh, d, ref_vals, values, ref_rhs, rhs)}
 
     small = max(3, args.steps // 4)
     if want("atomic_alg1"):
@@ -579,6 +600,10 @@ def bench_plain(fea, torch, dev, kind, n, steps, warmup, flush):
             ps += s_ms
         out[name] = {"value": E / (tot / steps / 1e3), "ms_per_step": tot / steps, "elem_ms": pe / steps,
                      "scatter_ms": ps / steps}
+        if name == "fp64":
+            ref = (vals.clone(), rhs.clone())
+        else:
+            out[name]["error_vs_fp64"] = mixed_error(torch, m, d, ref[0], vals, ref[1], rhs)
     m.check()
     m.close()
     return out
