@@ -267,40 +267,36 @@ __global__ void __launch_bounds__(32 * UNIQ_WARPS) k_row_unique(int64_t nrows, c
       const int64_t e = p / NB;
       buf[t] = edof[(int64_t)(t % NB) * E + e];
     }
+    // pad to a power of two with INT_MAX (sorts last) and sort the warp's
+    // buffer (bitonic network, compare-exchanges spread over the lanes)
+    int n2 = 32;
+    while (n2 < k) n2 <<= 1;  // <= ROW_CAP
+    for (int t = k + lane; t < n2; t += 32) buf[t] = 0x7FFFFFFF;
     __syncwarp();
-    uint32_t dup = 0;  // bit j: item lane + 32 j repeats an earlier item
-    for (int j = 0; lane + 32 * j < k; ++j) {
-      const int t = lane + 32 * j;
-      const int32_t v = buf[t];
-      for (int u = 0; u < t; ++u)
-        if (buf[u] == v) {
-          dup |= 1u << j;
-          break;
+    for (int size = 2; size <= n2; size <<= 1)
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int t = lane; t < (n2 >> 1); t += 32) {
+          const int i = 2 * stride * (t / stride) + (t % stride), j = i + stride;
+          const int32_t a = buf[i], b = buf[j];
+          if ((a > b) == ((i & size) == 0)) {
+            buf[i] = b;
+            buf[j] = a;
+          }
         }
-    }
-    __syncwarp();
-    for (int j = 0; lane + 32 * j < k; ++j)
-      if (dup >> j & 1u) buf[lane + 32 * j] = -1;
-    __syncwarp();
-    if (!col_idx) {
-      int c = 0;
-      for (int j = 0; lane + 32 * j < k; ++j) c += !(dup >> j & 1u);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-      if (lane == 0) counts[row] = c;
-    } else {
-      const int32_t base = row_ptr[row];
-      for (int j = 0; lane + 32 * j < k; ++j) {
-        if (dup >> j & 1u) continue;
-        const int32_t v = buf[lane + 32 * j];
-        int rank = 0;
-        for (int u = 0; u < k; ++u) {
-          const int32_t q = buf[u];
-          rank += (q >= 0 && q < v);
-        }
-        col_idx[base + rank] = v;
+        __syncwarp();
       }
+    // the distinct columns in ascending order: first of each run
+    const int32_t base = col_idx ? row_ptr[row] : 0;
+    int c = 0;
+    for (int t0 = 0; t0 < k; t0 += 32) {
+      const int t = t0 + lane;
+      const int32_t v = t < k ? buf[t] : 0;
+      const bool keep = t < k && (t == 0 || buf[t - 1] != v);
+      const unsigned mask = __ballot_sync(0xffffffffu, keep);
+      if (col_idx && keep) col_idx[base + c + __popc(mask & ((1u << lane) - 1u))] = v;
+      c += __popc(mask);
     }
+    if (!col_idx && lane == 0) counts[row] = c;
     __syncwarp();
   }
 }
