@@ -162,3 +162,33 @@ def test_full_batch_256_meshes():
             np.testing.assert_array_equal(ci[rp[r]:rp[r + 1]], cols)
             assert np.abs(vals[rp[r]:rp[r + 1]] - v).max() <= TOL_FP64 * np.abs(v).max()
     b.close()
+
+
+@pytest.mark.parametrize("f_kind", ["const", "none"])
+def test_batch_other_loads_bitwise(f_kind):
+    """Batches with the constant load and with no load: every mesh bitwise
+    equal to its single-mesh assembly (rhs too for the constant load), before
+    and after tuning."""
+    import torch
+    from paper_1802_03433_gb300 import fea
+    specs = mg.batch(n_meshes=6, lo=2, hi=6, seed=8)
+    specs[2]["mass"] = 0.5
+    fk = fea.FEA_LOAD_CONST if f_kind == "const" else fea.FEA_LOAD_NONE
+    meshes, forms, quads, coeffs, keep = _build(specs)
+    coeffs = [fea.make_coeffs(kappa=k, f_kind=fk, f_param=(1.75,)) for k in keep]
+    single = []
+    for m, f, q, c in zip(meshes, forms, quads, coeffs):
+        v, r = m.assemble(f, c, q, with_rhs=fk != fea.FEA_LOAD_NONE)
+        single.append((v.clone(), None if r is None else r.clone()))
+    b = fea.Batch(meshes, forms, quads, coeffs, fk, with_rhs=fk != fea.FEA_LOAD_NONE)
+    for rep in range(2):
+        if rep == 1:
+            b.tune()
+        b.assemble()
+        torch.cuda.synchronize()
+        for k in range(len(meshes)):
+            nnz = meshes[k].pattern(forms[k].order)[1]
+            assert _bitwise_equal(b.values[k][:nnz], single[k][0]), (k, rep)
+            if fk != fea.FEA_LOAD_NONE:
+                assert _bitwise_equal(b.rhs[k], single[k][1]), (k, rep)
+    b.close()
