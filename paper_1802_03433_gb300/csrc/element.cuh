@@ -371,12 +371,6 @@ __device__ __forceinline__ long long sinpi_q62(double x) {
   const long long mag = sinpi_q62_mag(ra);
   return ((b >> 63) ^ par ^ rneg) ? -mag : mag;
 }
-static __device__ __noinline__ long long sinpi_q62_call(double x) { return sinpi_q62(x); }
-template <bool OUTLINE>
-__device__ __forceinline__ long long sinpi_q62_sel(double x) {
-  if constexpr (OUTLINE) return sinpi_q62_call(x);
-  else return sinpi_q62(x);
-}
 
 // sin(pi x) 2^62 for x given in fixed point, t = x 2^(61 - s) (0 <= s <= 60,
 // two's complement): the fraction of x in units of 2^-64 is t << (3 + s) and
