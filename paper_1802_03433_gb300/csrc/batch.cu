@@ -128,9 +128,12 @@ using ElemKernel = void (*)(const BMesh*, const BItem*, int);
 
 // Matrix warps and load warps (elem_roles_body) for the sine load: each item's
 // elements are taken twice, by the CTA's first BT threads for the local matrix
-// and by the next BT for the local load (variant 2, sine loads only).
+// and by the next BT for the local load (variant 2, sine loads only).  Held
+// to three CTAs per SM like the single-mesh form: the persistent loop spills
+// more here (about 420 bytes at 80 registers), and the residency still wins
+// (256-mesh batch 9.0 -> 8.5 ms against two CTAs at 128 registers).
 template <int ORDER, int LOAD, int NP>
-__global__ void __launch_bounds__(2 * BT, 2) k_batch_elem_roles(const BMesh* __restrict__ M,
+__global__ void __launch_bounds__(2 * BT, 3) k_batch_elem_roles(const BMesh* __restrict__ M,
                                                               const BItem* __restrict__ items, int nitems) {
   const bool matrix = threadIdx.x < BT;
   const int lane = threadIdx.x % BT;

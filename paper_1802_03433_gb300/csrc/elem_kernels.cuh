@@ -77,6 +77,8 @@ __device__ __forceinline__ void elem_scalar_body(const ElemArgs& A, int64_t e) {
   R Gr[4][3];
   grads<R>(g, Gr);
   R Kl[NB][NB];
+  constexpr bool STREAM = ORDER == 2 && !ATOMIC;  // P2 rows stored as they complete
+  [[maybe_unused]] int32_t spos[NB];               // their positions (STREAM)
   // Gram matrix G_ij = s grad lambda_i . grad lambda_j; FP64 P1 with a mass
   // term keeps it unscaled and applies s in the FMA that adds the mass
   const R s = R(kap * grad_scale<R>(adet) * (ORDER == 2 ? 1.0 / 20.0 : 1.0));
@@ -114,6 +116,13 @@ __device__ __forceinline__ void elem_scalar_body(const ElemArgs& A, int64_t e) {
 #pragma unroll
       for (int c = 0; c < 7; ++c) tm[c] = c == 1 ? t : R(p2_mass_value(c)) * t;
     }
+    // rows in order, upper entries computed at their row and mirrored; with
+    // STREAM each row is stored as soon as it is complete, so fewer entries
+    // are live at a time
+    if constexpr (STREAM) {
+#pragma unroll
+      for (int a = 0; a < NB; ++a) spos[a] = __ldg(A.ipos + a * A.E + e);
+    }
     static_for<55>([&](auto K) {
       constexpr int a = upper_a(10, K), b = upper_b(10, K);
       R v;
@@ -125,6 +134,8 @@ __device__ __forceinline__ void elem_scalar_body(const ElemArgs& A, int64_t e) {
       }
       Kl[a][b] = v;
       Kl[b][a] = v;
+      if constexpr (STREAM && b == 9)
+        store_row<NB>(static_cast<R*>(A.Lm) + (int64_t)spos[a] * lstride(NB, sizeof(R)), Kl[a]);
     });
   }
   if constexpr (ATOMIC) {
@@ -147,10 +158,15 @@ __device__ __forceinline__ void elem_scalar_body(const ElemArgs& A, int64_t e) {
   } else {
     constexpr int LS = lstride(NB, sizeof(R));
     int32_t pos[NB];
+    if constexpr (STREAM) {
 #pragma unroll
-    for (int a = 0; a < NB; ++a) pos[a] = __ldg(A.ipos + a * A.E + e);
+      for (int a = 0; a < NB; ++a) pos[a] = spos[a];
+    } else {
 #pragma unroll
-    for (int a = 0; a < NB; ++a) store_row<NB>(static_cast<R*>(A.Lm) + (int64_t)pos[a] * LS, Kl[a]);
+      for (int a = 0; a < NB; ++a) pos[a] = __ldg(A.ipos + a * A.E + e);
+#pragma unroll
+      for (int a = 0; a < NB; ++a) store_row<NB>(static_cast<R*>(A.Lm) + (int64_t)pos[a] * LS, Kl[a]);
+    }
 
     if constexpr (LOAD != LOAD_NONE) {
       R Xr[4][3];
@@ -219,8 +235,13 @@ __device__ __forceinline__ void elem_roles_body(const ElemArgs& A, int64_t e, bo
   }
 }
 
+// Three resident blocks per SM (80 registers, about 100 bytes spilled to L1):
+// the extra warps hide more of the fixed-latency dependencies than the spills
+// cost (P2 64^3: 0.80 -> 0.72 ms against two blocks at 108 registers).
+constexpr int ROLES_MIN_BLOCKS = 3;
+
 template <int ORDER, bool MASS, int LOAD, int NPTS>
-__global__ void __launch_bounds__(2 * ELEM_T) k_elem_roles(ElemArgs A) {
+__global__ void __launch_bounds__(2 * ELEM_T, ROLES_MIN_BLOCKS) k_elem_roles(ElemArgs A) {
   const int64_t e = A.e0 + (int64_t)blockIdx.x * ELEM_T + (threadIdx.x % ELEM_T);
   if (e >= A.e1) return;
   elem_roles_body<ORDER, MASS, LOAD, NPTS>(A, e, threadIdx.x < ELEM_T);
