@@ -40,13 +40,16 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # captures are summarised under profiles/.  Absent where not captured for the
 # current kernels.
 FP64_FLOP_PER_ELEM = {
-    # P2: the kernel with matrix warps and load warps (the automatic launch)
-    ("p2_diffmass_64", "fp64"): 375.0,    # 150 DFMA + 26 DADD + 49 DMUL per element (+ ~6,300 integer instructions)
+    # P2: the kernel with matrix warps and load warps (the automatic launch).
+    # 375 = the element formulas in FP64 (150 DFMA + 26 DADD + 49 DMUL, the
+    # ncu count of the all-FP64 form); the kernel evaluates the 136 FMA terms
+    # of the local entries as exact 64-bit integer sums instead, so its own
+    # FP64 count is lower while the work per element is the same
+    ("p2_diffmass_64", "fp64"): 375.0,
     ("p1_kappa_96", "fp64"): 119.0,       # 30 DFMA + 27 DADD + 32 DMUL (+ ~2,200 integer instructions)
     ("p1_elast_128", "fp64"): 335.0,      # 102 DFMA + 16 DADD + 115 DMUL
 }
 DRAM_BYTES_PER_LAUNCH = {
-    ("p2_diffmass_64", "element"): 140.6e6 + 1741.5e6,
     ("p1_kappa_96", "element"): 238.4e6 + 793.2e6,
     # captured on the 64^3 mesh (1,572,864 tets) and scaled by 8 (traffic grows with the elements)
     ("p1_elast_128", "element"): 8 * (82.2e6 + 1907.8e6),

@@ -62,6 +62,34 @@ __device__ __forceinline__ void load_element(const ElemArgs& A, int64_t e, doubl
   load_vertices(A.x, A.y, A.z, v, X);
 }
 
+// The FP64 P2 rows by FMA chains, stored to their positions: the fallback of
+// the fixed-point entries for inputs outside their range (Gu: the ten upper
+// Gram entries row by row, then the mass scale t).  Out of line, so that the
+// kernels carry one copy of the rare path and none of its registers.
+template <bool MASS>
+static __device__ __noinline__ void p2_rows_fp64_call(const double* __restrict__ Gu, double* __restrict__ Lm,
+                                                      const int32_t* __restrict__ ipos, int64_t E, int64_t e) {
+  double G[4][4];
+  int k = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = i; j < 4; ++j) G[i][j] = Gu[k++];
+  const double t = Gu[10];
+  double tm[7];
+#pragma unroll
+  for (int c = 0; c < 7; ++c) tm[c] = MASS ? (c == 1 ? t : p2_mass_value(c) * t) : 0.0;
+  double Kl[10][10];
+  static_for<55>([&](auto K) {
+    constexpr int a = upper_a(10, K), b = upper_b(10, K);
+    const double v = MASS ? p2_stiff<K, double>(G, tm[p2_mass_class(a, b)]) : p2_stiff<K, double>(G);
+    Kl[a][b] = v;
+    Kl[b][a] = v;
+  });
+#pragma unroll
+  for (int a = 0; a < 10; ++a) store_row<10>(Lm + (int64_t)__ldg(ipos + a * E + e) * lstride(10, sizeof(double)), Kl[a]);
+}
+
 // ---------------------------------------------------------------- scalar forms
 // -div(kappa grad u) [+ mass u] on P1 (ORDER 1) or P2 (ORDER 2) tets.
 template <int ORDER, bool MASS, int LOAD, int NPTS, typename R, bool ATOMIC = false>
@@ -105,17 +133,8 @@ __device__ __forceinline__ void elem_scalar_body(const ElemArgs& A, int64_t e) {
   } else {
     // K_ab = kappa |T| / 20 sum_t num_t (grad lambda_i . grad lambda_j);
     // M_ab = |T| / 420 * m420_ab
-    // FP64: |T| / 420 times each of the seven values of the P2 mass pattern
-    // starts the entry's FMA chain (one FP64 operation less per entry); the
-    // FP32 products of the mixed path add the mass term last
-    constexpr bool FOLD = MASS && IsDouble<R>::value;
-    [[maybe_unused]] R tm[7];
     [[maybe_unused]] R t = R(0);
     if constexpr (MASS) t = R(A.mass * adet * (1.0 / 2520.0));
-    if constexpr (FOLD) {
-#pragma unroll
-      for (int c = 0; c < 7; ++c) tm[c] = c == 1 ? t : R(p2_mass_value(c)) * t;
-    }
     // rows in order, upper entries computed at their row and mirrored; with
     // STREAM each row is stored as soon as it is complete, so fewer entries
     // are live at a time
@@ -123,20 +142,70 @@ __device__ __forceinline__ void elem_scalar_body(const ElemArgs& A, int64_t e) {
 #pragma unroll
       for (int a = 0; a < NB; ++a) spos[a] = __ldg(A.ipos + a * A.E + e);
     }
-    static_for<55>([&](auto K) {
+    auto put = [&](auto K, R v) {
       constexpr int a = upper_a(10, K), b = upper_b(10, K);
-      R v;
-      if constexpr (FOLD) {
-        v = p2_stiff<K, R>(G, tm[p2_mass_class(a, b)]);
-      } else {
-        v = p2_stiff<K, R>(G);
-        if constexpr (MASS) v = fma(t, R(p2_mass420(a, b)), v);
-      }
       Kl[a][b] = v;
       Kl[b][a] = v;
       if constexpr (STREAM && b == 9)
         store_row<NB>(static_cast<R*>(A.Lm) + (int64_t)spos[a] * lstride(NB, sizeof(R)), Kl[a]);
-    });
+    };
+    // FP64 (deterministic path): the entries as exact integer sums of the
+    // Gram and mass terms in 64-bit fixed point (p2_stiff_fx), on the integer
+    // pipes; the FMA chains below for the FP32 path and the atomic kernel
+    if constexpr (IsDouble<R>::value && STREAM) {
+      int E = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = i; j < 4; ++j) E = max(E, exp_bits(G[i][j]) + 2);
+      if constexpr (MASS) E = max(E, exp_bits(t) + 5);
+      if (E >= P2FX_EMIN && E <= P2FX_EMAX) {
+        long long Gf[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = i; j < 4; ++j) Gf[i][j] = to_fx(G[i][j], E - 1019);
+        [[maybe_unused]] long long tf = 0;
+        if constexpr (MASS) tf = to_fx(t, E - 1017);
+        const int p = 1078 - E;
+        static_for<55>([&](auto K) {
+          constexpr int a = upper_a(10, K), b = upper_b(10, K);
+          long long m = 0;
+          if constexpr (MASS) m = static_cast<long long>(p2_mass420(a, b)) * tf;
+          put(K, fx_to_double(p2_stiff_fx<K>(Gf, m), p));
+        });
+      } else {
+        double Gu[11];
+        int k = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = i; j < 4; ++j) Gu[k++] = G[i][j];
+        Gu[10] = t;
+        p2_rows_fp64_call<MASS>(Gu, static_cast<double*>(A.Lm), A.ipos, A.E, e);
+      }
+    } else {
+      // FP64: |T| / 420 times each of the seven values of the P2 mass pattern
+      // starts the entry's FMA chain (one FP64 operation less per entry); the
+      // FP32 products of the mixed path add the mass term last
+      constexpr bool FOLD = MASS && IsDouble<R>::value;
+      [[maybe_unused]] R tm[7];
+      if constexpr (FOLD) {
+#pragma unroll
+        for (int c = 0; c < 7; ++c) tm[c] = c == 1 ? t : R(p2_mass_value(c)) * t;
+      }
+      static_for<55>([&](auto K) {
+        constexpr int a = upper_a(10, K), b = upper_b(10, K);
+        R v;
+        if constexpr (FOLD) {
+          v = p2_stiff<K, R>(G, tm[p2_mass_class(a, b)]);
+        } else {
+          v = p2_stiff<K, R>(G);
+          if constexpr (MASS) v = fma(t, R(p2_mass420(a, b)), v);
+        }
+        put(K, v);
+      });
+    }
   }
   if constexpr (ATOMIC) {
     int32_t d[NB];
@@ -235,9 +304,9 @@ __device__ __forceinline__ void elem_roles_body(const ElemArgs& A, int64_t e, bo
   }
 }
 
-// Three resident blocks per SM (80 registers, about 100 bytes spilled to L1):
+// Three resident blocks per SM (80 registers, about 350 bytes spilled to L1):
 // the extra warps hide more of the fixed-latency dependencies than the spills
-// cost (P2 64^3: 0.80 -> 0.72 ms against two blocks at 108 registers).
+// cost (P2 64^3: 0.71 ms against 0.82 ms for two blocks).
 constexpr int ROLES_MIN_BLOCKS = 3;
 
 template <int ORDER, bool MASS, int LOAD, int NPTS>

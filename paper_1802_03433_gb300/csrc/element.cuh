@@ -890,6 +890,59 @@ __device__ __forceinline__ R p2_stiff(const R G[4][4], R c) {
   return v;
 }
 
+// ------------------------------------------------------------------ P2 entries in fixed point
+// The FP64 P2 local matrix as exact integer sums.  Every stiffness coefficient
+// num_t is a multiple of 4 with sum_t |num_t| / 4 <= 24 in any entry, and
+// every mass value is at most 32 in magnitude (p2_fx_coeffs_ok).  With E the
+// largest biased exponent of 4 G_ij and of 32 t (t = the mass scale), both
+// lie below 2^(E - 1022); 4 G_ij and t are rounded to integers at the scale
+// 2^p, p = 1078 - E, so every input is below 2^56 and every entry below
+// 25 * 2^56 < 2^61.  The sums are then exact and each entry is rounded once,
+// on the way back to FP64: its error is at most 28 * 2^-55 of the largest
+// input (the rounded inputs, 28 units of 2^-p) plus half an ulp of the entry
+// (a bit-exact model checked this on random inputs).  For E outside
+// [P2FX_EMIN, P2FX_EMAX] (non-finite or vanishing inputs) the kernels keep
+// the FP64 chains; inside it the results stay normal FP64 numbers.
+constexpr int P2FX_EMIN = 64, P2FX_EMAX = 2032;
+
+__host__ __device__ constexpr bool p2_fx_coeffs_ok() {
+  for (int K = 0; K < 55; ++K) {
+    const Terms t = p2_terms(upper_a(10, K), upper_b(10, K));
+    int sum = 0;
+    for (int k = 0; k < t.n; ++k) {
+      if (t.num[k] % 4 != 0) return false;
+      sum += t.num[k] < 0 ? -t.num[k] / 4 : t.num[k] / 4;
+    }
+    if (sum > 24) return false;
+    const int m = p2_mass420(upper_a(10, K), upper_b(10, K));
+    if (m > 32 || m < -32) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ int exp_bits(double v) { return (__double2hiint(v) >> 20) & 0x7FF; }
+
+// Entry K at scale 2^p: m (its mass term) + sum_t (num_t / 4) Gf[i_t][j_t],
+// Gf = 4 G at scale 2^p.
+template <int K>
+__device__ __forceinline__ long long p2_stiff_fx(const long long Gf[4][4], long long m) {
+  static_assert(p2_fx_coeffs_ok(), "P2 coefficients outside the fixed-point bounds");
+  constexpr int A = upper_a(10, K), B = upper_b(10, K);
+  constexpr Terms t = p2_terms(A, B);
+  long long v = m + static_cast<long long>(t.num[0] / 4) * Gf[t.i[0]][t.j[0]];
+  if constexpr (t.n > 1) v += static_cast<long long>(t.num[1] / 4) * Gf[t.i[1]][t.j[1]];
+  if constexpr (t.n > 2) v += static_cast<long long>(t.num[2] / 4) * Gf[t.i[2]][t.j[2]];
+  if constexpr (t.n > 3) v += static_cast<long long>(t.num[3] / 4) * Gf[t.i[3]][t.j[3]];
+  return v;
+}
+
+// F 2^-p as a double: one correctly rounded conversion, then an exact shift
+// of the exponent field (the caller keeps the result normal).
+__device__ __forceinline__ double fx_to_double(long long F, int p) {
+  const double d = __ll2double_rn(F);
+  return F == 0 ? 0.0 : __longlong_as_double(__double_as_longlong(d) - (static_cast<long long>(p) << 52));
+}
+
 // The P2 mass pattern 420 |T|^{-1} M_ab takes seven values; mass_class(a, b)
 // numbers them, so the element kernels form t * value once per class and
 // start each entry's stiffness FMA chain from it.
