@@ -50,6 +50,7 @@ FP64_FLOP_PER_ELEM = {
     ("p1_elast_128", "fp64"): 335.0,      # 102 DFMA + 16 DADD + 115 DMUL
 }
 DRAM_BYTES_PER_LAUNCH = {
+    ("p2_diffmass_64", "element"): 149.3e6 + 1985.1e6,
     ("p1_kappa_96", "element"): 238.4e6 + 793.2e6,
     # captured on the 64^3 mesh (1,572,864 tets) and scaled by 8 (traffic grows with the elements)
     ("p1_elast_128", "element"): 8 * (82.2e6 + 1907.8e6),

@@ -388,3 +388,47 @@ def test_bounded_wait_times_out_and_context_survives(torch_cuda):
     assert row_scaled_error(o["rp"], o["vals"], g["vals"]) <= TOL_FP64
     with pytest.raises(fea.FeaError):
         fea.fea_diag_wait_timeout(m.h, 0)
+
+
+@pytest.mark.parametrize("log2_scale", [-1000, -60, 60, 1000])
+@pytest.mark.parametrize("kind", ["p2_poisson", "p2_diffmass"])
+def test_p2_entries_across_coefficient_scales(torch_cuda, kind, log2_scale):
+    """The FP64 P2 entries are integer sums on one fixed-point scale set by
+    the element's largest Gram or mass term.  kappa scaled by 2^k moves that
+    scale through its range: 2^1000 puts the Gram terms near its top, 2^-1000
+    (Poisson) below its bottom, where the FMA chains take over.  Against the
+    oracle; without a mass term the values must also scale exactly, bitwise
+    2^k times the unscaled ones (k = -1000 excepted: there the FMA chains may
+    meet subnormal cancellations)."""
+    c = case(kind, 4, seed=11)
+    base = gpu_system(c)
+    cs = dict(c)
+    cs["kappa"] = np.ldexp(c["kappa"], log2_scale)
+    g = gpu_system(cs)
+    o = oracle_system(cs)
+    assert row_scaled_error(o["rp"], o["vals"], g["vals"]) <= TOL_FP64
+    assert np.array_equal(g["rhs"].view(np.uint64), base["rhs"].view(np.uint64))
+    if kind == "p2_poisson" and log2_scale != -1000:
+        scaled = np.ldexp(base["vals"], log2_scale)
+        assert np.array_equal(g["vals"].view(np.uint64), scaled.view(np.uint64))
+
+
+def test_p2_nonfinite_coefficient_propagates(torch_cuda):
+    """A NaN kappa on one element (outside the fixed-point range, so its
+    entries take the FMA chains) gives NaN in exactly the CSR entries that
+    element touches and finite values everywhere else, as plain FP64
+    arithmetic would."""
+    c = dict(case("p2_poisson", 4, seed=12))
+    kap = c["kappa"].copy()
+    kap[7] = np.nan
+    c["kappa"] = kap
+    g = gpu_system(c)
+    edof, _ = oracle.dof_table(2, c["coords"].shape[1], c["tets"])
+    d = set(int(x) for x in edof[:, 7])
+    rp, ci = g["rp"], g["ci"]
+    expect = np.zeros(len(ci), dtype=bool)
+    for r in d:
+        for p in range(rp[r], rp[r + 1]):
+            expect[p] = int(ci[p]) in d
+    assert np.array_equal(np.isnan(g["vals"]), expect)
+    assert np.isfinite(g["rhs"]).all()
