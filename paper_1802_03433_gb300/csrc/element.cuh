@@ -920,13 +920,14 @@ __host__ __device__ constexpr bool p2_fx_coeffs_ok() {
   return true;
 }
 
+static_assert(p2_fx_coeffs_ok(), "P2 coefficients outside the fixed-point bounds");
+
 __device__ __forceinline__ int exp_bits(double v) { return (__double2hiint(v) >> 20) & 0x7FF; }
 
 // Entry K at scale 2^p: m (its mass term) + sum_t (num_t / 4) Gf[i_t][j_t],
 // Gf = 4 G at scale 2^p.
 template <int K>
 __device__ __forceinline__ long long p2_stiff_fx(const long long Gf[4][4], long long m) {
-  static_assert(p2_fx_coeffs_ok(), "P2 coefficients outside the fixed-point bounds");
   constexpr int A = upper_a(10, K), B = upper_b(10, K);
   constexpr Terms t = p2_terms(A, B);
   long long v = m + static_cast<long long>(t.num[0] / 4) * Gf[t.i[0]][t.j[0]];

@@ -39,10 +39,15 @@ def test_same_specialisation_is_cached(fea):
         fea.fea_jit_destroy(h)
 
 
-def test_no_expressions_gives_the_constant_coefficient_kernel(fea):
-    j = fea.fea_jit_compile(fea.make_form(1, 2, 1.0), fea.make_quadrature(11), None, None)
+@pytest.mark.parametrize("kind,prec", [(1, 0), (0, 0), (1, 1), (0, 1)])
+def test_no_expressions_gives_the_constant_coefficient_kernel(fea, kind, prec):
+    """P2 without k(x): the closed-form entries of the precompiled kernels'
+    FMA chains, FP64 and FP32, with and without mass."""
+    j = fea.fea_jit_compile(fea.make_form(kind, 2, 1.0 if kind else 0.0), fea.make_quadrature(11, prec), None, None)
     src = fea.fea_jit_source(j)
     assert "HAS_K = false" in src and "HAS_F = false" in src
+    assert f"elem_user_body<2, {'true' if kind else 'false'}, 11, {'double' if prec == 0 else 'float'}," in src
+    assert fea.fea_jit_info(j)[1] > 1000
     fea.fea_jit_destroy(j)
 
 
