@@ -237,47 +237,54 @@ __global__ void k_inc_sort(const int32_t* __restrict__ ptr, int64_t n, int32_t* 
 }
 
 // ------------------------------------------------------------------ rows
-// One warp per scalar row.  The row's candidate columns are the nb dofs of
-// each incident element; repeats are dropped and each survivor's column is
-// its rank among the survivors.  count mode (col_idx == NULL): writes the
-// number of distinct columns; fill mode: writes the sorted columns.
-template <int NB>
-__global__ void __launch_bounds__(32 * UNIQ_WARPS) k_row_unique(int64_t nrows, const int32_t* __restrict__ inc_ptr,
-                                                                const int32_t* __restrict__ inc,
-                                                                const int32_t* __restrict__ edof, int64_t E,
-                                                                const int32_t* __restrict__ row_ptr,
-                                                                int32_t* __restrict__ counts,
-                                                                int32_t* __restrict__ col_idx, int* err) {
-  __shared__ int32_t sbuf[UNIQ_WARPS][ROW_CAP];
+// One warp per scalar row, one pass: the row's candidate columns (the nb dofs
+// of each incident element, in incidence order t = incidence * NB + local
+// dof) are sorted as 64-bit keys (column << 32 | t) by a bitonic network in
+// the warp's shared-memory buffer.  The first key of each run of equal
+// columns is a distinct column, in ascending order, and the rank of its run
+// is the slot of every candidate in the run.  Writes the distinct columns to
+// cols[inc_ptr[row] * NB ...] (scratch with room for every candidate), their
+// count, and each candidate's slot.  cap: keys per warp buffer (dynamic
+// shared memory, UNIQ_WARPS * cap keys), a power of two >= 32 holding the
+// mesh's longest candidate list, <= ROW_CAP.
+template <int NB, int SW>
+__global__ void __launch_bounds__(32 * UNIQ_WARPS) k_row_build(int64_t nrows, const int32_t* __restrict__ inc_ptr,
+                                                               const int32_t* __restrict__ inc,
+                                                               const int32_t* __restrict__ edof, int64_t E,
+                                                               int cap, int32_t* __restrict__ counts,
+                                                               int32_t* __restrict__ cols,
+                                                               uint8_t* __restrict__ slot, int* err) {
+  extern __shared__ unsigned long long sbuf[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int32_t* buf = sbuf[w];
+  unsigned long long* buf = sbuf + (size_t)w * cap;
   const int64_t nwarps = (int64_t)gridDim.x * UNIQ_WARPS;
   for (int64_t row = (int64_t)blockIdx.x * UNIQ_WARPS + w; row < nrows; row += nwarps) {
     const int32_t i0 = inc_ptr[row], i1 = inc_ptr[row + 1];
     const int k = (i1 - i0) * NB;
-    if (k > ROW_CAP) {
+    if (k > cap) {
       if (lane == 0) {
         atomicOr(err, DEV_ERR_OVERFLOW);
-        if (!col_idx) counts[row] = 0;
+        counts[row] = 0;
       }
       continue;
     }
     for (int t = lane; t < k; t += 32) {
       const int32_t p = inc[i0 + t / NB];
       const int64_t e = p / NB;
-      buf[t] = edof[(int64_t)(t % NB) * E + e];
+      const uint32_t d = (uint32_t)edof[(int64_t)(t % NB) * E + e];
+      buf[t] = ((unsigned long long)d << 32) | (uint32_t)t;
     }
-    // pad to a power of two with INT_MAX (sorts last) and sort the warp's
-    // buffer (bitonic network, compare-exchanges spread over the lanes)
+    // pad to a power of two with keys that sort last, then sort (the
+    // compare-exchanges of each stage spread over the lanes)
     int n2 = 32;
-    while (n2 < k) n2 <<= 1;  // <= ROW_CAP
-    for (int t = k + lane; t < n2; t += 32) buf[t] = 0x7FFFFFFF;
+    while (n2 < k) n2 <<= 1;  // <= cap
+    for (int t = k + lane; t < n2; t += 32) buf[t] = ~0ull;
     __syncwarp();
     for (int size = 2; size <= n2; size <<= 1)
       for (int stride = size >> 1; stride > 0; stride >>= 1) {
         for (int t = lane; t < (n2 >> 1); t += 32) {
           const int i = 2 * stride * (t / stride) + (t % stride), j = i + stride;
-          const int32_t a = buf[i], b = buf[j];
+          const unsigned long long a = buf[i], b = buf[j];
           if ((a > b) == ((i & size) == 0)) {
             buf[i] = b;
             buf[j] = a;
@@ -285,46 +292,44 @@ __global__ void __launch_bounds__(32 * UNIQ_WARPS) k_row_unique(int64_t nrows, c
         }
         __syncwarp();
       }
-    // the distinct columns in ascending order: first of each run
-    const int32_t base = col_idx ? row_ptr[row] : 0;
+    // runs of equal columns: the first of each is kept, every key gets the
+    // run's rank (the distinct columns before it)
+    const int64_t cbase = (int64_t)i0 * NB;
     int c = 0;
     for (int t0 = 0; t0 < k; t0 += 32) {
       const int t = t0 + lane;
-      const int32_t v = t < k ? buf[t] : 0;
-      const bool keep = t < k && (t == 0 || buf[t - 1] != v);
+      const unsigned long long key = t < k ? buf[t] : 0ull;
+      const uint32_t col = (uint32_t)(key >> 32);
+      const bool keep = t < k && (t == 0 || (uint32_t)(buf[t - 1] >> 32) != col);
       const unsigned mask = __ballot_sync(0xffffffffu, keep);
-      if (col_idx && keep) col_idx[base + c + __popc(mask & ((1u << lane) - 1u))] = v;
+      const int rank = c + __popc(mask & (0xffffffffu >> (31 - lane))) - 1;
+      if (t < k) {
+        if (keep) cols[cbase + rank] = (int32_t)col;
+        if (rank >= 255) {  // rows of more than 255 entries exceed the slot bytes
+          atomicOr(err, DEV_ERR_OVERFLOW);
+        } else {
+          const uint32_t o = (uint32_t)key;
+          slot[((int64_t)i0 + o / NB) * SW + o % NB] = (uint8_t)rank;
+        }
+      }
       c += __popc(mask);
     }
-    if (!col_idx && lane == 0) counts[row] = c;
+    if (lane == 0) counts[row] = c;
     __syncwarp();
   }
 }
 
-// Position of every local dof of each incidence inside the incidence's row.
-template <int NB, int SW>
-__global__ void k_slots(int64_t nrows, const int32_t* __restrict__ inc_ptr, const int32_t* __restrict__ inc,
-                        const int32_t* __restrict__ edof, int64_t E, const int32_t* __restrict__ rp,
-                        const int32_t* __restrict__ ci, uint8_t* __restrict__ slot, int* err) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nrows) return;
-  const int32_t lo = rp[r], len = rp[r + 1] - lo;
-  if (len > 255) {
-    atomicOr(err, DEV_ERR_OVERFLOW);
-    return;
-  }
-  for (int32_t i = inc_ptr[r]; i < inc_ptr[r + 1]; ++i) {
-    const int64_t e = inc[i] / NB;
-    for (int b = 0; b < NB; ++b) {
-      const int32_t c = edof[(int64_t)b * E + e];
-      int l = 0, h = len;
-      while (l < h) {
-        const int m = (l + h) >> 1;
-        if (ci[lo + m] < c) l = m + 1;
-        else h = m;
-      }
-      slot[(int64_t)i * SW + b] = (uint8_t)l;
-    }
+// col_idx of each row from the row's distinct columns in the scratch of
+// k_row_build; one warp per row.
+__global__ void k_cols_compact(int64_t nrows, const int32_t* __restrict__ inc_ptr, int nb,
+                               const int32_t* __restrict__ cols, const int32_t* __restrict__ rp,
+                               int32_t* __restrict__ ci) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < nrows; row += nwarps) {
+    const int32_t* src = cols + (int64_t)inc_ptr[row] * nb;
+    const int32_t lo = rp[row], len = rp[row + 1] - lo;
+    for (int32_t j = lane; j < len; j += 32) ci[lo + j] = src[j];
   }
 }
 
@@ -551,25 +556,34 @@ template <int NB>
 fea_status rows_and_slots(fea_mesh* m, Base* B, cudaStream_t s) {
   const int64_t n = B->nsd, E = m->n_elems;
   const int uniq_blocks = (int)std::min<int64_t>(std::max<int64_t>(1, (n + UNIQ_WARPS - 1) / UNIQ_WARPS), 152 * 64);
-  Tmp<int32_t> cnt;
+  constexpr int SW = NB <= 4 ? 4 : 16;
+  B->slot_width = SW;
+  FEA_TRY(dalloc(&B->slot, (size_t)E * NB * SW));
+  Tmp<int32_t> cnt, cols;
+  Tmp<int> mx;
   FEA_TRY(cnt.alloc(n));
-  k_row_unique<NB><<<uniq_blocks, 32 * UNIQ_WARPS, 0, s>>>(n, B->inc_ptr, B->inc, B->edof, E, nullptr, cnt.p,
-                                                           nullptr, m->err);
+  FEA_TRY(cols.alloc(std::max<size_t>((size_t)E * NB * NB, 1)));
+  FEA_TRY(mx.alloc(1));
+  // the sort buffers hold the longest candidate list (most incidences x NB)
+  FEA_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(int), s));
+  k_max_row<<<blocks_for(n, 256), 256, 0, s>>>(B->inc_ptr, n, mx.p);
+  int max_inc = 0;
+  FEA_CUDA(cudaMemcpyAsync(&max_inc, mx.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FEA_CUDA(cudaStreamSynchronize(s));
+  if ((int64_t)max_inc * NB > ROW_CAP)
+    return fail(FEA_ERR_OVERFLOW, "pattern: a row exceeds the scatter limits (more than 1024 candidate "
+                                  "couplings or more than 255 entries in a scalar row)");
+  int cap = 32;
+  while (cap < max_inc * NB) cap <<= 1;
+  const size_t smem = (size_t)UNIQ_WARPS * cap * sizeof(unsigned long long);
+  k_row_build<NB, SW><<<uniq_blocks, 32 * UNIQ_WARPS, smem, s>>>(n, B->inc_ptr, B->inc, B->edof, E, cap, cnt.p,
+                                                                 cols.p, B->slot, m->err);
   FEA_TRY(check_err(m, s, "pattern"));
   FEA_TRY(dalloc(&B->rp, n + 1));
   FEA_TRY(scan_to_ptr32(cnt.p, n, B->rp, &B->nnz, s, "nonzero"));
   FEA_TRY(dalloc(&B->ci, B->nnz));
-  k_row_unique<NB><<<uniq_blocks, 32 * UNIQ_WARPS, 0, s>>>(n, B->inc_ptr, B->inc, B->edof, E, B->rp, nullptr,
-                                                           B->ci, m->err);
-  FEA_TRY(check_err(m, s, "pattern"));
-  constexpr int SW = NB <= 4 ? 4 : 16;
-  B->slot_width = SW;
-  FEA_TRY(dalloc(&B->slot, (size_t)E * NB * SW));
-  k_slots<NB, SW><<<blocks_for(n, 128), 128, 0, s>>>(n, B->inc_ptr, B->inc, B->edof, E, B->rp, B->ci, B->slot,
-                                                    m->err);
-  FEA_TRY(check_err(m, s, "slots"));
-  Tmp<int> mx;
-  FEA_TRY(mx.alloc(1));
+  k_cols_compact<<<uniq_blocks, 32 * UNIQ_WARPS, 0, s>>>(n, B->inc_ptr, NB, cols.p, B->rp, B->ci);
+  FEA_CUDA(cudaGetLastError());
   FEA_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(int), s));
   k_max_row<<<blocks_for(n, 256), 256, 0, s>>>(B->rp, n, mx.p);
   FEA_CUDA(cudaMemcpyAsync(&B->max_row, mx.p, sizeof(int), cudaMemcpyDeviceToHost, s));

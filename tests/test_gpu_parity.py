@@ -141,6 +141,55 @@ def test_bad_index_rejected(torch_cuda):
     assert ei.value.status == 2
 
 
+def _fan(ntets):
+    """ntets tetrahedra sharing vertex 0 and nothing else, all positively
+    oriented: tet i = (0, 3i+1, 3i+2, 3i+3), its other three vertices a unit
+    corner far from vertex 0."""
+    pts = [np.zeros(3)]
+    tets = []
+    for i in range(ntets):
+        o = np.array([10 + 5 * np.cos(0.1 * i), 10 + 5 * np.sin(0.1 * i), 10 + 0.05 * i])
+        pts += [o + [1, 0, 0], o + [0, 1, 0], o + [0, 0, 1]]
+        tets.append([0, 3 * i + 1, 3 * i + 2, 3 * i + 3])
+    coords = np.ascontiguousarray(np.array(pts).T)
+    tets = np.ascontiguousarray(np.array(tets, dtype=np.int32).T)
+    # orient each tet positively
+    for e in range(ntets):
+        x = coords[:, tets[:, e]]
+        if np.linalg.det(x[:, 1:] - x[:, :1]) < 0:
+            tets[[1, 2], e] = tets[[2, 1], e]
+    return coords, tets
+
+
+def test_row_limits_raise_overflow_and_leave_the_mesh_usable(torch_cuda):
+    """The scatter's row limits: at most 1024 candidate couplings per scalar
+    row (incidences x local dofs) and at most 255 entries.  A vertex shared by
+    60 tets gives a P1 row of 181 entries (built, equal to the oracle's) and a
+    P2 row of 541 (FEA_ERR_OVERFLOW); 110 tets give 1100 P2 candidates (also
+    FEA_ERR_OVERFLOW).  The handle stays usable after each refusal."""
+    from paper_1802_03433_gb300 import fea
+    coords, tets = _fan(60)
+    m = fea.Mesh(coords, tets)
+    with pytest.raises(fea.FeaError) as ei:
+        m.pattern(2)
+    assert ei.value.status == 4
+    m.pattern(1)
+    rp, ci = m.pattern_tensors(1)
+    edof, nsd = oracle.dof_table(1, coords.shape[1], tets)
+    orp, oci = oracle.pattern(nsd, edof, ndpn=1)
+    np.testing.assert_array_equal(rp.cpu().numpy(), orp)
+    np.testing.assert_array_equal(ci.cpu().numpy(), oci)
+    m.check()
+    m.close()
+    coords, tets = _fan(110)
+    m = fea.Mesh(coords, tets)
+    with pytest.raises(fea.FeaError) as ei:
+        m.pattern(2)
+    assert ei.value.status == 4
+    m.check()
+    m.close()
+
+
 def test_inverted_element_flagged(torch_cuda):
     import torch
     from paper_1802_03433_gb300 import fea
