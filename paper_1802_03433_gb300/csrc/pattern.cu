@@ -239,14 +239,145 @@ __global__ void k_inc_sort(const int32_t* __restrict__ ptr, int64_t n, int32_t* 
 // ------------------------------------------------------------------ rows
 // One warp per scalar row, one pass: the row's candidate columns (the nb dofs
 // of each incident element, in incidence order t = incidence * NB + local
-// dof) are sorted as 64-bit keys (column << 32 | t) by a bitonic network in
-// the warp's shared-memory buffer.  The first key of each run of equal
-// columns is a distinct column, in ascending order, and the rank of its run
-// is the slot of every candidate in the run.  Writes the distinct columns to
-// cols[inc_ptr[row] * NB ...] (scratch with room for every candidate), their
-// count, and each candidate's slot.  cap: keys per warp buffer (dynamic
-// shared memory, UNIQ_WARPS * cap keys), a power of two >= 32 holding the
-// mesh's longest candidate list, <= ROW_CAP.
+// dof) are sorted as 64-bit keys (column << 32 | t) by a bitonic network.
+// The first key of each run of equal columns is a distinct column, in
+// ascending order, and the rank of its run is the slot of every candidate in
+// the run.  Writes the distinct columns to cols[inc_ptr[row] * NB ...]
+// (scratch with room for every candidate), their count, and each
+// candidate's slot.
+
+// Candidate t of a row as its sort key (t < k), or a key that sorts last.
+template <int NB>
+__device__ __forceinline__ unsigned long long row_key(int t, int k, int32_t i0, const int32_t* __restrict__ inc,
+                                                      const int32_t* __restrict__ edof, int64_t E) {
+  if (t >= k) return ~0ull;
+  const int64_t e = inc[i0 + t / NB] / NB;
+  const uint32_t d = (uint32_t)edof[(int64_t)(t % NB) * E + e];
+  return ((unsigned long long)d << 32) | (uint32_t)t;
+}
+
+// Outputs of one sorted key: the distinct column (first of its run) and the
+// candidate's slot (its run's rank; rows past 255 entries are refused).
+template <int NB, int SW>
+__device__ __forceinline__ void row_emit(unsigned long long key, bool keep, int rank, int32_t i0, int32_t* cols,
+                                         int64_t cbase, uint8_t* slot, int* err) {
+  if (keep) cols[cbase + rank] = (int32_t)(key >> 32);
+  if (rank >= 255) {  // rows of more than 255 entries exceed the slot bytes
+    atomicOr(err, DEV_ERR_OVERFLOW);
+  } else {
+    const uint32_t o = (uint32_t)key;
+    slot[((int64_t)i0 + o / NB) * SW + o % NB] = (uint8_t)rank;
+  }
+}
+
+// Rows of up to 32 * R candidates, in registers: lane L holds sorted
+// positions L * R .. L * R + R - 1.  Compare-exchanges within a lane for
+// strides below R, across lanes by shuffles above.  Returns the count of
+// distinct columns.
+template <int NB, int SW, int R>
+__device__ __forceinline__ int row_build_reg(int k, int32_t i0, const int32_t* __restrict__ inc,
+                                             const int32_t* __restrict__ edof, int64_t E, int32_t* cols,
+                                             uint8_t* slot, int* err) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long key[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) key[r] = row_key<NB>(lane * R + r, k, i0, inc, edof, E);
+#pragma unroll
+  for (int size = 2; size <= 32 * R; size <<= 1) {
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      if (stride < R) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          if ((r & stride) == 0) {
+            const bool asc = ((lane * R + r) & size) == 0;
+            const unsigned long long a = key[r], b = key[r | stride];
+            const bool sw = (a > b) == asc;
+            key[r] = sw ? b : a;
+            key[r | stride] = sw ? a : b;
+          }
+        }
+      } else {
+        const int ls = stride / R;
+        const bool lower = (lane & ls) == 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const bool asc = ((lane * R + r) & size) == 0;
+          const unsigned long long o = __shfl_xor_sync(0xffffffffu, key[r], ls);
+          const bool take_min = lower == asc;
+          key[r] = take_min ? (o < key[r] ? o : key[r]) : (o > key[r] ? o : key[r]);
+        }
+      }
+    }
+  }
+  // run starts: the previous position is in this lane, or the last of the
+  // lane before
+  const unsigned long long before = __shfl_up_sync(0xffffffffu, key[R - 1], 1);
+  bool keep[R];
+  int pre[R], nkeep = 0;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = lane * R + r;
+    const uint32_t prev = (uint32_t)((r == 0 ? before : key[r - 1]) >> 32);
+    keep[r] = i < k && (i == 0 || prev != (uint32_t)(key[r] >> 32));
+    nkeep += keep[r];
+    pre[r] = nkeep;
+  }
+  int incl = nkeep;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const int64_t cbase = (int64_t)i0 * NB;
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (lane * R + r < k) row_emit<NB, SW>(key[r], keep[r], incl - nkeep + pre[r] - 1, i0, cols, cbase, slot, err);
+  return __shfl_sync(0xffffffffu, incl, 31);
+}
+
+// Rows of up to `cap` candidates (a power of two <= ROW_CAP) in the warp's
+// shared-memory buffer, the same network with the lanes striding over each
+// stage's compare-exchanges.
+template <int NB, int SW>
+__device__ __forceinline__ int row_build_smem(int k, int32_t i0, const int32_t* __restrict__ inc,
+                                              const int32_t* __restrict__ edof, int64_t E, int32_t* cols,
+                                              uint8_t* slot, int* err, unsigned long long* buf) {
+  const int lane = threadIdx.x & 31;
+  int n2 = 32;
+  while (n2 < k) n2 <<= 1;
+  for (int t = lane; t < n2; t += 32) buf[t] = row_key<NB>(t, k, i0, inc, edof, E);
+  __syncwarp();
+  for (int size = 2; size <= n2; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = lane; t < (n2 >> 1); t += 32) {
+        const int i = 2 * stride * (t / stride) + (t % stride), j = i + stride;
+        const unsigned long long a = buf[i], b = buf[j];
+        if ((a > b) == ((i & size) == 0)) {
+          buf[i] = b;
+          buf[j] = a;
+        }
+      }
+      __syncwarp();
+    }
+  const int64_t cbase = (int64_t)i0 * NB;
+  int c = 0;
+  for (int t0 = 0; t0 < k; t0 += 32) {
+    const int t = t0 + lane;
+    const unsigned long long key = t < k ? buf[t] : 0ull;
+    const bool keep = t < k && (t == 0 || (uint32_t)(buf[t - 1] >> 32) != (uint32_t)(key >> 32));
+    const unsigned mask = __ballot_sync(0xffffffffu, keep);
+    if (t < k) row_emit<NB, SW>(key, keep, c + __popc(mask & (0xffffffffu >> (31 - lane))) - 1, i0, cols, cbase, slot, err);
+    c += __popc(mask);
+  }
+  __syncwarp();
+  return c;
+}
+
+// cap: the mesh's longest candidate list rounded up to a power of two >= 32
+// (<= ROW_CAP).  Rows of up to 256 candidates sort in registers; above that
+// in the warp's buffer of the dynamic shared memory (UNIQ_WARPS * cap keys,
+// present only when cap > 256).
 template <int NB, int SW>
 __global__ void __launch_bounds__(32 * UNIQ_WARPS) k_row_build(int64_t nrows, const int32_t* __restrict__ inc_ptr,
                                                                const int32_t* __restrict__ inc,
@@ -256,66 +387,26 @@ __global__ void __launch_bounds__(32 * UNIQ_WARPS) k_row_build(int64_t nrows, co
                                                                uint8_t* __restrict__ slot, int* err) {
   extern __shared__ unsigned long long sbuf[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  unsigned long long* buf = sbuf + (size_t)w * cap;
   const int64_t nwarps = (int64_t)gridDim.x * UNIQ_WARPS;
   for (int64_t row = (int64_t)blockIdx.x * UNIQ_WARPS + w; row < nrows; row += nwarps) {
     const int32_t i0 = inc_ptr[row], i1 = inc_ptr[row + 1];
     const int k = (i1 - i0) * NB;
+    int c;
     if (k > cap) {
-      if (lane == 0) {
-        atomicOr(err, DEV_ERR_OVERFLOW);
-        counts[row] = 0;
-      }
-      continue;
-    }
-    for (int t = lane; t < k; t += 32) {
-      const int32_t p = inc[i0 + t / NB];
-      const int64_t e = p / NB;
-      const uint32_t d = (uint32_t)edof[(int64_t)(t % NB) * E + e];
-      buf[t] = ((unsigned long long)d << 32) | (uint32_t)t;
-    }
-    // pad to a power of two with keys that sort last, then sort (the
-    // compare-exchanges of each stage spread over the lanes)
-    int n2 = 32;
-    while (n2 < k) n2 <<= 1;  // <= cap
-    for (int t = k + lane; t < n2; t += 32) buf[t] = ~0ull;
-    __syncwarp();
-    for (int size = 2; size <= n2; size <<= 1)
-      for (int stride = size >> 1; stride > 0; stride >>= 1) {
-        for (int t = lane; t < (n2 >> 1); t += 32) {
-          const int i = 2 * stride * (t / stride) + (t % stride), j = i + stride;
-          const unsigned long long a = buf[i], b = buf[j];
-          if ((a > b) == ((i & size) == 0)) {
-            buf[i] = b;
-            buf[j] = a;
-          }
-        }
-        __syncwarp();
-      }
-    // runs of equal columns: the first of each is kept, every key gets the
-    // run's rank (the distinct columns before it)
-    const int64_t cbase = (int64_t)i0 * NB;
-    int c = 0;
-    for (int t0 = 0; t0 < k; t0 += 32) {
-      const int t = t0 + lane;
-      const unsigned long long key = t < k ? buf[t] : 0ull;
-      const uint32_t col = (uint32_t)(key >> 32);
-      const bool keep = t < k && (t == 0 || (uint32_t)(buf[t - 1] >> 32) != col);
-      const unsigned mask = __ballot_sync(0xffffffffu, keep);
-      const int rank = c + __popc(mask & (0xffffffffu >> (31 - lane))) - 1;
-      if (t < k) {
-        if (keep) cols[cbase + rank] = (int32_t)col;
-        if (rank >= 255) {  // rows of more than 255 entries exceed the slot bytes
-          atomicOr(err, DEV_ERR_OVERFLOW);
-        } else {
-          const uint32_t o = (uint32_t)key;
-          slot[((int64_t)i0 + o / NB) * SW + o % NB] = (uint8_t)rank;
-        }
-      }
-      c += __popc(mask);
+      if (lane == 0) atomicOr(err, DEV_ERR_OVERFLOW);
+      c = 0;
+    } else if (k <= 32) {
+      c = row_build_reg<NB, SW, 1>(k, i0, inc, edof, E, cols, slot, err);
+    } else if (k <= 64) {
+      c = row_build_reg<NB, SW, 2>(k, i0, inc, edof, E, cols, slot, err);
+    } else if (k <= 128) {
+      c = row_build_reg<NB, SW, 4>(k, i0, inc, edof, E, cols, slot, err);
+    } else if (k <= 256) {
+      c = row_build_reg<NB, SW, 8>(k, i0, inc, edof, E, cols, slot, err);
+    } else {
+      c = row_build_smem<NB, SW>(k, i0, inc, edof, E, cols, slot, err, sbuf + (size_t)w * cap);
     }
     if (lane == 0) counts[row] = c;
-    __syncwarp();
   }
 }
 
@@ -575,7 +666,7 @@ fea_status rows_and_slots(fea_mesh* m, Base* B, cudaStream_t s) {
                                   "couplings or more than 255 entries in a scalar row)");
   int cap = 32;
   while (cap < max_inc * NB) cap <<= 1;
-  const size_t smem = (size_t)UNIQ_WARPS * cap * sizeof(unsigned long long);
+  const size_t smem = cap > 256 ? (size_t)UNIQ_WARPS * cap * sizeof(unsigned long long) : 0;
   k_row_build<NB, SW><<<uniq_blocks, 32 * UNIQ_WARPS, smem, s>>>(n, B->inc_ptr, B->inc, B->edof, E, cap, cnt.p,
                                                                  cols.p, B->slot, m->err);
   FEA_TRY(check_err(m, s, "pattern"));
