@@ -202,6 +202,43 @@ __global__ void k_validate(const int32_t* __restrict__ tets, int64_t E, int64_t 
   if (bad) atomicOr(err, DEV_ERR_INDEX);
 }
 
+// ------------------------------------------------------------------ warp sort
+// Bitonic sort of 32 * R keys held R per lane (lane L holds sorted positions
+// L * R .. L * R + R - 1), ascending: compare-exchanges within a lane for
+// strides below R, across lanes by shuffles above.
+template <typename T, int R>
+__device__ __forceinline__ void warp_sort_reg(T (&key)[R]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int size = 2; size <= 32 * R; size <<= 1) {
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      if (stride < R) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          if ((r & stride) == 0) {
+            const bool asc = ((lane * R + r) & size) == 0;
+            const T a = key[r], b = key[r | stride];
+            const bool sw = (a > b) == asc;
+            key[r] = sw ? b : a;
+            key[r | stride] = sw ? a : b;
+          }
+        }
+      } else {
+        const int ls = stride / R;
+        const bool lower = (lane & ls) == 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const bool asc = ((lane * R + r) & size) == 0;
+          const T o = __shfl_xor_sync(0xffffffffu, key[r], ls);
+          const bool take_min = lower == asc;
+          key[r] = take_min ? (o < key[r] ? o : key[r]) : (o > key[r] ? o : key[r]);
+        }
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------ incidences
 __global__ void k_inc_count(const int32_t* __restrict__ edof, int64_t n, int32_t* __restrict__ cnt) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -220,19 +257,48 @@ __global__ void k_inc_fill(const int32_t* __restrict__ edof, int64_t E, int nb,
   inc[pos] = (int32_t)(e * nb + a);
 }
 
-// Insertion sort of every dof's incidence list (ascending element id).
-__global__ void k_inc_sort(const int32_t* __restrict__ ptr, int64_t n, int32_t* __restrict__ inc) {
-  const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (d >= n) return;
-  const int32_t b = ptr[d], e = ptr[d + 1];
-  for (int32_t i = b + 1; i < e; ++i) {
-    const int32_t v = inc[i];
-    int32_t j = i - 1;
-    while (j >= b && inc[j] > v) {
-      inc[j + 1] = inc[j];
-      --j;
+// Every dof's incidence list in ascending element id, one warp per dof: lists
+// of up to 256 sort in registers (warp_sort_reg), longer ones by insertion
+// sort in lane 0.
+template <int R>
+__device__ __forceinline__ void inc_sort_reg(int32_t* __restrict__ list, int len) {
+  const int lane = threadIdx.x & 31;
+  int32_t key[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) key[r] = lane * R + r < len ? list[lane * R + r] : 0x7FFFFFFF;
+  warp_sort_reg<int32_t, R>(key);
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (lane * R + r < len) list[lane * R + r] = key[r];
+}
+
+__global__ void __launch_bounds__(128) k_inc_sort(const int32_t* __restrict__ ptr, int64_t n, int32_t* __restrict__ inc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t d = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; d < n; d += nwarps) {
+    const int32_t b = ptr[d], len = ptr[d + 1] - b;
+    int32_t* list = inc + b;
+    if (len <= 1) continue;
+    if (len <= 32) {
+      inc_sort_reg<1>(list, len);
+    } else if (len <= 64) {
+      inc_sort_reg<2>(list, len);
+    } else if (len <= 128) {
+      inc_sort_reg<4>(list, len);
+    } else if (len <= 256) {
+      inc_sort_reg<8>(list, len);
+    } else if (lane == 0) {
+      for (int32_t i = 1; i < len; ++i) {
+        const int32_t v = list[i];
+        int32_t j = i - 1;
+        while (j >= 0 && list[j] > v) {
+          list[j + 1] = list[j];
+          --j;
+        }
+        list[j + 1] = v;
+      }
     }
-    inc[j + 1] = v;
+    __syncwarp();
   }
 }
 
@@ -270,10 +336,8 @@ __device__ __forceinline__ void row_emit(unsigned long long key, bool keep, int 
   }
 }
 
-// Rows of up to 32 * R candidates, in registers: lane L holds sorted
-// positions L * R .. L * R + R - 1.  Compare-exchanges within a lane for
-// strides below R, across lanes by shuffles above.  Returns the count of
-// distinct columns.
+// Rows of up to 32 * R candidates, in registers (warp_sort_reg).  Returns the
+// count of distinct columns.
 template <int NB, int SW, int R>
 __device__ __forceinline__ int row_build_reg(int k, int32_t i0, const int32_t* __restrict__ inc,
                                              const int32_t* __restrict__ edof, int64_t E, int32_t* cols,
@@ -282,34 +346,7 @@ __device__ __forceinline__ int row_build_reg(int k, int32_t i0, const int32_t* _
   unsigned long long key[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) key[r] = row_key<NB>(lane * R + r, k, i0, inc, edof, E);
-#pragma unroll
-  for (int size = 2; size <= 32 * R; size <<= 1) {
-#pragma unroll
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      if (stride < R) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          if ((r & stride) == 0) {
-            const bool asc = ((lane * R + r) & size) == 0;
-            const unsigned long long a = key[r], b = key[r | stride];
-            const bool sw = (a > b) == asc;
-            key[r] = sw ? b : a;
-            key[r | stride] = sw ? a : b;
-          }
-        }
-      } else {
-        const int ls = stride / R;
-        const bool lower = (lane & ls) == 0;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const bool asc = ((lane * R + r) & size) == 0;
-          const unsigned long long o = __shfl_xor_sync(0xffffffffu, key[r], ls);
-          const bool take_min = lower == asc;
-          key[r] = take_min ? (o < key[r] ? o : key[r]) : (o > key[r] ? o : key[r]);
-        }
-      }
-    }
-  }
+  warp_sort_reg<unsigned long long, R>(key);
   // run starts: the previous position is in this lane, or the last of the
   // lane before
   const unsigned long long before = __shfl_up_sync(0xffffffffu, key[R - 1], 1);
@@ -504,14 +541,18 @@ __global__ void k_expand_rowptr(const int32_t* __restrict__ rp, int64_t N, int n
   rp3[r] = (int32_t)((int64_t)ndpn * ndpn * rp[a] + ndpn * c * (int64_t)(rp[a + 1] - rp[a]));
 }
 
+// Columns of the ndpn x ndpn block expansion, one warp per expanded row
+// (coalesced stores).
 __global__ void k_expand_cols(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int64_t N, int ndpn,
                               const int32_t* __restrict__ rp3, int32_t* __restrict__ ci3) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= N * ndpn) return;
-  const int64_t a = r / ndpn;
-  int32_t o = rp3[r];
-  for (int32_t p = rp[a]; p < rp[a + 1]; ++p)
-    for (int d = 0; d < ndpn; ++d) ci3[o++] = ndpn * ci[p] + d;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < N * ndpn; r += nwarps) {
+    const int64_t a = r / ndpn;
+    const int32_t p0 = rp[a], len = (rp[a + 1] - p0) * ndpn;
+    int32_t* out = ci3 + rp3[r];
+    for (int32_t j = lane; j < len; j += 32) out[j] = ndpn * ci[p0 + j / ndpn] + j % ndpn;
+  }
 }
 
 // ------------------------------------------------------------------ ipos
@@ -696,7 +737,7 @@ fea_status incidences(fea_mesh* m, Base* B, cudaStream_t s) {
   FEA_TRY(scan_to_ptr32(cnt.p, n, B->inc_ptr, &tot, s, "incidence"));
   FEA_TRY(dalloc(&B->inc, nI));
   k_inc_fill<<<blocks_for(nI, 256), 256, 0, s>>>(B->edof, E, B->nb, B->inc_ptr, cur.p, B->inc);
-  k_inc_sort<<<blocks_for(n, 128), 128, 0, s>>>(B->inc_ptr, n, B->inc);
+  k_inc_sort<<<(int)std::min<int64_t>(blocks_for(n, 4), 152 * 64), 128, 0, s>>>(B->inc_ptr, n, B->inc);
   FEA_TRY(dalloc(&B->ipos, nI));
   k_ipos<<<blocks_for(nI, 256), 256, 0, s>>>(nI, B->nb, E, B->inc, B->ipos);
   FEA_CUDA(cudaGetLastError());
@@ -815,7 +856,8 @@ fea_status build_pattern(fea_mesh* m, int order, int ndpn, cudaStream_t s) {
       if ((st = dalloc(&P->row_ptr, P->ndof + 1)) != FEA_OK) break;
       if ((st = dalloc(&P->col_idx, nnz)) != FEA_OK) break;
       k_expand_rowptr<<<blocks_for(P->ndof + 1, 256), 256, 0, s>>>(B->rp, B->nsd, ndpn, P->row_ptr);
-      k_expand_cols<<<blocks_for(P->ndof, 128), 128, 0, s>>>(B->rp, B->ci, B->nsd, ndpn, P->row_ptr, P->col_idx);
+      k_expand_cols<<<(int)std::min<int64_t>(blocks_for(P->ndof, 4), 152 * 64), 128, 0, s>>>(B->rp, B->ci, B->nsd, ndpn,
+                                                                                           P->row_ptr, P->col_idx);
     }
     // gather tiles: as many rows per CTA (<= 128) as keep the tile's CSR span
     // within the shared-memory budget
