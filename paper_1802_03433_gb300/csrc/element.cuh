@@ -900,7 +900,8 @@ __device__ __forceinline__ R p2_stiff(const R G[4][4], R c) {
 // 25 * 2^56 < 2^61.  The sums are then exact and each entry is rounded once,
 // on the way back to FP64: its error is at most 28 * 2^-55 of the largest
 // input (the rounded inputs, 28 units of 2^-p) plus half an ulp of the entry
-// (a bit-exact model checked this on random inputs).  For E outside
+// (tests/test_p2_fixed_point_model.py checks a bit-exact host model of this
+// arithmetic against exact sums across the exponent range).  For E outside
 // [P2FX_EMIN, P2FX_EMAX] (non-finite or vanishing inputs) the kernels keep
 // the FP64 chains; inside it the results stay normal FP64 numbers.
 constexpr int P2FX_EMIN = 64, P2FX_EMAX = 2032;
