@@ -306,7 +306,8 @@ __device__ __forceinline__ void elem_roles_body(const ElemArgs& A, int64_t e, bo
 
 // Three resident blocks per SM (80 registers, about 350 bytes spilled to L1):
 // the extra warps hide more of the fixed-latency dependencies than the spills
-// cost (P2 64^3: 0.71 ms against 0.82 ms for two blocks).
+// cost (P2 64^3: 0.71 ms against 0.82 ms for two blocks; four blocks at 64
+// registers spill about 670 bytes and take 0.76 ms).
 constexpr int ROLES_MIN_BLOCKS = 3;
 
 template <int ORDER, bool MASS, int LOAD, int NPTS>

@@ -541,17 +541,18 @@ __global__ void k_expand_rowptr(const int32_t* __restrict__ rp, int64_t N, int n
   rp3[r] = (int32_t)((int64_t)ndpn * ndpn * rp[a] + ndpn * c * (int64_t)(rp[a + 1] - rp[a]));
 }
 
-// Columns of the ndpn x ndpn block expansion, one warp per expanded row
+// Columns of the NDPN x NDPN block expansion, one warp per expanded row
 // (coalesced stores).
-__global__ void k_expand_cols(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int64_t N, int ndpn,
+template <int NDPN>
+__global__ void k_expand_cols(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int64_t N,
                               const int32_t* __restrict__ rp3, int32_t* __restrict__ ci3) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < N * ndpn; r += nwarps) {
-    const int64_t a = r / ndpn;
-    const int32_t p0 = rp[a], len = (rp[a + 1] - p0) * ndpn;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < N * NDPN; r += nwarps) {
+    const int64_t a = r / NDPN;
+    const int32_t p0 = rp[a], len = (rp[a + 1] - p0) * NDPN;
     int32_t* out = ci3 + rp3[r];
-    for (int32_t j = lane; j < len; j += 32) out[j] = ndpn * ci[p0 + j / ndpn] + j % ndpn;
+    for (int32_t j = lane; j < len; j += 32) out[j] = NDPN * ci[p0 + j / NDPN] + j % NDPN;
   }
 }
 
@@ -856,8 +857,8 @@ fea_status build_pattern(fea_mesh* m, int order, int ndpn, cudaStream_t s) {
       if ((st = dalloc(&P->row_ptr, P->ndof + 1)) != FEA_OK) break;
       if ((st = dalloc(&P->col_idx, nnz)) != FEA_OK) break;
       k_expand_rowptr<<<blocks_for(P->ndof + 1, 256), 256, 0, s>>>(B->rp, B->nsd, ndpn, P->row_ptr);
-      k_expand_cols<<<(int)std::min<int64_t>(blocks_for(P->ndof, 4), 152 * 64), 128, 0, s>>>(B->rp, B->ci, B->nsd, ndpn,
-                                                                                           P->row_ptr, P->col_idx);
+      k_expand_cols<3><<<(int)std::min<int64_t>(blocks_for(P->ndof, 4), 152 * 64), 128, 0, s>>>(B->rp, B->ci, B->nsd,
+                                                                                              P->row_ptr, P->col_idx);
     }
     // gather tiles: as many rows per CTA (<= 128) as keep the tile's CSR span
     // within the shared-memory budget
