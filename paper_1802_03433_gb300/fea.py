@@ -391,9 +391,14 @@ class Batch:
         fea_batch_bind(self.h, coeffs, self.values, self.rhs if with_rhs else None)
 
     def tune(self, stream=None):
+        """Time the launch parameters on these meshes, keep the fastest and
+        return them: (elements per item, P2 element CTAs, P1 element CTAs,
+        scatter CTAs, P2 register variant, P1 register variant)."""
         return fea_batch_tune(self.h, stream)
 
     def assemble(self, stream=None):
+        """Assemble every mesh into values[k] / rhs[k] with one graph launch
+        (asynchronous on `stream`)."""
         fea_batch_assemble(self.h, stream)
 
     def close(self):
@@ -427,16 +432,21 @@ class Mesh:
         self._pat = {}
 
     def set_coords(self, x, y, z):
+        """Point the handle at new device coordinates (same node count); the
+        pattern and scatter structures are kept."""
         self.x, self.y, self.z = x, y, z
         fea_mesh_set_coords(self.h, x, y, z)
 
     def pattern(self, order=1, dofs_per_node=1):
+        """Build (once, cached) the CSR pattern of this order; returns
+        (ndof, nnz)."""
         key = (order, dofs_per_node)
         if key not in self._pat:
             self._pat[key] = fea_pattern(self.h, order, dofs_per_node)
         return self._pat[key]
 
     def pattern_tensors(self, order=1, dofs_per_node=1):
+        """(row_ptr, col_idx) of the pattern as int32 device tensors."""
         ndof, nnz = self.pattern(order, dofs_per_node)
         rp = torch.empty(ndof + 1, dtype=torch.int32, device=self.x.device)
         ci = torch.empty(max(nnz, 1), dtype=torch.int32, device=self.x.device)
@@ -444,6 +454,8 @@ class Mesh:
         return rp, ci[:nnz]
 
     def dof_table(self, order=1):
+        """Element -> scalar dof table, int32 (nb, E) on the device (P2: the
+        four vertex dofs, then the six edge dofs)."""
         self.pattern(order, 1)
         nb = self.tets.shape[0] if order == 1 else 10
         ed = torch.empty((nb, self.n_elems), dtype=torch.int32, device=self.x.device)
@@ -452,6 +464,9 @@ class Mesh:
         return ed
 
     def assemble(self, form, coeffs, quad, values=None, rhs=None, with_rhs=True, stream=None):
+        """Assemble the CSR values and the load vector of `form`; returns
+        (values[:nnz], rhs) as FP64 device tensors (allocated unless given).
+        Asynchronous on `stream`; device-side faults surface at check()."""
         ndpn = 3 if form.kind == FEA_ELASTICITY else 1
         ndof, nnz = self.pattern(form.order, ndpn)
         dev = self.x.device
@@ -463,6 +478,8 @@ class Mesh:
         return values[:nnz], rhs
 
     def assemble_2d(self, form2d, values=None, rhs=None, with_rhs=True, stream=None):
+        """The paper's 2-D form on a triangle mesh (make_form2d); returns
+        (values[:nnz], rhs)."""
         ndof, nnz = self.pattern(1, 1)
         if values is None:
             values = torch.empty(max(nnz, 1), dtype=torch.float64, device=self.x.device)
@@ -472,6 +489,8 @@ class Mesh:
         return values[:nnz], rhs
 
     def check(self, stream=None):
+        """Synchronise and raise FeaError for a fault latched by earlier
+        calls (bad index, det J <= 0, timeout)."""
         fea_mesh_check(self.h, stream)
 
     def close(self):
