@@ -182,6 +182,16 @@ def max_over_ranks(value, device="cpu"):
     return t.item()
 
 
+# Clock-event reasons that reject a timed region (sw_power_cap is kept and
+# noted: a dense kernel on a 1.4 kW part may run at the power cap).
+THROTTLE_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
+
+
+def throttled(clk):
+    """Whether the clock record of a timed region rejects its number."""
+    return bool(clk) and any(r in clk.get("reasons", ()) for r in THROTTLE_REASONS)
+
+
 def weak_scaling_value(world_size, units_per_rank, steps, total_ms):
     """Whole-job throughput: every rank processes its own units each step."""
     return world_size * units_per_rank * steps / (total_ms / 1e3)
@@ -267,6 +277,13 @@ def run_ours(args):
 
     clocks = ClockSampler(local) if rank == 0 else None
     total_ms, step_ms, phase, clk = timed_loop(fea.FEA_FP64, args.steps, args.warmup, clocks)
+    # a slowdown seen during the timed region rejects it: measure once more
+    # (every rank takes the same decision; the loop has barriers)
+    if max_over_ranks(1.0 if throttled(clk) else 0.0, dev) > 0.0:
+        first = clk
+        total_ms, step_ms, phase, clk = timed_loop(fea.FEA_FP64, args.steps, args.warmup, clocks)
+        if clk is not None:
+            clk = dict(clk, remeasured_after=first.get("reasons", []) if first else [])
     value = weak_scaling_value(ws, E, args.steps, total_ms)
     elem_ms = statistics.mean(p[0] for p in phase)
     scat_ms = statistics.mean(p[1] for p in phase)

@@ -60,6 +60,18 @@ def _run_bench(args, env_extra=None):
                           env=env, timeout=600, cwd=ROOT)
 
 
+def test_throttle_rule():
+    """Hardware and thermal slowdowns reject a timed region; the power cap
+    alone does not."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert not bench.throttled(None)
+    assert not bench.throttled({"reasons": []})
+    assert not bench.throttled({"reasons": ["sw_power_cap"]})
+    for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"):
+        assert bench.throttled({"reasons": ["sw_power_cap", r]})
+
+
 def test_reference_arm_prints_one_json_line():
     r = _run_bench(["--impl", "reference", "--steps", "2", "--warmup", "3"])
     assert r.returncode == 0, r.stderr
