@@ -234,16 +234,23 @@ fea_status fea_assemble_2d(fea_mesh* mesh, const fea_form2d* form, double* value
  * this is a deployment variant).  For callers that cannot let a library
  * call cudaMalloc - a process whose device memory is reserved by another
  * allocator, or a latency-critical loop that cannot afford the device
- * synchronisation cudaMalloc/cudaFree imply.  Same arguments, kernels and
- * results as fea_assemble, but the per-call scratch (local rows and local
- * loads) lives in one fixed 32 MiB device array inside the library instead
- * of the mesh handle: about 200 K P1 scalar elements, 32 K P2 elements or
- * 25 K P1 elasticity elements in FP64.  Larger meshes are rejected with
- * FEA_ERR_ARG before anything runs.
- *  - The array is held by every device that loads the library until the
- *    process exits.  Its device address is looked up (cudaGetSymbolAddress)
- *    on the first call on each device, with that device current; make that
- *    first call before any stream capture.
+ * synchronisation cudaMalloc/cudaFree imply.  Same arguments, argument
+ * checks and results as fea_assemble with the local-row scatter (values
+ * within the FP64 tolerance of the oracle, bitwise equal to fea_assemble
+ * whenever fea_assemble uses the same element and scatter launches).  It
+ * always runs the fused element kernel and the automatic local-row scatter:
+ * the load-split, stage and scatter-algorithm settings of the mesh do not
+ * apply to it.  The per-call scratch (local rows and local loads) lives in
+ * one fixed 32 MiB device array inside the library instead of the mesh
+ * handle: about 200 K P1 scalar elements, 32 K P2 elements or 25 K P1
+ * elasticity elements in FP64.  Larger meshes are rejected with FEA_ERR_ARG
+ * before anything runs, as are misaligned or NULL arguments.
+ *  - The array is taken on a device by the first call there (CUDA loads the
+ *    library's module lazily), when its address is looked up with
+ *    cudaGetSymbolAddress, with that device current; make that first call
+ *    before any stream capture and before another allocator reserves the
+ *    device's memory (FEA_ERR_NOMEM otherwise).  The device then holds it
+ *    until the process exits.
  *  - Every call shares the array and it keeps the last call's contents;
  *    nothing in it needs clearing (every value is written before it is read).
  *    Calls whose kernels overlap on the GPU (other streams, other threads)

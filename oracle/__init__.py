@@ -149,12 +149,12 @@ def local(X, order=1, kind="diffusion", mass=0.0, kappa=None, lam=None, mu=None,
     return Ke, Fe, det
 
 
-def rows(coords, tets, order, edof, rows_, kind="diffusion", mass=0.0, kappa=None,
-         kappa_const=1.0, lam=None, lam_const=1.0, mu=None, mu_const=1.0, f_kind="sinprod",
-         f_param=(3 * np.pi ** 2,), npts=4):
-    """Selected assembled rows by brute force (no pattern needed).
-
-    Returns dict row -> (cols int64 ascending, vals), and rhs per row."""
+def rows_arrays(coords, tets, order, edof, rows_, kind="diffusion", mass=0.0, kappa=None,
+                kappa_const=1.0, lam=None, lam_const=1.0, mu=None, mu_const=1.0, f_kind="sinprod",
+                f_param=(3 * np.pi ** 2,), npts=4):
+    """Selected assembled rows by brute force (no pattern needed), as flat
+    arrays: (rows int64, cols int64, vals) sorted by (row, col), the rows
+    asked for (ascending, unique), and their load entries."""
     coords = np.ascontiguousarray(coords, dtype=np.float64)
     tets = np.ascontiguousarray(tets, dtype=np.int32)
     edof = np.ascontiguousarray(edof, dtype=np.int32)
@@ -177,10 +177,17 @@ def rows(coords, tets, order, edof, rows_, kind="diffusion", mass=0.0, kappa=Non
     v = np.ctypeslib.as_array(V, shape=(max(n, 1),))[:n].copy()
     for p in (R, Cc, V):
         lib().orc_free(C.cast(p, C.c_void_p))
-    out = {}
-    for i, row in enumerate(rr):
-        m = r == row
-        out[int(row)] = (c[m], v[m])
+    return r, c, v, rr, rhs
+
+
+def rows(coords, tets, order, edof, rows_, **kw):
+    """Selected assembled rows by brute force (no pattern needed).
+
+    Returns dict row -> (cols int64 ascending, vals), and rhs per row."""
+    r, c, v, rr, rhs = rows_arrays(coords, tets, order, edof, rows_, **kw)
+    lo = np.searchsorted(r, rr, side="left")
+    hi = np.searchsorted(r, rr, side="right")
+    out = {int(row): (c[a:b], v[a:b]) for row, a, b in zip(rr, lo, hi)}
     return out, dict(zip(rr.tolist(), rhs.tolist()))
 
 

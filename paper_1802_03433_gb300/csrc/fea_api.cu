@@ -55,8 +55,6 @@ fea_status read_and_clear_err(fea_mesh* m, cudaStream_t s) {
   return FEA_OK;
 }
 
-namespace {
-
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 fea_status check_form(const fea_mesh* m, const fea_form* f, const fea_coeffs* c, const fea_quadrature* q) {
@@ -74,7 +72,6 @@ fea_status check_form(const fea_mesh* m, const fea_form* f, const fea_coeffs* c,
   return FEA_OK;
 }
 
-}  // namespace
 }  // namespace fea
 
 using namespace fea;

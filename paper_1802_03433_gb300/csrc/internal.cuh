@@ -147,6 +147,12 @@ fea_status assemble_backward(fea_mesh* m, const fea_form* form, const fea_coeffs
                              const fea_quadrature* q, const double* gv, const double* gf,
                              double* gk, double* gx, cudaStream_t s);
 
+// argument checks shared by the assembly entry points (fea_api.cu): NULL
+// pointers, order / kind / rule / precision / load codes, 8-byte alignment
+// of the coefficient arrays
+bool aligned(const void* p, size_t a);
+fea_status check_form(const fea_mesh* m, const fea_form* f, const fea_coeffs* c, const fea_quadrature* q);
+
 // scratch management (fea_api.cu)
 fea_status ensure_scratch(Scratch& sc, size_t bytes);
 fea_status read_and_clear_err(fea_mesh* m, cudaStream_t s);

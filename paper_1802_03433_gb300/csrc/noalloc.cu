@@ -9,10 +9,14 @@
 // fixed file-scope device array (NOALLOC_SCRATCH_BYTES) instead of the mesh
 // handle's scratch, so the call itself allocates nothing.
 //
-// The array exists once per device for every process that loads the library
-// and is held until the process exits.  Its device address is looked up with
-// cudaGetSymbolAddress on the first call on each device (with that device
-// current) and cached.  Every call shares the array, and the array keeps the
+// The array belongs to the library's module for this file.  CUDA loads a
+// module on a device when it is first needed (lazy loading), so the array's
+// 32 MiB are taken on a device by the first call there, when its address is
+// looked up with cudaGetSymbolAddress (with that device current) and cached;
+// from then on the device holds it until the process exits.  A caller whose
+// allocator reserves the device's memory should make that first call before
+// the reservation; if the memory is gone by then the call fails with
+// FEA_ERR_NOMEM and nothing runs.  Every call shares the array, and the array keeps the
 // last call's contents; nothing in it has to start at zero, because the
 // element kernel writes every local row (padding included) and every local
 // load before the scatter reads them.  Calls whose kernels overlap on the GPU
@@ -61,15 +65,11 @@ using namespace fea;
 
 extern "C" fea_status fea_assemble_noalloc(fea_mesh* m, const fea_form* form, const fea_coeffs* co,
                                            const fea_quadrature* q, double* values, double* rhs, void* stream) {
-  if (!m || !form || !co || !q) return fail(FEA_ERR_ARG, "NULL mesh, form, coeffs or quadrature");
-  if (form->order != FEA_P1 && form->order != FEA_P2) return fail(FEA_ERR_ARG, "order must be FEA_P1 or FEA_P2");
-  if (form->kind != FEA_POISSON && form->kind != FEA_DIFFUSION_MASS && form->kind != FEA_ELASTICITY)
-    return fail(FEA_ERR_ARG, "unknown form kind");
-  if (form->kind == FEA_ELASTICITY && form->order != FEA_P1) return fail(FEA_ERR_ARG, "elasticity is P1 only");
-  if (q->npts != 1 && q->npts != 4 && q->npts != 11) return fail(FEA_ERR_ARG, "npts must be 1, 4 or 11");
-  if (q->prec != FEA_FP64 && q->prec != FEA_MIXED) return fail(FEA_ERR_ARG, "prec must be FEA_FP64 or FEA_MIXED");
-  if (co->f_kind < FEA_LOAD_NONE || co->f_kind > FEA_LOAD_SINPROD) return fail(FEA_ERR_ARG, "unknown load kind");
+  // the argument checks of fea_assemble (alignment included: the kernels use
+  // vector and bulk-copy accesses), all on the host before anything launches
+  FEA_TRY(check_form(m, form, co, q));
   if (!values) return fail(FEA_ERR_ARG, "values is NULL");
+  if (!aligned(values, 8) || (rhs && !aligned(rhs, 8))) return fail(FEA_ERR_ARG, "misaligned output");
   if (m->nvert != 4) return fail(FEA_ERR_ARG, "fea_assemble_noalloc takes tetrahedral meshes");
   const int order = form->order;
   const int ndpn = form->kind == FEA_ELASTICITY ? 3 : 1;
