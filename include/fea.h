@@ -162,6 +162,32 @@ fea_status fea_mesh_set_stages(fea_mesh* mesh, int32_t stages);
  * Results are bitwise identical for every mode. */
 fea_status fea_mesh_set_scatter_classes(fea_mesh* mesh, int32_t mode);
 
+/* Scatter algorithm of fea_assemble (the paper has the shared-memory batch
+ * plus global atomicAdd of Sec. 5, Algorithm 1; both algorithms here are
+ * deterministic instead):
+ *  FEA_SCATTER_LOCAL_ROWS: the element kernel writes every local row to HBM
+ *    scratch and a row-gather kernel adds each CSR row's contributions in
+ *    element order (all forms; the launch shapes above apply to it);
+ *  FEA_SCATTER_CHUNKED: P1 elasticity only.  The elements are grouped into
+ *    spatially compact chunks of at most 384; one CTA per chunk adds its
+ *    elements' entries into shared memory as 64-bit fixed-point integers,
+ *    one scale per node pair set from an exponent bound of the contributing
+ *    elements (integer sums are exact, so the order of the additions cannot
+ *    change the result), writes the couplings the chunk completes straight to
+ *    the CSR values, and one FP64 partial sum per chunk for the couplings it
+ *    shares, which a second kernel adds in chunk order.  Values agree with
+ *    the local-row scatter to rounding (within the FP64 tolerance of the
+ *    oracle), are bitwise reproducible and bitwise symmetric.  An element
+ *    with non-finite inputs or det J = 0 makes the entries it touches NaN.
+ *    The chunks are built (and the device synchronised) by the first chunked
+ *    assembly of a mesh; a mesh whose chunks cannot be built (a grid cell of
+ *    more than 1024 elements, a chunk too large for shared memory) reports
+ *    FEA_ERR_OVERFLOW when this mode is requested;
+ *  FEA_SCATTER_AUTO (default): chunked for P1 elasticity when its chunks can
+ *    be built, the local-row scatter otherwise. */
+enum { FEA_SCATTER_AUTO = 0, FEA_SCATTER_LOCAL_ROWS = 1, FEA_SCATTER_CHUNKED = 2 };
+fea_status fea_mesh_set_scatter(fea_mesh* mesh, int32_t mode);
+
 /* Shared-memory stages per CTA of the bulk-copy scatter (scatter mode 3):
  * 2, 3 or 4 steps of the row tile in flight per CTA; 0 (default) =
  * automatic, per launch the most resident CTAs per SM given the

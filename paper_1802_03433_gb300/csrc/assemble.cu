@@ -73,6 +73,16 @@ fea_status assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* co, con
   Pattern* P = m->pat[order][ndpn];
   Base* B = m->base[order];
   if (!P || !B) return fail(FEA_ERR_STATE, "fea_assemble: build the pattern with fea_pattern first");
+  // the chunked fixed-point scatter (elasticity): requested, or automatic
+  // when its chunks can be built for this mesh
+  if (m->scatter == FEA_SCATTER_CHUNKED && form->kind != FEA_ELASTICITY)
+    return fail(FEA_ERR_ARG, "the chunked scatter is implemented for P1 elasticity");
+  if (form->kind == FEA_ELASTICITY && m->scatter != FEA_SCATTER_LOCAL_ROWS &&
+      (m->scatter == FEA_SCATTER_CHUNKED || !P->chunks_failed)) {
+    const fea_status st = assemble_chunked(m, P, co, q, rhs ? co->f_kind : FEA_LOAD_NONE, values, rhs, s);
+    if (st == FEA_OK || m->scatter == FEA_SCATTER_CHUNKED || !P->chunks_failed) return st;
+    set_error("");  // automatic mode: the chunks cannot be built, take the local rows
+  }
   const int nb = B->nb, nl = nb * ndpn;
   const bool mixed = q->prec == FEA_MIXED;
   const size_t rb = mixed ? sizeof(float) : sizeof(double);

@@ -203,7 +203,7 @@ __device__ __forceinline__ void warp_sort_reg(T (&key)[R]) {
 
 // Sort each list ptr[d] .. ptr[d + 1] of int32 values ascending, one warp per
 // list (a dof's incidences by element id, a cell's elements, a shared
-// coupling's partial sums by chunk): lists of up to 256 sort in registers
+// coupling's partial sums by chunk): lists of up to 1024 sort in registers
 // (warp_sort_reg), longer ones by insertion sort in lane 0.
 template <int R>
 __device__ __forceinline__ void inc_sort_reg(int32_t* __restrict__ list, int len) {
@@ -232,6 +232,10 @@ __global__ void __launch_bounds__(128) k_sort_lists(const int32_t* __restrict__ 
       inc_sort_reg<4>(list, len);
     } else if (len <= 256) {
       inc_sort_reg<8>(list, len);
+    } else if (len <= 512) {
+      inc_sort_reg<16>(list, len);
+    } else if (len <= 1024) {
+      inc_sort_reg<32>(list, len);
     } else if (lane == 0) {
       for (int32_t i = 1; i < len; ++i) {
         const int32_t v = list[i];

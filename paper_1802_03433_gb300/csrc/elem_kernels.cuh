@@ -347,19 +347,11 @@ __device__ __forceinline__ void elast_store(const ElemArgs& A, int64_t e, const 
 
 // ---------------------------------------------------------------- elasticity
 // K_(a,i),(b,j) = |T| [lam d_i phi_a d_j phi_b + mu d_j phi_a d_i phi_b
-//                      + mu delta_ij grad phi_a . grad phi_b]  on P1 tets.
-template <int LOAD, int NPTS, typename R, bool ATOMIC = false>
-__global__ void __launch_bounds__(ELEM_T) k_elem_elast(ElemArgs A) {
-  const int64_t e = A.e0 + (int64_t)blockIdx.x * ELEM_T + threadIdx.x;
-  if (e >= A.e1) return;
-  double X[4][3];
-  load_element(A, e, X);
-  Geo g;
-  geometry(X, g);
-  if (!(g.det > 0.0)) atomicOr(A.err, DEV_ERR_DEGENERATE);
-  const double adet = fabs(g.det);
-  const double lam = A.lam ? __ldg(A.lam + e) : A.lam_const;
-  const double mu = A.mu ? __ldg(A.mu + e) : A.mu_const;
+//                      + mu delta_ij grad phi_a . grad phi_b]  on P1 tets:
+// the 78 upper entries r = 3a + i <= c = 3b + j, handed to put(K, value) in
+// upper-triangle order (K the compile-time index of the entry).
+template <typename R, typename F>
+__device__ __forceinline__ void elast_upper(const Geo& g, double adet, double lam, double mu, F&& put) {
   R Gr[4][3];
   grads<R>(g, Gr);
   const double sc = grad_scale<R>(adet);
@@ -380,7 +372,6 @@ __global__ void __launch_bounds__(ELEM_T) k_elem_elast(ElemArgs A) {
     D[a][b] = dot3(Mc[a], Gr[b]);  // mu |T| grad phi_a . grad phi_b
     if constexpr (a != b) D[b][a] = D[a][b];
   });
-  R Kl[12][12];
   static_for<78>([&](auto K) {
     constexpr int r = upper_a(12, K), c = upper_b(12, K);
     constexpr int a = r / 3, i = r % 3, b = c / 3, j = c % 3;
@@ -388,6 +379,25 @@ __global__ void __launch_bounds__(ELEM_T) k_elem_elast(ElemArgs A) {
     if constexpr (i == j) v = fma(LMc[a][i], Gr[b][i], D[a][b]);
     else if constexpr (a == b) v = LMc[a][i] * Gr[a][j];  // (lam + mu) d_i phi_a d_j phi_a
     else v = fma(Lc[a][i], Gr[b][j], Mc[a][j] * Gr[b][i]);
+    put(K, v);
+  });
+}
+
+template <int LOAD, int NPTS, typename R, bool ATOMIC = false>
+__global__ void __launch_bounds__(ELEM_T) k_elem_elast(ElemArgs A) {
+  const int64_t e = A.e0 + (int64_t)blockIdx.x * ELEM_T + threadIdx.x;
+  if (e >= A.e1) return;
+  double X[4][3];
+  load_element(A, e, X);
+  Geo g;
+  geometry(X, g);
+  if (!(g.det > 0.0)) atomicOr(A.err, DEV_ERR_DEGENERATE);
+  const double adet = fabs(g.det);
+  const double lam = A.lam ? __ldg(A.lam + e) : A.lam_const;
+  const double mu = A.mu ? __ldg(A.mu + e) : A.mu_const;
+  R Kl[12][12];
+  elast_upper<R>(g, adet, lam, mu, [&](auto K, R v) {
+    constexpr int r = upper_a(12, K), c = upper_b(12, K);
     Kl[r][c] = v;
     Kl[c][r] = v;
   });

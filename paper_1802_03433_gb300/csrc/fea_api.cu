@@ -204,6 +204,13 @@ fea_status fea_mesh_set_scatter_classes(fea_mesh* m, int32_t mode) {
   return FEA_OK;
 }
 
+fea_status fea_mesh_set_scatter(fea_mesh* m, int32_t mode) {
+  if (!m) return fail(FEA_ERR_ARG, "mesh is NULL");
+  if (mode < FEA_SCATTER_AUTO || mode > FEA_SCATTER_CHUNKED) return fail(FEA_ERR_ARG, "mode must be 0, 1 or 2");
+  m->scatter = mode;
+  return FEA_OK;
+}
+
 fea_status fea_mesh_set_scatter_stages(fea_mesh* m, int32_t stages) {
   if (!m) return fail(FEA_ERR_ARG, "mesh is NULL");
   if (stages != 0 && (stages < 2 || stages > 4)) return fail(FEA_ERR_ARG, "stages must be 0, 2, 3 or 4");
@@ -224,6 +231,8 @@ fea_status fea_mesh_destroy(fea_mesh* m) {
     if (m->ev[i]) cudaEventDestroy(m->ev[i]);
   if (m->lm.ptr) cudaFree(m->lm.ptr);
   if (m->fl.ptr) cudaFree(m->fl.ptr);
+  if (m->part.ptr) cudaFree(m->part.ptr);
+  if (m->npart.ptr) cudaFree(m->npart.ptr);
   if (m->gxs.ptr) cudaFree(m->gxs.ptr);
   if (m->bc.ptr) cudaFree(m->bc.ptr);
   if (m->cg.ptr) cudaFree(m->cg.ptr);

@@ -53,6 +53,46 @@ struct Base {
 // element with incidence index i = ipos[a][e] lives at row i * ndpn + comp of
 // a buffer whose rows are lstride(nl, bytes) values apart (devcommon.cuh).
 
+// Chunked scatter (chunks.cu, elast_chunk.cu) of the P1 vector pattern: the
+// elements are grouped into spatially compact chunks (whole cells of a grid
+// over the mesh's bounding box, visited in Morton order, at most
+// CHUNK_MAX_ELEMS elements each).  One CTA assembles one chunk: the local
+// entries of its elements are added as 64-bit fixed-point integers into
+// shared-memory accumulators, one 3 x 3 block per node pair ("slot") that the
+// chunk's elements couple.  A slot whose every contributing element lies in
+// the chunk is "owned" and written straight to the CSR values; the others are
+// written as one FP64 partial sum per chunk and added, in chunk order, by a
+// second kernel over the shared couplings.
+constexpr int CHUNK_MAX_ELEMS = 384;
+
+struct Chunks {
+  int64_t nchunk = 0, nslot = 0, nnode_slot = 0;
+  int max_slots = 0, max_nodes = 0;
+  int hbits = 0;                 // ceil(log2(most elements contributing to one slot of a chunk))
+  int32_t* cptr = nullptr;       // [nchunk + 1] element offsets into celem
+  int32_t* celem = nullptr;      // [E] element ids, chunk by chunk
+  uint16_t* eslot = nullptr;     // [10][E] (chunk order) slot of each vertex pair (a, b) of the element:
+                                 // k < 4 the node slot of vertex k, then (0,1) (0,2) (0,3) (1,2) (1,3) (2,3);
+                                 // bit 15 set when node(a) > node(b) (the slot holds the transposed block)
+  int32_t* sptr = nullptr;       // [nchunk + 1] slot offsets; each chunk's node slots come first
+  int32_t* nptr = nullptr;       // [nchunk + 1] node-slot offsets
+  int4* srec = nullptr;          // [nslot] {U, W, Li | Lj << 16, partial index or -1 when owned}: the
+                                 // CSR position of entry (3i, 3j) and of (3j, 3i), the lengths of rows
+                                 // 3i and 3j, for the slot's node pair i <= j
+  int2* nrec = nullptr;          // [nnode_slot] {node id, load partial index or -1 when owned}
+  // couplings shared by several chunks: partial sums listed in chunk order
+  int64_t npart = 0, ngroup = 0;
+  int32_t* gptr = nullptr;       // [ngroup + 1]
+  int32_t* glist = nullptr;      // [npart] partial indices
+  int4* grec = nullptr;          // [ngroup] {U, W, Li | Lj << 16, 0}
+  int64_t nnpart = 0, nngroup = 0;
+  int32_t* ngptr = nullptr;      // [nngroup + 1]
+  int32_t* nglist = nullptr;     // [nnpart]
+  int32_t* ngnode = nullptr;     // [nngroup] node id
+  int64_t niso = 0;
+  int32_t* iso = nullptr;        // [niso] nodes of no element (their load entries are zero)
+};
+
 // The dof-level CSR pattern of (order, dofs per node).
 struct Pattern {
   int order = 0, ndpn = 0;
@@ -86,12 +126,15 @@ struct Pattern {
   int64_t* tile_base = nullptr;   // [ntiles]
   int32_t* tile_steps = nullptr;  // [ntiles]
   int64_t npos = 0;               // positions, padding included (0: layout not built)
+  Chunks* chunks = nullptr;       // chunked scatter (P1 vector pattern; built on first use)
+  bool chunks_failed = false;     // the chunk structures cannot be built for this mesh
 };
 
 struct Scratch {
   void* ptr = nullptr;
   size_t bytes = 0;
 };
+
 
 }  // namespace fea
 
@@ -108,6 +151,7 @@ struct fea_mesh {
   fea::Pattern* pat[3][4] = {{nullptr}};                     // by order, ndpn
   fea::Scratch lm, fl;      // local matrices / local loads of the last assembly
   fea::Scratch gxs;         // per-incidence vertex gradients of the last backward
+  fea::Scratch part, npart; // chunked scatter: FP64 partial sums of shared couplings / of shared loads
   fea::Scratch bc;          // Dirichlet marks and values (fea_dirichlet)
   fea::Scratch cg;          // CG vectors, partial sums and state (fea_cg)
   cudaStream_t solve_stream = nullptr;  // stream the CG iteration graph is captured on
@@ -118,6 +162,7 @@ struct fea_mesh {
   cudaStream_t side = nullptr;             // scatter stream of the overlapped path
   cudaEvent_t chunk_ev[17] = {nullptr};    // chunk done (<= 16 stages) + join
   int tiled_stages = 0;     // bulk-copy scatter stages per CTA (2..4), 0 automatic
+  int scatter = 0;          // FEA_SCATTER_*: 0 automatic, 1 local rows through HBM, 2 chunked fixed point
   int load_split = -1;      // scalar forms: 0 fused element kernel; 1 matrix kernel then load kernel;
                             // 2 load kernel on the side stream, concurrent with the matrix kernel;
                             // 3 one kernel with matrix warps and load warps; -1 automatic (3 for
@@ -137,6 +182,14 @@ fea_status build_stages(fea_mesh* m, Pattern* P, int stages, cudaStream_t s);
 fea_status validate_connectivity(fea_mesh* m, cudaStream_t s);
 void free_base(Base* b);
 void free_pattern(Pattern* p);
+
+// chunks.cu
+fea_status build_chunks(fea_mesh* m, Pattern* P, cudaStream_t s);
+void free_chunks(Chunks* c);
+
+// elast_chunk.cu
+fea_status assemble_chunked(fea_mesh* m, Pattern* P, const fea_coeffs* co, const fea_quadrature* q, int load,
+                            double* values, double* rhs, cudaStream_t s);
 
 // assemble.cu
 fea_status assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* co,

@@ -534,6 +534,7 @@ void free_base(Base* b) {
 
 void free_pattern(Pattern* p) {
   if (!p) return;
+  free_chunks(p->chunks);
   dfree(p->tile_list);
   dfree(p->class_list);
   dfree(p->tpos);

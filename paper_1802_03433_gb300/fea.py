@@ -23,6 +23,7 @@ FEA_P1, FEA_P2 = 1, 2
 FEA_POISSON, FEA_DIFFUSION_MASS, FEA_ELASTICITY = 0, 1, 2
 FEA_FP64, FEA_MIXED = 0, 1
 FEA_LOAD_NONE, FEA_LOAD_CONST, FEA_LOAD_SINPROD = 0, 1, 2
+FEA_SCATTER_AUTO, FEA_SCATTER_LOCAL_ROWS, FEA_SCATTER_CHUNKED = 0, 1, 2
 
 
 class FeaError(RuntimeError):
@@ -82,6 +83,7 @@ def lib() -> C.CDLL:
         "fea_mesh_set_scatter_classes": [_vp, C.c_int32],
         "fea_mesh_set_load_split": [_vp, C.c_int32],
         "fea_mesh_set_scatter_stages": [_vp, C.c_int32],
+        "fea_mesh_set_scatter": [_vp, C.c_int32],
         "fea_mesh_check": [_vp, _vp],
         "fea_pattern": [_vp, C.c_int32, C.c_int32, i64p, i64p, _vp],
         "fea_pattern_copy": [_vp, C.c_int32, C.c_int32, _vp, _vp, _vp],
@@ -240,6 +242,12 @@ def fea_mesh_set_load_split(h, mode):
 
 def fea_mesh_set_scatter_classes(h, mode):
     _check(lib().fea_mesh_set_scatter_classes(h, mode), "fea_mesh_set_scatter_classes")
+
+
+def fea_mesh_set_scatter(h, mode):
+    """FEA_SCATTER_AUTO, FEA_SCATTER_LOCAL_ROWS or FEA_SCATTER_CHUNKED (P1
+    elasticity: fixed-point accumulation per chunk of elements)."""
+    _check(lib().fea_mesh_set_scatter(h, mode), "fea_mesh_set_scatter")
 
 
 def fea_mesh_set_scatter_stages(h, stages):

@@ -274,6 +274,7 @@ def test_overlapped_stages_bitwise_identical(torch_cuda, kind, n, prec):
     c = case(kind, n, seed=13)
     g1 = None
     m = fea.Mesh(c["coords"], c["tets"])
+    fea.fea_mesh_set_scatter(m.h, fea.FEA_SCATTER_LOCAL_ROWS)  # the stages belong to the local-row scatter
     for stages in (1, 2, 5, 8, 16):
         fea.fea_mesh_set_stages(m.h, stages)
         g = gpu_system(c, prec=prec, mesh=m)
@@ -327,6 +328,7 @@ def test_scatter_launch_shapes_bitwise_identical(torch_cuda, kind, n, prec):
     from paper_1802_03433_gb300 import fea
     c = case(kind, n, seed=23)
     m = fea.Mesh(c["coords"], c["tets"])
+    fea.fea_mesh_set_scatter(m.h, fea.FEA_SCATTER_LOCAL_ROWS)  # the launch shapes of the local-row scatter
     ref = None
     for mode in (0, 1, 2, 3, -1):
         fea.fea_mesh_set_scatter_classes(m.h, mode)
