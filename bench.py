@@ -5,9 +5,13 @@ One step = one pass of the assembly hot path over the workload: per-element
 Jacobians, local matrices and load vectors by quadrature, and the
 deterministic scatter into the CSR values and the load vector (the CSR
 pattern is built once beforehand and reported separately).  Default
-workload: P2 -div(kappa grad u) + u = f on the 64^3 Kuhn cube mesh
-(1,572,864 tets, 2,146,689 dofs, 60,859,905 nonzeros), kappa log-normal per
-element, f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z), 11-point rule, FP64.
+workload, the largest single-GPU configuration: P1 linear elasticity on the
+128^3 Kuhn cube mesh (12,582,912 tets, 6,440,067 dofs, 286,222,473
+nonzeros), Lame parameters uniform in [0.5, 2] per element, body force
+(0, 0, -1), FP64, with the chunked fixed-point scatter.  The other
+configurations (P2 diffusion + mass 64^3, P1 kappa-diffusion 96^3 and its
+adjoint, the 256-mesh batch, P1 Poisson 8^3) and the other forms are timed
+in the same run, each with its own roofline entry.
 
 Prints one JSON line.  `--impl reference` times the CPU oracle instead.
 """
@@ -30,38 +34,49 @@ import numpy as np  # noqa: E402
 
 from paper_1802_03433_gb300 import meshgen as mg  # noqa: E402
 
-# FP64 peak of the element kernels' pipe: 152 SMs x 2 DFMA/clk x 2 flop x
-# 2.07 GHz (GB300 nominal FP64, 1.25 TFLOP/s).
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# Nominal FP64 peak: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (1.26 TFLOP/s);
+# the roofline uses the rate fea_diag_fp64_rate measures on the device at the
+# start of every run and reports the nominal fraction beside it.
+FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
-# FP64 flops (2 x DFMA + DADD + DMUL, ncu SASS counters) executed per element
-# by the element kernel of each workload, and DRAM bytes per launch of the
-# dominant kernel (ncu, dram__bytes_read.sum + dram__bytes_write.sum); the
-# captures are summarised under profiles/.  Absent where not captured for the
-# current kernels.
-FP64_FLOP_PER_ELEM = {
-    # P2: the kernel with matrix warps and load warps (the automatic launch).
-    # 375 = the element formulas in FP64 (150 DFMA + 26 DADD + 49 DMUL, the
-    # ncu count of the all-FP64 form); the kernel evaluates the 136 FMA terms
-    # of the local entries as exact 64-bit integer sums instead, so its own
-    # FP64 count is lower while the work per element is the same
-    ("p2_diffmass_64", "fp64"): 375.0,
-    ("p1_kappa_96", "fp64"): 119.0,       # 30 DFMA + 27 DADD + 32 DMUL (+ ~2,200 integer instructions)
-    ("p1_elast_128", "fp64"): 335.0,      # 102 DFMA + 16 DADD + 115 DMUL
-}
-DRAM_BYTES_PER_LAUNCH = {
-    ("p2_diffmass_64", "element"): 149.3e6 + 1985.1e6,
-    ("p1_kappa_96", "element"): 238.4e6 + 793.2e6,
-    # captured on the 64^3 mesh (1,572,864 tets) and scaled by 8 (traffic grows with the elements)
-    ("p1_elast_128", "element"): 8 * (82.2e6 + 1907.8e6),
+# The dominant kernel of each workload: FP64 flop per element counted in FP64
+# terms ("equivalent": the element formulas as FP64 operations, DFMA = 2),
+# the FP64 flop the kernel executes per element (ncu SASS counters: 2 DFMA +
+# DADD + DMUL; lower where exact integer arithmetic replaced FP64 work), and
+# its DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum,
+# one capture; the captures are summarised under profiles/).
+KERNELS = {
+    # chunked scatter: the element arithmetic (335 flop, as the local-row
+    # element kernel: 102 DFMA + 16 DADD + 115 DMUL) plus the bound of phase
+    # A; counters of the 64^3 capture (103 DFMA + 25 DADD + 115 DMUL per
+    # element), DRAM bytes of the 64^3 launch x 8 (traffic grows with the
+    # elements: the same chunks, 8 times as many)
+    "p1_elast_128": dict(kernel="k_elast_chunk (element arithmetic + fixed-point accumulation per chunk)",
+                         flop_equiv=335.0, flop_exec=346.0, traffic=8 * (226.0e6 + 317.7e6),
+                         profile="profiles/element_chunk_kernel_p1_elast.md"),
+    "p1_elast_64": dict(kernel="k_elast_chunk", flop_equiv=335.0, flop_exec=346.0, traffic=226.0e6 + 317.7e6,
+                        profile="profiles/element_chunk_kernel_p1_elast.md"),
+    # P2: matrix warps + load warps; 375 = the formulas in FP64 (150 DFMA +
+    # 26 DADD + 49 DMUL); executed 33 DFMA + 30 DADD + 43 DMUL (the 136 FMA
+    # terms of the entries are exact 64-bit integer sums)
+    "p2_diffmass_64": dict(kernel="k_elem_roles (P2 element, FP64)", flop_equiv=375.0, flop_exec=139.0,
+                           traffic=149.3e6 + 1985.1e6, profile="profiles/element_kernel_p2_diffmass_64.md"),
+    "p1_kappa_96": dict(kernel="k_elem_scalar (P1 element, FP64)", flop_equiv=119.0, flop_exec=119.0,
+                        traffic=238.4e6 + 793.2e6, profile="profiles/element_kernel_p1_kappa_96.md"),
+    "p1_poisson_8": dict(kernel="k_elem_scalar (P1 element, FP64)", flop_equiv=119.0, flop_exec=119.0,
+                         traffic=None, profile=None),
+    "adjoint_96": dict(kernel="k_adjoint (P1 backward, FP64)", flop_equiv=483.0, flop_exec=483.0,
+                       traffic=438.1e6 + 672.6e6, profile="profiles/adjoint_kernel_p1_kappa_96.md"),
+    "paper_2d": dict(kernel="k_elem_tri (P1 triangle element, FP64)", flop_equiv=191.0, flop_exec=191.0,
+                     traffic=268.5e6 + 950.7e6, profile="profiles/element_kernel_paper_2d.md"),
 }
 
 METRIC = "elements/s assembled into CSR and % of HBM roofline, plain vs chosen forms"
 
 WORKLOADS = {
+    "p1_elast_128": dict(kind="elasticity", n=128),
     "p2_diffmass_64": dict(kind="p2_diffmass", n=64),
     "p1_poisson_8": dict(kind="p1_poisson", n=8),
-    "p1_elast_128": dict(kind="elasticity", n=128),
     "p1_elast_64": dict(kind="elasticity", n=64),     # small case of the same kernel, for multi-pass captures
     "p1_kappa_96": dict(kind="p1_kappa", n=96),
 }
@@ -87,11 +102,38 @@ def mixed_error(torch, mesh, d, ref_vals, vals, ref_rhs, rhs):
 
 
 def algorithmic_bytes(kind, E, N, ndof, nnz):
-    """Inputs read once + outputs written once (coords 24 B/node, element->node
-    table 16 B/element, coefficients 8 B per field per element, values 8 B/nnz,
-    rhs 8 B/dof)."""
+    """Inputs read once + outputs written once: coords 24 B/node, the element
+    -> dof table (16 B/element for P1, 40 B for the ten P2 dofs),
+    coefficients 8 B per field per element, values 8 B/nnz, rhs 8 B/dof."""
     coef = {"p1_poisson": 0, "p1_kappa": 8, "p2_diffmass": 8, "elasticity": 16}[kind]
-    return 24 * N + 16 * E + coef * E + 8 * nnz + 8 * ndof
+    table = 40 if kind == "p2_diffmass" else 16
+    return 24 * N + table * E + coef * E + 8 * nnz + 8 * ndof
+
+
+def roofline_block(key, E, kernel_ms, fp64_peak_tflops, note=None):
+    """Roofline entry of the dominant (FP64-bound) kernel of a workload:
+    achieved = FP64 flop per element x elements / the kernel's CUDA-event
+    time, against the FP64 rate measured on this device (frac) and the
+    nominal one (frac_nominal); the same for the FP64 flop the kernel
+    actually executes."""
+    k = KERNELS.get(key)
+    if k is None or not kernel_ms:
+        return None
+    ach = k["flop_equiv"] * E / (kernel_ms / 1e3) / 1e12
+    exe = k["flop_exec"] * E / (kernel_ms / 1e3) / 1e12
+    out = {"kernel": k["kernel"], "bound": "alu", "achieved": ach, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+           "frac": ach / fp64_peak_tflops, "peak_kind": "FP64 FMA rate measured on this GPU (fea_diag_fp64_rate)",
+           "frac_nominal": ach / FP64_NOMINAL_TFLOPS, "flop_per_element": k["flop_equiv"],
+           "executed": {"flop_per_element": k["flop_exec"], "achieved": exe, "frac": exe / fp64_peak_tflops},
+           "kernel_ms": kernel_ms, "traffic": k["traffic"], "profile": k["profile"]}
+    if note:
+        out["note"] = note
+    return out
+
+
+def hbm_block(alg_bytes, step_ms):
+    gbs = alg_bytes / (step_ms / 1e3) / 1e9
+    return {"algorithmic_bytes": alg_bytes, "achieved_gbs": gbs, "peak_gbs": _hbm_peak(), "frac": gbs / _hbm_peak()}
 
 
 def make_inputs(kind, n, seed=0):
@@ -219,7 +261,10 @@ def run_ours(args):
     E = d["tets"].shape[1]
     N = d["coords"].shape[1]
 
+    # the FP64 peak the rooflines divide by, measured on this device
+    fp64_peak = fea.fea_diag_fp64_rate() / 1e12
     mesh = fea.Mesh(d["coords"], d["tets"], device=dev)
+    fea.fea_mesh_set_scatter(mesh.h, args.scatter)
     fea.fea_mesh_set_stages(mesh.h, args.stages)
     if args.scatter_classes >= 0:
         fea.fea_mesh_set_scatter_classes(mesh.h, args.scatter_classes)
@@ -332,17 +377,28 @@ def run_ours(args):
     if want("batched"):
         forms["batched"] = bench_batched(fea, torch, dev, small, args.warmup, flush)
     if want("adjoint"):
-        forms["adjoint"] = bench_adjoint(fea, torch, dev, small, args.warmup, flush)
-    if want("elasticity_128"):
-        forms["elasticity_128"] = bench_plain(fea, torch, dev, "elasticity", 128, small, args.warmup, flush)
-    if want("p1_kappa_96"):
-        forms["p1_kappa_96"] = bench_plain(fea, torch, dev, "p1_kappa", 96, small, args.warmup, flush)
+        forms["adjoint"] = bench_adjoint(fea, torch, dev, small, args.warmup, flush, fp64_peak)
+    if want("local_rows") and d["form"] == 2 and args.scatter != fea.FEA_SCATTER_LOCAL_ROWS:
+        # the same workload with the local-row scatter (element kernel writes
+        # every local row to HBM, row-gather kernel adds them)
+        fea.fea_mesh_set_scatter(mesh.h, fea.FEA_SCATTER_LOCAL_ROWS)
+        l_total, _, l_phase, _ = timed_loop(fea.FEA_FP64, small, args.warmup)
+        fea.fea_mesh_set_scatter(mesh.h, args.scatter)
+        forms["local_rows"] = {"value": ws * E / (l_total / small / 1e3), "ms_per_step": l_total / small,
+                               "elem_ms": statistics.mean(p[0] for p in l_phase),
+                               "scatter_ms": statistics.mean(p[1] for p in l_phase),
+                               "note": "FEA_SCATTER_LOCAL_ROWS on the same workload, FP64"}
+    for name, kind, n in (("p2_diffmass_64", "p2_diffmass", 64), ("elasticity_128", "elasticity", 128),
+                          ("p1_kappa_96", "p1_kappa", 96), ("p1_poisson_8", "p1_poisson", 8)):
+        same = {"elasticity_128": "p1_elast_128"}.get(name, name) == args.workload
+        if want(name) and not same:
+            forms[name] = bench_plain(fea, torch, dev, kind, n, small, args.warmup, flush, fp64_peak)
     if want("jit"):
         forms["jit"] = bench_jit(fea, torch, dev, small, args.warmup, flush)
     if want("solve"):
         forms["solve"] = bench_solve(fea, torch, dev)
     if want("paper_2d"):
-        forms["paper_2d"] = bench_paper_2d(fea, torch, dev, small, args.warmup, flush)
+        forms["paper_2d"] = bench_paper_2d(fea, torch, dev, small, args.warmup, flush, fp64_peak)
 
     # end to end through the public API with host buffers: every step copies
     # its inputs (coordinates, coefficients) host -> device from pinned
@@ -414,30 +470,20 @@ def run_ours(args):
                "d2h_bytes_per_step": d2h, "pipelining": "two mesh handles on two streams"}
         lanes[1]["mesh"].close()
 
-    # roofline of the dominant kernel
-    key = (args.workload, "fp64")
-    if elem_ms >= scat_ms:
-        flop = FP64_FLOP_PER_ELEM.get(key)
-        if flop is not None:
-            ach = flop * E / (elem_ms / 1e3) / 1e12
-            roof = {"kernel": "element", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                    "peak_kind": "nominal FP64, 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (FMA = 2 flop)",
-                    "flop_per_element": flop,
-                    "traffic": DRAM_BYTES_PER_LAUNCH.get((args.workload, "element"))}
-        else:
-            roof = {"kernel": "element", "bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": None, "traffic": None}
-    else:
-        # scatter: algorithmic bytes = local matrices read once + values/rhs written once
-        nl = (4 if d["order"] == 1 else 10) * d["ndpn"]
-        byts = E * nl * nl * 8 + nnz * 8 + ndof * 8
-        ach = byts / (scat_ms / 1e3) / 1e9
-        peak = _hbm_peak()
-        roof = {"kernel": "scatter", "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "traffic": DRAM_BYTES_PER_LAUNCH.get((args.workload, "scatter"))}
+    # roofline of the dominant kernel (the element kernel, or for elasticity
+    # the chunk kernel that computes and accumulates the elements)
+    roof = roofline_block(args.workload, E, elem_ms, fp64_peak)
+    forms["fp64"]["roofline"] = roof
 
     alg = algorithmic_bytes(d["kind"], E, N, ndof, nnz)
+    forms["fp64"]["hbm"] = hbm_block(alg, total_ms / args.steps)
+    if "mixed" in forms:
+        forms["mixed"]["hbm"] = hbm_block(alg, forms["mixed"]["ms_per_step"])
+    # kernels launched per step: chunked elasticity = the chunk kernel and the
+    # two reduce kernels; the local-row path = the element kernel and the
+    # scatter (the bulk-copy scatter of the scalar forms splits its row tiles
+    # over two launches)
+    per_step = 3
     out = None
     if rank == 0:
         cpu = None
@@ -450,17 +496,19 @@ def run_ours(args):
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "elements": E, "nodes": N, "ndof": ndof, "nnz": nnz,
+                       "scatter": ("chunked fixed point" if (d["form"] == 2 and args.scatter != 1) else "local rows"),
                        "order": d["order"], "form": {0: "poisson", 1: "diffusion+mass", 2: "elasticity"}[d["form"]],
                        "npts": d["npts"], "mesh": f"{d['n']}^3 Kuhn cube, interior nodes perturbed 0.2h",
                        "l2": "256 MB buffer written between timed steps (> 129 MB L2)",
                        "parallelism": f"independent replica per GPU x{ws}"},
             "roofline": roof,
-            "hbm": {"algorithmic_bytes": alg, "achieved_gbs": alg / (total_ms / args.steps / 1e3) / 1e9,
-                    "peak_gbs": _hbm_peak(), "frac": alg / (total_ms / args.steps / 1e3) / 1e9 / _hbm_peak()},
+            "hbm": hbm_block(alg, total_ms / args.steps),
+            "fp64_peak_measured_tflops": fp64_peak,
+            "fp64_peak_nominal_tflops": FP64_NOMINAL_TFLOPS,
             "forms": forms,
             "pattern_ms": pattern_ms,
             "e2e": e2e,
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": per_step * args.steps,
             "clocks": clk,
             "cpu_baseline": cpu,
         }
@@ -528,9 +576,15 @@ def bench_batched(fea, torch, dev, steps, warmup, flush):
     for m in meshes:
         m.check()
     b.close()
+    patterns = [m.pattern(d["order"]) for d, m in zip(specs, meshes)]
     for m in meshes:
         m.close()
+    alg = sum(algorithmic_bytes("p1_kappa" if d["order"] == 1 else "p2_diffmass", d["tets"].shape[1],
+                                d["coords"].shape[1], nd, nz) for d, (nd, nz) in zip(specs, patterns))
     return {"value": E / (res["graph"] / 1e3), "unit": "elements/s", "ms_per_step": res["graph"],
+            "hbm": hbm_block(alg, res["graph"]),
+            "roofline": None, "roofline_note": "the P1 and P2 element kernels run concurrently in one graph; "
+                                                "their FP64 rooflines are those of p1_kappa_96 and p2_diffmass_64",
             "separate_value": E / (res["separate"] / 1e3), "separate_ms_per_step": res["separate"],
             "launches": {"graph": 1, "separate": 2 * len(specs)},
             "tuned": {"elements_per_item": params[0], "p2_element_ctas": params[1], "p1_element_ctas": params[2],
@@ -540,7 +594,7 @@ def bench_batched(fea, torch, dev, steps, warmup, flush):
                       "log-normal kappa, sin load, FP64"}
 
 
-def bench_adjoint(fea, torch, dev, steps, warmup, flush):
+def bench_adjoint(fea, torch, dev, steps, warmup, flush, fp64_peak):
     """P1 kappa-diffusion on the 96^3 mesh: forward assembly and the adjoint
     (dL/dkappa, dL/dx for L = v^T K w + g^T f)."""
     d = mg.adjoint_p1(96)
@@ -577,13 +631,20 @@ def bench_adjoint(fea, torch, dev, steps, warmup, flush):
         res[name] = tot / steps
     m.check()
     m.close()
+    # backward: reads gV (nnz), gF (ndof), coords, tets, kappa; writes
+    # dL/dkappa (E) and dL/dx (3 N)
+    alg_bwd = 8 * nnz + 8 * ndof + 24 * N + 16 * E + 8 * E + 8 * E + 24 * N
     return {"value": E / (res["backward"] / 1e3), "unit": "elements/s (backward)",
             "backward_ms": res["backward"], "forward_ms": res["forward"],
             "forward_value": E / (res["forward"] / 1e3), "elements": E,
+            "roofline": roofline_block("adjoint_96", E, res["backward"], fp64_peak,
+                                       note="kernel time taken as the whole backward step (the adjoint kernel "
+                                            "and its node reduction)"),
+            "hbm": hbm_block(alg_bwd, res["backward"]),
             "config": "P1 kappa-diffusion, 96^3 Kuhn cube (5,308,416 tets), 4-pt sin load, FP64"}
 
 
-def bench_plain(fea, torch, dev, kind, n, steps, warmup, flush):
+def bench_plain(fea, torch, dev, kind, n, steps, warmup, flush, fp64_peak):
     """FP64 and mixed assembly of one more workload (elements/s each)."""
     d = make_inputs(kind, n, seed=0)
     m = fea.Mesh(d["coords"], d["tets"], device=dev)
@@ -621,8 +682,16 @@ def bench_plain(fea, torch, dev, kind, n, steps, warmup, flush):
             ps += s_ms
         out[name] = {"value": E / (tot / steps / 1e3), "ms_per_step": tot / steps, "elem_ms": pe / steps,
                      "scatter_ms": ps / steps}
+        out[name]["hbm"] = hbm_block(algorithmic_bytes(kind, E, d["coords"].shape[1], ndof, nnz), tot / steps)
         if name == "fp64":
             ref = (vals.clone(), rhs.clone())
+            key = {"p2_diffmass": "p2_diffmass_64", "p1_kappa": "p1_kappa_96", "p1_poisson": "p1_poisson_8",
+                   "elasticity": "p1_elast_128"}[kind]
+            note = None
+            if n <= 8:
+                note = (f"{E} elements, a few microseconds of work: launch-bound, so the fraction says nothing "
+                        "about the kernel")
+            out[name]["roofline"] = roofline_block(key, E, pe / steps, fp64_peak, note=note)
         else:
             out[name]["error_vs_fp64"] = mixed_error(torch, m, d, ref[0], vals, ref[1], rhs)
     m.check()
@@ -630,7 +699,7 @@ def bench_plain(fea, torch, dev, kind, n, steps, warmup, flush):
     return out
 
 
-def bench_paper_2d(fea, torch, dev, steps, warmup, flush, n=2048):
+def bench_paper_2d(fea, torch, dev, steps, warmup, flush, fp64_peak, n=2048):
     """The paper's own 2-D example (Sec. 4.2) at the top of its 10K-10M node
     range: P1 triangles on n^2 squares, sigma = [[1, -x-y], [x+y, 1]],
     lambda = 1, f = -2 (x^2 + y^2) + 36, 6-point load rule, FP64."""
@@ -662,7 +731,7 @@ def bench_paper_2d(fea, torch, dev, steps, warmup, flush, n=2048):
     alg = 16 * ndof + 12 * E + 8 * nnz + 8 * ndof  # coords, connectivity, values, rhs
     return {"value": E / (ms / 1e3), "unit": "elements/s", "ms_per_step": ms, "elem_ms": pe / steps,
             "scatter_ms": ps / steps, "elements": E, "nodes": ndof, "nnz": nnz,
-            "hbm_algorithmic_gbs": alg / (ms / 1e3) / 1e9, "hbm_frac": alg / (ms / 1e3) / 1e9 / _hbm_peak(),
+            "hbm": hbm_block(alg, ms), "roofline": roofline_block("paper_2d", E, pe / steps, fp64_peak),
             "config": f"paper's 2-D example on {n}^2 squares (P1 triangles, perturbed), FP64"}
 
 
@@ -762,33 +831,84 @@ def bench_solve(fea, torch, dev, n=64, rtol=1e-8, max_iter=3000):
 
 
 # ---------------------------------------------------------------- CPU oracle
-CPU_SAMPLE_N = {"p2_diffmass": 40, "p1_poisson": 64, "p1_kappa": 64, "elasticity": 32}
+# Bounded samples of each workload (same recipe, smaller cube) for the CPU
+# baseline: each takes some 10-20 s of host time for three repetitions of the
+# pattern, the single-threaded values and the all-cores values.
+CPU_SAMPLE_N = {"p2_diffmass": 32, "p1_poisson": 48, "p1_kappa": 48, "elasticity": 32}
+
+
+def _oracle_kw(d):
+    return dict(f_kind={1: "const", 2: "sinprod"}[d["f_kind"]], f_param=d["f_param"], npts=d["npts"])
 
 
 def _oracle_assemble(d, edof, rp, ci):
     import oracle
-    kw = dict(f_kind={1: "const", 2: "sinprod"}[d["f_kind"]], f_param=d["f_param"], npts=d["npts"])
+    kw = _oracle_kw(d)
     if d["form"] == 2:
         return oracle.assemble(d["coords"], d["tets"], 1, edof, rp, ci, kind="elasticity", lam=d["lam"],
                                mu=d["mu"], **kw)
     return oracle.assemble(d["coords"], d["tets"], d["order"], edof, rp, ci, mass=d["mass"], kappa=d["kappa"], **kw)
 
 
+def _oracle_assemble_par(d, edof, rp, ci):
+    import oracle
+    kw = _oracle_kw(d)
+    if d["form"] == 2:
+        return oracle.assemble_par(d["coords"], d["tets"], 1, edof, rp, ci, kind="elasticity", lam=d["lam"],
+                                   mu=d["mu"], **kw)
+    return oracle.assemble_par(d["coords"], d["tets"], d["order"], edof, rp, ci, mass=d["mass"],
+                               kappa=d["kappa"], **kw)
+
+
+def host_info():
+    """Core count and CPU model of the host the oracle runs on."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    import platform
+    return {"host_cores": os.cpu_count(), "host_cpu": model, "host_arch": platform.machine()}
+
+
 def cpu_baseline(kind):
-    """The oracle, as it stands, on a bounded sample of the workload (same
-    recipe, smaller cube), single-threaded on the host."""
+    """The oracle, as it stands, on a bounded sample of the workload, on the
+    host: the pattern (sort + unique) and the values + load assembly timed
+    separately on one thread (median of 3), and the same element loop on all
+    host cores (OpenMP, per-thread copies of the outputs summed; median of 3)."""
     import oracle
     n = CPU_SAMPLE_N[kind]
     d = make_inputs(kind, n, seed=0)
     edof, nsd = oracle.dof_table(d["order"], d["coords"].shape[1], d["tets"])
-    rp, ci = oracle.pattern(nsd, edof, ndpn=d["ndpn"])
-    t = time.perf_counter()
-    _oracle_assemble(d, edof, rp, ci)
-    dt = time.perf_counter() - t
+    pat, vals, par = [], [], []
+    threads = 1
+    for _ in range(3):
+        t = time.perf_counter()
+        rp, ci = oracle.pattern(nsd, edof, ndpn=d["ndpn"])
+        pat.append(time.perf_counter() - t)
+    for _ in range(3):
+        t = time.perf_counter()
+        _oracle_assemble(d, edof, rp, ci)
+        vals.append(time.perf_counter() - t)
+    for _ in range(3):
+        t = time.perf_counter()
+        threads = _oracle_assemble_par(d, edof, rp, ci)[3]
+        par.append(time.perf_counter() - t)
     E = d["tets"].shape[1]
-    return {"value": E / dt, "unit": "elements/s", "cores": 1, "kind": "oracle",
-            "sample": f"{kind} on the {n}^3 cube ({E} tets), values + load assembly, pattern excluded",
-            "seconds": dt}
+    pv, vv, av = statistics.median(pat), statistics.median(vals), statistics.median(par)
+    out = {"value": E / vv, "unit": "elements/s", "cores": 1, "kind": "oracle",
+           "sample": f"{kind} on the {n}^3 cube ({E} tets, {rp[-1]} nonzeros) of the same recipe; value = values + "
+                     "load assembly on one thread, pattern timed separately",
+           "seconds": vv, "pattern_s": pv, "values_s": vv,
+           "all_cores": {"value": E / av, "unit": "elements/s", "cores": threads, "values_s": av,
+                         "kind": "the oracle's element loop on OpenMP threads (per-thread copies of the outputs, "
+                                 "summed); a timing baseline, not the checker"}}
+    out.update(host_info())
+    return out
 
 
 def run_reference(args):
@@ -816,8 +936,8 @@ def run_reference(args):
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "sample_elements": E,
                    "note": f"each step assembles a {n}^3 cube of the same recipe (bounded CPU sample)"},
-        "cpu_baseline": {"value": value, "unit": "elements/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{wl['kind']} on the {n}^3 cube ({E} tets) per step"},
+        "cpu_baseline": dict({"value": value, "unit": "elements/s", "cores": 1, "kind": "oracle",
+                              "sample": f"{wl['kind']} on the {n}^3 cube ({E} tets) per step"}, **host_info()),
         "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
@@ -830,7 +950,8 @@ def main():
     p.add_argument("--steps", type=int, default=50)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="p2_diffmass_64", choices=sorted(WORKLOADS))
+    p.add_argument("--workload", default="p1_elast_128", choices=sorted(WORKLOADS))
+    p.add_argument("--scatter", type=int, default=0, help="0 automatic, 1 local rows, 2 chunked (elasticity)")
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--stages", type=int, default=1, help="element chunks overlapped with the scatter (1 = none)")
     p.add_argument("--scatter-classes", type=int, default=-1, help="scatter launch shape 0-3 (-1 = library default)")
@@ -843,8 +964,9 @@ def main():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-forms", action="store_true")
     p.add_argument("--forms", default="all",
-                   help="comma list of extra forms to time: mixed, atomic_alg1, batched, adjoint, elasticity_128, "
-                        "p1_kappa_96, paper_2d, jit, solve (default all)")
+                   help="comma list of extra forms to time: mixed, local_rows, atomic_alg1, batched, adjoint, "
+                        "p2_diffmass_64, elasticity_128, p1_kappa_96, p1_poisson_8, paper_2d, jit, solve "
+                        "(default all)")
     args = p.parse_args()
     if args.warmup < 3:
         args.warmup = 3

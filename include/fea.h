@@ -181,8 +181,9 @@ fea_status fea_mesh_set_scatter_classes(fea_mesh* mesh, int32_t mode);
  *    with non-finite inputs or det J = 0 makes the entries it touches NaN.
  *    The chunks are built (and the device synchronised) by the first chunked
  *    assembly of a mesh; a mesh whose chunks cannot be built (a grid cell of
- *    more than 1024 elements, a chunk too large for shared memory) reports
- *    FEA_ERR_OVERFLOW when this mode is requested;
+ *    more than 1024 elements, a chunk too large for shared memory, a node
+ *    pair in more than 128 elements of one chunk) reports FEA_ERR_OVERFLOW
+ *    when this mode is requested;
  *  FEA_SCATTER_AUTO (default): chunked for P1 elasticity when its chunks can
  *    be built, the local-row scatter otherwise. */
 enum { FEA_SCATTER_AUTO = 0, FEA_SCATTER_LOCAL_ROWS = 1, FEA_SCATTER_CHUNKED = 2 };

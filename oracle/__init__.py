@@ -34,6 +34,7 @@ def lib():
         _lib.orc_assemble_tri.restype = C.c_int64
         _lib.orc_assemble_user.restype = C.c_int64
         _lib.orc_free.argtypes = [C.c_void_p]
+        _lib.orc_assemble_par.restype = C.c_int64
     return _lib
 
 
@@ -128,6 +129,35 @@ def assemble(coords, tets, order, edof, row_ptr, col_idx, kind="diffusion", mass
     if bad < 0:
         raise RuntimeError("local entry without a slot in the pattern")
     return values, rhs, int(bad)
+
+
+def assemble_par(coords, tets, order, edof, row_ptr, col_idx, kind="diffusion", mass=0.0,
+                 kappa=None, kappa_const=1.0, lam=None, lam_const=1.0, mu=None, mu_const=1.0,
+                 f_kind="sinprod", f_param=(3 * np.pi ** 2,), npts=4, threads=0):
+    """Timing baseline, not a checker: assemble() with the elements split over
+    OpenMP threads (per-thread copies of the outputs, summed at the end).
+    Returns (values, rhs, bad, threads used)."""
+    coords = np.ascontiguousarray(coords, dtype=np.float64)
+    tets = np.ascontiguousarray(tets, dtype=np.int32)
+    edof = np.ascontiguousarray(edof, dtype=np.int32)
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+    kappa, lam, mu = _keep(kappa, lam, mu)
+    ndof = row_ptr.size - 1
+    values = np.empty(int(row_ptr[-1]))
+    rhs = np.empty(ndof)
+    fp = _fparam(f_param)
+    used = C.c_int(0)
+    bad = lib().orc_assemble_par(
+        _d(coords[0]), _d(coords[1]), _d(coords[2]), C.c_int64(tets.shape[1]), tets.ctypes.data_as(_ip),
+        C.c_int(order), edof.ctypes.data_as(_ip), C.c_int(KIND[kind]), C.c_double(mass), _d(kappa),
+        C.c_double(kappa_const), _d(lam), C.c_double(lam_const), _d(mu), C.c_double(mu_const),
+        C.c_int(FKIND[f_kind]), fp.ctypes.data_as(_dp), C.c_int(npts), C.c_int64(ndof),
+        row_ptr.ctypes.data_as(_ip), col_idx.ctypes.data_as(_ip), values.ctypes.data_as(_dp),
+        rhs.ctypes.data_as(_dp), C.c_int(threads), C.byref(used))
+    if bad < 0:
+        raise RuntimeError("local entry without a slot in the pattern")
+    return values, rhs, int(bad), used.value
 
 
 def local(X, order=1, kind="diffusion", mass=0.0, kappa=None, lam=None, mu=None,

@@ -898,3 +898,79 @@ extern "C" void orc_dirichlet(int64_t ndof, const int32_t* row_ptr, const int32_
   for (int64_t i = 0; i < ndof; ++i)
     if (fixed[i]) rhs[i] = gv[i];
 }
+
+// ---------------------------------------------------------------- CPU baseline
+// Not a checker: the timing baseline of the benchmark on all host cores.  The
+// element loop of orc_assemble (same element routine, same binary-search
+// scatter), with the elements split over OpenMP threads: each thread adds
+// into its own zeroed copy of the values and the load vector, and the copies
+// are then summed position by position.  Without OpenMP it runs on one
+// thread.  Returns the number of elements with det J <= 0, or -1.
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+extern "C" int64_t orc_assemble_par(const double* x, const double* y, const double* z, int64_t n_elems,
+                                    const int32_t* tets, int order, const int32_t* edof, int kind,
+                                    double mass_coef, const double* kappa, double kappa_const, const double* lam,
+                                    double lam_const, const double* mu, double mu_const, int f_kind,
+                                    const double* f_param, int npts, int64_t ndof, const int32_t* row_ptr,
+                                    const int32_t* col_idx, double* values, double* rhs, int nthreads,
+                                    int* used_threads) {
+  Form F = make_form(order, kind, mass_coef, f_kind, f_param, npts);
+  const int nb = (order == 1) ? 4 : 10;
+  const int nl = nb * F.ndpn;
+  const int64_t nnz = row_ptr[ndof];
+  int T = 1;
+#ifdef _OPENMP
+  T = nthreads > 0 ? nthreads : omp_get_max_threads();
+#else
+  (void)nthreads;
+#endif
+  std::vector<std::vector<double>> V(T), R(T);
+  int64_t bad = 0, missing = 0;
+#pragma omp parallel num_threads(T) reduction(+ : bad, missing)
+  {
+    int t = 0;
+#ifdef _OPENMP
+    t = omp_get_thread_num();
+#endif
+    V[t].assign(nnz, 0.0);
+    R[t].assign(ndof, 0.0);
+    std::vector<double> Ke(nl * nl), Fe(nl);
+#pragma omp for schedule(static)
+    for (int64_t e = 0; e < n_elems; ++e) {
+      double X[4][3];
+      for (int v = 0; v < 4; ++v) {
+        int32_t n = tets[v * n_elems + e];
+        X[v][0] = x[n]; X[v][1] = y[n]; X[v][2] = z[n];
+      }
+      double det = element<double>(F, X, kappa ? kappa[e] : kappa_const, lam ? lam[e] : lam_const,
+                                   mu ? mu[e] : mu_const, Ke.data(), Fe.data());
+      if (!(det > 0)) ++bad;
+      for (int a = 0; a < nl; ++a) {
+        int64_t ra = (int64_t)edof[(a / F.ndpn) * n_elems + e] * F.ndpn + a % F.ndpn;
+        R[t][ra] += Fe[a];
+        for (int b = 0; b < nl; ++b) {
+          int64_t cb = (int64_t)edof[(b / F.ndpn) * n_elems + e] * F.ndpn + b % F.ndpn;
+          int64_t p = find_pos(row_ptr, col_idx, ra, cb);
+          if (p < 0) ++missing;
+          else V[t][p] += Ke[a * nl + b];
+        }
+      }
+    }
+  }
+#pragma omp parallel for num_threads(T) schedule(static)
+  for (int64_t p = 0; p < nnz; ++p) {
+    double s = 0.0;
+    for (int t = 0; t < T; ++t) s += V[t][p];
+    values[p] = s;
+  }
+#pragma omp parallel for num_threads(T) schedule(static)
+  for (int64_t i = 0; i < ndof; ++i) {
+    double s = 0.0;
+    for (int t = 0; t < T; ++t) s += R[t][i];
+    rhs[i] = s;
+  }
+  if (used_threads) *used_threads = T;
+  return missing ? -1 : bad;
+}

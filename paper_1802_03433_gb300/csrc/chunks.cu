@@ -19,7 +19,7 @@
 //     gets the CSR positions of its two 3 x 3 blocks and, when it is shared,
 //     the index of its partial sum;
 //  4. the partial sums of every shared coupling (and every shared node's
-//     load) are listed in chunk order for the second kernel.
+//     load) get consecutive places, in chunk order, for the second kernel.
 // Every step is deterministic: atomics only count, and every list filled
 // through an atomic cursor is sorted afterwards.
 #include <cuda_runtime.h>
@@ -329,19 +329,21 @@ __global__ void k_flags(const int32_t* __restrict__ cnt, int64_t n, int32_t* __r
   if (i < n) flag[i] = cnt[i] > 0;
 }
 
-// One entry per shared visit: its partial index goes to the list of its key;
-// the group's first list position and its record are written by every visit
-// (identical values).
+// One entry per shared visit: its chunk-major partial index goes to the list
+// of its key (inv maps it back to the visit); the group's first list
+// position and its record are written by every visit (identical values).
 __global__ void k_fill_groups(const int32_t* __restrict__ keyv, int kstride, const int32_t* __restrict__ part,
                               int pstride, int64_t n, const int64_t* __restrict__ goff, const int64_t* __restrict__ gid,
-                              int32_t* __restrict__ cursor, int32_t* __restrict__ list, int32_t* __restrict__ gptr,
-                              const int4* __restrict__ srec, int4* __restrict__ grec, int32_t* __restrict__ gnode) {
+                              int32_t* __restrict__ cursor, int32_t* __restrict__ list, int32_t* __restrict__ inv,
+                              int32_t* __restrict__ gptr, const int4* __restrict__ srec, int4* __restrict__ grec,
+                              int32_t* __restrict__ gnode) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int32_t pi = part[s * pstride];
   if (pi < 0) return;
   const int32_t k = keyv[s * kstride];
   list[goff[k] + atomicAdd(cursor + k, 1)] = pi;
+  inv[pi] = (int32_t)s;
   const int64_t g = gid[k];
   gptr[g] = (int32_t)goff[k];
   if (grec) {
@@ -351,19 +353,30 @@ __global__ void k_fill_groups(const int32_t* __restrict__ keyv, int kstride, con
   if (gnode) gnode[g] = k;
 }
 
-// Build the lists of partial sums per key (scalar CSR position of a coupling,
-// or node id): visits s = 0 .. n-1 with key keyv[s * kstride] and partial
-// index part[s * pstride] (< 0: not shared).
-fea_status build_groups(const int32_t* keyv, int kstride, const int32_t* part, int pstride, int64_t n, int64_t nkeys,
-                        const int4* srec, int64_t* ngroup, int64_t* nlist, int32_t** gptr, int32_t** list,
+// After each group's list is sorted (chunk order), every shared visit gets
+// its list position as its partial index: a group's partial sums are then
+// contiguous, in chunk order.
+__global__ void k_relink(const int32_t* __restrict__ list, int64_t n, const int32_t* __restrict__ inv,
+                         int32_t* __restrict__ part, int pstride) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) part[(int64_t)inv[list[p]] * pstride] = (int32_t)p;
+}
+
+// Build the partial-sum groups per key (scalar CSR position of a coupling,
+// or node id): visits s = 0 .. n-1 with key keyv[s * kstride] and
+// chunk-major partial index part[s * pstride] (< 0: not shared), which is
+// replaced by the visit's position in its group.
+fea_status build_groups(const int32_t* keyv, int kstride, int32_t* part, int pstride, int64_t n, int64_t nkeys,
+                        int64_t npart_in, const int4* srec, int64_t* ngroup, int64_t* nlist, int32_t** gptr,
                         int4** grec, int32_t** gnode, cudaStream_t s) {
-  Tmp<int32_t> cnt, flag, cur;
+  Tmp<int32_t> cnt, flag, cur, list, inv;
   Tmp<int64_t> goff, gid;
   FEA_TRY(cnt.alloc(nkeys));
   FEA_TRY(flag.alloc(nkeys));
   FEA_TRY(cur.alloc(nkeys));
   FEA_TRY(goff.alloc(nkeys + 1));
   FEA_TRY(gid.alloc(nkeys + 1));
+  FEA_TRY(inv.alloc(npart_in));
   FEA_CUDA(cudaMemsetAsync(cnt.p, 0, nkeys * sizeof(int32_t), s));
   FEA_CUDA(cudaMemsetAsync(cur.p, 0, nkeys * sizeof(int32_t), s));
   if (n > 0) k_count_keys<<<blocks_for(n, 256), 256, 0, s>>>(keyv, kstride, part, pstride, n, cnt.p);
@@ -373,19 +386,20 @@ fea_status build_groups(const int32_t* keyv, int kstride, const int32_t* part, i
   FEA_TRY(scan(flag.p, nkeys, gid.p, s));
   FEA_TRY(read_i64(goff.p + nkeys, nlist, s));
   FEA_TRY(read_i64(gid.p + nkeys, ngroup, s));
-  if (*nlist > (int64_t)INT32_MAX) return fail(FEA_ERR_OVERFLOW, "chunked scatter: too many partial sums");
+  if (*nlist != npart_in) return fail(FEA_ERR_STATE, "chunked scatter: inconsistent partial-sum count");
   FEA_TRY(dalloc(gptr, *ngroup + 1));
-  FEA_TRY(dalloc(list, *nlist));
+  FEA_TRY(list.alloc(*nlist));
   if (grec) FEA_TRY(dalloc(grec, *ngroup));
   if (gnode) FEA_TRY(dalloc(gnode, *ngroup));
   if (n > 0)
-    k_fill_groups<<<blocks_for(n, 256), 256, 0, s>>>(keyv, kstride, part, pstride, n, goff.p, gid.p, cur.p, *list, *gptr,
-                                                      srec,
-                                                      grec ? *grec : nullptr, gnode ? *gnode : nullptr);
+    k_fill_groups<<<blocks_for(n, 256), 256, 0, s>>>(keyv, kstride, part, pstride, n, goff.p, gid.p, cur.p, list.p,
+                                                      inv.p, *gptr, srec, grec ? *grec : nullptr,
+                                                      gnode ? *gnode : nullptr);
   const int32_t tot = (int32_t)*nlist;
   FEA_CUDA(cudaMemcpyAsync(*gptr + *ngroup, &tot, sizeof(int32_t), cudaMemcpyHostToDevice, s));
   if (*ngroup > 0)
-    k_sort_lists<<<(int)std::min<int64_t>(blocks_for(*ngroup, 4), 152 * 64), 128, 0, s>>>(*gptr, *ngroup, *list);
+    k_sort_lists<<<(int)std::min<int64_t>(blocks_for(*ngroup, 4), 152 * 64), 128, 0, s>>>(*gptr, *ngroup, list.p);
+  if (*nlist > 0) k_relink<<<blocks_for(*nlist, 256), 256, 0, s>>>(list.p, *nlist, inv.p, part, pstride);
   FEA_CUDA(cudaGetLastError());
   FEA_CUDA(cudaStreamSynchronize(s));
   return FEA_OK;
@@ -541,8 +555,10 @@ fea_status build(fea_mesh* m, Pattern* P, Chunks* C, cudaStream_t s) {
   C->hbits = 0;
   while ((1 << C->hbits) < maxcnt) ++C->hbits;
   // the accumulators of the largest chunk must fit one CTA's shared memory
-  // (9 sums and an exponent per slot, 3 sums and an exponent per node slot)
-  if ((size_t)C->max_slots * (9 * 8 + 4) + (size_t)C->max_nodes * (3 * 8 + 4) > 227 * 1024)
+  // (9 sums and an exponent per slot, 3 sums and an exponent per node slot),
+  // and a slot may take at most 128 contributions (the fixed-point scale
+  // 2^(63 - 2 hbits) keeps 49 bits or more)
+  if ((size_t)C->max_slots * (9 * 8 + 4) + (size_t)C->max_nodes * (3 * 8 + 4) > 227 * 1024 || C->hbits > 7)
     return fail(FEA_ERR_OVERFLOW, "chunked scatter: a chunk couples too many node pairs for shared memory");
   C->nslot = sptr[nc];
   C->nnode_slot = nptr[nc];
@@ -575,13 +591,12 @@ fea_status build(fea_mesh* m, Pattern* P, Chunks* C, cudaStream_t s) {
   FEA_CUDA(cudaGetLastError());
   // 4. partial-sum lists of the shared couplings (key: the scalar CSR position
   // of the coupling's upper entry) and of the shared nodes (key: node id)
-  const int32_t* partcol = reinterpret_cast<const int32_t*>(C->srec) + 3;  // .w of every record
-  FEA_TRY(build_groups(pkey.p, 1, partcol, 4, C->nslot, B->nnz, C->srec, &C->ngroup, &C->npart, &C->gptr,
-                       &C->glist, &C->grec, nullptr, s));
-  const int32_t* nodecol = reinterpret_cast<const int32_t*>(C->nrec);
-  const int32_t* npartcol = nodecol + 1;
-  FEA_TRY(build_groups(nodecol, 2, npartcol, 2, C->nnode_slot, N, nullptr, &C->nngroup, &C->nnpart, &C->ngptr,
-                       &C->nglist, nullptr, &C->ngnode, s));
+  int32_t* partcol = reinterpret_cast<int32_t*>(C->srec) + 3;  // .w of every record
+  FEA_TRY(build_groups(pkey.p, 1, partcol, 4, C->nslot, B->nnz, C->npart, C->srec, &C->ngroup, &C->npart, &C->gptr,
+                       &C->grec, nullptr, s));
+  int32_t* nodecol = reinterpret_cast<int32_t*>(C->nrec);
+  FEA_TRY(build_groups(nodecol, 2, nodecol + 1, 2, C->nnode_slot, N, C->nnpart, nullptr, &C->nngroup, &C->nnpart,
+                       &C->ngptr, nullptr, &C->ngnode, s));
   // nodes of no element: no chunk writes their load entries (the set, not
   // its order, matters: they are written with zeros)
   Tmp<int32_t> niso;
@@ -608,10 +623,8 @@ void free_chunks(Chunks* c) {
   dfree(c->srec);
   dfree(c->nrec);
   dfree(c->gptr);
-  dfree(c->glist);
   dfree(c->grec);
   dfree(c->ngptr);
-  dfree(c->nglist);
   dfree(c->ngnode);
   dfree(c->iso);
   delete c;

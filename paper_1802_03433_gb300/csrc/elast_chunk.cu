@@ -1,6 +1,6 @@
 // Chunked scatter of P1 linear elasticity (one CTA per chunk of elements,
 // chunks.cu): the local entries of the chunk's elements are accumulated in
-// shared memory as 64-bit fixed-point integers, then each coupling the chunk
+// shared memory as fixed-point integers, then each coupling the chunk
 // completes is written to the CSR values once, and each coupling it shares
 // with other chunks as one FP64 partial sum, which k_chunk_reduce adds in
 // chunk order.
@@ -14,12 +14,13 @@
 // atomic units, leaving the FP64 pipe (2 DFMA per SM and clock on this part)
 // to the element arithmetic.  Each slot (a node pair of the chunk) has its own
 // scale 2^(H - Es): Es is the largest exponent bound of the contributing
-// elements, computed before any entry is added (phase A), and H = 62 - hbits
-// leaves room for the slot's contributions to add up without overflow.  A
+// elements, computed before any entry is added (phase A), and H = 63 - 2 hbits
+// (2^hbits: the most contributions one slot receives) leaves room for the
+// contributions to add up without overflow in two 32-bit words (acc_add).  A
 // contribution below the slot's resolution 2^(Es - H) is rounded to it; the
-// bound is within a factor of a few hundred of the largest entry, so that
-// resolution is about 2^-50 of the largest contribution, the rounding of one
-// FP64 addition.  The sum is rounded to FP64 once.
+// bound is within a factor of a few hundred of the largest entry, so with
+// hbits = 5 (24 tets around a vertex) that resolution is about 2^-47 of the
+// largest contribution.  The sum is rounded to FP64 once.
 //
 // Phases of k_elast_chunk (one CTA, CHUNK_T threads, elements strided over
 // the threads):
@@ -52,6 +53,10 @@ constexpr int CHUNK_MIN_BLOCKS = 3;
 constexpr int EXP_POISON = 1 << 20;    // a slot exponent at or above: the slot is NaN
 constexpr int EXP_EMPTY = -(1 << 20);  // no contribution yet
 constexpr int EXP_ZERO = -1200;        // bound of contributions that are all zero
+// A partial sum of a shared 3 x 3 block takes 12 doubles (three whole 32-byte
+// sectors, so its stores never leave a sector partly written), a partial load
+// 4 (one sector).
+constexpr int PART_STRIDE = 12;
 
 struct ChunkArgs {
   const int32_t* cptr;
@@ -62,13 +67,14 @@ struct ChunkArgs {
   const int4* srec;
   const int2* nrec;
   int H;          // fixed-point scale of a slot: value * 2^(H - Es)
+  int K;          // split of a fixed-point value q = hi 2^K + lo, 0 <= lo < 2^K
   int ef;         // |f_c| < 2^ef for the load amplitudes (EXP_ZERO: no load, EXP_POISON: non-finite)
   int max_slots;  // shared-memory capacity
   int max_nodes;
   double* values;
   double* rhs;
-  double* part;   // [npart][9] partial sums of shared couplings
-  double* npart;  // [nnpart][3] partial sums of shared node loads
+  double* part;   // [npart][PART_STRIDE] partial sums of shared couplings (9 used)
+  double* npart;  // [nnpart][4] partial sums of shared node loads (3 used)
 };
 
 // |x| < 2^result for a positive normal float.
@@ -235,25 +241,54 @@ __host__ __device__ constexpr int pair_index(int a, int b) {
   return a == b ? a : (a == 0 ? 3 + b : (a == 1 ? 5 + b : 9));
 }
 
+// Add a fixed-point value into a two-word accumulator with two 32-bit
+// shared-memory atomics (native, no return value used, so the warp does not
+// wait for them): lo takes q mod 2^K, hi takes floor(q / 2^K).  With at most
+// 2^hbits contributions, K = 32 - hbits and H = 63 - 2 hbits neither word
+// overflows, and hi 2^K + lo is the exact sum.
+__device__ __forceinline__ void acc_add(unsigned* lo, int* hi, long long q, int K) {
+  atomicAdd(lo, static_cast<unsigned>(q) & ((1u << K) - 1u));
+  atomicAdd(hi, static_cast<int>(q >> K));
+}
+__device__ __forceinline__ long long acc_sum(const unsigned* lo, const int* hi, int K) {
+  return (static_cast<long long>(*hi) << K) + static_cast<long long>(*lo);
+}
+
 template <int LOAD, int NPTS, typename R>
 __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemArgs A, ChunkArgs C) {
-  extern __shared__ long long smem_acc[];
-  long long* acc = smem_acc;                                  // [max_slots][9]
-  long long* racc = acc + 9 * C.max_slots;                    // [max_nodes][3]
-  int* sexp = reinterpret_cast<int*>(racc + 3 * C.max_nodes);  // [max_slots]
-  int* rexp = sexp + C.max_slots;                             // [max_nodes]
+  extern __shared__ unsigned smem_acc[];
+  unsigned* alo = smem_acc;                                     // [max_slots][9] low words
+  int* ahi = reinterpret_cast<int*>(alo + 9 * C.max_slots);     // [max_slots][9] high words
+  unsigned* rlo = reinterpret_cast<unsigned*>(ahi + 9 * C.max_slots);  // [max_nodes][3]
+  int* rhi = reinterpret_cast<int*>(rlo + 3 * C.max_nodes);     // [max_nodes][3]
+  int* sexp = rhi + 3 * C.max_nodes;                            // [max_slots]
+  int* rexp = sexp + C.max_slots;                               // [max_nodes]
   const int c = blockIdx.x, tid = threadIdx.x;
   const int e0 = C.cptr[c], ne = C.cptr[c + 1] - e0;
   const int s0 = C.sptr[c], ns = C.sptr[c + 1] - s0;
   const int n0 = C.nptr[c], nn = C.nptr[c + 1] - n0;
   constexpr bool HAS_LOAD = LOAD != LOAD_NONE;
-  for (int i = tid; i < 9 * ns; i += CHUNK_T) acc[i] = 0;
-  for (int i = tid; i < 3 * nn; i += CHUNK_T) racc[i] = 0;
+  const int K = C.K;
+  for (int i = tid; i < 9 * ns; i += CHUNK_T) {
+    alo[i] = 0u;
+    ahi[i] = 0;
+  }
+  for (int i = tid; i < 3 * nn; i += CHUNK_T) {
+    rlo[i] = 0u;
+    rhi[i] = 0;
+  }
   for (int i = tid; i < ns; i += CHUNK_T) sexp[i] = EXP_EMPTY;
   for (int i = tid; i < nn; i += CHUNK_T) rexp[i] = EXP_EMPTY;
   __syncthreads();
+  // Elements are dealt to the lanes across 64 segments of the chunk (lane i
+  // takes position i / 64 of segment i % 64): neighbouring elements, which
+  // share node pairs, go to different warp instructions, so the atomics of
+  // one instruction seldom hit the same accumulator.
+  const int L = (ne + 63) >> 6;
   // A: exponent bounds of every slot
-  for (int t = tid; t < ne; t += CHUNK_T) {
+  for (int i = tid; i < 64 * L; i += CHUNK_T) {
+    const int t = (i & 63) * L + (i >> 6);
+    if (t >= ne) continue;
     const int64_t e = C.celem[e0 + t];
     double X[4][3];
     load_element(A, e, X);
@@ -269,7 +304,9 @@ __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemA
   }
   __syncthreads();
   // B: the entries, added in fixed point
-  for (int t = tid; t < ne; t += CHUNK_T) {
+  for (int i = tid; i < 64 * L; i += CHUNK_T) {
+    const int t = (i & 63) * L + (i >> 6);
+    if (t >= ne) continue;
     const int64_t e = C.celem[e0 + t];
     int slot[10], sh[10];
     bool tr[10];
@@ -288,13 +325,12 @@ __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemA
     const double adet = fabs(g.det);
     const double lam = A.lam ? __ldg(A.lam + e) : A.lam_const;
     const double mu = A.mu ? __ldg(A.mu + e) : A.mu_const;
-    elast_upper<R>(g, adet, lam, mu, [&](auto K, R v) {
-      constexpr int r = upper_a(12, K), cc = upper_b(12, K);
-      constexpr int a = r / 3, i = r % 3, b = cc / 3, j = cc % 3;
+    elast_upper<R>(g, adet, lam, mu, [&](auto KK, R v) {
+      constexpr int r = upper_a(12, KK), cc = upper_b(12, KK);
+      constexpr int a = r / 3, i3 = r % 3, b = cc / 3, j3 = cc % 3;
       constexpr int k = pair_index(a, b);
-      const int idx = (a != b && tr[k]) ? 3 * j + i : 3 * i + j;
-      atomicAdd(reinterpret_cast<unsigned long long*>(acc + 9 * slot[k] + idx),
-                static_cast<unsigned long long>(fx_of(v, sh[k])));
+      const int idx = 9 * slot[k] + ((a != b && tr[k]) ? 3 * j3 + i3 : 3 * i3 + j3);
+      acc_add(alo + idx, ahi + idx, fx_of(v, sh[k]), K);
     });
     if constexpr (HAS_LOAD) {
       R Xr[4][3];
@@ -307,9 +343,10 @@ __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemA
       for (int a = 0; a < 4; ++a) {
         const int shf = C.H - rexp[slot[a]];
 #pragma unroll
-        for (int q = 0; q < 3; ++q)
-          atomicAdd(reinterpret_cast<unsigned long long*>(racc + 3 * slot[a] + q),
-                    static_cast<unsigned long long>(fx_of(R(f[q] * Fs[a]), shf)));
+        for (int q = 0; q < 3; ++q) {
+          const int idx = 3 * slot[a] + q;
+          acc_add(rlo + idx, rhi + idx, fx_of(R(f[q] * Fs[a]), shf), K);
+        }
       }
     }
   }
@@ -324,7 +361,7 @@ __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemA
       for (int q = 0; q < 9; ++q) v[q] = __longlong_as_double(0x7FF8000000000000LL);
     } else {
 #pragma unroll
-      for (int q = 0; q < 9; ++q) v[q] = f64_of(acc[9 * k + q], es - C.H);
+      for (int q = 0; q < 9; ++q) v[q] = f64_of(acc_sum(alo + 9 * k + q, ahi + 9 * k + q, K), es - C.H);
     }
     if (k < nn) {  // node slot: the upper triangle was accumulated; mirror it
       v[3] = v[1];
@@ -344,9 +381,10 @@ __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemA
           for (int i = 0; i < 3; ++i) C.values[(int64_t)rec.y + j * Lj + i] = v[3 * i + j];
       }
     } else {
-      double* p = C.part + 9 * (int64_t)rec.w;
-#pragma unroll
-      for (int q = 0; q < 9; ++q) p[q] = v[q];
+      double* p = C.part + PART_STRIDE * (int64_t)rec.w;
+      st_v4(p, v[0], v[1], v[2], v[3]);
+      st_v4(p + 4, v[4], v[5], v[6], v[7]);
+      st_v4(p + 8, v[8], 0.0, 0.0, 0.0);
     }
   }
   if (C.rhs) {
@@ -356,28 +394,38 @@ __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemA
       double f[3];
 #pragma unroll
       for (int q = 0; q < 3; ++q)
-        f[q] = es >= EXP_POISON ? __longlong_as_double(0x7FF8000000000000LL) : f64_of(racc[3 * k + q], es - C.H);
-      double* dst = nr.y < 0 ? C.rhs + 3 * (int64_t)nr.x : C.npart + 3 * (int64_t)nr.y;
+        f[q] = es >= EXP_POISON ? __longlong_as_double(0x7FF8000000000000LL)
+                                : f64_of(acc_sum(rlo + 3 * k + q, rhi + 3 * k + q, K), es - C.H);
+      if (nr.y < 0) {
 #pragma unroll
-      for (int q = 0; q < 3; ++q) dst[q] = f[q];
+        for (int q = 0; q < 3; ++q) C.rhs[3 * (int64_t)nr.x + q] = f[q];
+      } else {
+        st_v4(C.npart + 4 * (int64_t)nr.y, f[0], f[1], f[2], 0.0);
+      }
     }
   }
 }
 
-// The couplings shared by several chunks: their partial sums in chunk order.
-__global__ void k_chunk_reduce(const int32_t* __restrict__ gptr, const int32_t* __restrict__ glist,
-                               const int4* __restrict__ grec, int64_t ngroup, const double* __restrict__ part,
-                               double* __restrict__ values) {
+// The couplings shared by several chunks: their partial sums, contiguous
+// and in chunk order, added and written as both 3 x 3 blocks.
+__global__ void k_chunk_reduce(const int32_t* __restrict__ gptr, const int4* __restrict__ grec, int64_t ngroup,
+                               const double* __restrict__ part, double* __restrict__ values) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= ngroup) return;
   const int32_t p0 = gptr[g], p1 = gptr[g + 1];
-  double v[9];
-#pragma unroll
-  for (int q = 0; q < 9; ++q) v[q] = part[9 * (int64_t)glist[p0] + q];
+  double v[12];
+  const double* src = part + PART_STRIDE * (int64_t)p0;
+  ld_v4(src, v[0], v[1], v[2], v[3]);
+  ld_v4(src + 4, v[4], v[5], v[6], v[7]);
+  ld_v4(src + 8, v[8], v[9], v[10], v[11]);
   for (int32_t p = p0 + 1; p < p1; ++p) {
-    const double* src = part + 9 * (int64_t)glist[p];
+    src = part + PART_STRIDE * (int64_t)p;
+    double w[12];
+    ld_v4(src, w[0], w[1], w[2], w[3]);
+    ld_v4(src + 4, w[4], w[5], w[6], w[7]);
+    ld_v4(src + 8, w[8], w[9], w[10], w[11]);
 #pragma unroll
-    for (int q = 0; q < 9; ++q) v[q] += src[q];
+    for (int q = 0; q < 9; ++q) v[q] += w[q];
   }
   const int4 rec = grec[g];
   const int Li = rec.z & 0xFFFF, Lj = rec.z >> 16;
@@ -393,18 +441,19 @@ __global__ void k_chunk_reduce(const int32_t* __restrict__ gptr, const int32_t* 
   }
 }
 
-__global__ void k_chunk_reduce_nodes(const int32_t* __restrict__ gptr, const int32_t* __restrict__ glist,
-                                     const int32_t* __restrict__ gnode, int64_t ngroup,
-                                     const double* __restrict__ npart, double* __restrict__ rhs) {
+__global__ void k_chunk_reduce_nodes(const int32_t* __restrict__ gptr, const int32_t* __restrict__ gnode,
+                                     int64_t ngroup, const double* __restrict__ npart, double* __restrict__ rhs) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= ngroup) return;
   const int32_t p0 = gptr[g], p1 = gptr[g + 1];
-  double f[3];
+  double f[4];
+  ld_v4(npart + 4 * (int64_t)p0, f[0], f[1], f[2], f[3]);
+  for (int32_t p = p0 + 1; p < p1; ++p) {
+    double w[4];
+    ld_v4(npart + 4 * (int64_t)p, w[0], w[1], w[2], w[3]);
 #pragma unroll
-  for (int q = 0; q < 3; ++q) f[q] = npart[3 * (int64_t)glist[p0] + q];
-  for (int32_t p = p0 + 1; p < p1; ++p)
-#pragma unroll
-    for (int q = 0; q < 3; ++q) f[q] += npart[3 * (int64_t)glist[p] + q];
+    for (int q = 0; q < 3; ++q) f[q] += w[q];
+  }
 #pragma unroll
   for (int q = 0; q < 3; ++q) rhs[3 * (int64_t)gnode[g] + q] = f[q];
 }
@@ -462,8 +511,8 @@ fea_status assemble_chunked(fea_mesh* m, Pattern* P, const fea_coeffs* co, const
                             double* values, double* rhs, cudaStream_t s) {
   FEA_TRY(build_chunks(m, P, s));
   const Chunks* K = P->chunks;
-  FEA_TRY(ensure_scratch(m->part, (size_t)std::max<int64_t>(K->npart, 1) * 9 * sizeof(double)));
-  if (rhs) FEA_TRY(ensure_scratch(m->npart, (size_t)std::max<int64_t>(K->nnpart, 1) * 3 * sizeof(double)));
+  FEA_TRY(ensure_scratch(m->part, (size_t)std::max<int64_t>(K->npart, 1) * PART_STRIDE * sizeof(double)));
+  if (rhs) FEA_TRY(ensure_scratch(m->npart, (size_t)std::max<int64_t>(K->nnpart, 1) * 4 * sizeof(double)));
   ElemArgs A{};
   A.x = m->x;
   A.y = m->y;
@@ -484,7 +533,8 @@ fea_status assemble_chunked(fea_mesh* m, Pattern* P, const fea_coeffs* co, const
   Cg.nptr = K->nptr;
   Cg.srec = K->srec;
   Cg.nrec = K->nrec;
-  Cg.H = 62 - K->hbits;
+  Cg.H = 63 - 2 * K->hbits;
+  Cg.K = 32 - K->hbits;
   const int ld = rhs ? load : LOAD_NONE;
   Cg.ef = load_exponent(co, ld);
   Cg.max_slots = K->max_slots;
@@ -493,8 +543,8 @@ fea_status assemble_chunked(fea_mesh* m, Pattern* P, const fea_coeffs* co, const
   Cg.rhs = rhs;
   Cg.part = static_cast<double*>(m->part.ptr);
   Cg.npart = rhs ? static_cast<double*>(m->npart.ptr) : nullptr;
-  const size_t smem = (size_t)K->max_slots * (9 * sizeof(long long) + sizeof(int)) +
-                      (size_t)K->max_nodes * (3 * sizeof(long long) + sizeof(int));
+  const size_t smem = (size_t)K->max_slots * (9 * 2 * sizeof(int) + sizeof(int)) +
+                      (size_t)K->max_nodes * (3 * 2 * sizeof(int) + sizeof(int));
   if (smem > 227 * 1024) return fail(FEA_ERR_OVERFLOW, "chunked scatter: chunk too large for shared memory");
   if (m->profile) FEA_CUDA(cudaEventRecord(m->ev[0], s));
   if (K->nchunk > 0) {
@@ -503,13 +553,13 @@ fea_status assemble_chunked(fea_mesh* m, Pattern* P, const fea_coeffs* co, const
   }
   if (m->profile) FEA_CUDA(cudaEventRecord(m->ev[1], s));
   if (K->ngroup > 0)
-    k_chunk_reduce<<<(unsigned)((K->ngroup + 127) / 128), 128, 0, s>>>(K->gptr, K->glist, K->grec, K->ngroup,
-                                                                       Cg.part, values);
+    k_chunk_reduce<<<(unsigned)((K->ngroup + 127) / 128), 128, 0, s>>>(K->gptr, K->grec, K->ngroup, Cg.part,
+                                                                       values);
   if (rhs && K->niso > 0)
     k_zero_nodes<<<(unsigned)((3 * K->niso + 255) / 256), 256, 0, s>>>(K->iso, K->niso, rhs);
   if (rhs && K->nngroup > 0)
-    k_chunk_reduce_nodes<<<(unsigned)((K->nngroup + 127) / 128), 128, 0, s>>>(K->ngptr, K->nglist, K->ngnode,
-                                                                             K->nngroup, Cg.npart, rhs);
+    k_chunk_reduce_nodes<<<(unsigned)((K->nngroup + 127) / 128), 128, 0, s>>>(K->ngptr, K->ngnode, K->nngroup,
+                                                                             Cg.npart, rhs);
   FEA_CUDA(cudaGetLastError());
   if (m->profile) {
     FEA_CUDA(cudaEventRecord(m->ev[2], s));

@@ -80,14 +80,14 @@ struct Chunks {
                                  // CSR position of entry (3i, 3j) and of (3j, 3i), the lengths of rows
                                  // 3i and 3j, for the slot's node pair i <= j
   int2* nrec = nullptr;          // [nnode_slot] {node id, load partial index or -1 when owned}
-  // couplings shared by several chunks: partial sums listed in chunk order
+  // couplings shared by several chunks: the partial sums of group g (one per
+  // chunk that touches it) are partials gptr[g] .. gptr[g + 1] - 1, in chunk
+  // order; a shared slot's record holds the index of its partial
   int64_t npart = 0, ngroup = 0;
   int32_t* gptr = nullptr;       // [ngroup + 1]
-  int32_t* glist = nullptr;      // [npart] partial indices
   int4* grec = nullptr;          // [ngroup] {U, W, Li | Lj << 16, 0}
   int64_t nnpart = 0, nngroup = 0;
   int32_t* ngptr = nullptr;      // [nngroup + 1]
-  int32_t* nglist = nullptr;     // [nnpart]
   int32_t* ngnode = nullptr;     // [nngroup] node id
   int64_t niso = 0;
   int32_t* iso = nullptr;        // [niso] nodes of no element (their load entries are zero)
