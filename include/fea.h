@@ -466,6 +466,34 @@ fea_status fea_dirichlet(fea_mesh* mesh, int32_t order, int32_t dofs_per_node, c
 fea_status fea_cg(fea_mesh* mesh, int32_t order, int32_t dofs_per_node, const double* values, const double* b,
                   double* x, double rtol, int32_t max_iter, int32_t* iters, double* rel_res, void* stream);
 
+/* ---------------------------------------------------------------- several GPUs
+ * Row partition of a P1 tetrahedral mesh (the paper assembles one mesh on one
+ * GPU, Sec. 5; this splits the same element-parallel assembly by rows).  Part
+ * `part` of `nparts` owns the nodes [lo, hi), lo = floor(part N / nparts),
+ * hi = floor((part + 1) N / nparts) (for node ids that run z-slowest, as on
+ * the cube meshes, a z-slab), and takes every element with a vertex in that
+ * range: its own elements and the ghost layer it shares with its neighbours.
+ * Assembled on its own, that sub-mesh gives the complete rows of every owned
+ * node - the rows of the whole mesh's matrix, with no exchange between parts:
+ * nodes are renumbered in ascending global order (so each row's columns stay
+ * in the same order) and elements keep their ascending order (so the
+ * local-row scatter adds each entry's contributions in the same order and
+ * the owned rows are bitwise those of the whole mesh).  P1 patterns only
+ * (scalar or 3 dofs per node); the owned rows of the sub-mesh are those of
+ * its local nodes [a, b) with nodes[a] = lo, nodes[b - 1] = hi - 1.
+ *   tets       : [4][n_elems] int32 connectivity, HOST memory;
+ *   node_lo/hi : receive lo, hi;  n_sub_elems / n_sub_nodes: the sub-mesh sizes;
+ *   elems      : [n_sub_elems] the global ids of its elements, ascending, or NULL;
+ *   nodes      : [n_sub_nodes] the global ids of its nodes, ascending (the
+ *                nodes of its elements and every owned node), or NULL;
+ *   sub_tets   : [4][n_sub_elems] its connectivity in local node numbers, or NULL.
+ * All arrays are host memory owned by the caller: call once with NULL arrays
+ * for the sizes, then with arrays of those sizes.  Host only (no CUDA call,
+ * no GPU needed); deterministic.  FEA_ERR_INDEX for a node id out of range. */
+fea_status fea_partition(const int32_t* tets, int64_t n_elems, int64_t n_nodes, int32_t nparts, int32_t part,
+                         int64_t* node_lo, int64_t* node_hi, int64_t* n_sub_elems, int64_t* n_sub_nodes,
+                         int32_t* elems, int32_t* nodes, int32_t* sub_tets);
+
 /* Message for the last error on the calling thread ("" if none). */
 const char* fea_last_error(void);
 

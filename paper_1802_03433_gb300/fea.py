@@ -115,6 +115,7 @@ def lib() -> C.CDLL:
         "fea_dirichlet": [_vp, C.c_int32, C.c_int32, _vp, C.c_int64, _vp, _vp, _vp, _vp],
         "fea_cg": [_vp, C.c_int32, C.c_int32, _vp, _vp, _vp, C.c_double, C.c_int32, C.POINTER(C.c_int32),
                    C.POINTER(C.c_double), _vp],
+        "fea_partition": [_vp, C.c_int64, C.c_int64, C.c_int32, C.c_int32, i64p, i64p, i64p, i64p, _vp, _vp, _vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -419,6 +420,46 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def fea_partition(tets, n_nodes, nparts, part):
+    """Row partition of a P1 mesh (host arrays; no GPU needed): part `part` of
+    `nparts` owns nodes [lo, hi) and takes every element with a vertex there.
+    tets: int32 (4, E) numpy array.  Returns dict(lo, hi, elems, nodes,
+    sub_tets) with numpy arrays: the global ids of the part's elements and
+    nodes (ascending) and its connectivity in local node numbers."""
+    import numpy as np
+    t = np.ascontiguousarray(tets, dtype=np.int32)
+    E = t.shape[1]
+    lo, hi, ne, nn = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+    tp = C.c_void_p(t.ctypes.data) if E else None
+    _check(lib().fea_partition(tp, E, n_nodes, nparts, part, C.byref(lo), C.byref(hi), C.byref(ne), C.byref(nn),
+                               None, None, None), "fea_partition")
+    elems = np.empty(max(ne.value, 1), dtype=np.int32)
+    nodes = np.empty(max(nn.value, 1), dtype=np.int32)
+    sub = np.empty((4, max(ne.value, 1)), dtype=np.int32)
+    _check(lib().fea_partition(tp, E, n_nodes, nparts, part, C.byref(lo), C.byref(hi), C.byref(ne), C.byref(nn),
+                               C.c_void_p(elems.ctypes.data), C.c_void_p(nodes.ctypes.data),
+                               C.c_void_p(sub.ctypes.data)), "fea_partition")
+    return dict(lo=lo.value, hi=hi.value, elems=elems[:ne.value], nodes=nodes[:nn.value],
+                sub_tets=np.ascontiguousarray(sub[:, :ne.value]))
+
+
+def owned_rows(part, row_ptr, col_idx, values, dofs_per_node=1):
+    """The owned rows of a part's assembled sub-mesh in global numbering:
+    (first global row, row lengths, global columns, values) as numpy arrays
+    (row_ptr, col_idx, values of the sub-mesh's CSR, host or device)."""
+    import numpy as np
+    rp = np.asarray(row_ptr.cpu() if hasattr(row_ptr, "cpu") else row_ptr).astype(np.int64)
+    ci = np.asarray(col_idx.cpu() if hasattr(col_idx, "cpu") else col_idx).astype(np.int64)
+    v = np.asarray(values.cpu() if hasattr(values, "cpu") else values)
+    nodes = part["nodes"].astype(np.int64)
+    a = int(np.searchsorted(nodes, part["lo"]))
+    b = int(np.searchsorted(nodes, part["hi"]))
+    r0, r1 = dofs_per_node * a, dofs_per_node * b
+    s0, s1 = int(rp[r0]), int(rp[r1])
+    cols = dofs_per_node * nodes[ci[s0:s1] // dofs_per_node] + ci[s0:s1] % dofs_per_node
+    return dofs_per_node * part["lo"], np.diff(rp[r0:r1 + 1]), cols, v[s0:s1]
 
 
 # ---------------------------------------------------------------- convenience wrapper

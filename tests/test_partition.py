@@ -1,0 +1,141 @@
+"""Row partition of a mesh over several GPUs (fea_partition; host only, no
+GPU needed here).  Checked on the CPU: the owned node ranges tile the mesh,
+each part's element set is exactly the elements with a vertex in its range
+(its own plus the ghost layer), its local numbering keeps the global order,
+and - with the CPU oracle assembling each part's sub-mesh - the owned rows of
+the parts, put together, are bitwise the rows of the whole mesh.  The
+bookkeeping runs as a world-size-2 gloo job, as the ranks of a multi-GPU run
+would."""
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1802_03433_gb300 import meshgen as mg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fea():
+    import torch  # noqa: F401  (CUDA runtime first)
+    from paper_1802_03433_gb300 import build_lib, fea
+    build_lib.build()
+    return fea
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    from paper_1802_03433_gb300 import fea
+    from paper_1802_03433_gb300 import meshgen as mg
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    coords, tets, _ = mg.make_cube(6, 0.2, 1)
+    p = fea.fea_partition(tets, coords.shape[1], world, rank)
+    # every rank learns every part's range and element count
+    mine = torch.tensor([p["lo"], p["hi"], p["elems"].size, p["nodes"].size], dtype=torch.int64)
+    allp = [torch.zeros(4, dtype=torch.int64) for _ in range(world)]
+    dist.all_gather(allp, mine)
+    q.put((rank, [t.tolist() for t in allp], p["elems"].tolist(), p["nodes"].tolist(), p["sub_tets"].tolist()))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_partition_bookkeeping_gloo(fea):
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    res = sorted(q.get(timeout=180) for _ in ps)
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    coords, tets, _ = mg.make_cube(6, 0.2, 1)
+    N, E = coords.shape[1], tets.shape[1]
+    ranges = res[0][1]
+    assert ranges == res[1][1]  # every rank saw the same table
+    # the owned ranges tile [0, N) in rank order
+    assert ranges[0][0] == 0 and ranges[-1][1] == N
+    assert all(ranges[k][1] == ranges[k + 1][0] for k in range(len(ranges) - 1))
+    for rank, _, elems, nodes, sub in res:
+        lo, hi = ranges[rank][0], ranges[rank][1]
+        want = np.flatnonzero(((tets >= lo) & (tets < hi)).any(axis=0))
+        np.testing.assert_array_equal(np.array(elems), want)  # own + ghost elements, exactly
+        want_nodes = np.union1d(np.unique(tets[:, want]), np.arange(lo, hi))
+        np.testing.assert_array_equal(np.array(nodes), want_nodes)
+        np.testing.assert_array_equal(np.array(nodes)[np.array(sub)], tets[:, want])  # local -> global
+    # ghosts: the two parts share the layer of elements that straddle the cut
+    shared = np.intersect1d(res[0][2], res[1][2])
+    straddle = np.flatnonzero(((tets < ranges[0][1]).any(axis=0)) & ((tets >= ranges[1][0]).any(axis=0)))
+    np.testing.assert_array_equal(shared, straddle)
+    assert 0 < shared.size < E
+
+
+@pytest.mark.parametrize("kind,ndpn,nparts", [("p1_kappa", 1, 3), ("elasticity", 3, 2), ("elasticity", 3, 4)])
+def test_owned_rows_of_the_parts_are_the_whole_mesh_rows(fea, kind, ndpn, nparts):
+    """The oracle on each part's sub-mesh: the owned rows, concatenated in
+    part order, are bitwise the oracle's rows of the whole mesh (same
+    elements in the same order, same coordinates)."""
+    from common import case
+    c = case(kind, 5, seed=21)
+    coords, tets = c["coords"], c["tets"]
+    N = coords.shape[1]
+    rp, ci = oracle.pattern(N, tets, ndpn=ndpn)
+    kw = dict(f_kind=c["f_kind"], f_param=c["f_param"], npts=c["npts"])
+    if kind == "elasticity":
+        vals, rhs, _ = oracle.assemble(coords, tets, 1, tets, rp, ci, kind="elasticity", lam=c["lam"], mu=c["mu"], **kw)
+    else:
+        vals, rhs, _ = oracle.assemble(coords, tets, 1, tets, rp, ci, kappa=c["kappa"], **kw)
+    lens, cols, vs, rh = [], [], [], []
+    for part in range(nparts):
+        p = fea.fea_partition(tets, N, nparts, part)
+        sc = np.ascontiguousarray(coords[:, p["nodes"]])
+        st = p["sub_tets"]
+        srp, sci = oracle.pattern(p["nodes"].size, st, ndpn=ndpn)
+        if kind == "elasticity":
+            sv, sr, _ = oracle.assemble(sc, st, 1, st, srp, sci, kind="elasticity", lam=c["lam"][p["elems"]],
+                                        mu=c["mu"][p["elems"]], **kw)
+        else:
+            sv, sr, _ = oracle.assemble(sc, st, 1, st, srp, sci, kappa=c["kappa"][p["elems"]], **kw)
+        r0, ln, cc, vv = fea.owned_rows(p, srp, sci, sv, ndpn)
+        assert r0 == ndpn * p["lo"]
+        lens.append(ln)
+        cols.append(cc)
+        vs.append(vv)
+        a = int(np.searchsorted(p["nodes"], p["lo"]))
+        rh.append(sr[ndpn * a: ndpn * a + ndpn * (p["hi"] - p["lo"])])
+    np.testing.assert_array_equal(np.concatenate(lens), np.diff(rp))
+    np.testing.assert_array_equal(np.concatenate(cols), ci)
+    assert np.array_equal(np.concatenate(vs).view(np.uint64), vals.view(np.uint64))
+    assert np.array_equal(np.concatenate(rh).view(np.uint64), rhs.view(np.uint64))
+
+
+def test_partition_rejects_bad_arguments(fea):
+    coords, tets, _ = mg.make_cube(2)
+    N = coords.shape[1]
+    for nparts, part in ((0, 0), (2, 2), (2, -1)):
+        with pytest.raises(fea.FeaError) as ei:
+            fea.fea_partition(tets, N, nparts, part)
+        assert ei.value.status == 1
+    bad = tets.copy()
+    bad[1, 3] = N + 5
+    with pytest.raises(fea.FeaError) as ei:
+        fea.fea_partition(bad, N, 2, 0)
+    assert ei.value.status == 2
+    # more parts than nodes: some parts own nothing and take no element
+    p = fea.fea_partition(tets, N, N + 3, 0)
+    assert p["lo"] == p["hi"] == 0 and p["elems"].size == 0
