@@ -529,6 +529,7 @@ fea_status fea_batch_bind(fea_batch* b, const fea_coeffs* coeffs, double* const*
 fea_status fea_batch_assemble(fea_batch* b, void* stream) {
   if (!b) return fail(FEA_ERR_ARG, "batch is NULL");
   if (!b->bound) return fail(FEA_ERR_STATE, "fea_batch_bind first");
+  NvtxRange range("fea_batch_assemble");
   if (!b->exec) FEA_TRY(rebuild_graph(b));
   FEA_CUDA(cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream)));
   return FEA_OK;

@@ -634,6 +634,7 @@ fea_status build_chunks(fea_mesh* m, Pattern* P, cudaStream_t s) {
   if (P->chunks) return FEA_OK;
   if (P->chunks_failed) return fail(FEA_ERR_OVERFLOW, "chunked scatter: not available for this mesh");
   if (P->order != 1 || P->ndpn != 3 || !m->base[1]) return fail(FEA_ERR_STATE, "chunked scatter: P1 vector pattern only");
+  NvtxRange range("chunk build");
   Chunks* C = new Chunks();
   fea_status st = build(m, P, C, s);
   if (st == FEA_OK) {

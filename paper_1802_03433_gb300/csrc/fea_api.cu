@@ -257,6 +257,7 @@ fea_status fea_pattern(fea_mesh* m, int32_t order, int32_t dofs_per_node, int64_
   if (m->nvert == 3 && (order != FEA_P1 || dofs_per_node != 1))
     return fail(FEA_ERR_ARG, "triangle meshes have the scalar P1 pattern only");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  NvtxRange range("fea_pattern");
   FEA_TRY(build_pattern(m, order, dofs_per_node, s));
   FEA_TRY(read_and_clear_err(m, s));
   const Pattern* P = m->pat[order][dofs_per_node];
@@ -294,6 +295,7 @@ fea_status fea_assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* coe
   FEA_TRY(check_form(m, form, coeffs, quad));
   if (!values) return fail(FEA_ERR_ARG, "values is NULL");
   if (!aligned(values, 8) || (rhs && !aligned(rhs, 8))) return fail(FEA_ERR_ARG, "misaligned output");
+  NvtxRange range("fea_assemble");
   return assemble(m, form, coeffs, quad, values, rhs, static_cast<cudaStream_t>(stream));
 }
 
@@ -304,6 +306,7 @@ fea_status fea_assemble_backward(fea_mesh* m, const fea_form* form, const fea_co
   if (form->kind == FEA_ELASTICITY) return fail(FEA_ERR_ARG, "backward is implemented for the scalar forms");
   if (m->nvert != 4) return fail(FEA_ERR_ARG, "backward takes tetrahedral meshes");
   if (quad->prec != FEA_FP64) return fail(FEA_ERR_ARG, "backward runs in FP64");
+  NvtxRange range("fea_assemble_backward");
   return assemble_backward(m, form, coeffs, quad, grad_values, grad_rhs, grad_kappa, grad_x,
                            static_cast<cudaStream_t>(stream));
 }

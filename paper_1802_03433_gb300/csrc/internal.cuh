@@ -7,10 +7,22 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/fea.h"
 #include "devcommon.cuh"
 
 namespace fea {
+
+// A named NVTX range over a scope (pattern build, assembly, backward, batch
+// launch): visible in a profiler's timeline; without one attached the calls
+// return at once.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ------------------------------------------------------------------ errors
 void set_error(const std::string& msg);
