@@ -73,13 +73,14 @@ fea_status assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* co, con
   Pattern* P = m->pat[order][ndpn];
   Base* B = m->base[order];
   if (!P || !B) return fail(FEA_ERR_STATE, "fea_assemble: build the pattern with fea_pattern first");
-  // the chunked fixed-point scatter (elasticity): requested, or automatic
+  // the chunked fixed-point scatter: requested, or automatic (elasticity)
   // when its chunks can be built for this mesh
-  if (m->scatter == FEA_SCATTER_CHUNKED && form->kind != FEA_ELASTICITY)
-    return fail(FEA_ERR_ARG, "the chunked scatter is implemented for P1 elasticity");
-  if (form->kind == FEA_ELASTICITY && m->scatter != FEA_SCATTER_LOCAL_ROWS &&
-      (m->scatter == FEA_SCATTER_CHUNKED || !P->chunks_failed)) {
-    const fea_status st = assemble_chunked(m, P, co, q, rhs ? co->f_kind : FEA_LOAD_NONE, values, rhs, s);
+  const bool chunked = m->scatter == FEA_SCATTER_CHUNKED ||
+                       (m->scatter == FEA_SCATTER_AUTO && form->kind == FEA_ELASTICITY && !P->chunks_failed);
+  if (chunked) {
+    const int ld = rhs ? co->f_kind : FEA_LOAD_NONE;
+    const fea_status st = form->kind == FEA_ELASTICITY ? assemble_chunked(m, P, co, q, ld, values, rhs, s)
+                                                       : assemble_chunked_scalar(m, P, form, co, q, ld, values, rhs, s);
     if (st == FEA_OK || m->scatter == FEA_SCATTER_CHUNKED || !P->chunks_failed) return st;
     set_error("");  // automatic mode: the chunks cannot be built, take the local rows
   }

@@ -1,7 +1,8 @@
-// Chunks of the chunked scatter of the P1 vector (elasticity) pattern, built
-// once per mesh on the first chunked assembly (the structures are described
-// with struct Chunks in internal.cuh; the assembly kernels are in
-// elast_chunk.cu).
+// Chunks of the chunked scatter, built once per (mesh, pattern) on the first
+// chunked assembly: the P1 vector (elasticity) pattern and the scalar P1 and
+// P2 patterns (the structures are described with struct Chunks in
+// internal.cuh; the assembly kernels are in elast_chunk.cu and
+// scalar_chunk.cu).
 //
 // The paper's Algorithm 1 (Sec. 5) first accumulates a batch of elements in
 // shared memory and only then adds the batch into the global matrix.  The
@@ -12,12 +13,14 @@
 //  2. the cells are visited in Morton order and cut into chunks of at most
 //     CHUNK_MAX_ELEMS elements (whole cells; a larger cell is split), the
 //     elements of a cell in ascending id;
-//  3. per chunk (one CTA): the element vertex pairs are sorted and
-//     de-duplicated into slots (node pairs i <= j, the node slots i == i
-//     first); a slot is owned when the chunk holds every element that
-//     contains both nodes (the incidence lists say how many do); each slot
-//     gets the CSR positions of its two 3 x 3 blocks and, when it is shared,
-//     the index of its partial sum;
+//  3. per chunk (one CTA): the pairs of local dofs (vertices for P1, the
+//     ten P2 dofs for P2) of its elements are sorted and de-duplicated into
+//     slots (scalar dof pairs i <= j, the dof slots i == i first); a slot is
+//     owned when the chunk holds every element that contains both dofs (the
+//     incidence lists say how many do); each slot gets the CSR positions of
+//     its two blocks ((i, j) and (j, i), 3 x 3 for elasticity, single
+//     entries otherwise) and, when it is shared, the index of its partial
+//     sum;
 //  4. the partial sums of every shared coupling (and every shared node's
 //     load) get consecutive places, in chunk order, for the second kernel.
 // Every step is deterministic: atomics only count, and every list filled
@@ -35,19 +38,30 @@ namespace fea {
 namespace {
 
 constexpr int BUILD_T = 256;
-constexpr int SORT_CAP = 4096;  // candidate vertex pairs of one chunk
-static_assert(CHUNK_MAX_ELEMS * 10 <= SORT_CAP, "chunk too large for the slot sort");
 constexpr int MAX_CELL_LIST = 1024;  // longest cell whose elements sort in registers
 
-// vertex pair k of an element: k < 4 the vertex itself, then the six edges
-__device__ __forceinline__ void pair_of(int k, int& a, int& b) {
-  if (k < 4) {
+// Candidate dof pairs of one chunk (its elements x their NB (NB + 1) / 2
+// pairs) that the slot kernel sorts in shared memory.
+template <int NB>
+constexpr int sort_cap() {
+  return NB == 4 ? 4096 : 8192;
+}
+static_assert(CHUNK_MAX_ELEMS * 10 <= sort_cap<4>(), "P1 chunk too large for the slot sort");
+static_assert(CHUNK_MAX_ELEMS_P2 * 55 <= sort_cap<10>(), "P2 chunk too large for the slot sort");
+
+// local dof pair k of an element (pair_index in internal.cuh, inverted)
+__device__ __forceinline__ void pair_of(int nb, int k, int& a, int& b) {
+  if (k < nb) {
     a = b = k;
-  } else {
-    const int q = k - 4;  // (0,1) (0,2) (0,3) (1,2) (1,3) (2,3)
-    a = q < 3 ? 0 : (q < 5 ? 1 : 2);
-    b = q < 3 ? q + 1 : (q < 5 ? q - 1 : 3);
+    return;
   }
+  int q = k - nb;
+  a = 0;
+  while (q >= nb - 1 - a) {
+    q -= nb - 1 - a;
+    ++a;
+  }
+  b = a + 1 + q;
 }
 
 // ------------------------------------------------------------------ cells
@@ -119,15 +133,16 @@ __global__ void k_cell_fill(const int32_t* __restrict__ cell, int64_t E, const i
 
 // ------------------------------------------------------------------ slots
 struct SlotArgs {
-  const int32_t* tets;
+  const int32_t* edof;     // [nb][E] element -> scalar dof
   int64_t E;
+  int ndpn;                // dofs per scalar dof of the pattern (3 for elasticity)
   const int32_t* cptr;
   const int32_t* celem;
-  const int32_t* rp;       // scalar P1 CSR
+  const int32_t* rp;       // scalar CSR of the element order
   const int32_t* ci;
-  const int32_t* inc_ptr;  // P1 incidences (e * 4 + a, ascending e)
+  const int32_t* inc_ptr;  // scalar incidences (e * nb + a, ascending e)
   const int32_t* inc;
-  const int32_t* rp3;      // vector CSR row pointer
+  const int32_t* rp3;      // row pointer of the pattern (vector or scalar)
   int pass;                // 0: counts; 1: records
   // pass 0
   int32_t* cnt_slot;
@@ -166,14 +181,14 @@ __device__ __forceinline__ void block_bitonic(unsigned long long* key, uint16_t*
     }
 }
 
-// Elements containing both nodes i and j: the intersection of their sorted
-// incidence lists (incidence = e * 4 + a).
-__device__ int common_elements(const int32_t* __restrict__ inc_ptr, const int32_t* __restrict__ inc, int32_t i,
-                               int32_t j) {
+// Elements containing both dofs i and j: the intersection of their sorted
+// incidence lists (incidence = e * nb + a).
+__device__ int common_elements(const int32_t* __restrict__ inc_ptr, const int32_t* __restrict__ inc, int nb,
+                               int32_t i, int32_t j) {
   int32_t p = inc_ptr[i], pe = inc_ptr[i + 1], q = inc_ptr[j], qe = inc_ptr[j + 1];
   int n = 0;
   while (p < pe && q < qe) {
-    const int32_t a = inc[p] >> 2, b = inc[q] >> 2;
+    const int32_t a = inc[p] / nb, b = inc[q] / nb;
     n += a == b;
     p += a <= b;
     q += b <= a;
@@ -202,7 +217,10 @@ __device__ __forceinline__ int block_scan_int(int v, int* total) {
   return (int)ex;
 }
 
+template <int NB>
 __global__ void __launch_bounds__(BUILD_T) k_chunk_slots(SlotArgs A) {
+  constexpr int SORT_CAP = sort_cap<NB>();
+  constexpr int NPAIR = NB * (NB + 1) / 2;
   extern __shared__ unsigned long long smem_u64[];
   unsigned long long* key = smem_u64;                             // [SORT_CAP]
   uint16_t* pay = reinterpret_cast<uint16_t*>(key + SORT_CAP);    // [SORT_CAP] candidate | transposed bit
@@ -212,7 +230,7 @@ __global__ void __launch_bounds__(BUILD_T) k_chunk_slots(SlotArgs A) {
   __shared__ int s_nn, s_shared, s_shnode, s_max;
   const int c = blockIdx.x, tid = threadIdx.x;
   const int e0 = A.cptr[c], ne = A.cptr[c + 1] - e0;
-  const int n = ne * 10;
+  const int n = ne * NPAIR;
   int np = 2;
   while (np < n) np <<= 1;
   if (tid == 0) {
@@ -223,13 +241,13 @@ __global__ void __launch_bounds__(BUILD_T) k_chunk_slots(SlotArgs A) {
   }
   for (int p = tid; p < np; p += BUILD_T) {
     if (p < n) {
-      const int t = p / 10, k = p - 10 * t;
+      const int t = p / NPAIR, k = p - NPAIR * t;
       const int64_t e = A.celem[e0 + t];
       int a, b;
-      pair_of(k, a, b);
-      const uint32_t va = (uint32_t)A.tets[a * A.E + e], vb = (uint32_t)A.tets[b * A.E + e];
+      pair_of(NB, k, a, b);
+      const uint32_t va = (uint32_t)A.edof[a * A.E + e], vb = (uint32_t)A.edof[b * A.E + e];
       const uint32_t lo = va < vb ? va : vb, hi = va < vb ? vb : va;
-      key[p] = ((unsigned long long)(k >= 4) << 62) | ((unsigned long long)lo << 31) | hi;
+      key[p] = ((unsigned long long)(k >= NB) << 62) | ((unsigned long long)lo << 31) | hi;
       pay[p] = (uint16_t)(p | (va > vb ? 0x8000 : 0));
     } else {
       key[p] = ~0ull;
@@ -260,7 +278,7 @@ __global__ void __launch_bounds__(BUILD_T) k_chunk_slots(SlotArgs A) {
     const bool off = (k0 >> 62) != 0;
     const int32_t i = (int32_t)((k0 >> 31) & 0x7FFFFFFFu), j = (int32_t)(k0 & 0x7FFFFFFFu);
     const int cnt = start[s + 1] - start[s];
-    const int g = off ? common_elements(A.inc_ptr, A.inc, i, j) : A.inc_ptr[i + 1] - A.inc_ptr[i];
+    const int g = off ? common_elements(A.inc_ptr, A.inc, NB, i, j) : A.inc_ptr[i + 1] - A.inc_ptr[i];
     own[s] = cnt == g;
     my_nn += !off;
     my_sh += cnt != g;
@@ -299,10 +317,11 @@ __global__ void __launch_bounds__(BUILD_T) k_chunk_slots(SlotArgs A) {
     const unsigned long long k0 = key[start[s]];
     const int32_t i = (int32_t)((k0 >> 31) & 0x7FFFFFFFu), j = (int32_t)(k0 & 0x7FFFFFFFu);
     const int32_t oij = col_offset(A.rp, A.ci, i, j), oji = i == j ? oij : col_offset(A.rp, A.ci, j, i);
-    const int32_t Li = A.rp3[3 * i + 1] - A.rp3[3 * i], Lj = A.rp3[3 * j + 1] - A.rp3[3 * j];
+    const int d = A.ndpn;
+    const int32_t Li = A.rp3[d * i + 1] - A.rp3[d * i], Lj = A.rp3[d * j + 1] - A.rp3[d * j];
     const int32_t part = own[s] ? -1 : (int32_t)(A.pbase[c] + r_sh);
     r_sh += !own[s];
-    A.srec[s_off + s] = make_int4(A.rp3[3 * i] + 3 * oij, A.rp3[3 * j] + 3 * oji, Li | (Lj << 16), part);
+    A.srec[s_off + s] = make_int4(A.rp3[d * i] + d * oij, A.rp3[d * j] + d * oji, Li | (Lj << 16), part);
     A.pkey[s_off + s] = A.rp[i] + oij;
     if (s < nn) {
       A.nrec[n_off + s] = make_int2(i, own[s] ? -1 : (int32_t)(A.npbase[c] + r_shn));
@@ -311,8 +330,8 @@ __global__ void __launch_bounds__(BUILD_T) k_chunk_slots(SlotArgs A) {
   }
   for (int p = tid; p < n; p += BUILD_T) {
     const int orig = pay[p] & 0x7FFF;
-    const int t = orig / 10, k = orig - 10 * t;
-    const bool tr = k >= 4 && (pay[p] & 0x8000);
+    const int t = orig / NPAIR, k = orig - NPAIR * t;
+    const bool tr = k >= NB && (pay[p] & 0x8000);
     A.eslot[k * A.E + e0 + t] = (uint16_t)(sid[p] | (tr ? 0x8000 : 0));
   }
 }
@@ -421,11 +440,17 @@ uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
 
 fea_status build(fea_mesh* m, Pattern* P, Chunks* C, cudaStream_t s) {
   const int64_t E = m->n_elems, N = m->n_nodes;
-  const Base* B = m->base[1];
+  const Base* B = m->base[P->order];
+  const int NB = B->nb, NPAIR = NB * (NB + 1) / 2;
+  const int64_t nsd = B->nsd;  // scalar dofs (the node-slot keys)
+  const int CE = NB == 4 ? CHUNK_MAX_ELEMS : CHUNK_MAX_ELEMS_P2;
+  C->nb = NB;
+  C->npair = NPAIR;
+  C->ndpn = P->ndpn;
   // 1. cells
-  // the smallest G with G^3 cells of CHUNK_MAX_ELEMS elements holding E
-  int G = std::max(1, (int)std::cbrt((double)E / CHUNK_MAX_ELEMS));
-  while ((int64_t)G * G * G * CHUNK_MAX_ELEMS < E) ++G;
+  // the smallest G with G^3 cells of CE elements holding E
+  int G = std::max(1, (int)std::cbrt((double)E / CE));
+  while ((int64_t)G * G * G * CE < E) ++G;
   const int nbb = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (N + BUILD_T - 1) / BUILD_T));
   Tmp<double> bb;
   FEA_TRY(bb.alloc((size_t)nbb * 6));
@@ -473,15 +498,15 @@ fea_status build(fea_mesh* m, Pattern* P, Chunks* C, cudaStream_t s) {
     if (k > MAX_CELL_LIST) return fail(FEA_ERR_OVERFLOW, "chunked scatter: a cell holds too many elements");
     off[oc.second] = (int32_t)pos;
     lists.push_back((int32_t)pos);
-    if (k > CHUNK_MAX_ELEMS) {
+    if (k > CE) {
       if (open) cptr.push_back((int32_t)pos);
-      const int parts = (k + CHUNK_MAX_ELEMS - 1) / CHUNK_MAX_ELEMS;
+      const int parts = (k + CE - 1) / CE;
       for (int q = 1; q < parts; ++q) cptr.push_back((int32_t)(pos + (int64_t)k * q / parts));
       pos += k;
       cptr.push_back((int32_t)pos);
       open = 0;
     } else {
-      if (open + k > CHUNK_MAX_ELEMS) {
+      if (open + k > CE) {
         cptr.push_back((int32_t)pos);
         open = 0;
       }
@@ -512,8 +537,9 @@ fea_status build(fea_mesh* m, Pattern* P, Chunks* C, cudaStream_t s) {
   FEA_TRY(cshn.alloc(nc));
   FEA_TRY(cmax.alloc(nc));
   SlotArgs A{};
-  A.tets = m->tets;
+  A.edof = B->edof;
   A.E = E;
+  A.ndpn = P->ndpn;
   A.cptr = C->cptr;
   A.celem = C->celem;
   A.rp = B->rp;
@@ -526,10 +552,19 @@ fea_status build(fea_mesh* m, Pattern* P, Chunks* C, cudaStream_t s) {
   A.cnt_shared = csh.p;
   A.cnt_shnode = cshn.p;
   A.cnt_max = cmax.p;
-  const size_t smem = SORT_CAP * (8 + 2 + 2 + 1) + (SORT_CAP + 1) * 2;
-  FEA_CUDA(cudaFuncSetAttribute(k_chunk_slots, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int cap = NB == 4 ? sort_cap<4>() : sort_cap<10>();
+  const size_t smem = (size_t)cap * (8 + 2 + 2 + 1) + (cap + 1) * 2;
+  auto slots = [&]() -> fea_status {
+    if (nc == 0) return FEA_OK;
+    if (NB == 4) k_chunk_slots<4><<<(unsigned)nc, BUILD_T, smem, s>>>(A);
+    else k_chunk_slots<10><<<(unsigned)nc, BUILD_T, smem, s>>>(A);
+    FEA_CUDA(cudaGetLastError());
+    return FEA_OK;
+  };
+  FEA_CUDA(cudaFuncSetAttribute(NB == 4 ? k_chunk_slots<4> : k_chunk_slots<10>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   A.pass = 0;
-  if (nc > 0) k_chunk_slots<<<(unsigned)nc, BUILD_T, smem, s>>>(A);
+  FEA_TRY(slots());
   FEA_CUDA(cudaGetLastError());
   std::vector<int32_t> hs(nc), hn(nc), hsh(nc), hshn(nc), hmax(nc);
   FEA_CUDA(cudaMemcpyAsync(hs.data(), cs.p, nc * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -555,10 +590,11 @@ fea_status build(fea_mesh* m, Pattern* P, Chunks* C, cudaStream_t s) {
   C->hbits = 0;
   while ((1 << C->hbits) < maxcnt) ++C->hbits;
   // the accumulators of the largest chunk must fit one CTA's shared memory
-  // (9 sums and an exponent per slot, 3 sums and an exponent per node slot),
-  // and a slot may take at most 128 contributions (the fixed-point scale
-  // 2^(63 - 2 hbits) keeps 49 bits or more)
-  if ((size_t)C->max_slots * (9 * 8 + 4) + (size_t)C->max_nodes * (3 * 8 + 4) > 227 * 1024 || C->hbits > 7)
+  // (ndpn^2 sums and an exponent per slot, ndpn sums and an exponent per
+  // node slot), and a slot may take at most 128 contributions (the
+  // fixed-point scale 2^(63 - 2 hbits) keeps 49 bits or more)
+  const size_t d = P->ndpn;
+  if ((size_t)C->max_slots * (d * d * 8 + 4) + (size_t)C->max_nodes * (d * 8 + 4) > 227 * 1024 || C->hbits > 7)
     return fail(FEA_ERR_OVERFLOW, "chunked scatter: a chunk couples too many node pairs for shared memory");
   C->nslot = sptr[nc];
   C->nnode_slot = nptr[nc];
@@ -568,7 +604,7 @@ fea_status build(fea_mesh* m, Pattern* P, Chunks* C, cudaStream_t s) {
   FEA_TRY(dalloc(&C->nptr, nc + 1));
   FEA_TRY(dalloc(&C->srec, C->nslot));
   FEA_TRY(dalloc(&C->nrec, C->nnode_slot));
-  FEA_TRY(dalloc(&C->eslot, (size_t)10 * E));
+  FEA_TRY(dalloc(&C->eslot, (size_t)NPAIR * E));
   Tmp<int64_t> dpb, dnpb;
   Tmp<int32_t> pkey;
   FEA_TRY(dpb.alloc(nc + 1));
@@ -587,23 +623,22 @@ fea_status build(fea_mesh* m, Pattern* P, Chunks* C, cudaStream_t s) {
   A.nrec = C->nrec;
   A.pkey = pkey.p;
   A.eslot = C->eslot;
-  if (nc > 0) k_chunk_slots<<<(unsigned)nc, BUILD_T, smem, s>>>(A);
-  FEA_CUDA(cudaGetLastError());
+  FEA_TRY(slots());
   // 4. partial-sum lists of the shared couplings (key: the scalar CSR position
   // of the coupling's upper entry) and of the shared nodes (key: node id)
   int32_t* partcol = reinterpret_cast<int32_t*>(C->srec) + 3;  // .w of every record
   FEA_TRY(build_groups(pkey.p, 1, partcol, 4, C->nslot, B->nnz, C->npart, C->srec, &C->ngroup, &C->npart, &C->gptr,
                        &C->grec, nullptr, s));
   int32_t* nodecol = reinterpret_cast<int32_t*>(C->nrec);
-  FEA_TRY(build_groups(nodecol, 2, nodecol + 1, 2, C->nnode_slot, N, C->nnpart, nullptr, &C->nngroup, &C->nnpart,
+  FEA_TRY(build_groups(nodecol, 2, nodecol + 1, 2, C->nnode_slot, nsd, C->nnpart, nullptr, &C->nngroup, &C->nnpart,
                        &C->ngptr, nullptr, &C->ngnode, s));
   // nodes of no element: no chunk writes their load entries (the set, not
   // its order, matters: they are written with zeros)
   Tmp<int32_t> niso;
   FEA_TRY(niso.alloc(1));
-  FEA_TRY(dalloc(&C->iso, N));
+  FEA_TRY(dalloc(&C->iso, nsd));
   FEA_CUDA(cudaMemsetAsync(niso.p, 0, sizeof(int32_t), s));
-  k_isolated<<<blocks_for(N, 256), 256, 0, s>>>(B->inc_ptr, N, niso.p, C->iso);
+  k_isolated<<<blocks_for(nsd, 256), 256, 0, s>>>(B->inc_ptr, nsd, niso.p, C->iso);
   int32_t hiso = 0;
   FEA_CUDA(cudaMemcpyAsync(&hiso, niso.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   FEA_CUDA(cudaStreamSynchronize(s));
@@ -633,7 +668,8 @@ void free_chunks(Chunks* c) {
 fea_status build_chunks(fea_mesh* m, Pattern* P, cudaStream_t s) {
   if (P->chunks) return FEA_OK;
   if (P->chunks_failed) return fail(FEA_ERR_OVERFLOW, "chunked scatter: not available for this mesh");
-  if (P->order != 1 || P->ndpn != 3 || !m->base[1]) return fail(FEA_ERR_STATE, "chunked scatter: P1 vector pattern only");
+  if (!m->base[P->order] || !(P->ndpn == 1 || (P->order == 1 && P->ndpn == 3)) || m->nvert != 4)
+    return fail(FEA_ERR_STATE, "chunked scatter: tetrahedral scalar P1/P2 or P1 vector patterns only");
   NvtxRange range("chunk build");
   Chunks* C = new Chunks();
   fea_status st = build(m, P, C, s);

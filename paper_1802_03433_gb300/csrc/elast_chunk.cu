@@ -43,216 +43,19 @@
 #include <algorithm>
 #include <cmath>
 
-#include "elem_kernels.cuh"
+#include "chunk_common.cuh"
 
 namespace fea {
 namespace {
 
+using namespace chunkfx;
+
 constexpr int CHUNK_T = 128;
 constexpr int CHUNK_MIN_BLOCKS = 3;
-constexpr int EXP_POISON = 1 << 20;    // a slot exponent at or above: the slot is NaN
-constexpr int EXP_EMPTY = -(1 << 20);  // no contribution yet
-constexpr int EXP_ZERO = -1200;        // bound of contributions that are all zero
 // A partial sum of a shared 3 x 3 block takes 12 doubles (three whole 32-byte
 // sectors, so its stores never leave a sector partly written), a partial load
 // 4 (one sector).
 constexpr int PART_STRIDE = 12;
-
-struct ChunkArgs {
-  const int32_t* cptr;
-  const int32_t* celem;
-  const uint16_t* eslot;
-  const int32_t* sptr;
-  const int32_t* nptr;
-  const int4* srec;
-  const int2* nrec;
-  int H;          // fixed-point scale of a slot: value * 2^(H - Es)
-  int K;          // split of a fixed-point value q = hi 2^K + lo, 0 <= lo < 2^K
-  int ef;         // |f_c| < 2^ef for the load amplitudes (EXP_ZERO: no load, EXP_POISON: non-finite)
-  int max_slots;  // shared-memory capacity
-  int max_nodes;
-  double* values;
-  double* rhs;
-  double* part;   // [npart][PART_STRIDE] partial sums of shared couplings (9 used)
-  double* npart;  // [nnpart][4] partial sums of shared node loads (3 used)
-};
-
-// |x| < 2^result for a positive normal float.
-__device__ __forceinline__ int fexp_bound(float y) { return ((__float_as_int(y) >> 23) & 0xFF) - 126; }
-
-// v * 2^(1022 - eb) as a float, truncated (eb: the largest biased exponent
-// among the values normalised together, so the result is below 1 in size);
-// values 2^-126 or more below the largest become 0.
-__device__ __forceinline__ float scaled_f32(double v, int eb) {
-  const int hi = __double2hiint(v);
-  const unsigned lo = static_cast<unsigned>(__double2loint(v));
-  const int ev = (hi >> 20) & 0x7FF;
-  const int fe = ev - eb + 126;
-  if (ev == 0 || fe <= 0) return 0.0f;
-  const unsigned bits = (static_cast<unsigned>(hi) & 0x80000000u) | (static_cast<unsigned>(fe) << 23) |
-                        ((static_cast<unsigned>(hi) & 0xFFFFFu) << 3) | (lo >> 29);
-  return __uint_as_float(bits);
-}
-
-// Exponent bounds of one element's matrix entries (EK) and load entries (EF)
-// from FP64 arithmetic: the fallback for very flat elements, where the FP32
-// determinant of the normalised edges is too small to trust.  det J = 0
-// gives zero loads and a poisoned matrix.
-static __device__ __noinline__ int2 elast_bounds_fp64(double e00, double e01, double e02, double e10, double e11,
-                                                      double e12, double e20, double e21, double e22, double C,
-                                                      int ef) {
-  const double e[3][3] = {{e00, e01, e02}, {e10, e11, e12}, {e20, e21, e22}};
-  double c[4][3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const double* u = e[(i + 1) % 3];
-    const double* w = e[(i + 2) % 3];
-    c[i + 1][0] = u[1] * w[2] - u[2] * w[1];
-    c[i + 1][1] = u[2] * w[0] - u[0] * w[2];
-    c[i + 1][2] = u[0] * w[1] - u[1] * w[0];
-  }
-#pragma unroll
-  for (int k = 0; k < 3; ++k) c[0][k] = -(c[1][k] + c[2][k] + c[3][k]);
-  const double det = fabs(e[0][0] * c[1][0] + e[0][1] * c[1][1] + e[0][2] * c[1][2]);
-  if (!isfinite(det)) return make_int2(EXP_POISON, EXP_POISON);
-  if (!(det > 0.0)) return make_int2(EXP_POISON, EXP_ZERO);
-  double n2 = 0.0;
-#pragma unroll
-  for (int a = 0; a < 4; ++a) n2 = fmax(n2, c[a][0] * c[a][0] + c[a][1] * c[a][1] + c[a][2] * c[a][2]);
-  // |K| <= (|lam| + 2|mu|) |T| max |grad phi|^2 = C n2 / (6 |det|); 2 bits of margin
-  const double B = C * n2 / (6.0 * det) * 4.0;
-  int ek = EXP_POISON, ed;
-  if (isfinite(B)) {
-    frexp(B, &ek);
-    if (B == 0.0) ek = EXP_ZERO;
-  }
-  frexp(det, &ed);
-  return make_int2(ek, ef >= EXP_POISON ? EXP_POISON : (ef <= EXP_ZERO ? EXP_ZERO : ef + ed - 1));
-}
-
-// The bounds of phase A: |entry| <= (|lam| + 2|mu|) |T| max_a |grad phi_a|^2
-// = C max_a |c_a|^2 / (6 |det J|) with c_a the cofactor rows of J (each term
-// of an entry is at most (|lam| + 2 |mu|) |grad phi_a| |grad phi_b| in size),
-// and |load entry| <= |f| (sum of the rule's |weights|) |T| < |f| |det J| / 4.
-// The edges of J are formed in FP64 (9 subtractions); everything else runs in
-// FP32 on the edges normalised by their largest exponent, with margins for
-// the FP32 rounding (the scale factors are exact powers of two).
-__device__ __forceinline__ int2 elast_bounds(const double X[4][3], double lam, double mu, int ef) {
-  double e[3][3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) e[i][k] = X[i + 1][k] - X[0][k];
-  int eb = 0;
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) eb = max(eb, (__double2hiint(e[i][k]) >> 20) & 0x7FF);
-  const double C = fma(2.0, fabs(mu), fabs(lam));
-  const int hC = __double2hiint(C);
-  const int eC = (hC >> 20) & 0x7FF;
-  if (eb == 2047) return make_int2(EXP_POISON, EXP_POISON);  // non-finite coordinates
-  if (eb == 0) return make_int2(EXP_POISON, EXP_ZERO);        // every edge zero: det J = 0
-  float f[3][3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) f[i][k] = scaled_f32(e[i][k], eb);
-  float c[4][3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const float* u = f[(i + 1) % 3];
-    const float* w = f[(i + 2) % 3];
-    c[i + 1][0] = fmaf(u[1], w[2], -u[2] * w[1]);
-    c[i + 1][1] = fmaf(u[2], w[0], -u[0] * w[2]);
-    c[i + 1][2] = fmaf(u[0], w[1], -u[1] * w[0]);
-  }
-#pragma unroll
-  for (int k = 0; k < 3; ++k) c[0][k] = -(c[1][k] + c[2][k] + c[3][k]);
-  const float ad = fabsf(fmaf(f[0][0], c[1][0], fmaf(f[0][1], c[1][1], f[0][2] * c[1][2])));
-  if (!(ad > 0x1p-12f))
-    return elast_bounds_fp64(e[0][0], e[0][1], e[0][2], e[1][0], e[1][1], e[1][2], e[2][0], e[2][1], e[2][2], C, ef);
-  float n2 = 0.0f;
-#pragma unroll
-  for (int a = 0; a < 4; ++a) n2 = fmaxf(n2, fmaf(c[a][0], c[a][0], fmaf(c[a][1], c[a][1], c[a][2] * c[a][2])));
-  // errors of the normalised FP32 quantities are below 2^-19 (edges truncated
-  // by 2^-23 relative, a few roundings of terms below 8 in size)
-  const float r = (n2 * (1.0f + 0x1p-10f) + 0x1p-17f) / (6.0f * (ad - 0x1p-17f));
-  int ek;
-  if (eC == 2047) {
-    ek = EXP_POISON;  // non-finite Lame parameters
-  } else if (eC == 0) {
-    if (C == 0.0) ek = EXP_ZERO;
-    else ek = -1022 + (eb - 1022) + fexp_bound(r) + 1;  // C < 2^-1022
-  } else {
-    const float mC = __uint_as_float(0x3F800000u | ((static_cast<unsigned>(hC) & 0xFFFFFu) << 3) |
-                                     (static_cast<unsigned>(__double2loint(C)) >> 29));
-    ek = (eC - 1023) + (eb - 1022) + fexp_bound(mC * r) + 1;
-  }
-  if (ek > 1023) ek = EXP_POISON;
-  else if (ek < EXP_ZERO) ek = EXP_ZERO;
-  int efo = EXP_ZERO;
-  if (ef >= EXP_POISON) efo = EXP_POISON;
-  else if (ef > EXP_ZERO) efo = max(EXP_ZERO, ef + 3 * (eb - 1022) + fexp_bound(ad + 0x1p-17f) - 1);
-  return make_int2(ek, efo);
-}
-
-// round(v 2^sh) as a 64-bit integer (ties away from zero); |v 2^sh| < 2^62
-// by the slot's bound.
-__device__ __forceinline__ long long fx_of(double v, int sh) {
-  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
-  const int ev = static_cast<int>(b >> 52) & 0x7FF;
-  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (ev ? (1ull << 52) : 0ull);
-  const int k = max(ev, 1) - 1075 + sh;  // v 2^sh = m 2^k
-  unsigned long long mag;
-  if (k >= 0) mag = m << min(k, 63);
-  else mag = -k > 63 ? 0ull : ((m >> (-k - 1)) + 1ull) >> 1;
-  return (b >> 63) ? -static_cast<long long>(mag) : static_cast<long long>(mag);
-}
-__device__ __forceinline__ long long fx_of(float v, int sh) {
-  const unsigned u = __float_as_uint(v);
-  const int ev = static_cast<int>(u >> 23) & 0xFF;
-  const unsigned long long m = (u & 0x7FFFFFu) | (ev ? 0x800000u : 0u);
-  const int k = max(ev, 1) - 150 + sh;
-  unsigned long long mag;
-  if (k >= 0) mag = m << min(k, 63);
-  else mag = -k > 63 ? 0ull : ((m >> (-k - 1)) + 1ull) >> 1;
-  return (u >> 31) ? -static_cast<long long>(mag) : static_cast<long long>(mag);
-}
-
-// q 2^e2 correctly rounded to FP64 (ties to even), with integer operations;
-// results outside the normal range take ldexp.
-__device__ __forceinline__ double f64_of(long long q, int e2) {
-  if (q == 0) return 0.0;
-  const unsigned long long sgn = q < 0 ? (1ull << 63) : 0ull;
-  unsigned long long mag = q < 0 ? 0ull - static_cast<unsigned long long>(q) : static_cast<unsigned long long>(q);
-  const int lz = __clzll(static_cast<long long>(mag));
-  mag <<= lz;
-  const unsigned long long low = mag & 0x7FFull;
-  unsigned long long mant = mag >> 11;  // 53 bits, the top one set
-  mant += (low > 0x400ull) || (low == 0x400ull && (mant & 1ull));
-  const int be = 63 - lz + e2 + 1023;   // biased exponent of the result
-  if (be <= 0 || be >= 2047) return ldexp(static_cast<double>(q), e2);
-  return __longlong_as_double(static_cast<long long>(sgn | ((static_cast<unsigned long long>(be - 1) << 52) + mant)));
-}
-
-// vertex pair (a, b), a < b, of an element -> its index among the ten pairs
-__host__ __device__ constexpr int pair_index(int a, int b) {
-  return a == b ? a : (a == 0 ? 3 + b : (a == 1 ? 5 + b : 9));
-}
-
-// Add a fixed-point value into a two-word accumulator with two 32-bit
-// shared-memory atomics (native, no return value used, so the warp does not
-// wait for them): lo takes q mod 2^K, hi takes floor(q / 2^K).  With at most
-// 2^hbits contributions, K = 32 - hbits and H = 63 - 2 hbits neither word
-// overflows, and hi 2^K + lo is the exact sum.
-__device__ __forceinline__ void acc_add(unsigned* lo, int* hi, long long q, int K) {
-  atomicAdd(lo, static_cast<unsigned>(q) & ((1u << K) - 1u));
-  atomicAdd(hi, static_cast<int>(q >> K));
-}
-__device__ __forceinline__ long long acc_sum(const unsigned* lo, const int* hi, int K) {
-  return (static_cast<long long>(*hi) << K) + static_cast<long long>(*lo);
-}
 
 template <int LOAD, int NPTS, typename R>
 __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemArgs A, ChunkArgs C) {
@@ -294,7 +97,7 @@ __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemA
     load_element(A, e, X);
     const double lam = A.lam ? __ldg(A.lam + e) : A.lam_const;
     const double mu = A.mu ? __ldg(A.mu + e) : A.mu_const;
-    const int2 eb = elast_bounds(X, lam, mu, C.ef);
+    const int2 eb = element_bounds(X, fma(2.0, fabs(mu), fabs(lam)), 0.0, C.ef);
 #pragma unroll
     for (int k = 0; k < 10; ++k) atomicMax(sexp + (C.eslot[k * A.E + e0 + t] & 0x7FFF), eb.x);
     if constexpr (HAS_LOAD) {
@@ -328,7 +131,7 @@ __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemA
     elast_upper<R>(g, adet, lam, mu, [&](auto KK, R v) {
       constexpr int r = upper_a(12, KK), cc = upper_b(12, KK);
       constexpr int a = r / 3, i3 = r % 3, b = cc / 3, j3 = cc % 3;
-      constexpr int k = pair_index(a, b);
+      constexpr int k = pair_index(4, a, b);
       const int idx = 9 * slot[k] + ((a != b && tr[k]) ? 3 * j3 + i3 : 3 * i3 + j3);
       acc_add(alo + idx, ahi + idx, fx_of(v, sh[k]), K);
     });

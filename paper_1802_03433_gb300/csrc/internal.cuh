@@ -65,33 +65,43 @@ struct Base {
 // element with incidence index i = ipos[a][e] lives at row i * ndpn + comp of
 // a buffer whose rows are lstride(nl, bytes) values apart (devcommon.cuh).
 
-// Chunked scatter (chunks.cu, elast_chunk.cu) of the P1 vector pattern: the
-// elements are grouped into spatially compact chunks (whole cells of a grid
-// over the mesh's bounding box, visited in Morton order, at most
-// CHUNK_MAX_ELEMS elements each).  One CTA assembles one chunk: the local
-// entries of its elements are added as 64-bit fixed-point integers into
-// shared-memory accumulators, one 3 x 3 block per node pair ("slot") that the
-// chunk's elements couple.  A slot whose every contributing element lies in
+// Chunked scatter (chunks.cu, elast_chunk.cu, scalar_chunk.cu): the elements
+// are grouped into spatially compact chunks (whole cells of a grid over the
+// mesh's bounding box, visited in Morton order, at most CHUNK_MAX_ELEMS or
+// CHUNK_MAX_ELEMS_P2 elements each).  One CTA assembles one chunk: the local
+// entries of its elements are added as fixed-point integers into
+// shared-memory accumulators, one block (3 x 3 for elasticity, one entry for
+// scalar forms) per scalar dof pair ("slot") that the chunk's elements
+// couple.  A slot whose every contributing element lies in
 // the chunk is "owned" and written straight to the CSR values; the others are
 // written as one FP64 partial sum per chunk and added, in chunk order, by a
 // second kernel over the shared couplings.
-constexpr int CHUNK_MAX_ELEMS = 384;
+constexpr int CHUNK_MAX_ELEMS = 384;     // P1 (scalar and vector)
+constexpr int CHUNK_MAX_ELEMS_P2 = 128;  // P2: 55 dof pairs per element
+
+// Index of the local dof pair (a, b), a <= b, of an element with nb local
+// dofs: the nb diagonal pairs (the dof slots) first, then the pairs a < b in
+// lexicographic order.
+__host__ __device__ constexpr int pair_index(int nb, int a, int b) {
+  return a == b ? a : nb + a * (nb - 1) - a * (a - 1) / 2 + (b - a - 1);
+}
 
 struct Chunks {
+  int nb = 0, npair = 0, ndpn = 0;  // local scalar dofs, dof pairs per element, dofs per scalar dof
   int64_t nchunk = 0, nslot = 0, nnode_slot = 0;
   int max_slots = 0, max_nodes = 0;
   int hbits = 0;                 // ceil(log2(most elements contributing to one slot of a chunk))
   int32_t* cptr = nullptr;       // [nchunk + 1] element offsets into celem
   int32_t* celem = nullptr;      // [E] element ids, chunk by chunk
-  uint16_t* eslot = nullptr;     // [10][E] (chunk order) slot of each vertex pair (a, b) of the element:
-                                 // k < 4 the node slot of vertex k, then (0,1) (0,2) (0,3) (1,2) (1,3) (2,3);
-                                 // bit 15 set when node(a) > node(b) (the slot holds the transposed block)
+  uint16_t* eslot = nullptr;     // [npair][E] (chunk order) slot of each local dof pair k = pair_index(a, b)
+                                 // of the element (k < nb: the dof slot of local dof k); bit 15 set when
+                                 // dof(a) > dof(b) (the slot holds the transposed block)
   int32_t* sptr = nullptr;       // [nchunk + 1] slot offsets; each chunk's node slots come first
   int32_t* nptr = nullptr;       // [nchunk + 1] node-slot offsets
   int4* srec = nullptr;          // [nslot] {U, W, Li | Lj << 16, partial index or -1 when owned}: the
                                  // CSR position of entry (3i, 3j) and of (3j, 3i), the lengths of rows
                                  // 3i and 3j, for the slot's node pair i <= j
-  int2* nrec = nullptr;          // [nnode_slot] {node id, load partial index or -1 when owned}
+  int2* nrec = nullptr;          // [nnode_slot] {scalar dof, load partial index or -1 when owned}
   // couplings shared by several chunks: the partial sums of group g (one per
   // chunk that touches it) are partials gptr[g] .. gptr[g + 1] - 1, in chunk
   // order; a shared slot's record holds the index of its partial
@@ -199,9 +209,11 @@ void free_pattern(Pattern* p);
 fea_status build_chunks(fea_mesh* m, Pattern* P, cudaStream_t s);
 void free_chunks(Chunks* c);
 
-// elast_chunk.cu
+// elast_chunk.cu, scalar_chunk.cu
 fea_status assemble_chunked(fea_mesh* m, Pattern* P, const fea_coeffs* co, const fea_quadrature* q, int load,
                             double* values, double* rhs, cudaStream_t s);
+fea_status assemble_chunked_scalar(fea_mesh* m, Pattern* P, const fea_form* form, const fea_coeffs* co,
+                                   const fea_quadrature* q, int load, double* values, double* rhs, cudaStream_t s);
 
 // assemble.cu
 fea_status assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* co,

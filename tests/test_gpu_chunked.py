@@ -1,6 +1,7 @@
-"""The chunked fixed-point scatter of P1 elasticity (FEA_SCATTER_CHUNKED, the
-automatic choice for elasticity) against the CPU oracle (Eq. 3), against the
-local-row scatter, and on the cases its construction has to get right:
+"""The chunked fixed-point scatter (FEA_SCATTER_CHUNKED; the automatic choice
+for elasticity, selectable for the scalar P1 and P2 forms) against the CPU
+oracle (Eq. 3), against the local-row scatter, and on the cases its
+construction has to get right:
 meshes smaller than one chunk, couplings shared by several chunks, vertices
 in many elements, a random element and node numbering, nodes of no element,
 power-of-two scaling of the coefficients, non-finite coefficients (GPU)."""
@@ -9,6 +10,7 @@ import pytest
 
 import oracle
 from common import TOL_FP64, TOL_MIXED, case, gpu_system, oracle_system, row_scaled_error, vec_scaled_error
+from paper_1802_03433_gb300 import meshgen as mg
 
 pytestmark = pytest.mark.gpu
 
@@ -81,13 +83,10 @@ def test_chunked_agrees_with_local_rows_and_auto_picks_it():
         g["mesh"].close()
 
 
-def test_chunked_rejects_scalar_forms():
+def test_chunked_rejects_a_bad_mode():
     from paper_1802_03433_gb300 import fea
     c = case("p1_kappa", 3)
     m = _mesh(c, fea.FEA_SCATTER_CHUNKED)
-    with pytest.raises(fea.FeaError) as ei:
-        gpu_system(c, mesh=m)
-    assert ei.value.status == 1
     with pytest.raises(fea.FeaError):
         fea.fea_mesh_set_scatter(m.h, 3)
     m.close()
@@ -218,3 +217,121 @@ def test_chunked_full_size_rows_against_oracle_at_96():
     grhs = rhs.cpu().numpy()
     assert np.abs(grhs[rr] - orhs).max() <= TOL_FP64 * np.abs(grhs).max()
     m.close()
+
+
+# ---------------------------------------------------------------- scalar forms
+SCALAR = [("p1_poisson", 8), ("p1_kappa", 7), ("p2_diffmass", 6), ("p2_poisson", 5), ("p2_diffmass", 1),
+          ("p1_kappa", 2)]
+
+
+@pytest.mark.parametrize("kind,n", SCALAR)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_chunked_scalar_matches_oracle(kind, n, prec):
+    c = case(kind, n, seed=n + 60)
+    o = oracle_system(c)
+    g = _chunked(c, prec)
+    np.testing.assert_array_equal(g["ci"], o["ci"])
+    tol = TOL_FP64 if prec == 0 else TOL_MIXED
+    assert row_scaled_error(o["rp"], o["vals"], g["vals"]) <= tol
+    assert vec_scaled_error(o["rhs"], g["rhs"]) <= tol
+    g["mesh"].close()
+
+
+@pytest.mark.parametrize("npts", [1, 4, 11])
+@pytest.mark.parametrize("order", [1, 2])
+def test_chunked_scalar_every_rule_and_load(npts, order):
+    c = case("p2_diffmass" if order == 2 else "p1_kappa", 4, seed=7)
+    c["npts"] = npts
+    for fk, fp in (("const", (2.5,)), ("sinprod", (mg.SIN_AMP,)), ("zero", (0.0,))):
+        c["f_kind"], c["f_param"] = fk, fp
+        o = oracle_system(c)
+        g = _chunked(c)
+        assert row_scaled_error(o["rp"], o["vals"], g["vals"]) <= TOL_FP64
+        assert vec_scaled_error(o["rhs"], g["rhs"]) <= TOL_FP64 if fk != "zero" else np.abs(g["rhs"]).max() == 0.0
+        g["mesh"].close()
+
+
+@pytest.mark.parametrize("kind", ["p1_kappa", "p2_diffmass"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_chunked_scalar_deterministic_symmetric_and_close_to_local_rows(kind, prec):
+    from paper_1802_03433_gb300 import fea
+    c = case(kind, 9, seed=4)
+    g1 = _chunked(c, prec)
+    g2 = gpu_system(c, prec=prec, mesh=g1["mesh"])
+    assert np.array_equal(g1["vals"].view(np.uint64), g2["vals"].view(np.uint64))
+    assert np.array_equal(g1["rhs"].view(np.uint64), g2["rhs"].view(np.uint64))
+    rp, ci, v = g1["rp"], g1["ci"], g1["vals"]
+    rows = np.repeat(np.arange(rp.size - 1), np.diff(rp))
+    tkey = ci.astype(np.int64) * (rp.size - 1) + rows
+    assert np.array_equal(v.view(np.uint64), v[np.argsort(tkey)].view(np.uint64))
+    gl = gpu_system(c, prec=prec, mesh=_mesh(c, fea.FEA_SCATTER_LOCAL_ROWS))
+    tol = TOL_FP64 if prec == 0 else TOL_MIXED
+    assert row_scaled_error(gl["rp"], gl["vals"], v) <= tol
+    assert vec_scaled_error(gl["rhs"], g1["rhs"]) <= tol
+    g1["mesh"].close()
+    gl["mesh"].close()
+
+
+@pytest.mark.parametrize("k", [60, -60, 1000, -900])
+def test_chunked_scalar_power_of_two_scaling_is_exact(k):
+    c = case("p2_poisson", 4, seed=16)
+    g1 = _chunked(c)
+    g2 = _chunked(dict(c, kappa=np.ldexp(c["kappa"], k)))
+    assert np.array_equal(np.ldexp(g1["vals"], k).view(np.uint64), g2["vals"].view(np.uint64))
+    assert np.array_equal(g1["rhs"].view(np.uint64), g2["rhs"].view(np.uint64))
+    g1["mesh"].close()
+    g2["mesh"].close()
+
+
+def test_chunked_scalar_nan_kappa_poisons_exactly_its_entries():
+    c = case("p2_diffmass", 5, seed=18)
+    g0 = _chunked(c)
+    e = 333
+    kap = c["kappa"].copy()
+    kap[e] = np.nan
+    g = _chunked(dict(c, kappa=kap))
+    rp, ci = g["rp"], g["ci"]
+    dofs = g["mesh"].dof_table(2).cpu().numpy()[:, e]
+    rows = np.repeat(np.arange(rp.size - 1), np.diff(rp))
+    hit = np.isin(rows, dofs) & np.isin(ci, dofs)
+    assert np.all(np.isnan(g["vals"][hit]))
+    assert np.array_equal(g["vals"][~hit].view(np.uint64), g0["vals"][~hit].view(np.uint64))
+    assert np.array_equal(g["rhs"].view(np.uint64), g0["rhs"].view(np.uint64))
+    g0["mesh"].close()
+    g["mesh"].close()
+
+
+def test_chunked_scalar_unstructured_numbering():
+    c = case("p2_diffmass", 5, seed=19)
+    rng = np.random.default_rng(3)
+    N = c["coords"].shape[1]
+    perm_n = rng.permutation(N)
+    inv = np.empty(N, dtype=np.int64)
+    inv[perm_n] = np.arange(N)
+    perm_e = rng.permutation(c["tets"].shape[1])
+    c["coords"] = np.ascontiguousarray(c["coords"][:, perm_n])
+    c["tets"] = np.ascontiguousarray(inv[c["tets"][:, perm_e]].astype(np.int32))
+    c["kappa"] = np.ascontiguousarray(c["kappa"][perm_e])
+    o = oracle_system(c)
+    g = _chunked(c)
+    np.testing.assert_array_equal(g["ci"], o["ci"])
+    assert row_scaled_error(o["rp"], o["vals"], g["vals"]) <= TOL_FP64
+    assert vec_scaled_error(o["rhs"], g["rhs"]) <= TOL_FP64
+    g["mesh"].close()
+
+
+@pytest.mark.parametrize("kind,n", [("p2_diffmass", 64), ("p1_kappa", 96)])
+def test_chunked_scalar_full_size_every_value(kind, n):
+    """The P2 64^3 and P1 96^3 workloads with the chunked scatter: every value
+    and load entry against the oracle."""
+    from paper_1802_03433_gb300 import meshgen as mgen
+    d = mgen.diffusion_mass_p2(n) if kind == "p2_diffmass" else mgen.adjoint_p1(n)
+    c = dict(coords=d["coords"], tets=d["tets"], order=d["order"], form="diffusion", mass=d["mass"],
+             kappa=d["kappa"], f_kind="sinprod", f_param=(d["f_amp"],), npts=d["npts"], ndpn=1)
+    g = _chunked(c)
+    o = oracle_system(c)
+    np.testing.assert_array_equal(g["rp"], o["rp"])
+    np.testing.assert_array_equal(g["ci"], o["ci"])
+    assert row_scaled_error(o["rp"], o["vals"], g["vals"]) <= TOL_FP64
+    assert vec_scaled_error(o["rhs"], g["rhs"]) <= TOL_FP64
+    g["mesh"].close()
