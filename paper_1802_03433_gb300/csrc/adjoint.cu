@@ -288,6 +288,7 @@ fea_status assemble_backward(fea_mesh* m, const fea_form* form, const fea_coeffs
   const int order = form->order;
   Base* B = m->base[order];
   if (!B || !m->pat[order][1]) return fail(FEA_ERR_STATE, "fea_assemble_backward: build the pattern first");
+  FEA_TRY(refuse_long_rows(B, "fea_assemble_backward"));
   const int64_t E = m->n_elems, N = m->n_nodes;
   if (!gk && !gx) return FEA_OK;
   if (E == 0) {

@@ -57,6 +57,63 @@ fea_status launch_gather(int nb, int ndpn, bool mixed, const GatherArgs& G, int 
 
 namespace {
 
+// The rows of more than 255 entries (whose column slots do not fit a byte),
+// one block per row, after the row-gather scatter: every local row of the
+// row's incidences, in ascending element order, added into a shared-memory
+// copy of the row at the columns found by binary search; between two
+// incidences a barrier, so each entry sums its contributions in element
+// order (deterministic, no atomics).  Overwrites what the row-gather wrote
+// for these rows; their loads are the row-gather's.
+template <typename LT>
+__global__ void __launch_bounds__(256) k_long_rows(const int32_t* __restrict__ rows, const int32_t* __restrict__ rp,
+                                                   const int32_t* __restrict__ ci, const int32_t* __restrict__ inc_ptr,
+                                                   const int32_t* __restrict__ inc, const int32_t* __restrict__ edof,
+                                                   int64_t E, int nb, const int32_t* __restrict__ pos,
+                                                   const LT* __restrict__ Lm, int ls, double* __restrict__ values) {
+  extern __shared__ double lacc[];
+  const int32_t row = rows[blockIdx.x];
+  const int32_t r0 = rp[row], len = rp[row + 1] - r0;
+  for (int j = threadIdx.x; j < len; j += blockDim.x) lacc[j] = 0.0;
+  __syncthreads();
+  for (int32_t t = inc_ptr[row]; t < inc_ptr[row + 1]; ++t) {
+    const int32_t v = inc[t];
+    const int64_t e = v / nb;
+    const int a = v - (int)e * nb;
+    if ((int)threadIdx.x < nb) {
+      const int32_t d = edof[threadIdx.x * E + e];
+      int32_t lo = 0, hi = len;
+      while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (ci[r0 + mid] < d) lo = mid + 1;
+        else hi = mid;
+      }
+      lacc[lo] += static_cast<double>(Lm[(int64_t)pos[(int64_t)a * E + e] * ls + threadIdx.x]);
+    }
+    __syncthreads();
+  }
+  for (int j = threadIdx.x; j < len; j += blockDim.x) values[r0 + j] = lacc[j];
+}
+
+fea_status long_rows(const Base* B, const Pattern* P, int64_t E, bool mixed, const int32_t* pos, const void* Lm,
+                     double* values, cudaStream_t s) {
+  if (B->nlong == 0) return FEA_OK;
+  const size_t smem = (size_t)B->max_row * sizeof(double);
+  if (mixed) {
+    FEA_CUDA(cudaFuncSetAttribute(k_long_rows<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_long_rows<float><<<(unsigned)B->nlong, 256, smem, s>>>(B->long_rows, P->row_ptr, P->col_idx, B->inc_ptr, B->inc,
+                                                             B->edof, E, B->nb, pos, static_cast<const float*>(Lm),
+                                                             lstride(B->nb, sizeof(float)), values);
+  } else {
+    FEA_CUDA(cudaFuncSetAttribute(k_long_rows<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_long_rows<double><<<(unsigned)B->nlong, 256, smem, s>>>(B->long_rows, P->row_ptr, P->col_idx, B->inc_ptr,
+                                                              B->inc, B->edof, E, B->nb, pos,
+                                                              static_cast<const double*>(Lm),
+                                                              lstride(B->nb, sizeof(double)), values);
+  }
+  FEA_CUDA(cudaGetLastError());
+  return FEA_OK;
+}
+
 fea_status launch_elements(const fea_form* form, const ElemArgs& A, int load, int npts, int prec, cudaStream_t s) {
   if (form->kind == FEA_ELASTICITY) return launch_elem_elast(A, load, npts, prec, s);
   const bool mass = form->kind == FEA_DIFFUSION_MASS && form->mass_coef != 0.0;
@@ -84,6 +141,9 @@ fea_status assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* co, con
     if (st == FEA_OK || m->scatter == FEA_SCATTER_CHUNKED || !P->chunks_failed) return st;
     set_error("");  // automatic mode: the chunks cannot be built, take the local rows
   }
+  if (B->nlong > 0 && ndpn != 1)
+    return fail(FEA_ERR_OVERFLOW, "rows of more than 255 scalar entries: the local-row scatter takes them for scalar "
+                                  "forms (elasticity: the chunked scatter)");
   const int nb = B->nb, nl = nb * ndpn;
   const bool mixed = q->prec == FEA_MIXED;
   const size_t rb = mixed ? sizeof(float) : sizeof(double);
@@ -213,6 +273,7 @@ fea_status assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* co, con
     FEA_CUDA(cudaEventRecord(m->chunk_ev[16], m->side));
     FEA_CUDA(cudaStreamWaitEvent(s, m->chunk_ev[16], 0));
   }
+  FEA_TRY(long_rows(B, P, E, mixed, A.ipos, A.Lm, values, s));
   if (m->profile) {
     FEA_CUDA(cudaEventRecord(m->ev[2], s));
     m->profiled = true;

@@ -357,6 +357,7 @@ fea_status fea_batch_create(fea_mesh* const* meshes, int32_t n, const fea_form* 
     for (int k = 0; k < n && st == FEA_OK; ++k) {
       const int order = forms[k].order;
       if ((st = build_pattern(meshes[k], order, 1, s)) != FEA_OK) break;
+      if ((st = refuse_long_rows(meshes[k]->base[order], "fea_batch_create")) != FEA_OK) break;
       const Pattern* P = meshes[k]->pat[order][1];
       const int nb = order == 1 ? 4 : 10;
       const bool tiled = use_tiled(meshes[k], P);

@@ -59,6 +59,8 @@ struct Base {
   int max_row = 0;             // longest scalar row
   int32_t* ipos = nullptr;     // [nb][E] incidence index of (element e, local dof a)
   int32_t* emap = nullptr;     // [E][nb][nb] CSR position of local (a, b) (built on demand)
+  int64_t nlong = 0;           // rows of more than 255 entries: their slot bytes are not used; the
+  int32_t* long_rows = nullptr;  // local-row scatter adds them with k_long_rows (list, any order)
 };
 
 // Local rows are stored in incidence order: local row (e, a[, comp]) of the
@@ -229,6 +231,15 @@ fea_status assemble_backward(fea_mesh* m, const fea_form* form, const fea_coeffs
 // of the coefficient arrays
 bool aligned(const void* p, size_t a);
 fea_status check_form(const fea_mesh* m, const fea_form* f, const fea_coeffs* c, const fea_quadrature* q);
+
+// Entry points other than fea_assemble read the one-byte column slots, which
+// rows of more than 255 entries do not have: they refuse such meshes.
+inline fea_status refuse_long_rows(const Base* B, const char* what) {
+  if (B && B->nlong > 0)
+    return fail(FEA_ERR_OVERFLOW, std::string(what) + ": rows of more than 255 entries are assembled by fea_assemble "
+                                                      "only");
+  return FEA_OK;
+}
 
 // scratch management (fea_api.cu)
 fea_status ensure_scratch(Scratch& sc, size_t bytes);

@@ -239,6 +239,7 @@ fea_status fea_jit_assemble(fea_mesh* m, fea_jit* j, const fea_coeffs* co, doubl
   Pattern* P = m->pat[j->order][1];
   Base* B = m->base[j->order];
   if (!P || !B) return fail(FEA_ERR_STATE, "fea_jit_assemble: build the pattern with fea_pattern(mesh, order, 1)");
+  FEA_TRY(refuse_long_rows(B, "fea_jit_assemble"));
   FEA_TRY(ensure_loaded(j));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int nb = B->nb;

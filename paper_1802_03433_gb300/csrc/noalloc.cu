@@ -76,6 +76,7 @@ extern "C" fea_status fea_assemble_noalloc(fea_mesh* m, const fea_form* form, co
   Pattern* P = m->pat[order][ndpn];
   Base* B = m->base[order];
   if (!P || !B) return fail(FEA_ERR_STATE, "fea_assemble_noalloc: build the pattern with fea_pattern first");
+  FEA_TRY(refuse_long_rows(B, "fea_assemble_noalloc"));
   const int nb = B->nb, nl = nb * ndpn;
   const bool mixed = q->prec == FEA_MIXED;
   const size_t rb = mixed ? sizeof(float) : sizeof(double);

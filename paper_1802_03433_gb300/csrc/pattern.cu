@@ -33,7 +33,8 @@ namespace fea {
 
 namespace {
 
-constexpr int ROW_CAP = 1024;   // candidate couplings per scalar row (warp buffer)
+constexpr int ROW_CAP = 1024;     // candidate couplings per scalar row sorted by one warp
+constexpr int LONG_CAP = 16384;   // candidate couplings per scalar row sorted by one block (longer: refused)
 constexpr int UNIQ_WARPS = 4;   // warps per block of the row kernels
 
 // ------------------------------------------------------------------ validation
@@ -94,14 +95,15 @@ __device__ __forceinline__ unsigned long long row_key(int t, int k, int32_t i0, 
 }
 
 // Outputs of one sorted key: the distinct column (first of its run) and the
-// candidate's slot (its run's rank; rows past 255 entries are refused).
+// candidate's slot (its run's rank).  Rows of more than 255 entries are long
+// rows: their slot bytes (a byte holds ranks below 255) are not used, a
+// separate kernel adds them (k_long_rows).
 template <int NB, int SW>
 __device__ __forceinline__ void row_emit(unsigned long long key, bool keep, int rank, int32_t i0, int32_t* cols,
                                          int64_t cbase, uint8_t* slot, int* err) {
+  (void)err;
   if (keep) cols[cbase + rank] = (int32_t)(key >> 32);
-  if (rank >= 255) {  // rows of more than 255 entries exceed the slot bytes
-    atomicOr(err, DEV_ERR_OVERFLOW);
-  } else {
+  if (rank < 255) {
     const uint32_t o = (uint32_t)key;
     slot[((int64_t)i0 + o / NB) * SW + o % NB] = (uint8_t)rank;
   }
@@ -201,8 +203,7 @@ __global__ void __launch_bounds__(32 * UNIQ_WARPS) k_row_build(int64_t nrows, co
     const int k = (i1 - i0) * NB;
     int c;
     if (k > cap) {
-      if (lane == 0) atomicOr(err, DEV_ERR_OVERFLOW);
-      c = 0;
+      c = 0;  // a long candidate list: k_row_build_long
     } else if (k <= 32) {
       c = row_build_reg<NB, SW, 1>(k, i0, inc, edof, E, cols, slot, err);
     } else if (k <= 64) {
@@ -216,6 +217,66 @@ __global__ void __launch_bounds__(32 * UNIQ_WARPS) k_row_build(int64_t nrows, co
     }
     if (lane == 0) counts[row] = c;
   }
+}
+
+// Rows whose candidate list exceeds the warp kernel's cap.
+__global__ void k_long_list(const int32_t* __restrict__ inc_ptr, int64_t n, int nb, int cap, int32_t* __restrict__ cursor,
+                            int32_t* __restrict__ out) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n && (int64_t)(inc_ptr[r + 1] - inc_ptr[r]) * nb > cap) out[atomicAdd(cursor, 1)] = (int32_t)r;
+}
+
+// Rows of more than ROW_CAP (up to LONG_CAP) candidates, one block each: the
+// warp kernel's sort and runs with the block striding over the network in
+// shared memory.
+template <int NB, int SW>
+__global__ void __launch_bounds__(256) k_row_build_long(const int32_t* __restrict__ rows,
+                                                        const int32_t* __restrict__ inc_ptr,
+                                                        const int32_t* __restrict__ inc,
+                                                        const int32_t* __restrict__ edof, int64_t E,
+                                                        int32_t* __restrict__ counts, int32_t* __restrict__ cols,
+                                                        uint8_t* __restrict__ slot, int* err) {
+  extern __shared__ unsigned long long lbuf[];
+  const int32_t row = rows[blockIdx.x];
+  const int32_t i0 = inc_ptr[row];
+  const int k = (inc_ptr[row + 1] - i0) * NB;
+  int n2 = 32;
+  while (n2 < k) n2 <<= 1;
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) lbuf[t] = row_key<NB>(t, k, i0, inc, edof, E);
+  __syncthreads();
+  for (int size = 2; size <= n2; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = threadIdx.x; t < (n2 >> 1); t += blockDim.x) {
+        const int i = 2 * stride * (t / stride) + (t % stride), j = i + stride;
+        const unsigned long long a = lbuf[i], b = lbuf[j];
+        if ((a > b) == ((i & size) == 0)) {
+          lbuf[i] = b;
+          lbuf[j] = a;
+        }
+      }
+      __syncthreads();
+    }
+  // runs: each thread a contiguous range of sorted positions
+  const int per = (k + blockDim.x - 1) / blockDim.x;
+  const int p0 = min(k, (int)threadIdx.x * per), p1 = min(k, p0 + per);
+  int nk = 0;
+  for (int p = p0; p < p1; ++p) nk += (p == 0 || (uint32_t)(lbuf[p - 1] >> 32) != (uint32_t)(lbuf[p] >> 32));
+  int64_t total;
+  int rank = (int)block_excl_scan(nk, &total) - 1;
+  const int64_t cbase = (int64_t)i0 * NB;
+  for (int p = p0; p < p1; ++p) {
+    const bool keep = p == 0 || (uint32_t)(lbuf[p - 1] >> 32) != (uint32_t)(lbuf[p] >> 32);
+    rank += keep;
+    row_emit<NB, SW>(lbuf[p], keep, rank, i0, cols, cbase, slot, err);
+  }
+  if (threadIdx.x == 0) counts[row] = (int32_t)total;
+}
+
+// Rows of more than 255 entries (the long rows of the local-row scatter).
+__global__ void k_wide_list(const int32_t* __restrict__ rp, int64_t n, int32_t* __restrict__ cursor,
+                            int32_t* __restrict__ out) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n && rp[r + 1] - rp[r] > 255) out[atomicAdd(cursor, 1)] = (int32_t)r;
 }
 
 // col_idx of each row from the row's distinct columns in the scratch of
@@ -463,6 +524,8 @@ fea_status rows_and_slots(fea_mesh* m, Base* B, cudaStream_t s) {
   constexpr int SW = NB <= 4 ? 4 : 16;
   B->slot_width = SW;
   FEA_TRY(dalloc(&B->slot, (size_t)E * NB * SW));
+  // the slot bytes of long rows stay 0 (never used)
+  FEA_CUDA(cudaMemsetAsync(B->slot, 0, (size_t)E * NB * SW, s));
   Tmp<int32_t> cnt, cols;
   Tmp<int> mx;
   FEA_TRY(cnt.alloc(n));
@@ -474,14 +537,31 @@ fea_status rows_and_slots(fea_mesh* m, Base* B, cudaStream_t s) {
   int max_inc = 0;
   FEA_CUDA(cudaMemcpyAsync(&max_inc, mx.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   FEA_CUDA(cudaStreamSynchronize(s));
-  if ((int64_t)max_inc * NB > ROW_CAP)
-    return fail(FEA_ERR_OVERFLOW, "pattern: a row exceeds the scatter limits (more than 1024 candidate "
-                                  "couplings or more than 255 entries in a scalar row)");
+  if ((int64_t)max_inc * NB > LONG_CAP)
+    return fail(FEA_ERR_OVERFLOW, "pattern: a row has more than 16384 candidate couplings (elements x local dofs)");
   int cap = 32;
-  while (cap < max_inc * NB) cap <<= 1;
+  while (cap < max_inc * NB && cap < ROW_CAP) cap <<= 1;
   const size_t smem = cap > 256 ? (size_t)UNIQ_WARPS * cap * sizeof(unsigned long long) : 0;
   k_row_build<NB, SW><<<uniq_blocks, 32 * UNIQ_WARPS, smem, s>>>(n, B->inc_ptr, B->inc, B->edof, E, cap, cnt.p,
                                                                  cols.p, B->slot, m->err);
+  if ((int64_t)max_inc * NB > ROW_CAP) {
+    // candidate lists above the warp's cap: one block per row
+    Tmp<int32_t> nl, list;
+    FEA_TRY(nl.alloc(1));
+    FEA_TRY(list.alloc(n));
+    FEA_CUDA(cudaMemsetAsync(nl.p, 0, sizeof(int32_t), s));
+    k_long_list<<<blocks_for(n, 256), 256, 0, s>>>(B->inc_ptr, n, NB, cap, nl.p, list.p);
+    int32_t hn = 0;
+    FEA_CUDA(cudaMemcpyAsync(&hn, nl.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    FEA_CUDA(cudaStreamSynchronize(s));
+    int n2 = 32;
+    while (n2 < max_inc * NB) n2 <<= 1;
+    const size_t lsmem = (size_t)n2 * sizeof(unsigned long long);
+    FEA_CUDA(cudaFuncSetAttribute(k_row_build_long<NB, SW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem));
+    if (hn > 0)
+      k_row_build_long<NB, SW><<<hn, 256, lsmem, s>>>(list.p, B->inc_ptr, B->inc, B->edof, E, cnt.p, cols.p, B->slot,
+                                                      m->err);
+  }
   FEA_TRY(check_err(m, s, "pattern"));
   FEA_TRY(dalloc(&B->rp, n + 1));
   FEA_TRY(scan_to_ptr32(cnt.p, n, B->rp, &B->nnz, s, "nonzero"));
@@ -492,6 +572,18 @@ fea_status rows_and_slots(fea_mesh* m, Base* B, cudaStream_t s) {
   k_max_row<<<blocks_for(n, 256), 256, 0, s>>>(B->rp, n, mx.p);
   FEA_CUDA(cudaMemcpyAsync(&B->max_row, mx.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   FEA_CUDA(cudaStreamSynchronize(s));
+  if (B->max_row > 255) {
+    // rows past the slot bytes: listed (ascending) for k_long_rows
+    Tmp<int32_t> nw;
+    FEA_TRY(nw.alloc(1));
+    FEA_TRY(dalloc(&B->long_rows, n));
+    FEA_CUDA(cudaMemsetAsync(nw.p, 0, sizeof(int32_t), s));
+    k_wide_list<<<blocks_for(n, 256), 256, 0, s>>>(B->rp, n, nw.p, B->long_rows);
+    int32_t hw = 0;
+    FEA_CUDA(cudaMemcpyAsync(&hw, nw.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    FEA_CUDA(cudaStreamSynchronize(s));
+    B->nlong = hw;
+  }
   return FEA_OK;
 }
 
@@ -529,6 +621,7 @@ void free_base(Base* b) {
   dfree(b->slot);
   dfree(b->ipos);
   dfree(b->emap);
+  dfree(b->long_rows);
   delete b;
 }
 

@@ -147,6 +147,7 @@ extern "C" fea_status fea_assemble_2d(fea_mesh* m, const fea_form2d* form, doubl
   Pattern* P = m->pat[1][1];
   Base* B = m->base[1];
   if (!P || !B) return fail(FEA_ERR_STATE, "fea_assemble_2d: build the pattern with fea_pattern(mesh, 1, 1) first");
+  FEA_TRY(refuse_long_rows(B, "fea_assemble_2d"));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int64_t E = m->n_elems;
   const bool tiled = use_tiled(m, P);

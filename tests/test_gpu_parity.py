@@ -161,31 +161,75 @@ def _fan(ntets):
     return coords, tets
 
 
-def test_row_limits_raise_overflow_and_leave_the_mesh_usable(torch_cuda):
-    """The scatter's row limits: at most 1024 candidate couplings per scalar
-    row (incidences x local dofs) and at most 255 entries.  A vertex shared by
-    60 tets gives a P1 row of 181 entries (built, equal to the oracle's) and a
-    P2 row of 541 (FEA_ERR_OVERFLOW); 110 tets give 1100 P2 candidates (also
-    FEA_ERR_OVERFLOW).  The handle stays usable after each refusal."""
+def _fan_case(ntets, order, seed=0):
+    coords, tets = _fan(ntets)
+    rng = np.random.default_rng(seed)
+    return dict(coords=coords, tets=tets, order=order, form="diffusion", mass=1.0 if order == 2 else 0.0,
+                kappa=np.exp(rng.standard_normal(ntets)), f_kind="sinprod", f_param=(mg.SIN_AMP,),
+                npts=11 if order == 2 else 4, ndpn=1)
+
+
+@pytest.mark.parametrize("ntets,order", [(60, 2), (110, 2), (110, 1), (300, 1)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_long_rows_match_the_oracle(torch_cuda, ntets, order, prec):
+    """Rows past the warp sort (more than 1024 candidate couplings: 110 P2 tets
+    around a vertex) and past the one-byte column slots (more than 255
+    entries: 541 and 991 in P2, 301 and 901 in P1) are built by one block per
+    row and assembled by the long-row kernel: the pattern equals the oracle's,
+    the values agree, and two runs give the same bits, symmetric."""
+    c = _fan_case(ntets, order, seed=ntets)
+    o = oracle_system(c)
+    g1 = gpu_system(c, prec=prec)
+    g2 = gpu_system(c, prec=prec, mesh=g1["mesh"])
+    np.testing.assert_array_equal(g1["rp"], o["rp"])
+    np.testing.assert_array_equal(g1["ci"], o["ci"])
+    assert np.diff(g1["rp"]).max() > 255
+    tol = TOL_FP64 if prec == 0 else TOL_MIXED
+    assert row_scaled_error(o["rp"], o["vals"], g1["vals"]) <= tol
+    assert vec_scaled_error(o["rhs"], g1["rhs"]) <= tol
+    assert np.array_equal(g1["vals"].view(np.uint64), g2["vals"].view(np.uint64))
+    rp, ci, v = g1["rp"], g1["ci"], g1["vals"]
+    rows = np.repeat(np.arange(rp.size - 1), np.diff(rp))
+    tkey = ci.astype(np.int64) * (rp.size - 1) + rows
+    assert np.array_equal(v.view(np.uint64), v[np.argsort(tkey)].view(np.uint64))
+    g1["mesh"].close()
+
+
+def test_long_rows_refused_where_slots_are_read_and_past_the_block_sort(torch_cuda):
+    """The entry points that read the one-byte column slots (backward, batch,
+    runtime-compiled kernels, no-alloc) refuse meshes with rows of more than
+    255 entries; a row of more than 16384 candidate couplings (1,700 P2 tets
+    around a vertex) is refused by the pattern build.  The handle stays usable
+    after each refusal."""
+    import torch
     from paper_1802_03433_gb300 import fea
-    coords, tets = _fan(60)
-    m = fea.Mesh(coords, tets)
-    with pytest.raises(fea.FeaError) as ei:
-        m.pattern(2)
-    assert ei.value.status == 4
-    m.pattern(1)
-    rp, ci = m.pattern_tensors(1)
-    edof, nsd = oracle.dof_table(1, coords.shape[1], tets)
-    orp, oci = oracle.pattern(nsd, edof, ndpn=1)
-    np.testing.assert_array_equal(rp.cpu().numpy(), orp)
-    np.testing.assert_array_equal(ci.cpu().numpy(), oci)
+    c = _fan_case(60, 2)
+    m = fea.Mesh(c["coords"], c["tets"])
+    ndof, nnz = m.pattern(2)
+    kap = torch.as_tensor(c["kappa"], device="cuda")
+    form = fea.make_form(fea.FEA_DIFFUSION_MASS, 2, 1.0)
+    co = fea.make_coeffs(kappa=kap, f_kind=2, f_param=(1.0,))
+    q = fea.make_quadrature(11)
+    v = torch.empty(nnz, dtype=torch.float64, device="cuda")
+    r = torch.empty(ndof, dtype=torch.float64, device="cuda")
+    gk = torch.empty(c["tets"].shape[1], dtype=torch.float64, device="cuda")
+    gx = torch.empty((3, c["coords"].shape[1]), dtype=torch.float64, device="cuda")
+    for call in (lambda: fea.fea_assemble_backward(m.h, form, co, q, v, r, gk, gx),
+                 lambda: fea.fea_assemble_noalloc(m.h, form, co, q, v, r),
+                 lambda: fea.Batch([m], [form], [q], [co], fea.FEA_LOAD_SINPROD)):
+        with pytest.raises(fea.FeaError) as ei:
+            call()
+        assert ei.value.status == 4
+    fea.fea_assemble(m.h, form, co, q, v, r)  # fea_assemble takes them
+    torch.cuda.synchronize()
     m.check()
     m.close()
-    coords, tets = _fan(110)
+    coords, tets = _fan(1700)
     m = fea.Mesh(coords, tets)
     with pytest.raises(fea.FeaError) as ei:
         m.pattern(2)
     assert ei.value.status == 4
+    m.pattern(1)  # 5,101 entries in the vertex's P1 row: built
     m.check()
     m.close()
 
