@@ -209,39 +209,25 @@ __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemA
   }
 }
 
-// The couplings shared by several chunks: their partial sums, contiguous
-// and in chunk order, added and written as both 3 x 3 blocks.
+// The couplings shared by several chunks: their partial sums (contiguous,
+// in chunk order) added and written as both 3 x 3 blocks.  One thread per
+// entry of a group: the nine threads of a group read its partial sums as
+// whole sectors and write each row of a block as one 24-byte run, so a warp
+// instruction touches about a dozen sectors instead of 32 scattered ones.
 __global__ void k_chunk_reduce(const int32_t* __restrict__ gptr, const int4* __restrict__ grec, int64_t ngroup,
                                const double* __restrict__ part, double* __restrict__ values) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= ngroup) return;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 9 * ngroup) return;
+  const int64_t g = t / 9;
+  const int q = (int)(t - 9 * g), i = q / 3, j = q - 3 * i;
   const int32_t p0 = gptr[g], p1 = gptr[g + 1];
-  double v[12];
-  const double* src = part + PART_STRIDE * (int64_t)p0;
-  ld_v4(src, v[0], v[1], v[2], v[3]);
-  ld_v4(src + 4, v[4], v[5], v[6], v[7]);
-  ld_v4(src + 8, v[8], v[9], v[10], v[11]);
-  for (int32_t p = p0 + 1; p < p1; ++p) {
-    src = part + PART_STRIDE * (int64_t)p;
-    double w[12];
-    ld_v4(src, w[0], w[1], w[2], w[3]);
-    ld_v4(src + 4, w[4], w[5], w[6], w[7]);
-    ld_v4(src + 8, w[8], w[9], w[10], w[11]);
-#pragma unroll
-    for (int q = 0; q < 9; ++q) v[q] += w[q];
-  }
   const int4 rec = grec[g];
+  double v = __ldg(part + PART_STRIDE * (int64_t)p0 + q);
+#pragma unroll 4
+  for (int32_t p = p0 + 1; p < p1; ++p) v += __ldg(part + PART_STRIDE * (int64_t)p + q);
   const int Li = rec.z & 0xFFFF, Lj = rec.z >> 16;
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) values[(int64_t)rec.x + i * Li + j] = v[3 * i + j];
-  if (rec.x != rec.y) {
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-#pragma unroll
-      for (int i = 0; i < 3; ++i) values[(int64_t)rec.y + j * Lj + i] = v[3 * i + j];
-  }
+  values[(int64_t)rec.x + i * Li + j] = v;
+  if (rec.x != rec.y) values[(int64_t)rec.y + j * Lj + i] = v;
 }
 
 __global__ void k_chunk_reduce_nodes(const int32_t* __restrict__ gptr, const int32_t* __restrict__ gnode,
@@ -356,8 +342,8 @@ fea_status assemble_chunked(fea_mesh* m, Pattern* P, const fea_coeffs* co, const
   }
   if (m->profile) FEA_CUDA(cudaEventRecord(m->ev[1], s));
   if (K->ngroup > 0)
-    k_chunk_reduce<<<(unsigned)((K->ngroup + 127) / 128), 128, 0, s>>>(K->gptr, K->grec, K->ngroup, Cg.part,
-                                                                       values);
+    k_chunk_reduce<<<(unsigned)((9 * K->ngroup + 255) / 256), 256, 0, s>>>(K->gptr, K->grec, K->ngroup, Cg.part,
+                                                                           values);
   if (rhs && K->niso > 0)
     k_zero_nodes<<<(unsigned)((3 * K->niso + 255) / 256), 256, 0, s>>>(K->iso, K->niso, rhs);
   if (rhs && K->nngroup > 0)
