@@ -49,12 +49,12 @@ KERNELS = {
     # chunked scatter: the element arithmetic (335 flop, as the local-row
     # element kernel: 102 DFMA + 16 DADD + 115 DMUL) plus the bound of phase
     # A; counters of the 64^3 capture (103 DFMA + 25 DADD + 115 DMUL per
-    # element), DRAM bytes of the 64^3 launch x 8 (traffic grows with the
-    # elements: the same chunks, 8 times as many)
+    # element); DRAM bytes of one 128^3 launch (one-pass launch list) and of
+    # one 64^3 launch (full capture)
     "p1_elast_128": dict(kernel="k_elast_chunk (element arithmetic + fixed-point accumulation per chunk)",
-                         flop_equiv=335.0, flop_exec=346.0, traffic=8 * (226.0e6 + 317.7e6),
+                         flop_equiv=335.0, flop_exec=346.0, traffic=1821.3e6 + 3185.2e6,
                          profile="profiles/element_chunk_kernel_p1_elast.md"),
-    "p1_elast_64": dict(kernel="k_elast_chunk", flop_equiv=335.0, flop_exec=346.0, traffic=226.0e6 + 317.7e6,
+    "p1_elast_64": dict(kernel="k_elast_chunk", flop_equiv=335.0, flop_exec=346.0, traffic=223.1e6 + 355.4e6,
                         profile="profiles/element_chunk_kernel_p1_elast.md"),
     # P2: matrix warps + load warps; 375 = the formulas in FP64 (150 DFMA +
     # 26 DADD + 49 DMUL); executed 33 DFMA + 30 DADD + 43 DMUL (the 136 FMA
@@ -850,7 +850,7 @@ def bench_solve(fea, torch, dev, n=64, rtol=1e-8, max_iter=3000):
 # Bounded samples of each workload (same recipe, smaller cube) for the CPU
 # baseline: each takes some 10-20 s of host time for three repetitions of the
 # pattern, the single-threaded values and the all-cores values.
-CPU_SAMPLE_N = {"p2_diffmass": 32, "p1_poisson": 48, "p1_kappa": 48, "elasticity": 32}
+CPU_SAMPLE_N = {"p2_diffmass": 48, "p1_poisson": 64, "p1_kappa": 64, "elasticity": 48}
 
 
 def _oracle_kw(d):
@@ -933,7 +933,7 @@ def run_reference(args):
         return None
     import oracle
     wl = WORKLOADS[args.workload]
-    n = {"p2_diffmass": 16, "p1_poisson": 8, "p1_kappa": 24, "elasticity": 12}[wl["kind"]]
+    n = {"p2_diffmass": 32, "p1_poisson": 48, "p1_kappa": 48, "elasticity": 32}[wl["kind"]]
     d = make_inputs(wl["kind"], n, seed=0)
     edof, nsd = oracle.dof_table(d["order"], d["coords"].shape[1], d["tets"])
     rp, ci = oracle.pattern(nsd, edof, ndpn=d["ndpn"])
