@@ -590,11 +590,13 @@ fea_status build(fea_mesh* m, Pattern* P, Chunks* C, cudaStream_t s) {
   C->hbits = 0;
   while ((1 << C->hbits) < maxcnt) ++C->hbits;
   // the accumulators of the largest chunk must fit one CTA's shared memory
-  // (ndpn^2 sums and an exponent per slot, ndpn sums and an exponent per
-  // node slot), and a slot may take at most 128 contributions (the
+  // (ndpn^2 sums of two words and an exponent per slot, ndpn sums and an
+  // exponent per node slot, and for elasticity the node's staged
+  // coordinates), and a slot may take at most 128 contributions (the
   // fixed-point scale 2^(63 - 2 hbits) keeps 49 bits or more)
   const size_t d = P->ndpn;
-  if ((size_t)C->max_slots * (d * d * 8 + 4) + (size_t)C->max_nodes * (d * 8 + 4) > 227 * 1024 || C->hbits > 7)
+  if ((size_t)C->max_slots * (d * d * 8 + 4) + (size_t)C->max_nodes * (d * 8 + 4 + (d == 3 ? 24 : 0)) > 227 * 1024 ||
+      C->hbits > 7)
     return fail(FEA_ERR_OVERFLOW, "chunked scatter: a chunk couples too many node pairs for shared memory");
   C->nslot = sptr[nc];
   C->nnode_slot = nptr[nc];

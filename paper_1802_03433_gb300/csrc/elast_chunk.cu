@@ -57,10 +57,19 @@ constexpr int CHUNK_MIN_BLOCKS = 3;
 // 4 (one sector).
 constexpr int PART_STRIDE = 12;
 
+// Vertex coordinates of an element from the chunk's staged vertices.
+__device__ __forceinline__ void staged_vertices(const double* sxyz, const int* slot, double X[4][3]) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) X[a][d] = sxyz[3 * slot[a] + d];
+}
+
 template <int LOAD, int NPTS, typename R>
 __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemArgs A, ChunkArgs C) {
-  extern __shared__ unsigned smem_acc[];
-  unsigned* alo = smem_acc;                                     // [max_slots][9] low words
+  extern __shared__ double smem_chunk[];
+  double* sxyz = smem_chunk;                                    // [max_nodes][3] vertex coordinates
+  unsigned* alo = reinterpret_cast<unsigned*>(sxyz + 3 * C.max_nodes);  // [max_slots][9] low words
   int* ahi = reinterpret_cast<int*>(alo + 9 * C.max_slots);     // [max_slots][9] high words
   unsigned* rlo = reinterpret_cast<unsigned*>(ahi + 9 * C.max_slots);  // [max_nodes][3]
   int* rhi = reinterpret_cast<int*>(rlo + 3 * C.max_nodes);     // [max_nodes][3]
@@ -82,6 +91,15 @@ __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemA
   }
   for (int i = tid; i < ns; i += CHUNK_T) sexp[i] = EXP_EMPTY;
   for (int i = tid; i < nn; i += CHUNK_T) rexp[i] = EXP_EMPTY;
+  // the chunk's vertices, staged once: an element's vertex a is node slot
+  // eslot[a] (the diagonal pairs come first), so the elements read their
+  // coordinates from shared memory instead of gathering them twice from HBM
+  for (int k = tid; k < nn; k += CHUNK_T) {
+    const int64_t v = C.nrec[n0 + k].x;
+    sxyz[3 * k] = __ldg(A.x + v);
+    sxyz[3 * k + 1] = __ldg(A.y + v);
+    sxyz[3 * k + 2] = __ldg(A.z + v);
+  }
   __syncthreads();
   // Elements are dealt to the lanes across 64 segments of the chunk (lane i
   // takes position i / 64 of segment i % 64): neighbouring elements, which
@@ -93,16 +111,19 @@ __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemA
     const int t = (i & 63) * L + (i >> 6);
     if (t >= ne) continue;
     const int64_t e = C.celem[e0 + t];
+    int slot[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) slot[k] = C.eslot[k * A.E + e0 + t] & 0x7FFF;
     double X[4][3];
-    load_element(A, e, X);
+    staged_vertices(sxyz, slot, X);
     const double lam = A.lam ? __ldg(A.lam + e) : A.lam_const;
     const double mu = A.mu ? __ldg(A.mu + e) : A.mu_const;
     const int2 eb = element_bounds(X, fma(2.0, fabs(mu), fabs(lam)), 0.0, C.ef);
 #pragma unroll
-    for (int k = 0; k < 10; ++k) atomicMax(sexp + (C.eslot[k * A.E + e0 + t] & 0x7FFF), eb.x);
+    for (int k = 0; k < 10; ++k) atomicMax(sexp + slot[k], eb.x);
     if constexpr (HAS_LOAD) {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) atomicMax(rexp + C.eslot[k * A.E + e0 + t], eb.y);
+      for (int k = 0; k < 4; ++k) atomicMax(rexp + slot[k], eb.y);
     }
   }
   __syncthreads();
@@ -121,7 +142,7 @@ __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemA
       sh[k] = C.H - sexp[slot[k]];
     }
     double X[4][3];
-    load_element(A, e, X);
+    staged_vertices(sxyz, slot, X);
     Geo g;
     geometry(X, g);
     if (!(g.det > 0.0)) atomicOr(A.err, DEV_ERR_DEGENERATE);
@@ -333,7 +354,7 @@ fea_status assemble_chunked(fea_mesh* m, Pattern* P, const fea_coeffs* co, const
   Cg.part = static_cast<double*>(m->part.ptr);
   Cg.npart = rhs ? static_cast<double*>(m->npart.ptr) : nullptr;
   const size_t smem = (size_t)K->max_slots * (9 * 2 * sizeof(int) + sizeof(int)) +
-                      (size_t)K->max_nodes * (3 * 2 * sizeof(int) + sizeof(int));
+                      (size_t)K->max_nodes * (3 * sizeof(double) + 3 * 2 * sizeof(int) + sizeof(int));
   if (smem > 227 * 1024) return fail(FEA_ERR_OVERFLOW, "chunked scatter: chunk too large for shared memory");
   if (m->profile) FEA_CUDA(cudaEventRecord(m->ev[0], s));
   if (K->nchunk > 0) {
