@@ -22,7 +22,7 @@
 // hbits = 5 (24 tets around a vertex) that resolution is about 2^-47 of the
 // largest contribution.  The sum is rounded to FP64 once.
 //
-// Phases of k_elast_chunk (one CTA, ChunkShape::T threads, elements strided over
+// Phases of k_elast_chunk (one CTA, CHUNK_T threads, elements strided over
 // the threads):
 //   A. per element: an upper bound on |K entry| from the Lame parameters, the
 //      cofactors of J (in FP32 on edges normalised by their largest exponent)
@@ -50,16 +50,12 @@ namespace {
 
 using namespace chunkfx;
 
-// Threads per CTA and CTAs per SM: three CTAs of 128 threads for FP64 (168
-// registers a thread: the register file and the shared memory both hold
-// three); the FP32 element arithmetic needs fewer registers, so two CTAs of
-// 256 threads give it 16 warps per SM instead of 12 for the same shared
-// memory.
-template <typename R>
-struct ChunkShape {
-  static constexpr int T = IsDouble<R>::value ? 128 : 256;
-  static constexpr int MIN_BLOCKS = IsDouble<R>::value ? 3 : 2;
-};
+// Three CTAs of 128 threads per SM: at 168 registers a thread (FP64) the
+// register file and the shared memory both hold three.  Sixteen warps per SM
+// (two CTAs of 256 threads, registers capped at 128) measured the same for
+// both precisions.
+constexpr int CHUNK_T = 128;
+constexpr int CHUNK_MIN_BLOCKS = 3;
 // A partial sum of a shared 3 x 3 block takes 12 doubles (three whole 32-byte
 // sectors, so its stores never leave a sector partly written), a partial load
 // 4 (one sector).
@@ -74,8 +70,7 @@ __device__ __forceinline__ void staged_vertices(const double* sxyz, const int* s
 }
 
 template <int LOAD, int NPTS, typename R>
-__global__ void __launch_bounds__(ChunkShape<R>::T, ChunkShape<R>::MIN_BLOCKS) k_elast_chunk(ElemArgs A, ChunkArgs C) {
-  constexpr int CHUNK_T = ChunkShape<R>::T;
+__global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemArgs A, ChunkArgs C) {
   extern __shared__ double smem_chunk[];
   double* sxyz = smem_chunk;                                    // [max_nodes][3] vertex coordinates
   unsigned* alo = reinterpret_cast<unsigned*>(sxyz + 3 * C.max_nodes);  // [max_slots][9] low words
@@ -290,7 +285,7 @@ fea_status launch_one(const ElemArgs& A, const ChunkArgs& Cg, int64_t nchunk, si
                                   (int)smem));
     configured = smem;
   }
-  k_elast_chunk<LOAD, NPTS, R><<<(unsigned)nchunk, ChunkShape<R>::T, smem, s>>>(A, Cg);
+  k_elast_chunk<LOAD, NPTS, R><<<(unsigned)nchunk, CHUNK_T, smem, s>>>(A, Cg);
   FEA_CUDA(cudaGetLastError());
   return FEA_OK;
 }
