@@ -141,7 +141,7 @@ struct SlotArgs {
   const int32_t* rp;       // scalar CSR of the element order
   const int32_t* ci;
   const int32_t* inc_ptr;  // scalar incidences (e * nb + a, ascending e)
-  const int32_t* inc;
+  const int32_t* mult;     // [scalar nnz] elements holding both dofs of a coupling (upper positions)
   const int32_t* rp3;      // row pointer of the pattern (vector or scalar)
   int pass;                // 0: counts; 1: records
   // pass 0
@@ -181,21 +181,6 @@ __device__ __forceinline__ void block_bitonic(unsigned long long* key, uint16_t*
     }
 }
 
-// Elements containing both dofs i and j: the intersection of their sorted
-// incidence lists (incidence = e * nb + a).
-__device__ int common_elements(const int32_t* __restrict__ inc_ptr, const int32_t* __restrict__ inc, int nb,
-                               int32_t i, int32_t j) {
-  int32_t p = inc_ptr[i], pe = inc_ptr[i + 1], q = inc_ptr[j], qe = inc_ptr[j + 1];
-  int n = 0;
-  while (p < pe && q < qe) {
-    const int32_t a = inc[p] / nb, b = inc[q] / nb;
-    n += a == b;
-    p += a <= b;
-    q += b <= a;
-  }
-  return n;
-}
-
 __device__ __forceinline__ int32_t col_offset(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int32_t i,
                                               int32_t j) {
   int32_t lo = rp[i], hi = rp[i + 1];
@@ -206,6 +191,26 @@ __device__ __forceinline__ int32_t col_offset(const int32_t* __restrict__ rp, co
     else hi = m;
   }
   return lo - base;
+}
+
+// Multiplicity of every coupling: for each element and each pair of its
+// distinct dofs lo < hi, one count at the scalar CSR position (lo, hi).  A
+// chunk owns a coupling when it holds all of the elements counted there.
+template <int NB>
+__global__ void k_pair_mult(const int32_t* __restrict__ edof, int64_t E, const int32_t* __restrict__ rp,
+                            const int32_t* __restrict__ ci, int32_t* __restrict__ mult) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  int32_t v[NB];
+#pragma unroll
+  for (int a = 0; a < NB; ++a) v[a] = edof[a * E + e];
+#pragma unroll
+  for (int a = 0; a < NB; ++a)
+#pragma unroll
+    for (int b = a + 1; b < NB; ++b) {
+      const int32_t lo = min(v[a], v[b]), hi = max(v[a], v[b]);
+      atomicAdd(mult + rp[lo] + col_offset(rp, ci, lo, hi), 1);
+    }
 }
 
 // Exclusive scan over the block of one int per thread (a thread's count of a
@@ -278,7 +283,7 @@ __global__ void __launch_bounds__(BUILD_T) k_chunk_slots(SlotArgs A) {
     const bool off = (k0 >> 62) != 0;
     const int32_t i = (int32_t)((k0 >> 31) & 0x7FFFFFFFu), j = (int32_t)(k0 & 0x7FFFFFFFu);
     const int cnt = start[s + 1] - start[s];
-    const int g = off ? common_elements(A.inc_ptr, A.inc, NB, i, j) : A.inc_ptr[i + 1] - A.inc_ptr[i];
+    const int g = off ? A.mult[A.rp[i] + col_offset(A.rp, A.ci, i, j)] : A.inc_ptr[i + 1] - A.inc_ptr[i];
     own[s] = cnt == g;
     my_nn += !off;
     my_sh += cnt != g;
@@ -545,7 +550,14 @@ fea_status build(fea_mesh* m, Pattern* P, Chunks* C, cudaStream_t s) {
   A.rp = B->rp;
   A.ci = B->ci;
   A.inc_ptr = B->inc_ptr;
-  A.inc = B->inc;
+  Tmp<int32_t> mult;
+  FEA_TRY(mult.alloc(std::max<int64_t>(B->nnz, 1)));
+  FEA_CUDA(cudaMemsetAsync(mult.p, 0, std::max<int64_t>(B->nnz, 1) * sizeof(int32_t), s));
+  if (E > 0) {
+    if (NB == 4) k_pair_mult<4><<<blocks_for(E, 256), 256, 0, s>>>(B->edof, E, B->rp, B->ci, mult.p);
+    else k_pair_mult<10><<<blocks_for(E, 256), 256, 0, s>>>(B->edof, E, B->rp, B->ci, mult.p);
+  }
+  A.mult = mult.p;
   A.rp3 = P->row_ptr;
   A.cnt_slot = cs.p;
   A.cnt_node = cn.p;
