@@ -386,6 +386,17 @@ fea_status fea_diag_sinpi(const double* x, int64_t n, int32_t variant, double* m
  * context stays usable.  Asynchronous. */
 fea_status fea_diag_wait_timeout(fea_mesh* mesh, int32_t polls, void* stream);
 
+/* Failure-path check of the bounds-checked build (libfea_checked.so, built
+ * with -DFEA_CHECKED; see build_lib.py): *checked receives 1 for that build,
+ * 0 otherwise.  In the checked build one thread reads src[idx] (device) into
+ * out[0] (device) through the same check as the library's gathers: with idx
+ * outside [0, n) nothing is read, out[0] receives -1 and DEV_ERR_INDEX is
+ * latched in the mesh's error word (the next fea_mesh_check returns
+ * FEA_ERR_INDEX and clears it).  The normal build launches nothing (it would
+ * read unchecked).  Asynchronous. */
+fea_status fea_diag_checked_gather(fea_mesh* mesh, const double* src, int64_t n, int64_t idx, double* out,
+                                   int32_t* checked, void* stream);
+
 /* Measure the device's sustained FP64 FMA throughput (flop/s, FMA = 2)
  * with independent DFMA chains on every SM.  Synchronises. */
 fea_status fea_diag_fp64_rate(double* flops_per_s, void* stream);

@@ -49,6 +49,7 @@ struct AdjArgs {
   double* gk;            // dL/dkappa [E] or NULL
   double* gxs;           // per-incidence vertex gradients [incidence][4]
   int* err;
+  int64_t N;  // node count (bounds of the coordinate gathers in the checked build)
 };
 
 constexpr int ADJ_T = 128;
@@ -62,7 +63,7 @@ __global__ void __launch_bounds__(ADJ_T) k_adjoint(AdjArgs A) {
   {
     int32_t v[4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) v[a] = __ldg(A.tets + a * A.E + e);
+    for (int a = 0; a < 4; ++a) v[a] = checked_index(__ldg(A.tets + a * A.E + e), A.N, A.err);
     load_vertices(A.x, A.y, A.z, v, X);
   }
   Geo geo;
@@ -306,6 +307,7 @@ fea_status assemble_backward(fea_mesh* m, const fea_form* form, const fea_coeffs
   A.rp = B->rp;
   A.slot = B->slot;
   A.E = E;
+  A.N = m->n_nodes;
   A.kappa = co->kappa;
   A.kappa_const = co->kappa_const;
   A.mass = form->mass_coef;

@@ -163,6 +163,7 @@ fea_status assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* co, con
   A.y = m->y;
   A.z = m->z;
   A.tets = m->tets;
+  A.N = m->n_nodes;
   A.E = E;
   A.kappa = co->kappa;
   A.kappa_const = co->kappa_const;
@@ -187,6 +188,7 @@ fea_status assemble(fea_mesh* m, const fea_form* form, const fea_coeffs* co, con
   G.Fl = A.Fl;
   G.values = values;
   G.rhs = rhs;
+  G.err = m->err;
 
   // automatic: matrix warps and load warps in one kernel for the FP64 P2 sine
   // load (its sines run on the integer pipes beside the matrix's FP64 work:

@@ -81,6 +81,7 @@ extern "C" fea_status fea_assemble_atomic(fea_mesh* m, const fea_form* form, con
   A.y = m->y;
   A.z = m->z;
   A.tets = m->tets;
+  A.N = m->n_nodes;
   A.E = m->n_elems;
   A.e0 = 0;
   A.e1 = m->n_elems;

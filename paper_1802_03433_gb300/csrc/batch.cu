@@ -432,6 +432,7 @@ fea_status fea_batch_create(fea_mesh* const* meshes, int32_t n, const fea_form* 
       d.el.y = m->y;
       d.el.z = m->z;
       d.el.tets = m->tets;
+      d.el.N = m->n_nodes;
       d.el.E = m->n_elems;
       d.el.e0 = 0;
       d.el.e1 = m->n_elems;
@@ -448,6 +449,7 @@ fea_status fea_batch_create(fea_mesh* const* meshes, int32_t n, const fea_form* 
       d.ga.slot = B->slot;
       d.ga.Lm = d.el.Lm;
       d.ga.Fl = d.el.Fl;
+      d.ga.err = m->err;
       d.tg.ndof = P->ndof;
       d.tg.rows = P->rows_per_tile;
       d.tg.span_cap = P->max_tile_nnz;

@@ -33,7 +33,15 @@ struct ChunkArgs {
   double* rhs;
   double* part;   // partial sums of shared couplings
   double* npart;  // partial sums of shared loads
+  // extents, for the bounds checks of the checked build
+  int64_t n_nodes, nnz, n_part, n_npart;
 };
+
+// A 3 x 3 block of the CSR values at p, rows L apart, inside [0, nnz)
+// (checked build; always true otherwise).
+__device__ __forceinline__ bool block_ok(int64_t p, int L, int64_t nnz, int* err) {
+  return index_ok(p, nnz, err) && index_ok(p + 2 * (int64_t)L + 2, nnz, err);
+}
 
 // |x| < 2^result for a positive normal float.
 __device__ __forceinline__ int fexp_bound(float y) { return ((__float_as_int(y) >> 23) & 0xFF) - 126; }

@@ -91,6 +91,33 @@ extern "C" fea_status fea_diag_sinpi(const double* x, int64_t n, int32_t variant
   return FEA_OK;
 }
 
+namespace fea {
+namespace {
+__global__ void k_diag_checked_gather(const double* src, int64_t n, int64_t idx, double* out, int* err) {
+  out[0] = index_ok(idx, n, err) ? src[idx] : -1.0;
+}
+}  // namespace
+}  // namespace fea
+
+extern "C" fea_status fea_diag_checked_gather(fea_mesh* m, const double* src, int64_t n, int64_t idx, double* out,
+                                              int32_t* checked, void* stream) {
+  if (!m || !checked) return fea::fail(FEA_ERR_ARG, "NULL argument");
+#ifdef FEA_CHECKED
+  *checked = 1;
+  if (!src || !out || n < 1) return fea::fail(FEA_ERR_ARG, "src, out and n >= 1 are required");
+  fea::k_diag_checked_gather<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(src, n, idx, out, m->err);
+  FEA_CUDA(cudaGetLastError());
+#else
+  (void)src;
+  (void)n;
+  (void)idx;
+  (void)out;
+  (void)stream;
+  *checked = 0;
+#endif
+  return FEA_OK;
+}
+
 extern "C" fea_status fea_diag_wait_timeout(fea_mesh* m, int32_t polls, void* stream) {
   if (!m) return fea::fail(FEA_ERR_ARG, "mesh is NULL");
   if (polls < 1 || polls > (1 << 20)) return fea::fail(FEA_ERR_ARG, "polls must be in [1, 2^20]");

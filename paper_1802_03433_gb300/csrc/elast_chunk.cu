@@ -99,7 +99,8 @@ __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemA
   // eslot[a] (the diagonal pairs come first), so the elements read their
   // coordinates from shared memory instead of gathering them twice from HBM
   for (int k = tid; k < nn; k += CHUNK_T) {
-    const int64_t v = C.nrec[n0 + k].x;
+    int64_t v = C.nrec[n0 + k].x;
+    if (!index_ok(v, C.n_nodes, A.err)) v = 0;
     sxyz[3 * k] = __ldg(A.x + v);
     sxyz[3 * k + 1] = __ldg(A.y + v);
     sxyz[3 * k + 2] = __ldg(A.z + v);
@@ -117,7 +118,10 @@ __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemA
     const int64_t e = C.celem[e0 + t];
     int slot[10];
 #pragma unroll
-    for (int k = 0; k < 10; ++k) slot[k] = C.eslot[k * A.E + e0 + t] & 0x7FFF;
+    for (int k = 0; k < 10; ++k) {
+      slot[k] = C.eslot[k * A.E + e0 + t] & 0x7FFF;
+      if (!index_ok(slot[k], k < 4 ? nn : ns, A.err)) slot[k] = 0;
+    }
     double X[4][3];
     staged_vertices(sxyz, slot, X);
     const double lam = A.lam ? __ldg(A.lam + e) : A.lam_const;
@@ -142,6 +146,7 @@ __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemA
     for (int k = 0; k < 10; ++k) {
       const int v = C.eslot[k * A.E + e0 + t];
       slot[k] = v & 0x7FFF;
+      if (!index_ok(slot[k], k < 4 ? nn : ns, A.err)) slot[k] = 0;
       tr[k] = (v & 0x8000) != 0;
       sh[k] = C.H - sexp[slot[k]];
     }
@@ -198,17 +203,19 @@ __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemA
     }
     if (rec.w < 0) {
       const int Li = rec.z & 0xFFFF, Lj = rec.z >> 16;
+      if (block_ok(rec.x, Li, C.nnz, A.err)) {
 #pragma unroll
-      for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) C.values[(int64_t)rec.x + i * Li + j] = v[3 * i + j];
-      if (k >= nn) {
+          for (int j = 0; j < 3; ++j) C.values[(int64_t)rec.x + i * Li + j] = v[3 * i + j];
+      }
+      if (k >= nn && block_ok(rec.y, Lj, C.nnz, A.err)) {
 #pragma unroll
         for (int j = 0; j < 3; ++j)
 #pragma unroll
           for (int i = 0; i < 3; ++i) C.values[(int64_t)rec.y + j * Lj + i] = v[3 * i + j];
       }
-    } else {
+    } else if (index_ok(rec.w, C.n_part, A.err)) {
       double* p = C.part + PART_STRIDE * (int64_t)rec.w;
       st_v4(p, v[0], v[1], v[2], v[3]);
       st_v4(p + 4, v[4], v[5], v[6], v[7]);
@@ -225,9 +232,11 @@ __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemA
         f[q] = es >= EXP_POISON ? __longlong_as_double(0x7FF8000000000000LL)
                                 : f64_of(acc_sum(rlo + 3 * k + q, rhi + 3 * k + q, K), es - C.H);
       if (nr.y < 0) {
+        if (index_ok(nr.x, C.n_nodes, A.err)) {
 #pragma unroll
-        for (int q = 0; q < 3; ++q) C.rhs[3 * (int64_t)nr.x + q] = f[q];
-      } else {
+          for (int q = 0; q < 3; ++q) C.rhs[3 * (int64_t)nr.x + q] = f[q];
+        }
+      } else if (index_ok(nr.y, C.n_npart, A.err)) {
         st_v4(C.npart + 4 * (int64_t)nr.y, f[0], f[1], f[2], 0.0);
       }
     }
@@ -240,26 +249,30 @@ __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemA
 // whole sectors and write each row of a block as one 24-byte run, so a warp
 // instruction touches about a dozen sectors instead of 32 scattered ones.
 __global__ void k_chunk_reduce(const int32_t* __restrict__ gptr, const int4* __restrict__ grec, int64_t ngroup,
-                               const double* __restrict__ part, double* __restrict__ values) {
+                               const double* __restrict__ part, double* __restrict__ values, int64_t n_part,
+                               int64_t nnz, int* err) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 9 * ngroup) return;
   const int64_t g = t / 9;
   const int q = (int)(t - 9 * g), i = q / 3, j = q - 3 * i;
   const int32_t p0 = gptr[g], p1 = gptr[g + 1];
   const int4 rec = grec[g];
+  if (!index_ok(p0, n_part, err) || !index_ok(p1 - 1, n_part, err)) return;
   double v = __ldg(part + PART_STRIDE * (int64_t)p0 + q);
 #pragma unroll 4
   for (int32_t p = p0 + 1; p < p1; ++p) v += __ldg(part + PART_STRIDE * (int64_t)p + q);
   const int Li = rec.z & 0xFFFF, Lj = rec.z >> 16;
-  values[(int64_t)rec.x + i * Li + j] = v;
-  if (rec.x != rec.y) values[(int64_t)rec.y + j * Lj + i] = v;
+  if (block_ok(rec.x, Li, nnz, err)) values[(int64_t)rec.x + i * Li + j] = v;
+  if (rec.x != rec.y && block_ok(rec.y, Lj, nnz, err)) values[(int64_t)rec.y + j * Lj + i] = v;
 }
 
 __global__ void k_chunk_reduce_nodes(const int32_t* __restrict__ gptr, const int32_t* __restrict__ gnode,
-                                     int64_t ngroup, const double* __restrict__ npart, double* __restrict__ rhs) {
+                                     int64_t ngroup, const double* __restrict__ npart, double* __restrict__ rhs,
+                                     int64_t n_npart, int64_t n_nodes, int* err) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= ngroup) return;
   const int32_t p0 = gptr[g], p1 = gptr[g + 1];
+  if (!index_ok(p0, n_npart, err) || !index_ok(p1 - 1, n_npart, err) || !index_ok(gnode[g], n_nodes, err)) return;
   double f[4];
   ld_v4(npart + 4 * (int64_t)p0, f[0], f[1], f[2], f[3]);
   for (int32_t p = p0 + 1; p < p1; ++p) {
@@ -332,6 +345,7 @@ fea_status assemble_chunked(fea_mesh* m, Pattern* P, const fea_coeffs* co, const
   A.y = m->y;
   A.z = m->z;
   A.tets = m->tets;
+  A.N = m->n_nodes;
   A.E = m->n_elems;
   A.lam = co->lame_lambda;
   A.lam_const = co->lambda_const;
@@ -357,6 +371,10 @@ fea_status assemble_chunked(fea_mesh* m, Pattern* P, const fea_coeffs* co, const
   Cg.rhs = rhs;
   Cg.part = static_cast<double*>(m->part.ptr);
   Cg.npart = rhs ? static_cast<double*>(m->npart.ptr) : nullptr;
+  Cg.n_nodes = m->n_nodes;
+  Cg.nnz = P->nnz;
+  Cg.n_part = K->npart;
+  Cg.n_npart = K->nnpart;
   const size_t smem = (size_t)K->max_slots * (9 * 2 * sizeof(int) + sizeof(int)) +
                       (size_t)K->max_nodes * (3 * sizeof(double) + 3 * 2 * sizeof(int) + sizeof(int));
   if (smem > 227 * 1024) return fail(FEA_ERR_OVERFLOW, "chunked scatter: chunk too large for shared memory");
@@ -368,12 +386,13 @@ fea_status assemble_chunked(fea_mesh* m, Pattern* P, const fea_coeffs* co, const
   if (m->profile) FEA_CUDA(cudaEventRecord(m->ev[1], s));
   if (K->ngroup > 0)
     k_chunk_reduce<<<(unsigned)((9 * K->ngroup + 255) / 256), 256, 0, s>>>(K->gptr, K->grec, K->ngroup, Cg.part,
-                                                                           values);
+                                                                           values, Cg.n_part, Cg.nnz, m->err);
   if (rhs && K->niso > 0)
     k_zero_nodes<<<(unsigned)((3 * K->niso + 255) / 256), 256, 0, s>>>(K->iso, K->niso, rhs);
   if (rhs && K->nngroup > 0)
     k_chunk_reduce_nodes<<<(unsigned)((K->nngroup + 127) / 128), 128, 0, s>>>(K->ngptr, K->ngnode, K->nngroup,
-                                                                             Cg.npart, rhs);
+                                                                             Cg.npart, rhs, Cg.n_npart, Cg.n_nodes,
+                                                                             m->err);
   FEA_CUDA(cudaGetLastError());
   if (m->profile) {
     FEA_CUDA(cudaEventRecord(m->ev[2], s));

@@ -40,6 +40,7 @@ struct ElemArgs {
   const int32_t* ci;
   double* values;
   double* rhs;
+  int64_t N;  // node count (bounds of the coordinate gathers in the checked build)
 };
 
 // Algorithm 1, sparse variant (Sec. 5): each local entry is added into the
@@ -58,7 +59,7 @@ constexpr int ELEM_T = 128;
 __device__ __forceinline__ void load_element(const ElemArgs& A, int64_t e, double X[4][3]) {
   int32_t v[4];
 #pragma unroll
-  for (int a = 0; a < 4; ++a) v[a] = __ldg(A.tets + a * A.E + e);
+  for (int a = 0; a < 4; ++a) v[a] = checked_index(__ldg(A.tets + a * A.E + e), A.N, A.err);
   load_vertices(A.x, A.y, A.z, v, X);
 }
 

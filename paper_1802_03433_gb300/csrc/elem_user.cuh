@@ -47,6 +47,7 @@ struct UserArgs {
   void* Lm;              // local rows, incidence order, lstride(nb) apart
   void* Fl;              // local loads, incidence order (HAS_F only)
   int* err;
+  int64_t N;  // node count (bounds of the coordinate gathers in the checked build)
 };
 
 constexpr int USER_T = 128;
@@ -62,7 +63,7 @@ __device__ __forceinline__ void elem_user_body(const UserArgs& A, int64_t e) {
   {
     int32_t v[4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) v[a] = __ldg(A.tets + a * A.E + e);
+    for (int a = 0; a < 4; ++a) v[a] = checked_index(__ldg(A.tets + a * A.E + e), A.N, A.err);
     load_vertices(A.x, A.y, A.z, v, X);
   }
   Geo g;

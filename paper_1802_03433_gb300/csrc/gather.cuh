@@ -131,6 +131,16 @@ __device__ __forceinline__ void add_row(double* __restrict__ a, const int s[NB],
     for (int j = 0; j < NDPN; ++j) a[NDPN * s[b] + j] = t[NDPN * b + j];
 }
 
+// The NB slots of a local row, added at offset `off` of a CSR span of `span`
+// values, stay inside it (checked build; always true otherwise).
+template <int NB, int NDPN>
+__device__ __forceinline__ bool slots_ok(int off, const int s[NB], int span, int* err) {
+  bool ok = true;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) ok = ok && index_ok(off + NDPN * s[b] + NDPN - 1, span, err) && index_ok(s[b], span, err);
+  return ok;
+}
+
 // Load the NL values of one local row (32-byte aligned, whole sectors).
 template <int NL>
 __device__ __forceinline__ void load_row(const double* __restrict__ p, double v[NL]) {
@@ -181,6 +191,7 @@ struct GatherArgs {
   const void* Fl;          // local loads in incidence order, or NULL
   double* values;
   double* rhs;             // or NULL
+  int* err;                // device error word (bounds checks of the checked build)
 };
 
 // Loads of one incidence: the column slots, the local row, the local load.
@@ -214,7 +225,8 @@ __device__ __forceinline__ void gather_tile(const GatherArgs& G, int64_t tile, i
   if (threadIdx.x < rows && r < r1) {
     const int64_t node = r / NDPN;
     const int comp = (int)(r - node * NDPN);
-    double* __restrict__ a = acc + (__ldg(G.row_ptr + r) - base);
+    const int off = __ldg(G.row_ptr + r) - base;
+    double* __restrict__ a = acc + off;
     double f = 0.0;
     const int32_t i1 = __ldg(G.inc_ptr + node + 1);
     int32_t i = __ldg(G.inc_ptr + node);
@@ -225,10 +237,10 @@ __device__ __forceinline__ void gather_tile(const GatherArgs& G, int64_t tile, i
       while (i < i1) {
         if (i + 2 < i1) n0.load(G, i + 2, comp);
         if (i + 3 < i1) n1.load(G, i + 3, comp);
-        add_row<NB, NDPN, LT>(a, c0.s, c0.v);
+        if (slots_ok<NB, NDPN>(off, c0.s, span, G.err)) add_row<NB, NDPN, LT>(a, c0.s, c0.v);
         f += widen(c0.f);
         if (i + 1 < i1) {
-          add_row<NB, NDPN, LT>(a, c1.s, c1.v);
+          if (slots_ok<NB, NDPN>(off, c1.s, span, G.err)) add_row<NB, NDPN, LT>(a, c1.s, c1.v);
           f += widen(c1.f);
         }
         c0 = n0;
@@ -241,7 +253,7 @@ __device__ __forceinline__ void gather_tile(const GatherArgs& G, int64_t tile, i
       if (i < i1) c0.load(G, i, comp);
       while (i < i1) {
         if (i + 1 < i1) n0.load(G, i + 1, comp);
-        add_row<NB, NDPN, LT>(a, c0.s, c0.v);
+        if (slots_ok<NB, NDPN>(off, c0.s, span, G.err)) add_row<NB, NDPN, LT>(a, c0.s, c0.v);
         f += widen(c0.f);
         c0 = n0;
         ++i;

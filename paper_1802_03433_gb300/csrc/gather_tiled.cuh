@@ -228,11 +228,12 @@ __device__ __forceinline__ void gather_tiled_tile(const TiledArgs& G, int64_t ti
   const bool mine = tid < R;
   const int64_t r = r0 + tid;
   int cnt = 0;
-  double* a = acc;
+  int off = 0;
   if (mine) {
     cnt = __ldg(G.inc_ptr + r + 1) - __ldg(G.inc_ptr + r);
-    a = acc + (__ldg(G.row_ptr + r) - base);
+    off = __ldg(G.row_ptr + r) - base;
   }
+  double* a = acc + off;
   double f = 0.0;
   int k = 0;
   bool failed = false;
@@ -245,7 +246,7 @@ __device__ __forceinline__ void gather_tiled_tile(const TiledArgs& G, int64_t ti
       smem_slots<NB>(sp + lm_b + (size_t)tid * L::SW, sl);
       LT v[NB];
       load_smem_row<NB, LT>(reinterpret_cast<const LT*>(sp) + (size_t)tid * L::LS, v);
-      add_row<NB, 1, LT>(a, sl, v);
+      if (slots_ok<NB, 1>(off, sl, span, G.err)) add_row<NB, 1, LT>(a, sl, v);
       if (has_f) f += widen(reinterpret_cast<const LT*>(sp + lm_b + sl_b)[tid]);
     }
     if (__syncthreads_or(!ok)) {

@@ -113,7 +113,11 @@ std::string make_source(const fea_jit& j, const char* k_expr, const char* f_expr
   return s;
 }
 
+#ifdef FEA_CHECKED
+const char* const NVRTC_OPTS[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-default-device", "-DFEA_CHECKED"};
+#else
 const char* const NVRTC_OPTS[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-default-device"};
+#endif
 
 std::mutex g_cache_mu;
 std::map<std::string, std::vector<char>>& cubin_cache() {
@@ -256,6 +260,7 @@ fea_status fea_jit_assemble(fea_mesh* m, fea_jit* j, const fea_coeffs* co, doubl
   A.z = m->z;
   A.tets = m->tets;
   A.E = E;
+  A.N = m->n_nodes;
   A.kappa = co->kappa;
   A.kappa_const = co->kappa_const;
   A.mass = j->mass_coef;
@@ -283,6 +288,7 @@ fea_status fea_jit_assemble(fea_mesh* m, fea_jit* j, const fea_coeffs* co, doubl
     G.Fl = A.Fl;
     G.values = values;
     G.rhs = rhs;
+  G.err = m->err;
     FEA_TRY(launch_gather(nb, 1, mixed, G, P->rows_per_tile, P->max_tile_nnz, s));
   }
   if (m->profile) {

@@ -99,6 +99,7 @@ extern "C" fea_status fea_assemble_noalloc(fea_mesh* m, const fea_form* form, co
   A.y = m->y;
   A.z = m->z;
   A.tets = m->tets;
+  A.N = m->n_nodes;
   A.E = E;
   A.e0 = 0;
   A.e1 = E;
@@ -132,5 +133,6 @@ extern "C" fea_status fea_assemble_noalloc(fea_mesh* m, const fea_form* form, co
   G.Fl = A.Fl;
   G.values = values;
   G.rhs = rhs;
+  G.err = m->err;
   return launch_gather(nb, ndpn, mixed, G, P->rows_per_tile, P->max_tile_nnz, s);
 }

@@ -56,6 +56,7 @@ fea_status assemble_chunked_scalar(fea_mesh* m, Pattern* P, const fea_form* form
   A.y = m->y;
   A.z = m->z;
   A.tets = m->tets;
+  A.N = m->n_nodes;
   A.E = m->n_elems;
   A.kappa = co->kappa;
   A.kappa_const = co->kappa_const;

@@ -38,6 +38,7 @@ struct TriArgs {
   double* Lm;
   double* Fl;
   int* err;
+  int64_t N;  // node count (bounds of the coordinate gathers in the checked build)
 };
 
 template <int NPTS, bool LOAD>
@@ -47,7 +48,7 @@ __global__ void __launch_bounds__(128) k_elem_tri(TriArgs A) {
   double X[3][2];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const int32_t n = __ldg(A.tris + a * A.E + e);
+    const int32_t n = checked_index(__ldg(A.tris + a * A.E + e), A.N, A.err);
     X[a][0] = __ldg(A.x + n);
     X[a][1] = __ldg(A.y + n);
   }
@@ -159,6 +160,7 @@ extern "C" fea_status fea_assemble_2d(fea_mesh* m, const fea_form2d* form, doubl
   A.y = m->y;
   A.tris = m->tets;
   A.E = E;
+  A.N = m->n_nodes;
   for (int k = 0; k < 4; ++k) {
     A.S0[k] = form->sigma0[k];
     A.Sx[k] = form->sigma_x[k];
@@ -189,6 +191,7 @@ extern "C" fea_status fea_assemble_2d(fea_mesh* m, const fea_form2d* form, doubl
     G.Fl = A.Fl;
     G.values = values;
     G.rhs = rhs;
+  G.err = m->err;
     FEA_TRY(launch_gather(3, 1, false, G, P->rows_per_tile, P->max_tile_nnz, s));
   }
   if (m->profile) {

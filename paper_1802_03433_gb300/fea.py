@@ -13,7 +13,8 @@ import os
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libfea.so")
+# FEA_CHECKED=1 selects the bounds-checked build (build_lib.build(checked=True))
+LIB_PATH = os.path.join(_HERE, "libfea_checked.so" if os.environ.get("FEA_CHECKED") == "1" else "libfea.so")
 
 FEA_OK = 0
 STATUS = {0: "FEA_OK", 1: "FEA_ERR_ARG", 2: "FEA_ERR_INDEX", 3: "FEA_ERR_DEGENERATE",
@@ -100,6 +101,7 @@ def lib() -> C.CDLL:
         "fea_profile_last": [_vp, C.POINTER(C.c_float), C.POINTER(C.c_float)],
         "fea_diag_sinpi": [_vp, C.c_int64, C.c_int32, _vp, _vp, _vp],
         "fea_diag_wait_timeout": [_vp, C.c_int32, _vp],
+        "fea_diag_checked_gather": [_vp, _vp, C.c_int64, C.c_int64, _vp, C.POINTER(C.c_int32), _vp],
         "fea_diag_fp64_rate": [C.POINTER(C.c_double), _vp],
         "fea_batch_create": [C.POINTER(_vp), C.c_int32, C.POINTER(fea_form), C.POINTER(fea_quadrature),
                              C.c_int32, _vp, C.POINTER(_vp)],
@@ -331,6 +333,15 @@ def fea_profile_last(h):
 
 def fea_diag_wait_timeout(h, polls=1024, stream=None):
     _check(lib().fea_diag_wait_timeout(h, polls, _stream(stream)), "fea_diag_wait_timeout")
+
+
+def fea_diag_checked_gather(h, src, n, idx, out, stream=None):
+    """Read src[idx] into out[0] through the checked build's bounds check;
+    returns True for the checked build (False: nothing was launched)."""
+    chk = C.c_int32()
+    _check(lib().fea_diag_checked_gather(h, _ptr(src), n, idx, _ptr(out), C.byref(chk), _stream(stream)),
+           "fea_diag_checked_gather")
+    return bool(chk.value)
 
 
 def fea_diag_sinpi(x, variant=0, stream=None):
