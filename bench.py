@@ -44,7 +44,11 @@ FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # the FP64 flop the kernel executes per element (ncu SASS counters: 2 DFMA +
 # DADD + DMUL; lower where exact integer arithmetic replaced FP64 work), and
 # its DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum,
-# one capture; the captures are summarised under profiles/).
+# one capture; the captures are summarised under profiles/).  fp64_instr is
+# the FP64 instructions (DFMA + DADD + DMUL, ncu SASS thread counts) the
+# kernel executes per element: the FP64 pipe issues one of them per slot
+# whatever its kind, so their rate against the measured DFMA instruction
+# rate is how busy that pipe is kept.
 KERNELS = {
     # chunked scatter: the element arithmetic (335 flop, as the local-row
     # element kernel: 102 DFMA + 16 DADD + 115 DMUL) plus the bound of phase
@@ -52,22 +56,22 @@ KERNELS = {
     # element); DRAM bytes of one 128^3 launch (one-pass launch list) and of
     # one 64^3 launch (full capture)
     "p1_elast_128": dict(kernel="k_elast_chunk (element arithmetic + fixed-point accumulation per chunk)",
-                         flop_equiv=335.0, flop_exec=346.0, traffic=1821.3e6 + 3185.2e6,
+                         flop_equiv=335.0, flop_exec=346.0, traffic=None,
                          profile="profiles/element_chunk_kernel_p1_elast.md"),
-    "p1_elast_64": dict(kernel="k_elast_chunk", flop_equiv=335.0, flop_exec=346.0, traffic=223.1e6 + 355.4e6,
+    "p1_elast_64": dict(kernel="k_elast_chunk", flop_equiv=335.0, flop_exec=346.0, traffic=None,
                         profile="profiles/element_chunk_kernel_p1_elast.md"),
     # P2: matrix warps + load warps; 375 = the formulas in FP64 (150 DFMA +
     # 26 DADD + 49 DMUL); executed 33 DFMA + 30 DADD + 43 DMUL (the 136 FMA
     # terms of the entries are exact 64-bit integer sums)
-    "p2_diffmass_64": dict(kernel="k_elem_roles (P2 element, FP64)", flop_equiv=375.0, flop_exec=139.0,
+    "p2_diffmass_64": dict(kernel="k_elem_roles (P2 element, FP64)", flop_equiv=375.0, flop_exec=139.0, fp64_instr=106.0,
                            traffic=149.3e6 + 1985.1e6, profile="profiles/element_kernel_p2_diffmass_64.md"),
-    "p1_kappa_96": dict(kernel="k_elem_scalar (P1 element, FP64)", flop_equiv=119.0, flop_exec=119.0,
+    "p1_kappa_96": dict(kernel="k_elem_scalar (P1 element, FP64)", flop_equiv=119.0, flop_exec=119.0, fp64_instr=89.0,
                         traffic=238.4e6 + 793.2e6, profile="profiles/element_kernel_p1_kappa_96.md"),
-    "p1_poisson_8": dict(kernel="k_elem_scalar (P1 element, FP64)", flop_equiv=119.0, flop_exec=119.0,
+    "p1_poisson_8": dict(kernel="k_elem_scalar (P1 element, FP64)", flop_equiv=119.0, flop_exec=119.0, fp64_instr=89.0,
                          traffic=None, profile=None),
-    "adjoint_96": dict(kernel="k_adjoint (P1 backward, FP64)", flop_equiv=483.0, flop_exec=483.0,
+    "adjoint_96": dict(kernel="k_adjoint (P1 backward, FP64)", flop_equiv=483.0, flop_exec=483.0, fp64_instr=300.0,
                        traffic=438.1e6 + 672.6e6, profile="profiles/adjoint_kernel_p1_kappa_96.md"),
-    "paper_2d": dict(kernel="k_elem_tri (P1 triangle element, FP64)", flop_equiv=191.0, flop_exec=191.0,
+    "paper_2d": dict(kernel="k_elem_tri (P1 triangle element, FP64)", flop_equiv=191.0, flop_exec=191.0, fp64_instr=127.0,
                      traffic=268.5e6 + 950.7e6, profile="profiles/element_kernel_paper_2d.md"),
 }
 
@@ -126,6 +130,13 @@ def roofline_block(key, E, kernel_ms, fp64_peak_tflops, note=None):
            "frac_nominal": ach / FP64_NOMINAL_TFLOPS, "flop_per_element": k["flop_equiv"],
            "executed": {"flop_per_element": k["flop_exec"], "achieved": exe, "frac": exe / fp64_peak_tflops},
            "kernel_ms": kernel_ms, "traffic": k["traffic"], "profile": k["profile"]}
+    if k.get("fp64_instr"):
+        # FP64 pipe issue: instructions per second against the measured DFMA
+        # instruction rate (the measured flop rate / 2)
+        ips = k["fp64_instr"] * E / (kernel_ms / 1e3) / 1e9
+        peak_ips = fp64_peak_tflops * 1e3 / 2
+        out["fp64_pipe"] = {"instr_per_element": k["fp64_instr"], "achieved_ginstr_s": ips,
+                            "peak_ginstr_s": peak_ips, "frac": ips / peak_ips}
     if note:
         out["note"] = note
     return out

@@ -20,6 +20,7 @@ struct ChunkArgs {
   const int32_t* cptr;
   const int32_t* celem;
   const uint16_t* eslot;
+  int64_t es;     // row stride of eslot
   const int32_t* sptr;
   const int32_t* nptr;
   const int4* srec;

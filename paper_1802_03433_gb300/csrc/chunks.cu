@@ -159,6 +159,7 @@ struct SlotArgs {
   int2* nrec;
   int32_t* pkey;
   uint16_t* eslot;
+  int64_t es;              // row stride of eslot
 };
 
 __device__ __forceinline__ void block_bitonic(unsigned long long* key, uint16_t* pay, int np) {
@@ -337,7 +338,7 @@ __global__ void __launch_bounds__(BUILD_T) k_chunk_slots(SlotArgs A) {
     const int orig = pay[p] & 0x7FFF;
     const int t = orig / NPAIR, k = orig - NPAIR * t;
     const bool tr = k >= NB && (pay[p] & 0x8000);
-    A.eslot[k * A.E + e0 + t] = (uint16_t)(sid[p] | (tr ? 0x8000 : 0));
+    A.eslot[k * A.es + e0 + t] = (uint16_t)(sid[p] | (tr ? 0x8000 : 0));
   }
 }
 
@@ -523,7 +524,7 @@ fea_status build(fea_mesh* m, Pattern* P, Chunks* C, cudaStream_t s) {
   lists.push_back((int32_t)pos);
   C->nchunk = (int64_t)cptr.size() - 1;
   FEA_TRY(dalloc(&C->cptr, cptr.size()));
-  FEA_TRY(dalloc(&C->celem, E));
+  FEA_TRY(dalloc(&C->celem, E + 4));  // padded: bulk copies of a chunk round up to 16 bytes
   Tmp<int32_t> lptr;
   FEA_TRY(lptr.alloc(lists.size()));
   FEA_CUDA(cudaMemcpy(C->cptr, cptr.data(), cptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
@@ -607,7 +608,8 @@ fea_status build(fea_mesh* m, Pattern* P, Chunks* C, cudaStream_t s) {
   // coordinates), and a slot may take at most 128 contributions (the
   // fixed-point scale 2^(63 - 2 hbits) keeps 49 bits or more)
   const size_t d = P->ndpn;
-  if ((size_t)C->max_slots * (d * d * 8 + 4) + (size_t)C->max_nodes * (d * 8 + 4 + (d == 3 ? 24 : 0)) > 227 * 1024 ||
+  if ((size_t)C->max_slots * (d * d * 8 + 4) + (size_t)C->max_nodes * (d * 8 + 4 + (d == 3 ? 24 : 0)) +
+              (d == 3 ? CHUNK_STAGE_BYTES : 0) > 227 * 1024 ||
       C->hbits > 7)
     return fail(FEA_ERR_OVERFLOW, "chunked scatter: a chunk couples too many node pairs for shared memory");
   C->nslot = sptr[nc];
@@ -618,7 +620,8 @@ fea_status build(fea_mesh* m, Pattern* P, Chunks* C, cudaStream_t s) {
   FEA_TRY(dalloc(&C->nptr, nc + 1));
   FEA_TRY(dalloc(&C->srec, C->nslot));
   FEA_TRY(dalloc(&C->nrec, C->nnode_slot));
-  FEA_TRY(dalloc(&C->eslot, (size_t)NPAIR * E));
+  C->estride = (E + 7) & ~(int64_t)7;
+  FEA_TRY(dalloc(&C->eslot, (size_t)NPAIR * C->estride + 8));
   Tmp<int64_t> dpb, dnpb;
   Tmp<int32_t> pkey;
   FEA_TRY(dpb.alloc(nc + 1));
@@ -637,6 +640,7 @@ fea_status build(fea_mesh* m, Pattern* P, Chunks* C, cudaStream_t s) {
   A.nrec = C->nrec;
   A.pkey = pkey.p;
   A.eslot = C->eslot;
+  A.es = C->estride;
   FEA_TRY(slots());
   // 4. partial-sum lists of the shared couplings (key: the scalar CSR position
   // of the coupling's upper entry) and of the shared nodes (key: node id)

@@ -23,7 +23,9 @@
 // largest contribution.  The sum is rounded to FP64 once.
 //
 // Phases of k_elast_chunk (one CTA, CHUNK_T threads, elements strided over
-// the threads):
+// the threads), after the chunk's vertex coordinates are staged in shared
+// memory (and, in the FP32 instance, its element ids and dof-pair slots,
+// brought in by bulk copies on the TMA engine):
 //   A. per element: an upper bound on |K entry| from the Lame parameters, the
 //      cofactors of J (in FP32 on edges normalised by their largest exponent)
 //      and det J; its exponent is max-reduced into the element's ten slots
@@ -43,6 +45,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "bulkcopy.cuh"
 #include "chunk_common.cuh"
 
 namespace fea {
@@ -61,6 +64,14 @@ constexpr int CHUNK_MIN_BLOCKS = 3;
 // 4 (one sector).
 constexpr int PART_STRIDE = 12;
 
+// The chunk's element ids and dof-pair slots staged in shared memory by bulk
+// copies (STAGE): rows of STAGE_E entries, wide enough for the largest chunk
+// plus the elements before the chunk's first one that round its copies down
+// to a 16-byte boundary; then the mbarrier the copies complete.
+constexpr int STAGE_E = CHUNK_STAGE_E;
+constexpr int STAGE_BYTES = CHUNK_STAGE_BYTES;
+static_assert((STAGE_E * 4) % 16 == 0 && (STAGE_E * 2) % 16 == 0, "staged rows must start on 16-byte boundaries");
+
 // Vertex coordinates of an element from the chunk's staged vertices.
 __device__ __forceinline__ void staged_vertices(const double* sxyz, const int* slot, double X[4][3]) {
 #pragma unroll
@@ -69,10 +80,13 @@ __device__ __forceinline__ void staged_vertices(const double* sxyz, const int* s
     for (int d = 0; d < 3; ++d) X[a][d] = sxyz[3 * slot[a] + d];
 }
 
-template <int LOAD, int NPTS, typename R>
+template <int LOAD, int NPTS, typename R, bool STAGE>
 __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemArgs A, ChunkArgs C) {
-  extern __shared__ double smem_chunk[];
-  double* sxyz = smem_chunk;                                    // [max_nodes][3] vertex coordinates
+  extern __shared__ __align__(16) double smem_chunk[];
+  int32_t* s_ce = reinterpret_cast<int32_t*>(smem_chunk);      // STAGE: [STAGE_E] element ids
+  uint16_t* s_es = reinterpret_cast<uint16_t*>(s_ce + STAGE_E); // STAGE: [10][STAGE_E] dof-pair slots
+  uint64_t* bar = reinterpret_cast<uint64_t*>(s_es + 10 * STAGE_E);
+  double* sxyz = smem_chunk + (STAGE ? STAGE_BYTES / 8 : 0);   // [max_nodes][3] vertex coordinates
   unsigned* alo = reinterpret_cast<unsigned*>(sxyz + 3 * C.max_nodes);  // [max_slots][9] low words
   int* ahi = reinterpret_cast<int*>(alo + 9 * C.max_slots);     // [max_slots][9] high words
   unsigned* rlo = reinterpret_cast<unsigned*>(ahi + 9 * C.max_slots);  // [max_nodes][3]
@@ -84,7 +98,32 @@ __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemA
   const int s0 = C.sptr[c], ns = C.sptr[c + 1] - s0;
   const int n0 = C.nptr[c], nn = C.nptr[c + 1] - n0;
   constexpr bool HAS_LOAD = LOAD != LOAD_NONE;
+  // STAGE: the chunk's element ids and its ten rows of slots are copied to
+  // shared memory with bulk copies (the TMA engine), each rounded out to 16-byte
+  // boundaries (ca, ea: the entries before the chunk's first one)
+  const int ca = e0 & 3, ea = e0 & 7;
+  if constexpr (STAGE) {
+    if (ne > CHUNK_MAX_ELEMS) {  // cannot happen with chunks from chunks.cu
+      if (tid == 0) atomicOr(A.err, DEV_ERR_INDEX);
+      return;
+    }
+    if (tid == 0) {
+      mbar_init(bar, 1);
+      mbar_init_fence();
+      const uint32_t cb = (uint32_t)(((ca + ne) * 4 + 15) & ~15), eb = (uint32_t)(((ea + ne) * 2 + 15) & ~15);
+      mbar_expect_tx(bar, cb + 10u * eb);
+      if (cb) bulk_load(s_ce, C.celem + (e0 - ca), cb, bar);
+      if (eb) {
+#pragma unroll
+        for (int k = 0; k < 10; ++k) bulk_load(s_es + k * STAGE_E, C.eslot + k * C.es + (e0 - ea), eb, bar);
+      }
+    }
+  }
+  auto elem_id = [&](int t) -> int64_t { return STAGE ? s_ce[ca + t] : C.celem[e0 + t]; };
+  auto pair_slot = [&](int k, int t) -> int { return STAGE ? s_es[k * STAGE_E + ea + t] : C.eslot[k * C.es + e0 + t]; };
   const int K = C.K;
+  // f_c |T| = f_c |det J| / 6: the amplitudes over 6, once per thread
+  [[maybe_unused]] const double fp6[3] = {A.fp[0] * (1.0 / 6.0), A.fp[1] * (1.0 / 6.0), A.fp[2] * (1.0 / 6.0)};
   for (int i = tid; i < 9 * ns; i += CHUNK_T) {
     alo[i] = 0u;
     ahi[i] = 0;
@@ -106,6 +145,19 @@ __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemA
     sxyz[3 * k + 2] = __ldg(A.z + v);
   }
   __syncthreads();
+  if constexpr (STAGE) {
+    // every thread waits (bounded) for the staged rows; if they never land the
+    // chunk raises DEV_ERR_TIMEOUT and writes nothing, after thread 0 has
+    // waited (bounded) once more for the copies still in flight
+    const bool ok = mbar_wait(bar, 0);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicOr(A.err, DEV_ERR_TIMEOUT);
+        mbar_wait(bar, 0);
+      }
+      return;
+    }
+  }
   // Elements are dealt to the lanes across 64 segments of the chunk (lane i
   // takes position i / 64 of segment i % 64): neighbouring elements, which
   // share node pairs, go to different warp instructions, so the atomics of
@@ -115,11 +167,11 @@ __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemA
   for (int i = tid; i < 64 * L; i += CHUNK_T) {
     const int t = (i & 63) * L + (i >> 6);
     if (t >= ne) continue;
-    const int64_t e = C.celem[e0 + t];
+    const int64_t e = elem_id(t);
     int slot[10];
 #pragma unroll
     for (int k = 0; k < 10; ++k) {
-      slot[k] = C.eslot[k * A.E + e0 + t] & 0x7FFF;
+      slot[k] = pair_slot(k, t) & 0x7FFF;
       if (!index_ok(slot[k], k < 4 ? nn : ns, A.err)) slot[k] = 0;
     }
     double X[4][3];
@@ -139,12 +191,12 @@ __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemA
   for (int i = tid; i < 64 * L; i += CHUNK_T) {
     const int t = (i & 63) * L + (i >> 6);
     if (t >= ne) continue;
-    const int64_t e = C.celem[e0 + t];
+    const int64_t e = elem_id(t);
     int slot[10], sh[10];
     bool tr[10];
 #pragma unroll
     for (int k = 0; k < 10; ++k) {
-      const int v = C.eslot[k * A.E + e0 + t];
+      const int v = pair_slot(k, t);
       slot[k] = v & 0x7FFF;
       if (!index_ok(slot[k], k < 4 ? nn : ns, A.err)) slot[k] = 0;
       tr[k] = (v & 0x8000) != 0;
@@ -166,19 +218,36 @@ __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemA
       acc_add(alo + idx, ahi + idx, fx_of(v, sh[k]), K);
     });
     if constexpr (HAS_LOAD) {
-      R Xr[4][3];
-      vertices_r<R>(X, Xr);
-      R Fs[4];
-      shape_load<1, NPTS, LOAD, R>(Xr, Fs);
-      const double vol = adet * (1.0 / 6.0);
-      const R f[3] = {R(A.fp[0] * vol), R(A.fp[1] * vol), R(A.fp[2] * vol)};
+      int shf[4];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const int shf = C.H - rexp[slot[a]];
+      for (int a = 0; a < 4; ++a) shf[a] = C.H - rexp[slot[a]];
+      if constexpr (LOAD == LOAD_CONST) {
+        // a constant f: every rule integrates f lambda_a exactly, f |T| / 4 at
+        // each vertex; the factor 1/4 is taken by the fixed-point shift
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-          const int idx = 3 * slot[a] + q;
-          acc_add(rlo + idx, rhi + idx, fx_of(R(f[q] * Fs[a]), shf), K);
+          if (A.fp[q] == 0.0) continue;  // same for every thread
+          const R fq = R(fp6[q] * adet);
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            const int idx = 3 * slot[a] + q;
+            acc_add(rlo + idx, rhi + idx, fx_of(fq, shf[a] - 2), K);
+          }
+        }
+      } else {
+        R Xr[4][3];
+        vertices_r<R>(X, Xr);
+        R Fs[4];
+        shape_load<1, NPTS, LOAD, R>(Xr, Fs);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          if (A.fp[q] == 0.0) continue;  // same for every thread
+          const R fq = R(fp6[q] * adet);
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            const int idx = 3 * slot[a] + q;
+            acc_add(rlo + idx, rhi + idx, fx_of(R(fq * Fs[a]), shf[a]), K);
+          }
         }
       }
     }
@@ -290,17 +359,26 @@ __global__ void k_zero_nodes(const int32_t* __restrict__ nodes, int64_t n, doubl
   if (i < 3 * n) rhs[3 * (int64_t)nodes[i / 3] + i % 3] = 0.0;
 }
 
-template <int LOAD, int NPTS, typename R>
-fea_status launch_one(const ElemArgs& A, const ChunkArgs& Cg, int64_t nchunk, size_t smem, cudaStream_t s) {
+template <int LOAD, int NPTS, typename R, bool STAGE>
+fea_status launch_stage(const ElemArgs& A, const ChunkArgs& Cg, int64_t nchunk, size_t smem, cudaStream_t s) {
   static size_t configured = 0;  // opt-in above the 48 KB default, once per instance
   if (smem > 48 * 1024 && smem > configured) {
-    FEA_CUDA(cudaFuncSetAttribute(k_elast_chunk<LOAD, NPTS, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    FEA_CUDA(cudaFuncSetAttribute(k_elast_chunk<LOAD, NPTS, R, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
     configured = smem;
   }
-  k_elast_chunk<LOAD, NPTS, R><<<(unsigned)nchunk, CHUNK_T, smem, s>>>(A, Cg);
+  k_elast_chunk<LOAD, NPTS, R, STAGE><<<(unsigned)nchunk, CHUNK_T, smem, s>>>(A, Cg);
   FEA_CUDA(cudaGetLastError());
   return FEA_OK;
+}
+
+// The FP32 (mixed) kernel stages the chunk's connectivity with bulk copies:
+// 3.79 -> 3.69 ms at 128^3.  The FP64 kernel, bound by its FP64 pipe, reads
+// it from global memory: staged it measured 6.31 -> 6.33 ms.
+template <int LOAD, int NPTS, typename R>
+fea_status launch_one(const ElemArgs& A, const ChunkArgs& Cg, int64_t nchunk, size_t smem, cudaStream_t s) {
+  constexpr bool STAGE = !IsDouble<R>::value;
+  return launch_stage<LOAD, NPTS, R, STAGE>(A, Cg, nchunk, smem + (STAGE ? STAGE_BYTES : 0), s);
 }
 
 template <typename R>
@@ -357,6 +435,7 @@ fea_status assemble_chunked(fea_mesh* m, Pattern* P, const fea_coeffs* co, const
   Cg.cptr = K->cptr;
   Cg.celem = K->celem;
   Cg.eslot = K->eslot;
+  Cg.es = K->estride;
   Cg.sptr = K->sptr;
   Cg.nptr = K->nptr;
   Cg.srec = K->srec;
@@ -377,7 +456,8 @@ fea_status assemble_chunked(fea_mesh* m, Pattern* P, const fea_coeffs* co, const
   Cg.n_npart = K->nnpart;
   const size_t smem = (size_t)K->max_slots * (9 * 2 * sizeof(int) + sizeof(int)) +
                       (size_t)K->max_nodes * (3 * sizeof(double) + 3 * 2 * sizeof(int) + sizeof(int));
-  if (smem > 227 * 1024) return fail(FEA_ERR_OVERFLOW, "chunked scatter: chunk too large for shared memory");
+  if (smem + STAGE_BYTES > 227 * 1024)
+    return fail(FEA_ERR_OVERFLOW, "chunked scatter: chunk too large for shared memory");
   if (m->profile) FEA_CUDA(cudaEventRecord(m->ev[0], s));
   if (K->nchunk > 0) {
     if (q->prec == FEA_MIXED) FEA_TRY(launch_prec<float>(A, Cg, K->nchunk, smem, ld, q->npts, s));

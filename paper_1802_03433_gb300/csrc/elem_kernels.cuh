@@ -368,11 +368,22 @@ __device__ __forceinline__ void elast_upper(const Geo& g, double adet, double la
       Mc[a][k] = Ms * Gr[a][k];
       LMc[a][k] = LMs * Gr[a][k];
     }
+  // mu |T| grad phi_a . grad phi_b for a, b >= 1; the gradients sum to zero,
+  // so the row of vertex 0 is minus the sum of the others (4 FP64 operations
+  // fewer than its four dot products)
   static_for<10>([&](auto K) {
     constexpr int a = upper_a(4, K), b = upper_b(4, K);
-    D[a][b] = dot3(Mc[a], Gr[b]);  // mu |T| grad phi_a . grad phi_b
-    if constexpr (a != b) D[b][a] = D[a][b];
+    if constexpr (a >= 1) {
+      D[a][b] = dot3(Mc[a], Gr[b]);
+      if constexpr (a != b) D[b][a] = D[a][b];
+    }
   });
+#pragma unroll
+  for (int b = 1; b < 4; ++b) {
+    D[0][b] = -(D[1][b] + D[2][b] + D[3][b]);
+    D[b][0] = D[0][b];
+  }
+  D[0][0] = -(D[0][1] + D[0][2] + D[0][3]);
   static_for<78>([&](auto K) {
     constexpr int r = upper_a(12, K), c = upper_b(12, K);
     constexpr int a = r / 3, i = r % 3, b = c / 3, j = c % 3;

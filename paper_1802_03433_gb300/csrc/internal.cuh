@@ -80,6 +80,12 @@ struct Base {
 // second kernel over the shared couplings.
 constexpr int CHUNK_MAX_ELEMS = 384;     // P1 (scalar and vector)
 constexpr int CHUNK_MAX_ELEMS_P2 = 128;  // P2: 55 dof pairs per element
+// The elasticity chunk kernel stages a chunk's element ids and its ten rows of
+// dof-pair slots in shared memory (rows of CHUNK_STAGE_E entries: the largest
+// chunk plus the slack of rounding its bulk copies out to 16-byte boundaries),
+// with the copies' mbarrier: CHUNK_STAGE_BYTES on top of its accumulators.
+constexpr int CHUNK_STAGE_E = CHUNK_MAX_ELEMS + 8;
+constexpr int CHUNK_STAGE_BYTES = CHUNK_STAGE_E * 4 + 10 * CHUNK_STAGE_E * 2 + 16;
 
 // Index of the local dof pair (a, b), a <= b, of an element with nb local
 // dofs: the nb diagonal pairs (the dof slots) first, then the pairs a < b in
@@ -95,9 +101,12 @@ struct Chunks {
   int hbits = 0;                 // ceil(log2(most elements contributing to one slot of a chunk))
   int32_t* cptr = nullptr;       // [nchunk + 1] element offsets into celem
   int32_t* celem = nullptr;      // [E] element ids, chunk by chunk
-  uint16_t* eslot = nullptr;     // [npair][E] (chunk order) slot of each local dof pair k = pair_index(a, b)
-                                 // of the element (k < nb: the dof slot of local dof k); bit 15 set when
-                                 // dof(a) > dof(b) (the slot holds the transposed block)
+  uint16_t* eslot = nullptr;     // [npair][estride] (chunk order) slot of each local dof pair k =
+                                 // pair_index(a, b) of the element (k < nb: the dof slot of local dof k);
+                                 // bit 15 set when dof(a) > dof(b) (the slot holds the transposed block)
+  int64_t estride = 0;           // row stride of eslot: E rounded up to 8, so every row starts 16-byte aligned
+                                 // (celem and eslot have 16 bytes of padding past their ends, so bulk copies
+                                 // rounded up to 16 bytes stay inside them)
   int32_t* sptr = nullptr;       // [nchunk + 1] slot offsets; each chunk's node slots come first
   int32_t* nptr = nullptr;       // [nchunk + 1] node-slot offsets
   int4* srec = nullptr;          // [nslot] {U, W, Li | Lj << 16, partial index or -1 when owned}: the

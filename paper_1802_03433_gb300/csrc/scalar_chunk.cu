@@ -67,6 +67,7 @@ fea_status assemble_chunked_scalar(fea_mesh* m, Pattern* P, const fea_form* form
   Cg.cptr = K->cptr;
   Cg.celem = K->celem;
   Cg.eslot = K->eslot;
+  Cg.es = K->estride;
   Cg.sptr = K->sptr;
   Cg.nptr = K->nptr;
   Cg.srec = K->srec;

@@ -170,10 +170,10 @@ __global__ void __launch_bounds__(ROLES ? 2 * SC_T : SC_T, ROLES ? 3 : 4) k_scal
     const double kap = A.kappa ? __ldg(A.kappa + e) : A.kappa_const;
     const int2 eb = element_bounds(X, (ORDER == 2 ? 16.0 : 1.0) * fabs(kap), MASS ? fabs(A.mass) : 0.0, C.ef);
     constexpr int NP = NB * (NB + 1) / 2;
-    for (int k = 0; k < NP; ++k) atomicMax(sexp + (C.eslot[k * A.E + e0 + t] & 0x7FFF), eb.x);
+    for (int k = 0; k < NP; ++k) atomicMax(sexp + (C.eslot[k * C.es + e0 + t] & 0x7FFF), eb.x);
     if constexpr (HAS_LOAD) {
 #pragma unroll
-      for (int k = 0; k < NB; ++k) atomicMax(rexp + C.eslot[k * A.E + e0 + t], eb.y);
+      for (int k = 0; k < NB; ++k) atomicMax(rexp + C.eslot[k * C.es + e0 + t], eb.y);
     }
   }
   __syncthreads();
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(ROLES ? 2 * SC_T : SC_T, ROLES ? 3 : 4) k_scal
     load_element(A, e, X);
     double adet = 0.0;
     if (mat) {
-      auto slot_of = [&](int a, int b) { return es[pair_index(NB, a, b) * A.E] & 0x7FFF; };
+      auto slot_of = [&](int a, int b) { return es[pair_index(NB, a, b) * C.es] & 0x7FFF; };
       adet = scalar_upper<ORDER, MASS, R>(
           A, e, X,
           [&](auto K, R v) {
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(ROLES ? 2 * SC_T : SC_T, ROLES ? 3 : 4) k_scal
         const R amp = R(A.fp[0] * adet * (1.0 / 6.0));
 #pragma unroll
         for (int a = 0; a < NB; ++a) {
-          const int sl = es[a * A.E];
+          const int sl = es[a * C.es];
           acc_add(rlo + sl, rhi + sl, fx_of(R(amp * Fs[a]), C.H - rexp[sl]), KS);
         }
       }
