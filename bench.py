@@ -50,16 +50,15 @@ FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # whatever its kind, so their rate against the measured DFMA instruction
 # rate is how busy that pipe is kept.
 KERNELS = {
-    # chunked scatter: the element arithmetic (335 flop, as the local-row
-    # element kernel: 102 DFMA + 16 DADD + 115 DMUL) plus the bound of phase
-    # A; counters of the 64^3 capture (103 DFMA + 25 DADD + 115 DMUL per
-    # element); DRAM bytes of one 128^3 launch (one-pass launch list) and of
-    # one 64^3 launch (full capture)
+    # chunked scatter: the element arithmetic plus the bound of phase A;
+    # counters of the 64^3 capture (95 DFMA + 33 DADD + 103 DMUL = 231 FP64
+    # instructions, 326 flop per element); DRAM bytes of one 128^3 launch
+    # (one-pass launch list) and of one 64^3 launch (full capture)
     "p1_elast_128": dict(kernel="k_elast_chunk (element arithmetic + fixed-point accumulation per chunk)",
-                         flop_equiv=335.0, flop_exec=346.0, traffic=None,
+                         flop_equiv=326.0, flop_exec=326.0, fp64_instr=231.0, traffic=1629.4e6 + 3187.3e6,
                          profile="profiles/element_chunk_kernel_p1_elast.md"),
-    "p1_elast_64": dict(kernel="k_elast_chunk", flop_equiv=335.0, flop_exec=346.0, traffic=None,
-                        profile="profiles/element_chunk_kernel_p1_elast.md"),
+    "p1_elast_64": dict(kernel="k_elast_chunk", flop_equiv=326.0, flop_exec=326.0, fp64_instr=231.0,
+                        traffic=199.3e6 + 355.1e6, profile="profiles/element_chunk_kernel_p1_elast.md"),
     # P2: matrix warps + load warps; 375 = the formulas in FP64 (150 DFMA +
     # 26 DADD + 49 DMUL); executed 33 DFMA + 30 DADD + 43 DMUL (the 136 FMA
     # terms of the entries are exact 64-bit integer sums)
