@@ -15,7 +15,10 @@
 //     elements of a cell in ascending id;
 //  3. per chunk (one CTA): the pairs of local dofs (vertices for P1, the
 //     ten P2 dofs for P2) of its elements are sorted and de-duplicated into
-//     slots (scalar dof pairs i <= j, the dof slots i == i first); a slot is
+//     slots (scalar dof pairs i <= j, the dof slots i == i first;
+//     k_chunk_slots, which also counts them), then, once the slot offsets
+//     are known, each slot's record is written from its first candidate
+//     (k_chunk_records, no second sort); a slot is
 //     owned when the chunk holds every element that contains both dofs (the
 //     incidence lists say how many do); each slot gets the CSR positions of
 //     its two blocks ((i, j) and (j, i), 3 x 3 for elasticity, single
@@ -23,11 +26,12 @@
 //     sum;
 //  4. the partial sums of every shared coupling (and every shared node's
 //     load) get consecutive places, in chunk order, for the second kernel.
-// Every step is deterministic: atomics only count, and every list filled
-// through an atomic cursor is sorted afterwards.
+// Every step is deterministic: atomics only count or take a minimum, and
+// every list filled through an atomic cursor is sorted afterwards.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <vector>
 
@@ -143,7 +147,6 @@ struct SlotArgs {
   const int32_t* inc_ptr;  // scalar incidences (e * nb + a, ascending e)
   const int32_t* mult;     // [scalar nnz] elements holding both dofs of a coupling (upper positions)
   const int32_t* rp3;      // row pointer of the pattern (vector or scalar)
-  int pass;                // 0: counts; 1: records
   // pass 0
   int32_t* cnt_slot;
   int32_t* cnt_node;
@@ -296,49 +299,101 @@ __global__ void __launch_bounds__(BUILD_T) k_chunk_slots(SlotArgs A) {
   atomicAdd(&s_shnode, my_shn);
   atomicMax(&s_max, my_max);
   __syncthreads();
-  const int nn = s_nn;
-  if (A.pass == 0) {
-    if (tid == 0) {
-      A.cnt_slot[c] = ns;
-      A.cnt_node[c] = nn;
-      A.cnt_shared[c] = s_shared;
-      A.cnt_shnode[c] = s_shnode;
-      A.cnt_max[c] = s_max;
-    }
-    return;
-  }
-  // ranks of the shared slots and shared node slots, in slot order
-  const int sper = (ns + BUILD_T - 1) / BUILD_T;
-  const int q0 = min(ns, tid * sper), q1 = min(ns, q0 + sper);
-  int a_sh = 0, a_shn = 0;
-  for (int s = q0; s < q1; ++s) {
-    a_sh += !own[s];
-    a_shn += !own[s] && s < nn;
-  }
-  int tot;
-  int r_sh = block_scan_int(a_sh, &tot);
-  int r_shn = block_scan_int(a_shn, &tot);
-  const int64_t s_off = A.sptr[c], n_off = A.nptr[c];
-  for (int s = q0; s < q1; ++s) {
-    const unsigned long long k0 = key[start[s]];
-    const int32_t i = (int32_t)((k0 >> 31) & 0x7FFFFFFFu), j = (int32_t)(k0 & 0x7FFFFFFFu);
-    const int32_t oij = col_offset(A.rp, A.ci, i, j), oji = i == j ? oij : col_offset(A.rp, A.ci, j, i);
-    const int d = A.ndpn;
-    const int32_t Li = A.rp3[d * i + 1] - A.rp3[d * i], Lj = A.rp3[d * j + 1] - A.rp3[d * j];
-    const int32_t part = own[s] ? -1 : (int32_t)(A.pbase[c] + r_sh);
-    r_sh += !own[s];
-    A.srec[s_off + s] = make_int4(A.rp3[d * i] + d * oij, A.rp3[d * j] + d * oji, Li | (Lj << 16), part);
-    A.pkey[s_off + s] = A.rp[i] + oij;
-    if (s < nn) {
-      A.nrec[n_off + s] = make_int2(i, own[s] ? -1 : (int32_t)(A.npbase[c] + r_shn));
-      r_shn += !own[s];
-    }
-  }
+  // every candidate's slot (chunk-local, the rank of its key), with the
+  // transposed bit
   for (int p = tid; p < n; p += BUILD_T) {
     const int orig = pay[p] & 0x7FFF;
     const int t = orig / NPAIR, k = orig - NPAIR * t;
     const bool tr = k >= NB && (pay[p] & 0x8000);
     A.eslot[k * A.es + e0 + t] = (uint16_t)(sid[p] | (tr ? 0x8000 : 0));
+  }
+  if (tid == 0) {
+    A.cnt_slot[c] = ns;
+    A.cnt_node[c] = s_nn;
+    A.cnt_shared[c] = s_shared;
+    A.cnt_shnode[c] = s_shnode;
+    A.cnt_max[c] = s_max;
+  }
+}
+
+// Pass 1: the records of every slot of a chunk, once the slot offsets are
+// known, from the slots pass 0 left in eslot (no second sort): a slot's key
+// is that of its first candidate, its count the number of candidates that
+// name it (shared-memory atomics; only the minimum and the count are taken
+// from them, so the records do not depend on their order).
+template <int NB>
+__global__ void __launch_bounds__(BUILD_T) k_chunk_records(SlotArgs A) {
+  constexpr int CAP = sort_cap<NB>();
+  constexpr int NPAIR = NB * (NB + 1) / 2;
+  extern __shared__ int smem_i32[];
+  int* first = smem_i32;                                  // [CAP] first candidate of each slot
+  int* cnt = first + CAP;                                 // [CAP] candidates of each slot
+  uint8_t* own = reinterpret_cast<uint8_t*>(cnt + CAP);  // [CAP]
+  const int c = blockIdx.x, tid = threadIdx.x;
+  const int e0 = A.cptr[c], ne = A.cptr[c + 1] - e0;
+  const int n = ne * NPAIR;
+  const int64_t s_off = A.sptr[c], n_off = A.nptr[c];
+  const int ns = A.sptr[c + 1] - A.sptr[c], nn = A.nptr[c + 1] - A.nptr[c];
+  for (int q = tid; q < ns; q += BUILD_T) {
+    first[q] = INT_MAX;
+    cnt[q] = 0;
+  }
+  __syncthreads();
+  for (int p = tid; p < n; p += BUILD_T) {
+    const int t = p / NPAIR, k = p - NPAIR * t;
+    const int sl = A.eslot[k * A.es + e0 + t] & 0x7FFF;
+    if (sl < ns) {
+      atomicMin(first + sl, p);
+      atomicAdd(cnt + sl, 1);
+    }
+  }
+  __syncthreads();
+  // each slot's dof pair i <= j (off_pair: a pair of two local dofs, not a
+  // dof with itself) and whether the chunk holds all its elements
+  bool off_pair = false;
+  auto pair_of_slot = [&](int q, int32_t& i, int32_t& j) {
+    const int p = first[q];
+    const int t = p / NPAIR, k = p - NPAIR * t;
+    off_pair = k >= NB;
+    const int64_t e = A.celem[e0 + t];
+    int a, b;
+    pair_of(NB, k, a, b);
+    const int32_t va = A.edof[a * A.E + e], vb = A.edof[b * A.E + e];
+    i = va < vb ? va : vb;
+    j = va < vb ? vb : va;
+  };
+  for (int q = tid; q < ns; q += BUILD_T) {
+    int32_t i, j;
+    pair_of_slot(q, i, j);
+    const int g = off_pair ? A.mult[A.rp[i] + col_offset(A.rp, A.ci, i, j)] : A.inc_ptr[i + 1] - A.inc_ptr[i];
+    own[q] = cnt[q] == g;
+  }
+  __syncthreads();
+  // ranks of the shared slots and shared node slots, in slot order
+  const int sper = (ns + BUILD_T - 1) / BUILD_T;
+  const int q0 = min(ns, tid * sper), q1 = min(ns, q0 + sper);
+  int a_sh = 0, a_shn = 0;
+  for (int q = q0; q < q1; ++q) {
+    a_sh += !own[q];
+    a_shn += !own[q] && q < nn;
+  }
+  int tot;
+  int r_sh = block_scan_int(a_sh, &tot);
+  int r_shn = block_scan_int(a_shn, &tot);
+  for (int q = q0; q < q1; ++q) {
+    int32_t i, j;
+    pair_of_slot(q, i, j);
+    const int32_t oij = col_offset(A.rp, A.ci, i, j), oji = i == j ? oij : col_offset(A.rp, A.ci, j, i);
+    const int d = A.ndpn;
+    const int32_t Li = A.rp3[d * i + 1] - A.rp3[d * i], Lj = A.rp3[d * j + 1] - A.rp3[d * j];
+    const int32_t part = own[q] ? -1 : (int32_t)(A.pbase[c] + r_sh);
+    r_sh += !own[q];
+    A.srec[s_off + q] = make_int4(A.rp3[d * i] + d * oij, A.rp3[d * j] + d * oji, Li | (Lj << 16), part);
+    A.pkey[s_off + q] = A.rp[i] + oij;
+    if (q < nn) {
+      A.nrec[n_off + q] = make_int2(i, own[q] ? -1 : (int32_t)(A.npbase[c] + r_shn));
+      r_shn += !own[q];
+    }
   }
 }
 
@@ -566,18 +621,18 @@ fea_status build(fea_mesh* m, Pattern* P, Chunks* C, cudaStream_t s) {
   A.cnt_shnode = cshn.p;
   A.cnt_max = cmax.p;
   const int cap = NB == 4 ? sort_cap<4>() : sort_cap<10>();
+  // pass 0 (sort): every candidate's slot into eslot, and the counts
+  C->estride = (E + 7) & ~(int64_t)7;
+  FEA_TRY(dalloc(&C->eslot, (size_t)NPAIR * C->estride + 8));
+  A.eslot = C->eslot;
+  A.es = C->estride;
   const size_t smem = (size_t)cap * (8 + 2 + 2 + 1) + (cap + 1) * 2;
-  auto slots = [&]() -> fea_status {
-    if (nc == 0) return FEA_OK;
-    if (NB == 4) k_chunk_slots<4><<<(unsigned)nc, BUILD_T, smem, s>>>(A);
-    else k_chunk_slots<10><<<(unsigned)nc, BUILD_T, smem, s>>>(A);
-    FEA_CUDA(cudaGetLastError());
-    return FEA_OK;
-  };
   FEA_CUDA(cudaFuncSetAttribute(NB == 4 ? k_chunk_slots<4> : k_chunk_slots<10>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  A.pass = 0;
-  FEA_TRY(slots());
+  if (nc > 0) {
+    if (NB == 4) k_chunk_slots<4><<<(unsigned)nc, BUILD_T, smem, s>>>(A);
+    else k_chunk_slots<10><<<(unsigned)nc, BUILD_T, smem, s>>>(A);
+  }
   FEA_CUDA(cudaGetLastError());
   std::vector<int32_t> hs(nc), hn(nc), hsh(nc), hshn(nc), hmax(nc);
   FEA_CUDA(cudaMemcpyAsync(hs.data(), cs.p, nc * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -620,8 +675,6 @@ fea_status build(fea_mesh* m, Pattern* P, Chunks* C, cudaStream_t s) {
   FEA_TRY(dalloc(&C->nptr, nc + 1));
   FEA_TRY(dalloc(&C->srec, C->nslot));
   FEA_TRY(dalloc(&C->nrec, C->nnode_slot));
-  C->estride = (E + 7) & ~(int64_t)7;
-  FEA_TRY(dalloc(&C->eslot, (size_t)NPAIR * C->estride + 8));
   Tmp<int64_t> dpb, dnpb;
   Tmp<int32_t> pkey;
   FEA_TRY(dpb.alloc(nc + 1));
@@ -631,7 +684,7 @@ fea_status build(fea_mesh* m, Pattern* P, Chunks* C, cudaStream_t s) {
   FEA_CUDA(cudaMemcpy(C->nptr, nptr.data(), (nc + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
   FEA_CUDA(cudaMemcpy(dpb.p, pbase.data(), (nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
   FEA_CUDA(cudaMemcpy(dnpb.p, npbase.data(), (nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
-  A.pass = 1;
+  // pass 1 (no sort): the slot records
   A.sptr = C->sptr;
   A.nptr = C->nptr;
   A.pbase = dpb.p;
@@ -639,9 +692,14 @@ fea_status build(fea_mesh* m, Pattern* P, Chunks* C, cudaStream_t s) {
   A.srec = C->srec;
   A.nrec = C->nrec;
   A.pkey = pkey.p;
-  A.eslot = C->eslot;
-  A.es = C->estride;
-  FEA_TRY(slots());
+  const size_t rsmem = (size_t)cap * (4 + 4 + 1);
+  FEA_CUDA(cudaFuncSetAttribute(NB == 4 ? k_chunk_records<4> : k_chunk_records<10>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem));
+  if (nc > 0) {
+    if (NB == 4) k_chunk_records<4><<<(unsigned)nc, BUILD_T, rsmem, s>>>(A);
+    else k_chunk_records<10><<<(unsigned)nc, BUILD_T, rsmem, s>>>(A);
+  }
+  FEA_CUDA(cudaGetLastError());
   // 4. partial-sum lists of the shared couplings (key: the scalar CSR position
   // of the coupling's upper entry) and of the shared nodes (key: node id)
   int32_t* partcol = reinterpret_cast<int32_t*>(C->srec) + 3;  // .w of every record
