@@ -398,7 +398,7 @@ def run_ours(args):
                                 "note": "paper's sparse Algorithm 1: global FP64 atomicAdd after a row search"}
         del runs
     if want("batched"):
-        forms["batched"] = bench_batched(fea, torch, dev, small, args.warmup, flush)
+        forms["batched"] = bench_batched(fea, torch, dev, small, args.warmup, flush, ws, rank)
     if want("adjoint"):
         forms["adjoint"] = bench_adjoint(fea, torch, dev, small, args.warmup, flush, fp64_peak)
     if want("local_rows") and d["form"] == 2 and args.scatter != fea.FEA_SCATTER_LOCAL_ROWS:
@@ -559,10 +559,26 @@ def _events(torch):
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
-def bench_batched(fea, torch, dev, steps, warmup, flush):
+# Relative cost of a P2 element against a P1 element in the batch's Poisson
+# forms (element kernel + scatter per element of the single-mesh forms: P2
+# 64^3 1.26 ms / 1.57M, P1 96^3 1.19 ms / 5.3M), the weight of the batch's
+# split over several GPUs.
+BATCH_P2_WEIGHT = 3.6
+
+
+def bench_batched(fea, torch, dev, steps, warmup, flush, ws=1, rank=0):
     """256 uneven meshes (n ~ U{4..32}, half P1 / half P2 Poisson, log-normal
-    kappa): one CUDA-graph launch (autotuned) vs one fea_assemble per mesh."""
+    kappa): one CUDA-graph launch (autotuned) vs one fea_assemble per mesh.
+    With several ranks the meshes are split by longest processing time first
+    (fea_partition_batch on element counts weighted by order) and each rank
+    assembles its own as a batch; the time is the slowest rank's."""
     specs = mg.batch()
+    E_all = sum(d["tets"].shape[1] for d in specs)
+    if ws > 1:
+        sides, orders = mg.batch_sides()
+        cost = 6.0 * sides.astype(np.float64) ** 3 * np.where(orders == 2, BATCH_P2_WEIGHT, 1.0)
+        part, _ = fea.fea_partition_batch(cost, ws)
+        specs = [d for d, p in zip(specs, part) if p == rank]
     meshes, forms, quads, coeffs, keep = [], [], [], [], []
     for d in specs:
         m = fea.Mesh(d["coords"], d["tets"], device=dev)
@@ -598,7 +614,7 @@ def bench_batched(fea, torch, dev, steps, warmup, flush):
             c.record()
             torch.cuda.synchronize()
             tot += a.elapsed_time(c)
-        res[name] = tot / steps
+        res[name] = max_over_ranks(tot, dev) / steps
     for m in meshes:
         m.check()
     b.close()
@@ -607,15 +623,19 @@ def bench_batched(fea, torch, dev, steps, warmup, flush):
         m.close()
     alg = sum(algorithmic_bytes("p1_kappa" if d["order"] == 1 else "p2_diffmass", d["tets"].shape[1],
                                 d["coords"].shape[1], nd, nz) for d, (nd, nz) in zip(specs, patterns))
-    return {"value": E / (res["graph"] / 1e3), "unit": "elements/s", "ms_per_step": res["graph"],
+    if ws > 1:
+        alg = max_over_ranks(float(alg), dev)  # the largest rank's share
+    return {"value": E_all / (res["graph"] / 1e3), "unit": "elements/s", "ms_per_step": res["graph"],
             "hbm": hbm_block(alg, res["graph"]),
             "roofline": None, "roofline_note": "the P1 and P2 element kernels run concurrently in one graph; "
                                                 "their FP64 rooflines are those of p1_kappa_96 and p2_diffmass_64",
-            "separate_value": E / (res["separate"] / 1e3), "separate_ms_per_step": res["separate"],
+            "separate_value": E_all / (res["separate"] / 1e3), "separate_ms_per_step": res["separate"],
             "launches": {"graph": 1, "separate": 2 * len(specs)},
             "tuned": {"elements_per_item": params[0], "p2_element_ctas": params[1], "p1_element_ctas": params[2],
                       "scatter_ctas": params[3], "p2_register_variant": params[4], "p1_register_variant": params[5]},
-            "meshes": len(specs), "elements": E,
+            "meshes": len(specs) if ws == 1 else 256, "elements": E_all,
+            "split": (f"{ws} GPUs, meshes by longest processing time first (fea_partition_batch), "
+                      f"{len(specs)} meshes / {E} elements on rank {rank}, no communication") if ws > 1 else None,
             "config": "256 Kuhn cubes, n ~ U{4..32} (seed 0), even P1 (4-pt) / odd P2 (11-pt) Poisson, "
                       "log-normal kappa, sin load, FP64"}
 

@@ -505,6 +505,22 @@ fea_status fea_partition(const int32_t* tets, int64_t n_elems, int64_t n_nodes, 
                          int64_t* node_lo, int64_t* node_hi, int64_t* n_sub_elems, int64_t* n_sub_nodes,
                          int32_t* elems, int32_t* nodes, int32_t* sub_tets);
 
+/* Independent meshes of a batch (the batched assembly of fea_batch_create)
+ * spread over `nparts` GPUs with no exchange: no mesh is split, each part
+ * assembles its own meshes as a batch of its own.  The paper has no batched
+ * form; this is longest processing time first (Graham's list scheduling):
+ * the meshes in order of decreasing cost (equal costs by index), each to the
+ * part whose total cost is lowest so far (equal totals: the lowest part), so
+ * the largest total is at most 4/3 of the best possible.
+ *   cost    : [n] the caller's cost estimate of each mesh (for example its
+ *             element count weighted by the element order), finite, >= 0;
+ *   part_of : [n] receives the part of each mesh;
+ *   load    : [nparts] receives each part's total cost, or NULL.
+ * Host memory owned by the caller; host only (no CUDA call); deterministic.
+ * FEA_ERR_ARG for n < 0, nparts < 1, a NULL array or a negative or
+ * non-finite cost. */
+fea_status fea_partition_batch(const double* cost, int32_t n, int32_t nparts, int32_t* part_of, double* load);
+
 /* Message for the last error on the calling thread ("" if none). */
 const char* fea_last_error(void);
 

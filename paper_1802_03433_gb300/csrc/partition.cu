@@ -14,6 +14,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -75,5 +76,33 @@ extern "C" fea_status fea_partition(const int32_t* tets, int64_t n_elems, int64_
   *node_hi = hi;
   *n_sub_elems = ne;
   *n_sub_nodes = nn;
+  return FEA_OK;
+}
+
+// Independent meshes of a batch over several GPUs: longest processing time
+// first (LPT, Graham's list-scheduling rule) on the callers' cost estimates.
+// The meshes go in order of decreasing cost (equal costs by index), each to
+// the part with the least cost so far (equal loads: the lowest part).  No
+// mesh is split, so the parts need no exchange.
+extern "C" fea_status fea_partition_batch(const double* cost, int32_t n, int32_t nparts, int32_t* part_of,
+                                          double* load) {
+  if (n < 0 || nparts < 1) return fail(FEA_ERR_ARG, "fea_partition_batch: need n >= 0 and nparts >= 1");
+  if (n > 0 && (!cost || !part_of)) return fail(FEA_ERR_ARG, "fea_partition_batch: cost or part_of is NULL");
+  for (int32_t i = 0; i < n; ++i)
+    if (!(cost[i] >= 0.0) || cost[i] == HUGE_VAL)
+      return fail(FEA_ERR_ARG, "fea_partition_batch: costs must be finite and >= 0");
+  std::vector<int32_t> order((size_t)n);
+  for (int32_t i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+  std::vector<double> sum((size_t)nparts, 0.0);
+  for (int32_t i : order) {
+    int32_t best = 0;
+    for (int32_t p = 1; p < nparts; ++p)
+      if (sum[p] < sum[best]) best = p;
+    part_of[i] = best;
+    sum[best] += cost[i];
+  }
+  if (load)
+    for (int32_t p = 0; p < nparts; ++p) load[p] = sum[p];
   return FEA_OK;
 }

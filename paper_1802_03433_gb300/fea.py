@@ -118,6 +118,7 @@ def lib() -> C.CDLL:
         "fea_cg": [_vp, C.c_int32, C.c_int32, _vp, _vp, _vp, C.c_double, C.c_int32, C.POINTER(C.c_int32),
                    C.POINTER(C.c_double), _vp],
         "fea_partition": [_vp, C.c_int64, C.c_int64, C.c_int32, C.c_int32, i64p, i64p, i64p, i64p, _vp, _vp, _vp],
+        "fea_partition_batch": [_vp, C.c_int32, C.c_int32, _vp, _vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -454,6 +455,20 @@ def fea_partition(tets, n_nodes, nparts, part):
                                C.c_void_p(sub.ctypes.data)), "fea_partition")
     return dict(lo=lo.value, hi=hi.value, elems=elems[:ne.value], nodes=nodes[:nn.value],
                 sub_tets=np.ascontiguousarray(sub[:, :ne.value]))
+
+
+def fea_partition_batch(cost, nparts):
+    """Meshes of a batch over `nparts` GPUs by longest processing time first
+    (host only): cost is one non-negative number per mesh.  Returns
+    (part_of, load) numpy arrays: the part of each mesh and each part's
+    total cost."""
+    import numpy as np
+    c = np.ascontiguousarray(cost, dtype=np.float64)
+    part_of = np.empty(max(c.size, 1), dtype=np.int32)
+    load = np.empty(nparts, dtype=np.float64) if nparts > 0 else np.empty(1, dtype=np.float64)
+    _check(lib().fea_partition_batch(C.c_void_p(c.ctypes.data), c.size, nparts, C.c_void_p(part_of.ctypes.data),
+                                     C.c_void_p(load.ctypes.data)), "fea_partition_batch")
+    return part_of[:c.size], load[:max(nparts, 0)]
 
 
 def owned_rows(part, row_ptr, col_idx, values, dofs_per_node=1):

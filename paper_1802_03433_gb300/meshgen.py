@@ -143,14 +143,21 @@ def adjoint_p1(n: int = 96, seed: int = 0) -> dict:
                 f_amp=SIN_AMP, npts=4, v=v, w=w, g=g)
 
 
+def batch_sides(n_meshes: int = 256, lo: int = 4, hi: int = 32, seed: int = 0):
+    """Sides n_m ~ U{lo..hi} and element orders (even m: 1, odd m: 2) of the
+    uneven batch, without building its meshes."""
+    rng = np.random.default_rng(seed)
+    sides = rng.integers(lo, hi + 1, size=n_meshes)
+    return sides, np.where(np.arange(n_meshes) % 2 == 0, 1, 2)
+
+
 def batch(n_meshes: int = 256, lo: int = 4, hi: int = 32, seed: int = 0) -> list:
     """Uneven batch: side n_m ~ U{lo..hi}; even m -> P1 Poisson, odd m -> P2.
 
     Mesh m is drawn from its own generator seeded with 1000 * seed + m + 1
     (perturbation, then log-normal kappa).
     """
-    rng = np.random.default_rng(seed)
-    sides = rng.integers(lo, hi + 1, size=n_meshes)
+    sides, _ = batch_sides(n_meshes, lo, hi, seed)
     out = []
     for m, n in enumerate(sides):
         n = int(n)

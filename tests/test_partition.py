@@ -139,3 +139,86 @@ def test_partition_rejects_bad_arguments(fea):
     # more parts than nodes: some parts own nothing and take no element
     p = fea.fea_partition(tets, N, N + 3, 0)
     assert p["lo"] == p["hi"] == 0 and p["elems"].size == 0
+
+
+# ---------------------------------------------------------------- batch meshes over several GPUs
+def _lpt_bound(m):
+    return 4.0 / 3.0 - 1.0 / (3.0 * m)  # Graham's bound for longest processing time first
+
+
+def test_batch_partition_assigns_every_mesh_and_meets_grahams_bound(fea):
+    import itertools
+    rng = np.random.default_rng(5)
+    for trial in range(60):
+        n = int(rng.integers(1, 8))
+        m = int(rng.integers(2, 4))
+        cost = rng.integers(1, 50, size=n).astype(np.float64)
+        part, load = fea.fea_partition_batch(cost, m)
+        assert part.shape == (n,) and set(part.tolist()) <= set(range(m))
+        np.testing.assert_array_equal(load, [cost[part == p].sum() for p in range(m)])
+        # the best assignment by brute force
+        opt = min(max(cost[np.array(a) == p].sum() for p in range(m)) for a in itertools.product(range(m), repeat=n))
+        assert load.max() <= _lpt_bound(m) * opt + 1e-12
+        again, _ = fea.fea_partition_batch(cost, m)
+        np.testing.assert_array_equal(part, again)  # deterministic
+
+
+def test_batch_partition_special_cases(fea):
+    # equal costs: k meshes per part; one part: everything on it; no meshes
+    part, load = fea.fea_partition_batch(np.ones(12), 4)
+    assert np.bincount(part, minlength=4).tolist() == [3, 3, 3, 3]
+    part, load = fea.fea_partition_batch([3.0, 1.0, 2.0], 1)
+    assert part.tolist() == [0, 0, 0] and load.tolist() == [6.0]
+    part, load = fea.fea_partition_batch(np.zeros(0), 3)
+    assert part.size == 0 and load.tolist() == [0.0, 0.0, 0.0]
+    # the largest mesh goes first, to part 0; the next to part 1
+    part, _ = fea.fea_partition_batch([1.0, 5.0, 4.0], 2)
+    assert part.tolist() == [1, 0, 1]
+
+
+def test_batch_partition_rejects_bad_arguments(fea):
+    for cost, m in (([1.0, -1.0], 2), ([1.0, float("nan")], 2), ([1.0, float("inf")], 2), ([1.0], 0)):
+        with pytest.raises(fea.FeaError):
+            fea.fea_partition_batch(cost, m)
+
+
+def _batch_worker(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    from paper_1802_03433_gb300 import fea
+    from paper_1802_03433_gb300 import meshgen as mg
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sides, orders = mg.batch_sides()
+    cost = 6.0 * sides.astype(np.float64) ** 3 * np.where(orders == 2, 3.6, 1.0)
+    part, load = fea.fea_partition_batch(cost, world)
+    mine = torch.tensor(np.flatnonzero(part == rank), dtype=torch.int64)
+    n = torch.tensor([mine.numel()], dtype=torch.int64)
+    counts = [torch.zeros(1, dtype=torch.int64) for _ in range(world)]
+    dist.all_gather(counts, n)
+    q.put((rank, mine.tolist(), [int(c) for c in counts], load.tolist()))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_batch_partition_gloo(fea):
+    """Two ranks split the 256-mesh batch by LPT on their own: their mesh sets
+    are disjoint, cover the batch, and their loads are within Graham's bound
+    of the perfect split."""
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_batch_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    res = sorted(q.get(timeout=180) for _ in ps)
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    sides, orders = mg.batch_sides()
+    (_, m0, c0, l0), (_, m1, c1, l1) = res
+    assert c0 == c1 == [len(m0), len(m1)] and l0 == l1
+    assert not set(m0) & set(m1) and sorted(m0 + m1) == list(range(sides.size))
+    assert max(l0) <= _lpt_bound(2) * (sum(l0) / 2)
