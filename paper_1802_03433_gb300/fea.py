@@ -488,6 +488,31 @@ def owned_rows(part, row_ptr, col_idx, values, dofs_per_node=1):
     return dofs_per_node * part["lo"], np.diff(rp[r0:r1 + 1]), cols, v[s0:s1]
 
 
+def sub_positions(part, sub_row_ptr, sub_col_idx, row_ptr, col_idx, dofs_per_node=1):
+    """Global CSR position of every entry of a part's sub-mesh pattern (int64
+    numpy array, host logic): with it, a gradient with respect to the whole
+    mesh's CSR values gives the sub-mesh's (grad_values[positions]), so the
+    adjoint of a partitioned mesh runs part by part - each part's backward
+    gives complete dL/dx for its owned nodes and dL/dkappa for all its
+    elements, with no exchange."""
+    import numpy as np
+
+    def host(a):
+        return np.asarray(a.cpu() if hasattr(a, "cpu") else a).astype(np.int64)
+    srp, sci, rp, ci = host(sub_row_ptr), host(sub_col_idx), host(row_ptr), host(col_idx)
+    d = dofs_per_node
+    nodes = part["nodes"].astype(np.int64)
+    rows = np.repeat(np.arange(srp.size - 1, dtype=np.int64), np.diff(srp))
+    grow = d * nodes[rows // d] + rows % d
+    gcol = d * nodes[sci[:srp[-1]] // d] + sci[:srp[-1]] % d
+    nd = rp.size - 1
+    gkeys = np.repeat(np.arange(nd, dtype=np.int64), np.diff(rp)) * nd + ci[:rp[-1]]
+    pos = np.searchsorted(gkeys, grow * nd + gcol)
+    if pos.size and (pos.max() >= gkeys.size or not np.array_equal(gkeys[pos], grow * nd + gcol)):
+        raise ValueError("sub_positions: a sub-mesh entry is not in the global pattern")
+    return pos
+
+
 # ---------------------------------------------------------------- convenience wrapper
 class Mesh:
     """Owns an fea_mesh handle plus the device tensors it references.

@@ -222,3 +222,52 @@ def test_batch_partition_gloo(fea):
     assert c0 == c1 == [len(m0), len(m1)] and l0 == l1
     assert not set(m0) & set(m1) and sorted(m0 + m1) == list(range(sides.size))
     assert max(l0) <= _lpt_bound(2) * (sum(l0) / 2)
+
+
+# ---------------------------------------------------------------- adjoint of a partitioned mesh
+def _adjoint_case(n=5, seed=23):
+    from common import case
+    c = case("p1_kappa", n, seed=seed)
+    N = c["coords"].shape[1]
+    rp, ci = oracle.pattern(N, c["tets"])
+    rng = np.random.default_rng(seed + 1)
+    v, w, g = rng.standard_normal(N), rng.standard_normal(N), rng.standard_normal(N)
+    rows = np.repeat(np.arange(N), np.diff(rp))
+    gV = v[rows] * w[ci]  # L = v^T K w + g^T f
+    return c, N, rp, ci, gV, g
+
+
+@pytest.mark.parametrize("nparts", [2, 3])
+def test_adjoint_by_parts_gives_the_whole_mesh_gradient(fea, nparts):
+    """The oracle's dual-number gradient on each part's sub-mesh, with the
+    whole mesh's dL/dvalues taken at the sub-mesh's entries (sub_positions):
+    dL/dx of the owned nodes and dL/dkappa of every element of the part are
+    bitwise those of the whole mesh."""
+    c, N, rp, ci, gV, g = _adjoint_case()
+    kw = dict(kappa=c["kappa"], f_kind=c["f_kind"], f_param=c["f_param"], npts=c["npts"])
+    gk, gx = oracle.assemble_grad(c["coords"], c["tets"], 1, c["tets"], rp, ci, gV, g, **kw)
+    covered = np.zeros(N, dtype=bool)
+    for part in range(nparts):
+        p = fea.fea_partition(c["tets"], N, nparts, part)
+        st = p["sub_tets"]
+        srp, sci = oracle.pattern(p["nodes"].size, st)
+        pos = fea.sub_positions(p, srp, sci, rp, ci)
+        kw_p = dict(kw, kappa=c["kappa"][p["elems"]])
+        sgk, sgx = oracle.assemble_grad(np.ascontiguousarray(c["coords"][:, p["nodes"]]), st, 1, st, srp, sci,
+                                        gV[pos], g[p["nodes"]], **kw_p)
+        assert np.array_equal(sgk.view(np.uint64), gk[p["elems"]].view(np.uint64))
+        a, b = np.searchsorted(p["nodes"], [p["lo"], p["hi"]])
+        assert np.array_equal(sgx[:, a:b].view(np.uint64), gx[:, p["lo"]:p["hi"]].view(np.uint64))
+        covered[p["lo"]:p["hi"]] = True
+    assert covered.all()
+
+
+def test_sub_positions_rejects_a_foreign_pattern(fea):
+    c, N, rp, ci, _, _ = _adjoint_case(n=3)
+    p = fea.fea_partition(c["tets"], N, 2, 0)
+    srp, sci = oracle.pattern(p["nodes"].size, p["sub_tets"])
+    # the global pattern of another mesh does not hold the sub-mesh's entries
+    c2 = mg.make_cube(2)
+    rp2, ci2 = oracle.pattern(c2[0].shape[1], c2[1])
+    with pytest.raises(ValueError):
+        fea.sub_positions(p, srp, sci, rp2, ci2)
