@@ -140,21 +140,21 @@ __global__ void __launch_bounds__(ADJ_T) k_adjoint(AdjArgs A) {
       }
     }
   });
-  double S2 = 0.0;
-#pragma unroll
-  for (int a = 0; a < 4; ++a) S2 = fma(g[a][0], dS[a][0], fma(g[a][1], dS[a][1], fma(g[a][2], dS[a][2], S2)));
-  const double S = 0.5 * S2;
-  // Q = sum_{i=1..3} g_i (dS_i - dS_0)^T
+  // Q = sum_{i=1..3} g_i (dS_i - dS_0)^T = sum_a g_a dS_a^T (the g_a sum to
+  // zero) = sum_ab Hsym_ab g_a g_b^T: symmetric, so its upper triangle is
+  // formed; S = 1/2 sum_a g_a . dS_a = tr(Q) / 2
   double Q[3][3];
 #pragma unroll
   for (int r = 0; r < 3; ++r)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      double q = 0.0;
+    for (int c = r; c < 3; ++c) {
+      double q = g[0][r] * dS[0][c];
 #pragma unroll
-      for (int i = 1; i < 4; ++i) q = fma(g[i][r], dS[i][c] - dS[0][c], q);
+      for (int a = 1; a < 4; ++a) q = fma(g[a][r], dS[a][c], q);
       Q[r][c] = q;
+      Q[c][r] = q;
     }
+  const double S = 0.5 * (Q[0][0] + Q[1][1] + Q[2][2]);
 
   // ---- load terms
   double sF = 0.0;
@@ -230,17 +230,23 @@ __global__ void __launch_bounds__(ADJ_T) k_adjoint(AdjArgs A) {
   if constexpr (LOAD == LOAD_SIN) sF *= A.fp0;
   if (A.gk) A.gk[e] = vol * S;
   const double sigma = kap * S + (MASS ? A.mass * sM : 0.0) + sF;
-  // |T| [sigma grad lambda_c - kappa Q grad lambda_c + lg_c], with |T| folded
-  // into sigma, kappa and (through vpf) lg
+  // |T| [(sigma I - kappa Q) grad lambda_c + lg_c], with |T| folded into
+  // sigma, kappa and (through vpf) lg: the symmetric matrix
+  // M = |T| (sigma I - kappa Q) once, then M g_c + lg_c per vertex
   const double vs = vol * sigma, vk = -vol * kap;
+  double M[3][3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = r; c < 3; ++c) {
+      M[r][c] = r == c ? fma(vk, Q[r][r], vs) : vk * Q[r][c];
+      M[c][r] = M[r][c];
+    }
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     double d[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const double qg = fma(Q[k][0], g[c][0], fma(Q[k][1], g[c][1], Q[k][2] * g[c][2]));
-      d[k] = fma(vs, g[c][k], fma(vk, qg, lg[c][k]));
-    }
+    for (int k = 0; k < 3; ++k) d[k] = fma(M[k][0], g[c][0], fma(M[k][1], g[c][1], fma(M[k][2], g[c][2], lg[c][k])));
     st_v4(A.gxs + (int64_t)pos[c] * 4, d[0], d[1], d[2], 0.0);
   }
 }
