@@ -134,8 +134,10 @@ def roofline_block(key, E, kernel_ms, fp64_peak_tflops, note=None):
         # instruction rate (the measured flop rate / 2)
         ips = k["fp64_instr"] * E / (kernel_ms / 1e3) / 1e9
         peak_ips = fp64_peak_tflops * 1e3 / 2
+        nominal_ips = FP64_NOMINAL_TFLOPS * 1e3 / 2  # 2 FP64 instructions per SM and clock
         out["fp64_pipe"] = {"instr_per_element": k["fp64_instr"], "achieved_ginstr_s": ips,
-                            "peak_ginstr_s": peak_ips, "frac": ips / peak_ips}
+                            "peak_ginstr_s": peak_ips, "frac": ips / peak_ips,
+                            "peak_nominal_ginstr_s": nominal_ips, "frac_nominal": ips / nominal_ips}
     if note:
         out["note"] = note
     return out
