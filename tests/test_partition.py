@@ -271,3 +271,23 @@ def test_sub_positions_rejects_a_foreign_pattern(fea):
     rp2, ci2 = oracle.pattern(c2[0].shape[1], c2[1])
     with pytest.raises(ValueError):
         fea.sub_positions(p, srp, sci, rp2, ci2)
+
+
+@pytest.mark.parametrize("ndpn,nparts", [(1, 3), (3, 2)])
+def test_sub_positions_point_at_the_same_global_entries(fea, ndpn, nparts):
+    """Every entry of a part's sub-mesh pattern maps to the whole mesh's entry
+    of the same global row and column (scalar and 3 dofs per node)."""
+    coords, tets, _ = mg.make_cube(4, 0.2, 3)
+    N = coords.shape[1]
+    rp, ci = oracle.pattern(N, tets, ndpn=ndpn)
+    grow_of = np.repeat(np.arange(rp.size - 1), np.diff(rp))
+    for part in range(nparts):
+        p = fea.fea_partition(tets, N, nparts, part)
+        srp, sci = oracle.pattern(p["nodes"].size, p["sub_tets"], ndpn=ndpn)
+        pos = fea.sub_positions(p, srp, sci, rp, ci, ndpn)
+        srow = np.repeat(np.arange(srp.size - 1), np.diff(srp))
+        want_row = ndpn * p["nodes"][srow // ndpn] + srow % ndpn
+        want_col = ndpn * p["nodes"][sci // ndpn] + sci % ndpn
+        np.testing.assert_array_equal(grow_of[pos], want_row)
+        np.testing.assert_array_equal(ci[pos], want_col)
+        assert np.unique(pos).size == pos.size
