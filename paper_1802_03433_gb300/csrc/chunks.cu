@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(BUILD_T) k_chunk_records(SlotArgs A) {
   // dof with itself) and whether the chunk holds all its elements
   bool off_pair = false;
   auto pair_of_slot = [&](int q, int32_t& i, int32_t& j) {
-    const int p = first[q];
+    const int p = min(first[q], n - 1);  // every slot has a candidate (pass 0 made them from the candidates)
     const int t = p / NPAIR, k = p - NPAIR * t;
     off_pair = k >= NB;
     const int64_t e = A.celem[e0 + t];
