@@ -55,10 +55,10 @@ KERNELS = {
     # instructions, 326 flop per element); DRAM bytes of one 128^3 launch
     # (one-pass launch list) and of one 64^3 launch (full capture)
     "p1_elast_128": dict(kernel="k_elast_chunk (element arithmetic + fixed-point accumulation per chunk)",
-                         flop_equiv=326.0, flop_exec=326.0, fp64_instr=231.0, traffic=1629.4e6 + 3187.3e6,
+                         flop_equiv=326.0, flop_exec=326.0, fp64_instr=231.0, traffic=None,
                          profile="profiles/element_chunk_kernel_p1_elast.md"),
     "p1_elast_64": dict(kernel="k_elast_chunk", flop_equiv=326.0, flop_exec=326.0, fp64_instr=231.0,
-                        traffic=199.3e6 + 355.1e6, profile="profiles/element_chunk_kernel_p1_elast.md"),
+                        traffic=None, profile="profiles/element_chunk_kernel_p1_elast.md"),
     # P2: matrix warps + load warps; 375 = the formulas in FP64 (150 DFMA +
     # 26 DADD + 49 DMUL); executed 33 DFMA + 30 DADD + 43 DMUL (the 136 FMA
     # terms of the entries are exact 64-bit integer sums)

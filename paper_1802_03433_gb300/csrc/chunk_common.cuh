@@ -120,10 +120,49 @@ static __device__ __noinline__ int2 element_bounds_fp64(double e00, double e01, 
 //   |load entry|   <= |f| (sum of the rule's |weights|) |T| < |f| |det J| / 4,
 // with C1, C3 >= 0 from the form's coefficients (elasticity: C1 = |lambda| +
 // 2 |mu|; diffusion: C1 = |kappa| times the largest |grad phi|^2 of the basis
-// over max |grad lambda|^2, C3 = |mass|).  The edges of J are formed in FP64
-// (9 subtractions); everything else runs in FP32 on the edges normalised by
-// their largest exponent, with margins for the FP32 rounding (the scale
-// factors are exact powers of two).
+// over max |grad lambda|^2, C3 = |mass|).  Everything runs in FP32 on the
+// edges of J normalised by their largest exponent (f = e 2^(1022 - eb), the
+// largest |f| in [1/2, 1)), with margins for the FP32 rounding (the scale
+// factors are exact powers of two); fp64() gives the FP64 bounds of very flat
+// elements, where the FP32 determinant is too small to trust.
+template <typename FB>
+__device__ __forceinline__ int2 bounds_from_edges(const float f[3][3], int eb, double C1, double C3, int ef,
+                                                  FB&& fp64) {
+  float c[4][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float* u = f[(i + 1) % 3];
+    const float* w = f[(i + 2) % 3];
+    c[i + 1][0] = fmaf(u[1], w[2], -u[2] * w[1]);
+    c[i + 1][1] = fmaf(u[2], w[0], -u[0] * w[2]);
+    c[i + 1][2] = fmaf(u[0], w[1], -u[1] * w[0]);
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) c[0][k] = -(c[1][k] + c[2][k] + c[3][k]);
+  const float ad = fabsf(fmaf(f[0][0], c[1][0], fmaf(f[0][1], c[1][1], f[0][2] * c[1][2])));
+  if (!(ad > 0x1p-12f)) return fp64();
+  float n2 = 0.0f;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) n2 = fmaxf(n2, fmaf(c[a][0], c[a][0], fmaf(c[a][1], c[a][1], c[a][2] * c[a][2])));
+  // the normalised edges are within 2^-22.5 of the exact ones (truncated by
+  // 2^-23 relative, or formed from split coordinates: element_bounds_split);
+  // from there the cofactors are within 2^-18.6 and det within 2^-18 (a few
+  // roundings of terms below 8 in size), inside the margins below; the edges
+  // scale by 2^(eb - 1022), so max |c|^2 / det by that and det by its cube
+  const float r = (n2 * (1.0f + 0x1p-10f) + 0x1p-17f) / (6.0f * (ad - 0x1p-17f));
+  const float dhi = (ad + 0x1p-17f) * (1.0f / 6.0f);
+  int ek = scaled_exp(C1, r, eb - 1022);
+  if (C3 != 0.0) ek = max(ek, scaled_exp(C3, dhi, 3 * (eb - 1022))) + 1;  // the sum of two terms
+  if (ek > 1023) ek = EXP_POISON;
+  else if (ek < EXP_ZERO) ek = EXP_ZERO;
+  int efo = EXP_ZERO;
+  if (ef >= EXP_POISON) efo = EXP_POISON;
+  else if (ef > EXP_ZERO) efo = max(EXP_ZERO, ef + 3 * (eb - 1022) + fexp_bound(ad + 0x1p-17f) - 1);
+  return make_int2(ek, efo);
+}
+
+// Phase A bounds (bounds_from_edges) with the edges of J formed in FP64 (9
+// subtractions) and truncated to FP32 after normalisation.
 __device__ __forceinline__ int2 element_bounds(const double X[4][3], double C1, double C3, int ef) {
   double e[3][3];
 #pragma unroll
@@ -142,37 +181,77 @@ __device__ __forceinline__ int2 element_bounds(const double X[4][3], double C1, 
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int k = 0; k < 3; ++k) f[i][k] = scaled_f32(e[i][k], eb);
-  float c[4][3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const float* u = f[(i + 1) % 3];
-    const float* w = f[(i + 2) % 3];
-    c[i + 1][0] = fmaf(u[1], w[2], -u[2] * w[1]);
-    c[i + 1][1] = fmaf(u[2], w[0], -u[0] * w[2]);
-    c[i + 1][2] = fmaf(u[0], w[1], -u[1] * w[0]);
-  }
-#pragma unroll
-  for (int k = 0; k < 3; ++k) c[0][k] = -(c[1][k] + c[2][k] + c[3][k]);
-  const float ad = fabsf(fmaf(f[0][0], c[1][0], fmaf(f[0][1], c[1][1], f[0][2] * c[1][2])));
-  if (!(ad > 0x1p-12f))
+  return bounds_from_edges(f, eb, C1, C3, ef, [&]() {
     return element_bounds_fp64(e[0][0], e[0][1], e[0][2], e[1][0], e[1][1], e[1][2], e[2][0], e[2][1], e[2][2], C1,
                                C3, ef);
-  float n2 = 0.0f;
+  });
+}
+
+// v truncated to a float (24 significant bits), by bit moves; v zero or a
+// normal number inside FP32's normal range.
+__device__ __forceinline__ float trunc_f32(double v) {
+  if (v == 0.0) return 0.0f;
+  const int hi = __double2hiint(v);
+  const unsigned lo = static_cast<unsigned>(__double2loint(v));
+  const int ev = (hi >> 20) & 0x7FF;
+  return __uint_as_float((static_cast<unsigned>(hi) & 0x80000000u) | (static_cast<unsigned>(ev - 1023 + 127) << 23) |
+                         ((static_cast<unsigned>(hi) & 0xFFFFFu) << 3) | (lo >> 29));
+}
+// A float as a double (exact), by bit moves; f zero or normal.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  if ((u & 0x7FFFFFFFu) == 0u) return f;
+  const unsigned ef = (u >> 23) & 0xFF;
+  return __hiloint2double(static_cast<int>((u & 0x80000000u) | ((ef - 127 + 1023) << 20) | ((u & 0x7FFFFFu) >> 3)),
+                          static_cast<int>(u << 29));
+}
+
+// A staged coordinate as two floats, x = h + l + d with h = x truncated to
+// 24 bits, l = (x - h) truncated (x - h is exact in FP64: one subtraction),
+// |d| < 2^-46 |x|; false (and nothing to use) unless x is zero or
+// 2^-70 <= |x| < 2^70, which keeps h and l normal floats.
+__device__ __forceinline__ bool split_coord(double x, float& h, float& l) {
+  h = 0.0f;
+  l = 0.0f;
+  if (x == 0.0) return true;
+  const int ex = (__double2hiint(x) >> 20) & 0x7FF;
+  if (ex < 1023 - 70 || ex >= 1023 + 70) return false;  // also non-finite
+  h = trunc_f32(x);
+  l = trunc_f32(x - f32_to_f64(h));
+  return true;
+}
+
+// Phase A bounds (bounds_from_edges) from split coordinates (split_coord),
+// without FP64 arithmetic: each edge of J is (h1 - h0) + (l1 - l0) in FP32.
+// With X the largest |coordinate| of the element and emax its largest |edge|
+// component, an edge is within 2^-23 |e| + 2^-45.9 X of the exact one; the
+// element takes this path when X < 2^20 emax (so within 2^-22.5 of emax, the
+// accuracy the margins of bounds_from_edges allow), else fb() (FP64 edges).
+template <typename FB>
+__device__ __forceinline__ int2 element_bounds_split(const float H[4][3], const float Lo[4][3], double C1, double C3,
+                                                     int ef, FB&& fb) {
+  float e[3][3];
+  float emax = 0.0f, xmax = 0.0f;
 #pragma unroll
-  for (int a = 0; a < 4; ++a) n2 = fmaxf(n2, fmaf(c[a][0], c[a][0], fmaf(c[a][1], c[a][1], c[a][2] * c[a][2])));
-  // errors of the normalised FP32 quantities are below 2^-19 (edges truncated
-  // by 2^-23 relative, a few roundings of terms below 8 in size); the edges
-  // scale by 2^(eb - 1022), so max |c|^2 / det by that and det by its cube
-  const float r = (n2 * (1.0f + 0x1p-10f) + 0x1p-17f) / (6.0f * (ad - 0x1p-17f));
-  const float dhi = (ad + 0x1p-17f) * (1.0f / 6.0f);
-  int ek = scaled_exp(C1, r, eb - 1022);
-  if (C3 != 0.0) ek = max(ek, scaled_exp(C3, dhi, 3 * (eb - 1022))) + 1;  // the sum of two terms
-  if (ek > 1023) ek = EXP_POISON;
-  else if (ek < EXP_ZERO) ek = EXP_ZERO;
-  int efo = EXP_ZERO;
-  if (ef >= EXP_POISON) efo = EXP_POISON;
-  else if (ef > EXP_ZERO) efo = max(EXP_ZERO, ef + 3 * (eb - 1022) + fexp_bound(ad + 0x1p-17f) - 1);
-  return make_int2(ek, efo);
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      e[i][k] = (H[i + 1][k] - H[0][k]) + (Lo[i + 1][k] - Lo[0][k]);
+      emax = fmaxf(emax, fabsf(e[i][k]));
+    }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) xmax = fmaxf(xmax, fabsf(H[a][k]));
+  if (!(emax >= 0x1p-100f) || !(xmax < 0x1p20f * emax)) return fb();
+  const int Ef = ((__float_as_int(emax) >> 23) & 0xFF) - 127;  // 2^Ef <= emax < 2^(Ef + 1)
+  const float sc = __int_as_float((127 - Ef - 1) << 23);          // 2^(-Ef - 1), exact
+  float f[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) f[i][k] = e[i][k] * sc;
+  return bounds_from_edges(f, Ef + 1023, C1, C3, ef, fb);
 }
 
 // round(v 2^sh) as a 64-bit integer (ties away from zero); |v 2^sh| < 2^62

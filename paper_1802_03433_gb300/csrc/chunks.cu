@@ -660,10 +660,11 @@ fea_status build(fea_mesh* m, Pattern* P, Chunks* C, cudaStream_t s) {
   // the accumulators of the largest chunk must fit one CTA's shared memory
   // (ndpn^2 sums of two words and an exponent per slot, ndpn sums and an
   // exponent per node slot, and for elasticity the node's staged
-  // coordinates), and a slot may take at most 128 contributions (the
+  // coordinates, FP64 and split into floats), and a slot may take at most
+  // 128 contributions (the
   // fixed-point scale 2^(63 - 2 hbits) keeps 49 bits or more)
   const size_t d = P->ndpn;
-  if ((size_t)C->max_slots * (d * d * 8 + 4) + (size_t)C->max_nodes * (d * 8 + 4 + (d == 3 ? 24 : 0)) +
+  if ((size_t)C->max_slots * (d * d * 8 + 4) + (size_t)C->max_nodes * (d * 8 + 4 + (d == 3 ? 24 + 25 : 0)) +
               (d == 3 ? CHUNK_STAGE_BYTES : 0) > 227 * 1024 ||
       C->hbits > 7)
     return fail(FEA_ERR_OVERFLOW, "chunked scatter: a chunk couples too many node pairs for shared memory");

@@ -80,6 +80,17 @@ __device__ __forceinline__ void staged_vertices(const double* sxyz, const int* s
     for (int d = 0; d < 3; ++d) X[a][d] = sxyz[3 * slot[a] + d];
 }
 
+// Phase-A bounds from the FP64 staged coordinates: the path of elements whose
+// split coordinates do not serve (out of the split's range, or edges far
+// below the coordinates) and of very flat elements.
+static __device__ __noinline__ int2 staged_bounds_fp64(const double* sxyz, int s0, int s1, int s2, int s3, double C1,
+                                                       int ef) {
+  const int slot[4] = {s0, s1, s2, s3};
+  double X[4][3];
+  staged_vertices(sxyz, slot, X);
+  return element_bounds(X, C1, 0.0, ef);
+}
+
 template <int LOAD, int NPTS, typename R, bool STAGE>
 __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemArgs A, ChunkArgs C) {
   extern __shared__ __align__(16) double smem_chunk[];
@@ -93,6 +104,9 @@ __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemA
   int* rhi = reinterpret_cast<int*>(rlo + 3 * C.max_nodes);     // [max_nodes][3]
   int* sexp = rhi + 3 * C.max_nodes;                            // [max_slots]
   int* rexp = sexp + C.max_slots;                               // [max_nodes]
+  float* sxh = reinterpret_cast<float*>(rexp + C.max_nodes);    // [max_nodes][3] coordinates split into
+  float* sxl = sxh + 3 * C.max_nodes;                           //   h + l (split_coord)
+  uint8_t* sxok = reinterpret_cast<uint8_t*>(sxl + 3 * C.max_nodes);  // [max_nodes] the split serves
   const int c = blockIdx.x, tid = threadIdx.x;
   const int e0 = C.cptr[c], ne = C.cptr[c + 1] - e0;
   const int s0 = C.sptr[c], ns = C.sptr[c + 1] - s0;
@@ -140,9 +154,17 @@ __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemA
   for (int k = tid; k < nn; k += CHUNK_T) {
     int64_t v = C.nrec[n0 + k].x;
     if (!index_ok(v, C.n_nodes, A.err)) v = 0;
-    sxyz[3 * k] = __ldg(A.x + v);
-    sxyz[3 * k + 1] = __ldg(A.y + v);
-    sxyz[3 * k + 2] = __ldg(A.z + v);
+    const double xv[3] = {__ldg(A.x + v), __ldg(A.y + v), __ldg(A.z + v)};
+    bool ok = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      sxyz[3 * k + d] = xv[d];
+      float h, l;
+      ok = split_coord(xv[d], h, l) && ok;
+      sxh[3 * k + d] = h;
+      sxl[3 * k + d] = l;
+    }
+    sxok[k] = ok;
   }
   __syncthreads();
   if constexpr (STAGE) {
@@ -174,11 +196,24 @@ __global__ void __launch_bounds__(CHUNK_T, CHUNK_MIN_BLOCKS) k_elast_chunk(ElemA
       slot[k] = pair_slot(k, t) & 0x7FFF;
       if (!index_ok(slot[k], k < 4 ? nn : ns, A.err)) slot[k] = 0;
     }
-    double X[4][3];
-    staged_vertices(sxyz, slot, X);
+    // the edges in FP32 from the split coordinates (no FP64 work), or from
+    // the FP64 ones where the split does not serve
     const double lam = A.lam ? __ldg(A.lam + e) : A.lam_const;
     const double mu = A.mu ? __ldg(A.mu + e) : A.mu_const;
-    const int2 eb = element_bounds(X, fma(2.0, fabs(mu), fabs(lam)), 0.0, C.ef);
+    const double C1 = fma(2.0, fabs(mu), fabs(lam));
+    auto fb = [&]() { return staged_bounds_fp64(sxyz, slot[0], slot[1], slot[2], slot[3], C1, C.ef); };
+    bool split = true;
+    float Hh[4][3], Ll[4][3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      split = split && sxok[slot[a]];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        Hh[a][d] = sxh[3 * slot[a] + d];
+        Ll[a][d] = sxl[3 * slot[a] + d];
+      }
+    }
+    const int2 eb = split ? element_bounds_split(Hh, Ll, C1, 0.0, C.ef, fb) : fb();
 #pragma unroll
     for (int k = 0; k < 10; ++k) atomicMax(sexp + slot[k], eb.x);
     if constexpr (HAS_LOAD) {
@@ -455,7 +490,8 @@ fea_status assemble_chunked(fea_mesh* m, Pattern* P, const fea_coeffs* co, const
   Cg.n_part = K->npart;
   Cg.n_npart = K->nnpart;
   const size_t smem = (size_t)K->max_slots * (9 * 2 * sizeof(int) + sizeof(int)) +
-                      (size_t)K->max_nodes * (3 * sizeof(double) + 3 * 2 * sizeof(int) + sizeof(int));
+                      (size_t)K->max_nodes * (3 * sizeof(double) + 3 * 2 * sizeof(int) + sizeof(int) +
+                                              6 * sizeof(float) + 1);
   if (smem + STAGE_BYTES > 227 * 1024)
     return fail(FEA_ERR_OVERFLOW, "chunked scatter: chunk too large for shared memory");
   if (m->profile) FEA_CUDA(cudaEventRecord(m->ev[0], s));

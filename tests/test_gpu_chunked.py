@@ -339,3 +339,21 @@ def test_chunked_scalar_full_size_every_value(kind, n):
     assert row_scaled_error(o["rp"], o["vals"], g["vals"]) <= TOL_FP64
     assert vec_scaled_error(o["rhs"], g["rhs"]) <= TOL_FP64
     g["mesh"].close()
+
+
+@pytest.mark.parametrize("shift,scale,prec", [(1e3, 1.0, 0), (1e3, 1.0, 1), (3e6, 1.0, 0), (3e6, 1.0, 1),
+                                              (0.0, 2.0 ** 40, 0), (0.0, 2.0 ** -40, 0), (0.0, 2.0 ** 100, 0),
+                                              (0.0, 2.0 ** -100, 0)])
+def test_chunked_translated_and_scaled_coordinates(shift, scale, prec):
+    """Phase A takes each element's edges in FP32 from split coordinates when
+    its coordinates lie in [2^-70, 2^70) and are not far above its edges
+    (shift 1e3, scale 2^+-40), else from the FP64 coordinates (shift 3e6,
+    scale 2^+-100): both agree with the oracle."""
+    c = case("elasticity", 5, seed=14)
+    c = dict(c, coords=np.ascontiguousarray(c["coords"] * scale + shift))
+    o = oracle_system(c)
+    g = _chunked(c, prec)
+    tol = TOL_FP64 if prec == 0 else TOL_MIXED
+    assert row_scaled_error(o["rp"], o["vals"], g["vals"]) <= tol
+    assert vec_scaled_error(o["rhs"], g["rhs"]) <= tol
+    g["mesh"].close()
