@@ -27,9 +27,11 @@
 // memory (and, in the FP32 instance, its element ids and dof-pair slots,
 // brought in by bulk copies on the TMA engine):
 //   A. per element: an upper bound on |K entry| from the Lame parameters, the
-//      cofactors of J (in FP32 on edges normalised by their largest exponent)
-//      and det J; its exponent is max-reduced into the element's ten slots
-//      (and the load bound into its four node slots);
+//      cofactors of J (in FP32 on edges normalised by their largest exponent,
+//      the edges formed in FP32 from the staged coordinates split into two
+//      floats: element_bounds_split) and det J; its exponent is max-reduced
+//      into the element's ten slots (and the load bound into its four node
+//      slots);
 //   B. per element: the local matrix (the FP64 or FP32 arithmetic of the
 //      local-row path, elast_upper), each of its 78 upper entries converted
 //      at its slot's scale and atomically added into the slot's 3 x 3 block;
