@@ -165,26 +165,6 @@ struct SlotArgs {
   int64_t es;              // row stride of eslot
 };
 
-__device__ __forceinline__ void block_bitonic(unsigned long long* key, uint16_t* pay, int np) {
-  for (int size = 2; size <= np; size <<= 1)
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int i = threadIdx.x; i < (np >> 1); i += blockDim.x) {
-        const int lo = 2 * i - (i & (stride - 1));
-        const int hi = lo + stride;
-        const bool asc = (lo & size) == 0;
-        const unsigned long long a = key[lo], b = key[hi];
-        if ((a > b) == asc) {
-          key[lo] = b;
-          key[hi] = a;
-          const uint16_t t = pay[lo];
-          pay[lo] = pay[hi];
-          pay[hi] = t;
-        }
-      }
-      __syncthreads();
-    }
-}
-
 __device__ __forceinline__ int32_t col_offset(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int32_t i,
                                               int32_t j) {
   int32_t lo = rp[i], hi = rp[i + 1];
@@ -226,16 +206,47 @@ __device__ __forceinline__ int block_scan_int(int v, int* total) {
   return (int)ex;
 }
 
+// Bits of a slot-sort key (key_bits<NB>): the candidate's index in the
+// chunk (below sort_cap) and its transposed bit in the low PB bits, the two
+// scalar dofs lo <= hi (DB bits each) above, and the pair flag (a pair of two
+// local dofs, not a dof with itself) on top, so that sorting the keys sorts
+// the candidates by (pair flag, lo, hi) with no payload beside them.
+template <int NB>
+struct KeyBits {
+  static constexpr int PBITS = NB == 4 ? 12 : 13;  // log2(sort_cap<NB>())
+  static constexpr int PB = PBITS + 1;
+  static constexpr int DB = (63 - PB) / 2;        // dof bits: 25 (P1), 24 (P2)
+};
+static_assert((1 << KeyBits<4>::PBITS) == sort_cap<4>() && (1 << KeyBits<10>::PBITS) == sort_cap<10>(),
+              "candidate index bits");
+
+__device__ __forceinline__ void block_bitonic_keys(unsigned long long* key, int np) {
+  for (int size = 2; size <= np; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < (np >> 1); i += blockDim.x) {
+        const int lo = 2 * i - (i & (stride - 1));
+        const int hi = lo + stride;
+        const bool asc = (lo & size) == 0;
+        const unsigned long long a = key[lo], b = key[hi];
+        if ((a > b) == asc) {
+          key[lo] = b;
+          key[hi] = a;
+        }
+      }
+      __syncthreads();
+    }
+}
+
 template <int NB>
 __global__ void __launch_bounds__(BUILD_T) k_chunk_slots(SlotArgs A) {
   constexpr int SORT_CAP = sort_cap<NB>();
   constexpr int NPAIR = NB * (NB + 1) / 2;
+  using KB = KeyBits<NB>;
+  constexpr unsigned long long DMASK = (1ull << KB::DB) - 1, PMASK = (1ull << KB::PBITS) - 1;
   extern __shared__ unsigned long long smem_u64[];
-  unsigned long long* key = smem_u64;                             // [SORT_CAP]
-  uint16_t* pay = reinterpret_cast<uint16_t*>(key + SORT_CAP);    // [SORT_CAP] candidate | transposed bit
-  uint16_t* sid = pay + SORT_CAP;                                  // [SORT_CAP] slot of each sorted position
-  uint16_t* start = sid + SORT_CAP;                                // [SORT_CAP + 1] first position of each slot
-  uint8_t* own = reinterpret_cast<uint8_t*>(start + SORT_CAP + 1);  // [SORT_CAP]
+  unsigned long long* key = smem_u64;                              // [SORT_CAP]
+  uint16_t* sid = reinterpret_cast<uint16_t*>(key + SORT_CAP);      // [SORT_CAP] slot of each sorted position
+  uint16_t* start = sid + SORT_CAP;                                  // [SORT_CAP + 1] first position of each slot
   __shared__ int s_nn, s_shared, s_shnode, s_max;
   const int c = blockIdx.x, tid = threadIdx.x;
   const int e0 = A.cptr[c], ne = A.cptr[c + 1] - e0;
@@ -255,24 +266,24 @@ __global__ void __launch_bounds__(BUILD_T) k_chunk_slots(SlotArgs A) {
       int a, b;
       pair_of(NB, k, a, b);
       const uint32_t va = (uint32_t)A.edof[a * A.E + e], vb = (uint32_t)A.edof[b * A.E + e];
-      const uint32_t lo = va < vb ? va : vb, hi = va < vb ? vb : va;
-      key[p] = ((unsigned long long)(k >= NB) << 62) | ((unsigned long long)lo << 31) | hi;
-      pay[p] = (uint16_t)(p | (va > vb ? 0x8000 : 0));
+      const unsigned long long lo = va < vb ? va : vb, hi = va < vb ? vb : va;
+      key[p] = ((unsigned long long)(k >= NB) << 63) | (lo << (KB::PB + KB::DB)) | (hi << KB::PB) |
+               ((unsigned long long)(va > vb) << KB::PBITS) | (unsigned long long)p;
     } else {
       key[p] = ~0ull;
     }
   }
   __syncthreads();
-  block_bitonic(key, pay, np);
-  // runs of equal keys -> slots
+  block_bitonic_keys(key, np);
+  // runs of equal (pair flag, lo, hi) -> slots
   const int per = (n + BUILD_T - 1) / BUILD_T;
   const int p0 = min(n, tid * per), p1 = min(n, p0 + per);
   int nf = 0;
-  for (int p = p0; p < p1; ++p) nf += (p == 0 || key[p] != key[p - 1]);
+  for (int p = p0; p < p1; ++p) nf += (p == 0 || (key[p] >> KB::PB) != (key[p - 1] >> KB::PB));
   int ns;
   int sbase = block_scan_int(nf, &ns);
   for (int p = p0; p < p1; ++p) {
-    if (p == 0 || key[p] != key[p - 1]) {
+    if (p == 0 || (key[p] >> KB::PB) != (key[p - 1] >> KB::PB)) {
       start[sbase] = (uint16_t)p;
       ++sbase;
     }
@@ -284,11 +295,10 @@ __global__ void __launch_bounds__(BUILD_T) k_chunk_slots(SlotArgs A) {
   int my_nn = 0, my_sh = 0, my_shn = 0, my_max = 0;
   for (int s = tid; s < ns; s += BUILD_T) {
     const unsigned long long k0 = key[start[s]];
-    const bool off = (k0 >> 62) != 0;
-    const int32_t i = (int32_t)((k0 >> 31) & 0x7FFFFFFFu), j = (int32_t)(k0 & 0x7FFFFFFFu);
+    const bool off = (k0 >> 63) != 0;
+    const int32_t i = (int32_t)((k0 >> (KB::PB + KB::DB)) & DMASK), j = (int32_t)((k0 >> KB::PB) & DMASK);
     const int cnt = start[s + 1] - start[s];
     const int g = off ? A.mult[A.rp[i] + col_offset(A.rp, A.ci, i, j)] : A.inc_ptr[i + 1] - A.inc_ptr[i];
-    own[s] = cnt == g;
     my_nn += !off;
     my_sh += cnt != g;
     my_shn += (cnt != g) && !off;
@@ -302,9 +312,10 @@ __global__ void __launch_bounds__(BUILD_T) k_chunk_slots(SlotArgs A) {
   // every candidate's slot (chunk-local, the rank of its key), with the
   // transposed bit
   for (int p = tid; p < n; p += BUILD_T) {
-    const int orig = pay[p] & 0x7FFF;
+    const unsigned long long kp = key[p];
+    const int orig = (int)(kp & PMASK);
     const int t = orig / NPAIR, k = orig - NPAIR * t;
-    const bool tr = k >= NB && (pay[p] & 0x8000);
+    const bool tr = k >= NB && ((kp >> KB::PBITS) & 1ull);
     A.eslot[k * A.es + e0 + t] = (uint16_t)(sid[p] | (tr ? 0x8000 : 0));
   }
   if (tid == 0) {
@@ -626,7 +637,9 @@ fea_status build(fea_mesh* m, Pattern* P, Chunks* C, cudaStream_t s) {
   FEA_TRY(dalloc(&C->eslot, (size_t)NPAIR * C->estride + 8));
   A.eslot = C->eslot;
   A.es = C->estride;
-  const size_t smem = (size_t)cap * (8 + 2 + 2 + 1) + (cap + 1) * 2;
+  if (nsd >= (int64_t(1) << (NB == 4 ? KeyBits<4>::DB : KeyBits<10>::DB)))
+    return fail(FEA_ERR_OVERFLOW, "chunked scatter: more scalar dofs than the slot sort's keys hold");
+  const size_t smem = (size_t)cap * (8 + 2) + (cap + 1) * 2;
   FEA_CUDA(cudaFuncSetAttribute(NB == 4 ? k_chunk_slots<4> : k_chunk_slots<10>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (nc > 0) {
