@@ -68,8 +68,8 @@ KERNELS = {
                         traffic=238.4e6 + 793.2e6, profile="profiles/element_kernel_p1_kappa_96.md"),
     "p1_poisson_8": dict(kernel="k_elem_scalar (P1 element, FP64)", flop_equiv=119.0, flop_exec=119.0, fp64_instr=89.0,
                          traffic=None, profile=None),
-    "adjoint_96": dict(kernel="k_adjoint (P1 backward, FP64)", flop_equiv=413.0, flop_exec=413.0, fp64_instr=260.0,
-                       traffic=439.2e6 + 672.3e6, profile="profiles/adjoint_kernel_p1_kappa_96.md"),
+    "adjoint_96": dict(kernel="k_adjoint (P1 backward, FP64)", flop_equiv=370.0, flop_exec=370.0, fp64_instr=250.0,
+                       traffic=438.0e6 + 672.1e6, profile="profiles/adjoint_kernel_p1_kappa_96.md"),
     "paper_2d": dict(kernel="k_elem_tri (P1 triangle element, FP64)", flop_equiv=191.0, flop_exec=191.0, fp64_instr=127.0,
                      traffic=268.5e6 + 950.7e6, profile="profiles/element_kernel_paper_2d.md"),
 }

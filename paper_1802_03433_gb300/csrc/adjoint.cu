@@ -69,13 +69,11 @@ __global__ void __launch_bounds__(ADJ_T) k_adjoint(AdjArgs A) {
   Geo geo;
   geometry(X, geo);
   if (!(geo.det > 0.0)) atomicOr(A.err, DEV_ERR_DEGENERATE);
+  // grad lambda_a = c_a / det J: the cofactors c_a stay unscaled and 1/det J
+  // enters the few scalars below
   const double inv = 1.0 / geo.det;
   const double vol = fabs(geo.det) * (1.0 / 6.0);
-  double g[4][3];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) g[a][k] = geo.c[a][k] * inv;
+  const double (&cf)[4][3] = geo.c;
   const double kap = A.kappa ? __ldg(A.kappa + e) : A.kappa_const;
 
   int32_t pos[NB];
@@ -120,41 +118,41 @@ __global__ void __launch_bounds__(ADJ_T) k_adjoint(AdjArgs A) {
       });
     }
   }
-  // dS/dg_a = sum_j Hsym_aj g_j (Hsym = Hc + Hc^T), and, S being a quadratic
-  // form in the g_a, S = sum_{i<=j} Hc_ij g_i . g_j = 1/2 sum_a g_a . dS_a
-  double dS[4][3];
+  // Q = sum_{i=1..3} g_i (dS_i - dS_0)^T with dS_a = dS/dg_a = sum_b Hsym_ab g_b
+  // (Hsym = Hc + Hc^T) is sum_ab Hsym_ab g_a g_b^T, and with g_0 = -(g_1 + g_2
+  // + g_3) that is sum_{i,j>=1} H'_ij g_i g_j^T, H'_ij = Hsym_ij - Hsym_i0 -
+  // Hsym_0j + Hsym_00: the 3 x 3 reduced form, taken on the unscaled
+  // cofactors (Qc, so Q = Qc / det^2), symmetric (upper triangle formed);
+  // S = sum_{i<=j} Hc_ij g_i . g_j = tr(Q) / 2
+  double Hr[3][3];
+  {
+    const double h00 = Hc[0][0] + Hc[0][0];
+    double beta[3];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+    for (int i = 1; i < 4; ++i) beta[i - 1] = fma(-0.5, h00, Hc[0][i]);  // Hsym_0i - Hsym_00 / 2
+    static_for<6>([&](auto K) {
+      constexpr int i = upper_a(3, K), j = upper_b(3, K);
+      const double hs = i == j ? Hc[i + 1][i + 1] + Hc[i + 1][i + 1] : Hc[i + 1][j + 1];
+      Hr[i][j] = hs - beta[i] - beta[j];
+      Hr[j][i] = Hr[i][j];
+    });
+  }
+  double W[3][3];  // W_i = sum_j H'_ij c_j
 #pragma unroll
-    for (int k = 0; k < 3; ++k) dS[a][k] = 0.0;
-  static_for<10>([&](auto K) {
-    constexpr int i = upper_a(4, K), j = upper_b(4, K);
-    const double h = Hc[i][j];
+  for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      if constexpr (i == j) {
-        dS[i][k] = fma(h + h, g[i][k], dS[i][k]);
-      } else {
-        dS[i][k] = fma(h, g[j][k], dS[i][k]);
-        dS[j][k] = fma(h, g[i][k], dS[j][k]);
-      }
-    }
-  });
-  // Q = sum_{i=1..3} g_i (dS_i - dS_0)^T = sum_a g_a dS_a^T (the g_a sum to
-  // zero) = sum_ab Hsym_ab g_a g_b^T: symmetric, so its upper triangle is
-  // formed; S = 1/2 sum_a g_a . dS_a = tr(Q) / 2
-  double Q[3][3];
+    for (int k = 0; k < 3; ++k)
+      W[i][k] = fma(Hr[i][0], cf[1][k], fma(Hr[i][1], cf[2][k], Hr[i][2] * cf[3][k]));
+  double Qc[3][3];
 #pragma unroll
   for (int r = 0; r < 3; ++r)
 #pragma unroll
     for (int c = r; c < 3; ++c) {
-      double q = g[0][r] * dS[0][c];
-#pragma unroll
-      for (int a = 1; a < 4; ++a) q = fma(g[a][r], dS[a][c], q);
-      Q[r][c] = q;
-      Q[c][r] = q;
+      Qc[r][c] = fma(cf[1][r], W[0][c], fma(cf[2][r], W[1][c], cf[3][r] * W[2][c]));
+      Qc[c][r] = Qc[r][c];
     }
-  const double S = 0.5 * (Q[0][0] + Q[1][1] + Q[2][2]);
+  const double inv2 = inv * inv;
+  const double S = 0.5 * inv2 * (Qc[0][0] + Qc[1][1] + Qc[2][2]);
 
   // ---- load terms
   double sF = 0.0;
@@ -231,22 +229,24 @@ __global__ void __launch_bounds__(ADJ_T) k_adjoint(AdjArgs A) {
   if (A.gk) A.gk[e] = vol * S;
   const double sigma = kap * S + (MASS ? A.mass * sM : 0.0) + sF;
   // |T| [(sigma I - kappa Q) grad lambda_c + lg_c], with |T| folded into
-  // sigma, kappa and (through vpf) lg: the symmetric matrix
-  // M = |T| (sigma I - kappa Q) once, then M g_c + lg_c per vertex
-  const double vs = vol * sigma, vk = -vol * kap;
+  // sigma, kappa and (through vpf) lg, and grad lambda_c = c_c / det J: the
+  // symmetric matrix M = |T| (sigma I - kappa Qc / det^2) / det once, then
+  // M c_c + lg_c per vertex
+  const double vs = vol * sigma * inv, vk = -vol * kap * inv2 * inv;
   double M[3][3];
 #pragma unroll
   for (int r = 0; r < 3; ++r)
 #pragma unroll
     for (int c = r; c < 3; ++c) {
-      M[r][c] = r == c ? fma(vk, Q[r][r], vs) : vk * Q[r][c];
+      M[r][c] = r == c ? fma(vk, Qc[r][r], vs) : vk * Qc[r][c];
       M[c][r] = M[r][c];
     }
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     double d[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) d[k] = fma(M[k][0], g[c][0], fma(M[k][1], g[c][1], fma(M[k][2], g[c][2], lg[c][k])));
+    for (int k = 0; k < 3; ++k)
+      d[k] = fma(M[k][0], cf[c][0], fma(M[k][1], cf[c][1], fma(M[k][2], cf[c][2], lg[c][k])));
     st_v4(A.gxs + (int64_t)pos[c] * 4, d[0], d[1], d[2], 0.0);
   }
 }
