@@ -51,14 +51,14 @@ FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # rate is how busy that pipe is kept.
 KERNELS = {
     # chunked scatter: the element arithmetic plus the bound of phase A;
-    # counters of the 64^3 capture (95 DFMA + 25 DADD + 103 DMUL = 223 FP64
-    # instructions, 318 flop per element); DRAM bytes of one 128^3 launch
+    # counters of the 64^3 capture (95 DFMA + 25 DADD + 99 DMUL = 219 FP64
+    # instructions, 314 flop per element); DRAM bytes of one 128^3 launch
     # (one-pass launch list) and of one 64^3 launch (full capture)
     "p1_elast_128": dict(kernel="k_elast_chunk (element arithmetic + fixed-point accumulation per chunk)",
-                         flop_equiv=318.0, flop_exec=318.0, fp64_instr=223.0, traffic=1629.0e6 + 3185.8e6,
+                         flop_equiv=314.0, flop_exec=314.0, fp64_instr=219.0, traffic=1629.6e6 + 3186.4e6,
                          profile="profiles/element_chunk_kernel_p1_elast.md"),
-    "p1_elast_64": dict(kernel="k_elast_chunk", flop_equiv=318.0, flop_exec=318.0, fp64_instr=223.0,
-                        traffic=200.4e6 + 355.7e6, profile="profiles/element_chunk_kernel_p1_elast.md"),
+    "p1_elast_64": dict(kernel="k_elast_chunk", flop_equiv=314.0, flop_exec=314.0, fp64_instr=219.0,
+                        traffic=199.4e6 + 354.9e6, profile="profiles/element_chunk_kernel_p1_elast.md"),
     # P2: matrix warps + load warps; 375 = the formulas in FP64 (150 DFMA +
     # 26 DADD + 49 DMUL); executed 33 DFMA + 30 DADD + 43 DMUL (the 136 FMA
     # terms of the entries are exact 64-bit integer sums)

@@ -356,9 +356,11 @@ __device__ __forceinline__ void elast_upper(const Geo& g, double adet, double la
   R Gr[4][3];
   grads<R>(g, Gr);
   const double sc = grad_scale<R>(adet);
-  const R Ls = R(lam * sc), Ms = R(mu * sc), LMs = R((lam + mu) * sc);
+  const R Ls = R(lam * sc), Ms = R(mu * sc), LMs = Ls + Ms;
   // diagonal entries of a 3x3 block (i == j): the two product terms share
-  // d_i phi_b, so (lam + mu) d_i phi_a d_i phi_b + mu grad phi_a . grad phi_b
+  // d_i phi_b, so (lam + mu) d_i phi_a d_i phi_b + mu grad phi_a . grad phi_b.
+  // Off-diagonal blocks (a < b) take the lam- and mu-scaled gradients of the
+  // later vertex b, so vertex 0 needs neither (Lc, Mc of b >= 1 only).
   R Lc[4][3], Mc[4][3], LMc[4][3], D[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -390,7 +392,7 @@ __device__ __forceinline__ void elast_upper(const Geo& g, double adet, double la
     R v;
     if constexpr (i == j) v = fma(LMc[a][i], Gr[b][i], D[a][b]);
     else if constexpr (a == b) v = LMc[a][i] * Gr[a][j];  // (lam + mu) d_i phi_a d_j phi_a
-    else v = fma(Lc[a][i], Gr[b][j], Mc[a][j] * Gr[b][i]);
+    else v = fma(Gr[a][i], Lc[b][j], Gr[a][j] * Mc[b][i]);
     put(K, v);
   });
 }
