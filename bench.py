@@ -51,22 +51,23 @@ FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # rate is how busy that pipe is kept.
 KERNELS = {
     # chunked scatter: the element arithmetic plus the bound of phase A;
-    # counters of the 64^3 capture (95 DFMA + 25 DADD + 99 DMUL = 219 FP64
-    # instructions, 314 flop per element); DRAM bytes of one 128^3 launch
+    # counters of the 64^3 capture (93 DFMA + 25 DADD + 99 DMUL = 217 FP64
+    # instructions, 310 flop per element); DRAM bytes of one 128^3 launch
     # (one-pass launch list) and of one 64^3 launch (full capture)
     "p1_elast_128": dict(kernel="k_elast_chunk (element arithmetic + fixed-point accumulation per chunk)",
-                         flop_equiv=314.0, flop_exec=314.0, fp64_instr=219.0, traffic=1629.6e6 + 3186.4e6,
+                         flop_equiv=310.0, flop_exec=310.0, fp64_instr=217.0, traffic=1631.0e6 + 3187.9e6,
                          profile="profiles/element_chunk_kernel_p1_elast.md"),
-    "p1_elast_64": dict(kernel="k_elast_chunk", flop_equiv=314.0, flop_exec=314.0, fp64_instr=219.0,
+    "p1_elast_64": dict(kernel="k_elast_chunk", flop_equiv=310.0, flop_exec=310.0, fp64_instr=217.0,
                         traffic=199.4e6 + 354.9e6, profile="profiles/element_chunk_kernel_p1_elast.md"),
     # P2: matrix warps + load warps; 375 = the formulas in FP64 (150 DFMA +
-    # 26 DADD + 49 DMUL); executed 33 DFMA + 30 DADD + 43 DMUL (the 136 FMA
+    # 26 DADD + 49 DMUL); executed 31 DFMA + 30 DADD + 43 DMUL (the 136 FMA
     # terms of the entries are exact 64-bit integer sums)
-    "p2_diffmass_64": dict(kernel="k_elem_roles (P2 element, FP64)", flop_equiv=375.0, flop_exec=139.0, fp64_instr=106.0,
-                           traffic=149.3e6 + 1985.1e6, profile="profiles/element_kernel_p2_diffmass_64.md"),
-    "p1_kappa_96": dict(kernel="k_elem_scalar (P1 element, FP64)", flop_equiv=119.0, flop_exec=119.0, fp64_instr=89.0,
-                        traffic=238.4e6 + 793.2e6, profile="profiles/element_kernel_p1_kappa_96.md"),
-    "p1_poisson_8": dict(kernel="k_elem_scalar (P1 element, FP64)", flop_equiv=119.0, flop_exec=119.0, fp64_instr=89.0,
+    "p2_diffmass_64": dict(kernel="k_elem_roles (P2 element, FP64)", flop_equiv=375.0, flop_exec=135.0, fp64_instr=104.0,
+                           traffic=148.8e6 + 1967.0e6, profile="profiles/element_kernel_p2_diffmass_64.md"),
+    # P1: 27 DFMA + 25 DADD + 32 DMUL
+    "p1_kappa_96": dict(kernel="k_elem_scalar (P1 element, FP64)", flop_equiv=111.0, flop_exec=111.0, fp64_instr=84.0,
+                        traffic=238.9e6 + 792.2e6, profile="profiles/element_kernel_p1_kappa_96.md"),
+    "p1_poisson_8": dict(kernel="k_elem_scalar (P1 element, FP64)", flop_equiv=111.0, flop_exec=111.0, fp64_instr=84.0,
                          traffic=None, profile=None),
     "adjoint_96": dict(kernel="k_adjoint (P1 backward, FP64)", flop_equiv=370.0, flop_exec=370.0, fp64_instr=250.0,
                        traffic=438.0e6 + 672.1e6, profile="profiles/adjoint_kernel_p1_kappa_96.md"),

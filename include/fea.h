@@ -378,6 +378,14 @@ fea_status fea_profile_last(fea_mesh* mesh, float* elem_ms, float* scatter_ms);
  * points are formed in fixed point), for |x| < 2^58.  Asynchronous. */
 fea_status fea_diag_sinpi(const double* x, int64_t n, int32_t variant, double* mine, double* lib, void* stream);
 
+/* Self-check of the FP64 reciprocal the element kernels scale their
+ * gradient products with (no counterpart in the paper; 1 / (6 |det J|) of
+ * Eq. 3's |T| grad phi_a . grad phi_b): for x [n] (device) writes the helper's
+ * 1 / x (an FP32 seed and one third-order Newton step; within one ulp) to
+ * mine [n] and CUDA's division 1.0 / x to lib [n].  Asynchronous;
+ * FEA_ERR_ARG for n < 0 or NULL arrays with n > 0. */
+fea_status fea_diag_rcp(const double* x, int64_t n, double* mine, double* lib, void* stream);
+
 /* Failure-path check of the bounded device waits: one warp waits, with the
  * bulk-copy scatter's bounded mbarrier wait, on a barrier whose expected
  * arrival never comes, gives up after `polls` polls (1 to 2^20) and raises

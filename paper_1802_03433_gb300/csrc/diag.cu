@@ -6,6 +6,14 @@
 
 namespace fea {
 namespace {
+__global__ void k_diag_rcp(const double* __restrict__ x, int64_t n, double* __restrict__ mine,
+                           double* __restrict__ lib) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  mine[i] = rcp_pos(x[i]);
+  lib[i] = 1.0 / x[i];
+}
+
 __global__ void k_diag_sinpi(const double* __restrict__ x, int64_t n, int variant, double* __restrict__ mine,
                              double* __restrict__ lib) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -77,6 +85,14 @@ extern "C" fea_status fea_diag_fp64_rate(double* flops_per_s, void* stream) {
   FEA_CUDA(cudaFreeAsync(out, s));
   FEA_CUDA(cudaStreamSynchronize(s));
   *flops_per_s = 5.0 * blocks * threads * iters * 8 * 2.0 / (ms * 1e-3);
+  return FEA_OK;
+}
+
+extern "C" fea_status fea_diag_rcp(const double* x, int64_t n, double* mine, double* lib, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !mine || !lib))) return fea::fail(FEA_ERR_ARG, "bad argument");
+  if (n == 0) return FEA_OK;
+  fea::k_diag_rcp<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, n, mine, lib);
+  FEA_CUDA(cudaGetLastError());
   return FEA_OK;
 }
 

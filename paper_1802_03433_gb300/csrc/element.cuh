@@ -593,11 +593,32 @@ __device__ __forceinline__ void gram(const R Gr[4][3], R s, R G[4][4]) {
   }
 }
 
+// 1 / y for y > 0, within one ulp, in three FP64 instructions: y = m 2^k
+// with m in [1, 2) taken apart on the integer pipe, an FP32 seed r ~ 1/m
+// (relative error e, |e| < 2^-22), then one third-order Newton step for the
+// reciprocal, r (1 + e + e^2) with e = 1 - m r (the first terms of the series
+// of 1 / (1 - e); the step leaves an error of order e^3 < 2^-66 besides its
+// roundings), and 2^-k put back into the exponent field.  Zero, subnormal,
+// huge (outside [2^-1000, 2^1000]) and non-finite y take the division.
+__device__ __forceinline__ double rcp_pos(double y) {
+  const long long b = __double_as_longlong(y);
+  const int ex = (int)((b >> 52) & 0x7FF);  // biased exponent; b < 0: negative y
+  if (b < 0 || ex < 1023 - 1000 || ex > 1023 + 1000) return 1.0 / y;
+  const double m = __longlong_as_double((b & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
+  const float rf = __frcp_rn(__int_as_float(0x3F800000 | (int)((b >> 29) & 0x7FFFFF)));  // m to 24 bits
+  const unsigned u = __float_as_uint(rf);  // rf in [0.5, 1]: a normal float, widened by its bits
+  double r = __longlong_as_double(((long long)(((u >> 23) & 0xFF) - 127 + 1023) << 52) |
+                                  ((long long)(u & 0x7FFFFF) << 29));
+  const double e = fma(-m, r, 1.0);
+  r = fma(r, fma(e, e, e), r);
+  return __longlong_as_double(__double_as_longlong(r) - ((long long)(ex - 1023) << 52));
+}
+
 // Scale that turns products of grads<R> into |T| grad . grad:
 // FP64: |T| / det^2 = 1 / (6 |det|); mixed: |T| = |det| / 6.
 template <typename R>
 __device__ __forceinline__ double grad_scale(double adet) {
-  if constexpr (IsDouble<R>::value) return 1.0 / (6.0 * adet);
+  if constexpr (IsDouble<R>::value) return rcp_pos(6.0 * adet);
   else return adet * (1.0 / 6.0);
 }
 

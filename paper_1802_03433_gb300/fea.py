@@ -100,6 +100,7 @@ def lib() -> C.CDLL:
         "fea_profile_enable": [_vp, C.c_int32],
         "fea_profile_last": [_vp, C.POINTER(C.c_float), C.POINTER(C.c_float)],
         "fea_diag_sinpi": [_vp, C.c_int64, C.c_int32, _vp, _vp, _vp],
+        "fea_diag_rcp": [_vp, C.c_int64, _vp, _vp, _vp],
         "fea_diag_wait_timeout": [_vp, C.c_int32, _vp],
         "fea_diag_checked_gather": [_vp, _vp, C.c_int64, C.c_int64, _vp, C.POINTER(C.c_int32), _vp],
         "fea_diag_fp64_rate": [C.POINTER(C.c_double), _vp],
@@ -352,6 +353,14 @@ def fea_diag_sinpi(x, variant=0, stream=None):
     mine, ref = torch.empty_like(x), torch.empty_like(x)
     _check(lib().fea_diag_sinpi(_ptr(x), x.numel(), variant, _ptr(mine), _ptr(ref), _stream(stream)),
            "fea_diag_sinpi")
+    return mine, ref
+
+
+def fea_diag_rcp(x, stream=None):
+    """(helper 1 / x, CUDA's 1.0 / x) for a CUDA float64 tensor x."""
+    _dev(x, torch.float64, "x")
+    mine, ref = torch.empty_like(x), torch.empty_like(x)
+    _check(lib().fea_diag_rcp(_ptr(x), x.numel(), _ptr(mine), _ptr(ref), _stream(stream)), "fea_diag_rcp")
     return mine, ref
 
 
